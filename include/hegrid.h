@@ -1,0 +1,195 @@
+/*
+ * hegrid.h -- C ABI of libhegrid.so: GB300-native convolution gridding of
+ * non-uniform, multi-channel single-dish samples onto a regular map.
+ *
+ * The operation is Eq. 1 of HEGrid (Sec. 2.2): for every target cell g,
+ *     map[g, c] = sum_n w(g; s_n) v[s_n, c] / W[g],   W[g] = sum_n w(g; s_n),
+ * with a Gaussian kernel w = exp(-d^2 / (2 sigma^2)) of the great-circle
+ * separation d, truncated at d <= R (Algorithm 1, Sec. 4.1.2, inclusive),
+ * sigma = FWHM / sqrt(8 ln 2), R = support_sigmas * sigma.  The weights are
+ * computed once per (sample, cell) pair by hegrid_plan_create and shared by
+ * every channel (the "shared component" of Sec. 4.3.1).
+ *
+ * Conventions for every call:
+ *   - Pointers marked "device" are CUDA device (or managed) addresses on the
+ *     current device; "host" pointers are CPU memory (pinned where stated).
+ *   - The caller owns every input and output buffer.  A plan owns all of its
+ *     internal device memory and frees it in hegrid_plan_destroy.
+ *   - Calls return a status and never throw.  Argument errors are returned
+ *     before any launch.  hegrid_last_error() returns a thread-local message
+ *     describing the last failure.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Layouts are row-major: values[n * ld_values + c], map[m * ld_map + c]
+ *     with cell index m = iy * nx + ix (ix along RA, iy along Dec).
+ */
+#ifndef HEGRID_H
+#define HEGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hegrid_plan hegrid_plan;   /* opaque; owns its device memory */
+typedef struct hegrid_batch hegrid_batch; /* opaque; a captured batched launch */
+
+typedef enum {
+  HEGRID_OK = 0,
+  HEGRID_ERR_INVALID_ARG = -1,
+  HEGRID_ERR_OOM = -2,
+  HEGRID_ERR_CUDA = -3,
+  HEGRID_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up */
+  HEGRID_ERR_UNSUPPORTED = -5
+} hegrid_status;
+
+/* Storage type of the sample values. */
+typedef enum {
+  HEGRID_F32 = 0,
+  HEGRID_BF16 = 1,
+  HEGRID_F16 = 2,
+  HEGRID_BF16X2 = 3 /* two bf16 per value, hi then lo: v = hi + lo */
+} hegrid_dtype;
+
+/* Target map: the regular nx x ny grid of Sec. 2.2.  Cell (ix, iy) has its
+ * centre at lon0 + (ix - (nx-1)/2) dlon, lat0 + (iy - (ny-1)/2) dlat (degrees);
+ * no projection. */
+typedef struct {
+  int32_t nx, ny;
+  double lon0_deg, lat0_deg;
+  double dlon_deg, dlat_deg;
+} hegrid_map_geom;
+
+/* Gaussian kernel by its FWHM; support_sigmas is R / sigma (e.g. 3.0). */
+typedef struct {
+  double fwhm_deg;
+  double support_sigmas;
+} hegrid_kernel;
+
+/* hegrid_grid modes */
+#define HEGRID_MODE_FP32 0u     /* CUDA-core FP32 gather/accumulate */
+#define HEGRID_MODE_TC 1u       /* tcgen05 tensor cores, one BF16 (or F16) pass */
+#define HEGRID_MODE_TC_SPLIT 2u /* tcgen05 with hi/lo splits of values and weights */
+
+/* plan_create flags: bits 0-7 give the bin edge in map cells (0 = default 2). */
+#define HEGRID_PLAN_BIN_CELLS(b) ((uint32_t)(b) & 0xffu)
+
+/*
+ * hegrid_plan_create -- bin the samples and build the shared weights.
+ * (Sec. 4.1.1 pre-processing and Algorithm 1's contribution search, on the GPU.)
+ *
+ * n_samples        number of samples N (>= 1, < 2^31).
+ * lon_deg, lat_deg N coordinates in degrees (FP64); host memory if
+ *                  coords_on_device == 0, device memory otherwise.  Not kept.
+ * geom, kern       map geometry and kernel (host structs, copied).
+ * flags            HEGRID_PLAN_BIN_CELLS(b) or 0.
+ * stream           stream for every launch; the call synchronises it once to
+ *                  learn the number of (cell, sample) pairs.
+ *
+ * Errors: INVALID_ARG (N < 1, nx/ny < 1, cell size <= 0, FWHM <= 0, support
+ * <= 0); UNSUPPORTED (a cell row within R of a pole, a padded map wider than
+ * 360 deg, R > 11 deg, more than 65,535 candidate samples in one cell block);
+ * OOM; CUDA.  On error *out is set to NULL.
+ */
+hegrid_status hegrid_plan_create(hegrid_plan **out, int64_t n_samples, const double *lon_deg,
+                                 const double *lat_deg, int coords_on_device,
+                                 const hegrid_map_geom *geom, const hegrid_kernel *kern,
+                                 uint32_t flags, void *stream);
+
+/*
+ * hegrid_grid -- Eq. 1 for every cell and channel (the cell-update step of
+ * Algorithm 1, normalisation included).  Fully asynchronous on `stream`.
+ *
+ * values      device [n_samples x ld_values] of `dtype`, in the caller's own
+ *             sample order (the plan keeps the permutation); 16-byte aligned,
+ *             ld_values * element size a multiple of 16 bytes, ld_values >= C.
+ *             For HEGRID_BF16X2, ld_values counts values (pairs).
+ * n_channels  C >= 1.
+ * map_out     device FP32 [M x ld_map], ld_map >= C, M = nx * ny.  Cells with
+ *             W = 0 get NaN.
+ * weight_out  device FP32 [M] or NULL: W[m] as used for the normalisation.
+ * mode        HEGRID_MODE_FP32 (dtype F32 only), HEGRID_MODE_TC or
+ *             HEGRID_MODE_TC_SPLIT (any dtype).
+ *
+ * Errors: INVALID_ARG (NULL plan/values/map, bad C/ld/alignment/dtype/mode);
+ * UNSUPPORTED (mode not available for dtype); CUDA (launch failure).
+ */
+hegrid_status hegrid_grid(hegrid_plan *plan, const void *values, hegrid_dtype dtype,
+                          int64_t n_channels, int64_t ld_values, float *map_out, int64_t ld_map,
+                          float *weight_out, uint32_t mode, void *stream);
+
+/* Free the plan and all of its device memory (synchronises the device). */
+hegrid_status hegrid_plan_destroy(hegrid_plan *plan);
+
+/* One entry of a batched launch (the arguments of hegrid_grid). */
+typedef struct {
+  const void *values;
+  hegrid_dtype dtype;
+  int64_t n_channels, ld_values;
+  float *map_out;
+  int64_t ld_map;
+  float *weight_out;
+  uint32_t mode;
+} hegrid_grid_args;
+
+/*
+ * hegrid_grid_batched -- grid n independent fields in one persistent launch
+ * per kernel kind (the multi-pipeline FIFO of Sec. 4.2, as one device work
+ * queue).  plans[i] and args[i] describe field i (host arrays).  Asynchronous.
+ */
+hegrid_status hegrid_grid_batched(int n, hegrid_plan *const *plans, const hegrid_grid_args *args,
+                                  void *stream);
+
+/*
+ * hegrid_batch_create / _launch / _destroy -- the same batch with its work
+ * queue uploaded once and its launches captured in a CUDA graph; launch
+ * replays the graph on `stream`.  The plans and buffers named in args must
+ * outlive the batch.
+ */
+hegrid_status hegrid_batch_create(hegrid_batch **out, int n, hegrid_plan *const *plans,
+                                  const hegrid_grid_args *args, void *stream);
+hegrid_status hegrid_batch_launch(hegrid_batch *batch, void *stream);
+hegrid_status hegrid_batch_destroy(hegrid_batch *batch);
+
+/*
+ * hegrid_grid_stream -- grid n_chunks channel chunks that live in host memory
+ * (Sec. 4.3.2: pinned host buffers, asynchronous copies overlapped with the
+ * kernel).  Chunk k holds channels [k*chunk_channels, (k+1)*chunk_channels) as
+ * host [n_samples x chunk_channels] of `dtype` (pinned memory recommended).
+ * host_map is host FP32 [M x ld_host_map] with ld_host_map >= n_chunks *
+ * chunk_channels; host_weight is host FP32 [M] or NULL.  Uses internal
+ * streams and a device ring of two chunk buffers; blocks until done.
+ */
+hegrid_status hegrid_grid_stream(hegrid_plan *plan, const void *const *host_chunks, int n_chunks,
+                                 int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,
+                                 float *host_map, int64_t ld_host_map, float *host_weight);
+
+/* Plan sizes: pairs P, bins, cell blocks, candidate slots, device bytes held. */
+hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_t *n_bins,
+                               int64_t *n_blocks, int64_t *n_cand, int64_t *bytes);
+
+/*
+ * hegrid_plan_export -- copy plan structures to host buffers (any may be NULL):
+ *   perm[N]          sample indices sorted by (bin key, index); discarded last
+ *   bin_off[n_bins+1] start of each bin in perm (bin_off[n_bins] = kept count)
+ *   nb_off[M+1]      CSR row offsets of the (cell -> sample) pairs
+ *   nb_idx[P]        sample index of each pair, ascending per cell (canonical)
+ *   nb_w[P]          FP32 weight of each pair, in the same order as nb_idx
+ *   weight[M]        W[m] = sum of the FP32 weights of cell m
+ * Synchronises the plan's device work.
+ */
+hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t *bin_off,
+                                 int64_t *nb_off, int32_t *nb_idx, float *nb_w, float *weight);
+
+/* Device-side error word of the plan (bounded waits that timed out). */
+hegrid_status hegrid_status_poll(const hegrid_plan *plan);
+
+/* Thread-local message describing the most recent failure ("" if none). */
+const char *hegrid_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEGRID_H */

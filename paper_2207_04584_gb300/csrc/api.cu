@@ -1,0 +1,292 @@
+// C ABI of the grid step: validation, work-item tables, batched launches,
+// CUDA-graph batches and host-chunk streaming.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hegrid_internal.cuh"
+
+namespace hg {
+namespace {
+
+int elem_bytes(int dtype) {
+  switch (dtype) {
+    case HEGRID_F32: return 4;
+    case HEGRID_BF16: return 2;
+    case HEGRID_F16: return 2;
+    case HEGRID_BF16X2: return 4;
+    default: return 0;
+  }
+}
+
+hegrid_status check_args(const hegrid_plan* plan, const hegrid_grid_args& a) {
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  HG_ARG_CHECK(a.values != nullptr && a.map_out != nullptr, "values or map_out is NULL");
+  HG_ARG_CHECK(a.n_channels >= 1, "n_channels must be >= 1");
+  int eb = elem_bytes((int)a.dtype);
+  HG_ARG_CHECK(eb > 0, "unknown dtype");
+  HG_ARG_CHECK(a.ld_values >= a.n_channels, "ld_values < n_channels");
+  HG_ARG_CHECK((a.ld_values * eb) % 16 == 0, "ld_values * element size must be a multiple of 16");
+  HG_ARG_CHECK(((uintptr_t)a.values & 15u) == 0, "values must be 16-byte aligned");
+  HG_ARG_CHECK(a.ld_map >= a.n_channels, "ld_map < n_channels");
+  HG_ARG_CHECK(a.mode == HEGRID_MODE_FP32 || a.mode == HEGRID_MODE_TC ||
+                   a.mode == HEGRID_MODE_TC_SPLIT,
+               "unknown mode");
+  if (a.mode == HEGRID_MODE_FP32 && a.dtype != HEGRID_F32) {
+    set_error("HEGRID_MODE_FP32 needs HEGRID_F32 values");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  return HEGRID_OK;
+}
+
+GridJob make_job(const hegrid_plan* plan, const hegrid_grid_args& a, int64_t ctile) {
+  GridJob j;
+  std::memset(&j, 0, sizeof(j));
+  j.pv = plan->view();
+  j.values = a.values;
+  j.dtype = (int32_t)a.dtype;
+  j.mode = (int32_t)a.mode;
+  j.C = a.n_channels;
+  j.ld_values = a.ld_values;
+  j.map = a.map_out;
+  j.ld_map = a.ld_map;
+  j.weight_out = a.weight_out;
+  j.n_ctiles = (a.n_channels + ctile - 1) / ctile;
+  return j;
+}
+
+// Launch all jobs of one kernel family, kMaxJobs per launch.
+hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStream_t s) {
+  for (size_t base = 0; base < jobs.size(); base += kMaxJobs) {
+    JobTable jt;
+    std::memset(&jt, 0, sizeof(jt));
+    jt.n_jobs = (int32_t)std::min<size_t>(kMaxJobs, jobs.size() - base);
+    int64_t items = 0;
+    for (int i = 0; i < jt.n_jobs; ++i) {
+      jt.job[i] = jobs[base + i];
+      jt.job[i].item_base = items;
+      items += jt.job[i].pv.n_blocks * jt.job[i].n_ctiles;
+    }
+    jt.n_items = items;
+    hegrid_status st = tc ? launch_grid_tc(jt, s) : launch_grid_f32(jt, s);
+    if (st != HEGRID_OK) return st;
+  }
+  return HEGRID_OK;
+}
+
+hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args* args,
+                        cudaStream_t s) {
+  HG_ARG_CHECK(n >= 0, "n must be >= 0");
+  HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
+  std::vector<GridJob> f32, tc;
+  for (int i = 0; i < n; ++i) {
+    hegrid_status st = check_args(plans[i], args[i]);
+    if (st != HEGRID_OK) return st;
+    if (args[i].mode == HEGRID_MODE_FP32)
+      f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
+    else
+      tc.push_back(make_job(plans[i], args[i], tc_channel_tile()));
+  }
+  if (!f32.empty()) {
+    hegrid_status st = launch_family(f32, false, s);
+    if (st != HEGRID_OK) return st;
+  }
+  if (!tc.empty()) {
+    hegrid_status st = launch_family(tc, true, s);
+    if (st != HEGRID_OK) return st;
+  }
+  return HEGRID_OK;
+}
+
+}  // namespace
+}  // namespace hg
+
+struct hegrid_batch {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+hegrid_status hegrid_grid(hegrid_plan* plan, const void* values, hegrid_dtype dtype,
+                          int64_t n_channels, int64_t ld_values, float* map_out, int64_t ld_map,
+                          float* weight_out, uint32_t mode, void* stream) {
+  hegrid_grid_args a;
+  a.values = values;
+  a.dtype = dtype;
+  a.n_channels = n_channels;
+  a.ld_values = ld_values;
+  a.map_out = map_out;
+  a.ld_map = ld_map;
+  a.weight_out = weight_out;
+  a.mode = mode;
+  hegrid_plan* p[1] = {plan};
+  return hg::grid_many(1, p, &a, (cudaStream_t)stream);
+}
+
+hegrid_status hegrid_grid_batched(int n, hegrid_plan* const* plans, const hegrid_grid_args* args,
+                                  void* stream) {
+  return hg::grid_many(n, plans, args, (cudaStream_t)stream);
+}
+
+hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const* plans,
+                                  const hegrid_grid_args* args, void* stream) {
+  HG_ARG_CHECK(out != nullptr, "out is NULL");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    hegrid_status st = hg::check_args(plans ? plans[i] : nullptr, args[i]);
+    if (st != HEGRID_OK) return st;
+  }
+  cudaStream_t cap;
+  HG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  hegrid_batch* b = new hegrid_batch();
+  b->graph = nullptr;
+  b->exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  hegrid_status st = HEGRID_OK;
+  if (e == cudaSuccess) {
+    st = hg::grid_many(n, plans, args, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &b->graph);
+    if (st == HEGRID_OK && e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && st == HEGRID_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cap);
+  if (st != HEGRID_OK || e != cudaSuccess) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+    if (st == HEGRID_OK) {
+      hg::set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
+      st = HEGRID_ERR_CUDA;
+    }
+    return st;
+  }
+  (void)stream;
+  *out = b;
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_batch_launch(hegrid_batch* batch, void* stream) {
+  HG_ARG_CHECK(batch != nullptr, "batch is NULL");
+  HG_CUDA_TRY(cudaGraphLaunch(batch->exec, (cudaStream_t)stream));
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_batch_destroy(hegrid_batch* batch) {
+  if (!batch) return HEGRID_OK;
+  cudaGraphExecDestroy(batch->exec);
+  cudaGraphDestroy(batch->graph);
+  delete batch;
+  return HEGRID_OK;
+}
+
+// Streaming: a ring of two device chunk buffers and two map buffers.  Chunk
+// k's H2D copy runs on the copy-in stream, its kernel on the compute stream,
+// its D2H copy on the copy-out stream; events order reuse of ring slots.
+hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chunks, int n_chunks,
+                                 int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,
+                                 float* host_map, int64_t ld_host_map, float* host_weight) {
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  HG_ARG_CHECK(n_chunks >= 1 && host_chunks != nullptr, "need at least one chunk");
+  HG_ARG_CHECK(chunk_channels >= 1, "chunk_channels must be >= 1");
+  HG_ARG_CHECK(host_map != nullptr, "host_map is NULL");
+  HG_ARG_CHECK(ld_host_map >= (int64_t)n_chunks * chunk_channels, "ld_host_map too small");
+  int eb = 0;
+  switch (dtype) {
+    case HEGRID_F32: eb = 4; break;
+    case HEGRID_BF16: eb = 2; break;
+    case HEGRID_F16: eb = 2; break;
+    case HEGRID_BF16X2: eb = 4; break;
+    default: HG_ARG_CHECK(false, "unknown dtype");
+  }
+  for (int k = 0; k < n_chunks; ++k) HG_ARG_CHECK(host_chunks[k] != nullptr, "NULL chunk");
+  const int64_t N = plan->N, M = plan->M;
+  // device rows padded to 16 bytes
+  const int64_t ldv = ((chunk_channels * eb + 15) / 16 * 16) / eb;
+  const size_t vbytes = (size_t)N * ldv * eb;
+  const size_t mbytes = (size_t)M * chunk_channels * sizeof(float);
+  void* dv[2] = {nullptr, nullptr};
+  float* dm[2] = {nullptr, nullptr};
+  float* dw = nullptr;
+  cudaStream_t sin = nullptr, scomp = nullptr, sout = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  hegrid_status st = HEGRID_OK;
+  auto cleanup = [&]() {
+    if (sin) cudaStreamSynchronize(sin);
+    if (scomp) cudaStreamSynchronize(scomp);
+    if (sout) cudaStreamSynchronize(sout);
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(dv[i]);
+      cudaFree(dm[i]);
+      if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+      if (ev_k[i]) cudaEventDestroy(ev_k[i]);
+      if (ev_out[i]) cudaEventDestroy(ev_out[i]);
+      if (ev_free[i]) cudaEventDestroy(ev_free[i]);
+    }
+    cudaFree(dw);
+    if (sin) cudaStreamDestroy(sin);
+    if (scomp) cudaStreamDestroy(scomp);
+    if (sout) cudaStreamDestroy(sout);
+  };
+#define HG_STREAM_TRY(expr)                                                    \
+  do {                                                                         \
+    cudaError_t _e = (expr);                                                   \
+    if (_e != cudaSuccess) {                                                   \
+      hg::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));       \
+      st = _e == cudaErrorMemoryAllocation ? HEGRID_ERR_OOM : HEGRID_ERR_CUDA; \
+      cleanup();                                                               \
+      return st;                                                               \
+    }                                                                          \
+  } while (0)
+  for (int i = 0; i < 2; ++i) {
+    HG_STREAM_TRY(cudaMalloc(&dv[i], vbytes));
+    HG_STREAM_TRY(cudaMalloc((void**)&dm[i], mbytes));
+    HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming));
+    HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_k[i], cudaEventDisableTiming));
+    HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming));
+    HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_free[i], cudaEventDisableTiming));
+  }
+  HG_STREAM_TRY(cudaMalloc((void**)&dw, sizeof(float) * M));
+  HG_STREAM_TRY(cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking));
+  HG_STREAM_TRY(cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking));
+  HG_STREAM_TRY(cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking));
+  for (int k = 0; k < n_chunks; ++k) {
+    const int r = k & 1;
+    // slot r's value buffer is free once chunk k-2's kernel finished
+    if (k >= 2) HG_STREAM_TRY(cudaStreamWaitEvent(sin, ev_k[r], 0));
+    HG_STREAM_TRY(cudaMemcpy2DAsync(dv[r], ldv * eb, host_chunks[k], chunk_channels * eb,
+                                    chunk_channels * eb, N, cudaMemcpyHostToDevice, sin));
+    HG_STREAM_TRY(cudaEventRecord(ev_in[r], sin));
+    HG_STREAM_TRY(cudaStreamWaitEvent(scomp, ev_in[r], 0));
+    // slot r's map buffer is free once chunk k-2's D2H finished
+    if (k >= 2) HG_STREAM_TRY(cudaStreamWaitEvent(scomp, ev_out[r], 0));
+    st = hegrid_grid(plan, dv[r], dtype, chunk_channels, ldv, dm[r], chunk_channels,
+                     k == 0 ? dw : nullptr, mode, scomp);
+    if (st != HEGRID_OK) {
+      cleanup();
+      return st;
+    }
+    HG_STREAM_TRY(cudaEventRecord(ev_k[r], scomp));
+    HG_STREAM_TRY(cudaStreamWaitEvent(sout, ev_k[r], 0));
+    HG_STREAM_TRY(cudaMemcpy2DAsync(host_map + (int64_t)k * chunk_channels,
+                                    ld_host_map * sizeof(float), dm[r],
+                                    chunk_channels * sizeof(float),
+                                    chunk_channels * sizeof(float), M, cudaMemcpyDeviceToHost,
+                                    sout));
+    if (k == 0 && host_weight)
+      HG_STREAM_TRY(
+          cudaMemcpyAsync(host_weight, dw, sizeof(float) * M, cudaMemcpyDeviceToHost, sout));
+    HG_STREAM_TRY(cudaEventRecord(ev_out[r], sout));
+  }
+  HG_STREAM_TRY(cudaStreamSynchronize(sout));
+  HG_STREAM_TRY(cudaStreamSynchronize(scomp));
+#undef HG_STREAM_TRY
+  cleanup();
+  return HEGRID_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// Plain FP32 form of the cell update (Algorithm 1's accumulate and normalise
+// steps, Eq. 1) on CUDA cores.
+//
+// A persistent CTA pulls work items (field, 16x8 cell block, 128-channel tile)
+// from a device queue.  For each K chunk of 32 candidate samples of the block:
+//   * one thread stages the 32 sample rows (FP32, channel-contiguous) into
+//     shared memory with bulk async copies (TMA engine) completing on an
+//     mbarrier, double-buffered;
+//   * each of 128 threads scatters its cell's pairs that fall in the chunk
+//     into a dense 32 x 128 weight tile and ORs a per-patch occupancy mask;
+//   * each warp owns a 4x4-cell patch and 128 channels; a thread accumulates
+//     8 cells x 8 channels in registers, skipping samples that touch no cell
+//     of its patch.
+// The epilogue divides by W (NaN where W = 0) and writes the map row-major.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "hegrid_internal.cuh"
+#include "ptx.cuh"
+
+namespace hg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kKC = 32;   // candidates per K chunk
+constexpr int kCT = 128;  // channels per tile
+
+struct __align__(128) SmemF32 {
+  float V[2][kKC][kCT];   // staged sample rows
+  float Wt[2][kKC][kCT];  // dense weight tile [k][cell column]
+  uint32_t pmask[2][8];   // per patch: bit k set if any cell of the patch has sample k
+  uint64_t bar[2];
+};
+
+__device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
+  int j = 0;
+  while (j + 1 < jt.n_jobs && jt.job[j + 1].item_base <= item) ++j;
+  return j;
+}
+
+// Tile column t (0..127) -> block-local cell (lx, ly): 8 patches of 4x4 cells,
+// patches 4 across x 2 down; inside a patch, two 8-cell halves of 2 rows x 4.
+__device__ __forceinline__ void col_to_cell(int t, int& lx, int& ly) {
+  int p = t >> 4, q = t & 15;
+  int cs = q >> 3, i = q & 7;
+  int py = cs * 2 + (i >> 2), px = i & 3;
+  ly = (p >> 2) * 4 + py;
+  lx = (p & 3) * 4 + px;
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_grid_f32(const __grid_constant__ JobTable jt) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SmemF32& S = *reinterpret_cast<SmemF32*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase[2] = {0u, 0u};
+  bool bail = false;
+
+  for (int64_t item = blockIdx.x; item < jt.n_items && !bail; item += gridDim.x) {
+    const GridJob& J = jt.job[find_job(jt, item)];
+    const PlanView& pv = J.pv;
+    const int64_t local = item - J.item_base;
+    const int64_t b = local / J.n_ctiles;
+    const int64_t ct = local % J.n_ctiles;
+    const int64_t c0 = ct * kCT;
+    const int cw = (int)(J.C - c0 < kCT ? J.C - c0 : kCT);
+    const uint32_t row_bytes = (uint32_t)(((cw + 3) & ~3) * 4);
+    const float* __restrict__ vals = static_cast<const float*>(J.values);
+    const int bbx = (int)(b % pv.nbx_b), bby = (int)(b / pv.nbx_b);
+    const int64_t kb0 = pv.cand_off[b];
+    const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kKC);
+
+    // this thread's cell as the owner of tile column `tid` (threads 0..127)
+    int64_t p_cur = 0, p_end = 0;
+    if (tid < HG_BLOCK_CELLS) {
+      int lx, ly;
+      col_to_cell(tid, lx, ly);
+      int ix = bbx * HG_BX + lx, iy = bby * HG_BY + ly;
+      if (ix < pv.nx && iy < pv.ny) {
+        int64_t m = (int64_t)iy * pv.nx + ix;
+        p_cur = pv.nb_off[m];
+        p_end = pv.nb_off[m + 1];
+      }
+    }
+
+    auto issue = [&](int j) {
+      int s = j & 1;
+      mbar_arrive_expect_tx(&S.bar[s], row_bytes * kKC);
+      for (int k = 0; k < kKC; ++k) {
+        int32_t n = pv.cand_idx[kb0 + (int64_t)j * kKC + k];
+        bulk_g2s(&S.V[s][k][0], vals + (int64_t)n * J.ld_values + c0, row_bytes, &S.bar[s]);
+      }
+    };
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[i][e] = 0.0f;
+
+    const int patch = warp, cs = lane >> 4, cg = lane & 15;
+    if (tid == 0 && n_chunks > 0) issue(0);
+    for (int j = 0; j < n_chunks; ++j) {
+      const int s = j & 1;
+      if (tid == 0 && j + 1 < n_chunks) issue(j + 1);
+      // weight tile for chunk j
+      if (tid < HG_BLOCK_CELLS) {
+#pragma unroll 8
+        for (int k = 0; k < kKC; ++k) S.Wt[s][k][tid] = 0.0f;
+        uint32_t km = 0;
+        const int32_t kend = (j + 1) * kKC;
+        while (p_cur < p_end) {
+          int32_t loc = pv.nb_loc[p_cur];
+          if (loc >= kend) break;
+          int k = loc - j * kKC;
+          S.Wt[s][k][tid] = pv.nb_w[p_cur];
+          km |= 1u << k;
+          ++p_cur;
+        }
+        // OR over the 16 columns of this patch (lanes 0-15 or 16-31)
+        uint32_t hm = __reduce_or_sync(0xffffffffu, (lane < 16) ? km : 0u);
+        uint32_t lm = __reduce_or_sync(0xffffffffu, (lane >= 16) ? km : 0u);
+        if (lane == 0) S.pmask[s][tid >> 4] = hm;
+        if (lane == 16) S.pmask[s][tid >> 4] = lm;
+      }
+      __syncthreads();
+      const int timed_out = !mbar_wait(&S.bar[s], phase[s], pv.err_word);
+      if (__syncthreads_or(timed_out)) {
+        // give up: wait (bounded) for the other stage's copies, then leave
+        if (tid == 0 && j + 1 < n_chunks) mbar_wait(&S.bar[s ^ 1], phase[s ^ 1], nullptr);
+        bail = true;
+        break;
+      }
+      phase[s] ^= 1u;
+      const uint32_t pm = S.pmask[s][patch];
+      const float* wrow = &S.Wt[s][0][patch * 16 + cs * 8];
+      const float* vrow = &S.V[s][0][cg * 8];
+      for (int k = 0; k < kKC; ++k) {
+        if (!((pm >> k) & 1u)) continue;
+        float4 w0 = *reinterpret_cast<const float4*>(wrow + k * kCT);
+        float4 w1 = *reinterpret_cast<const float4*>(wrow + k * kCT + 4);
+        float4 v0 = *reinterpret_cast<const float4*>(vrow + k * kCT);
+        float4 v1 = *reinterpret_cast<const float4*>(vrow + k * kCT + 4);
+        float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[i][e] = __fmaf_rn(w[i], v[e], acc[i][e]);
+      }
+      __syncthreads();
+    }
+
+    if (bail) break;
+    // epilogue: normalise and store
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int lx, ly;
+      col_to_cell(patch * 16 + cs * 8 + i, lx, ly);
+      int ix = bbx * HG_BX + lx, iy = bby * HG_BY + ly;
+      if (ix >= pv.nx || iy >= pv.ny) continue;
+      int64_t m = (int64_t)iy * pv.nx + ix;
+      float W = pv.wsum[m];
+      float* out = J.map + m * J.ld_map + c0 + cg * 8;
+      int cbase = cg * 8;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        if (cbase + e < cw) out[e] = W > 0.0f ? __fdiv_rn(acc[i][e], W) : __int_as_float(0x7fc00000);
+      }
+      if (ct == 0 && cg == 0 && J.weight_out) J.weight_out[m] = W;
+    }
+  }
+}
+
+}  // namespace
+
+int f32_channel_tile() { return kCT; }
+
+hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s) {
+  static int sms = 0;
+  if (!sms) {
+    int dev;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_grid_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SmemF32));
+  }
+  int64_t grid = std::min<int64_t>(jt.n_items, (int64_t)sms * 2);
+  if (grid < 1) return HEGRID_OK;
+  k_grid_f32<<<(unsigned)grid, kThreads, sizeof(SmemF32), s>>>(jt);
+  HG_CUDA_TRY(cudaGetLastError());
+  return HEGRID_OK;
+}
+
+}  // namespace hg

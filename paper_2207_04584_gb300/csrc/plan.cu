@@ -1,0 +1,885 @@
+// Plan construction: the shared component of HEGrid (Sec. 4.1.1 and 4.3.1)
+// rebuilt for the GPU.
+//
+//   a1  coordinate prep: unit vectors of the samples in FP64
+//   a2  bin key of the padded map (replaces the HEALPix pixel index)
+//   a3  stable LSD radix sort of (key, index) and bin-range offsets (the LUT)
+//   a4  per-cell neighbour lists (Algorithm 1's ring/pixel search and its
+//       d <= R test), two passes: count, then fill
+//   a5  FP32 weights of every in-radius pair, computed once and shared by all
+//       channels, plus W[m] = sum of the weights
+//
+// Work on cells is organised in 16 x 8 cell blocks: a CTA owns one block, stages
+// the samples of the bins around it in shared memory and tests them against
+// its 128 cells.  The membership test runs in FP32 in a block-local frame with
+// a proven error band; pairs inside the band are decided in FP64.  Weights are
+// computed in float-float arithmetic from the same frame.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hegrid_internal.cuh"
+
+namespace hg {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* last_error() { return g_err.c_str(); }
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kDeg = kPi / 180.0;
+
+// ---------------------------------------------------------------------------
+// a1 + a2: per-sample unit vector and bin key.
+// ---------------------------------------------------------------------------
+struct KeyParams {
+  double lon0, lat0, dlon, dlat, cx, cy, wx, wy;
+  int32_t bin_cells, nbx;
+  uint32_t n_bins;
+};
+
+__global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* __restrict__ lat,
+                       KeyParams kp, uint32_t* __restrict__ key, int32_t* __restrict__ idx,
+                       double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ uz) {
+  int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double lo = lon[n], la = lat[n];
+  // Bin key: single IEEE operations only (no contraction), so the key is
+  // reproducible bit for bit by any IEEE-754 implementation.
+  double a = __dsub_rn(lo, kp.lon0);
+  double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
+  a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
+  double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
+  double qy = __dadd_rn(__ddiv_rn(__dsub_rn(la, kp.lat0), kp.dlat), kp.cy);
+  double fx = floor(qx), fy = floor(qy);
+  uint32_t k = kp.n_bins;
+  if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
+    int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
+    k = (uint32_t)(by * kp.nbx + bx);
+  }
+  key[n] = k;
+  idx[n] = n;
+  double sa, ca, sd, cd;
+  sincos(lo * kDeg, &sa, &ca);
+  sincos(la * kDeg, &sd, &cd);
+  ux[n] = cd * ca;
+  uy[n] = cd * sa;
+  uz[n] = sd;
+}
+
+// ---------------------------------------------------------------------------
+// a3: stable LSD radix sort (8-bit digits) of (key, index).
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;  // rounds of 256 consecutive elements per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_hist(const uint32_t* __restrict__ keys, int32_t N, int shift, int32_t n_tiles,
+                 int32_t* __restrict__ hist) {
+  __shared__ int32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + r * kSortThreads + threadIdx.x;
+    if (i < N) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];  // digit-major
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    k_radix_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                    uint32_t* __restrict__ kout, int32_t* __restrict__ vout, int32_t N, int shift,
+                    int32_t n_tiles, const int32_t* __restrict__ offs) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ int32_t wcnt[W][257];
+  __shared__ int32_t woff[W][257];
+  __shared__ int32_t run[256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  run[tid] = offs[(int64_t)tid * n_tiles + blockIdx.x];
+  for (int w = 0; w < W; ++w) wcnt[w][tid] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + r * kSortThreads + tid;
+    bool valid = i < N;
+    uint32_t k = valid ? kin[i] : 0u;
+    int32_t v = valid ? vin[i] : 0;
+    int d = valid ? (int)((k >> shift) & 255u) : 256;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      int dd = tid;  // one digit per thread
+      int32_t acc = run[dd];
+      for (int w = 0; w < W; ++w) {
+        woff[w][dd] = acc;
+        acc += wcnt[w][dd];
+        wcnt[w][dd] = 0;
+      }
+      run[dd] = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      int32_t dst = woff[warp][d] + rank;
+      kout[dst] = k;
+      vout[dst] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scans (three-phase, 4096 items per CTA).
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_tiles(const TI* in, int64_t n, TO* out, TO* tile_sums) {
+  __shared__ TO warp_sums[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
+  TO v[kScanItems];
+  TO local = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = (base + j < n) ? (TO)in[base + j] : (TO)0;
+    local += v[j];
+  }
+  TO x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    TO y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    TO s = warp_sums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      TO y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  TO excl = x - local + (warp > 0 ? warp_sums[warp - 1] : (TO)0);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < n) out[base + j] = excl;
+    excl += v[j];
+  }
+  if (tid == kScanThreads - 1 && tile_sums) tile_sums[blockIdx.x] = warp_sums[31];
+}
+
+template <typename TO>
+__global__ void k_scan_add(TO* __restrict__ out, int64_t n, const TO* __restrict__ tile_offs) {
+  int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  TO add = tile_offs[blockIdx.x];
+  for (int j = 0; j < kScanItems; ++j, i += kScanThreads)
+    if (i < n) out[i] += add;
+}
+
+template <typename T>
+__global__ void k_set_total(T* out, int64_t n, const T* excl_last, const T* in_last) {
+  out[n] = *excl_last + *in_last;
+}
+
+// out[0..n] = exclusive scan of in[0..n) with out[n] = total.  `tmp` needs
+// scan_tmp_elems(n) elements.
+int64_t scan_tmp_elems(int64_t n) {
+  int64_t t = 0;
+  while (n > kScanTile) {
+    n = (n + kScanTile - 1) / kScanTile;
+    t += n + 1;
+  }
+  return t + 1;
+}
+
+template <typename TI, typename TO>
+void scan_exclusive(const TI* in, int64_t n, TO* out, TO* tmp, cudaStream_t s);
+
+template <typename TO>
+void scan_in_place(TO* data, int64_t n, TO* tmp, cudaStream_t s) {
+  // data holds n inputs; replaced by their exclusive scan (no total).
+  int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    k_scan_tiles<TO, TO><<<1, kScanThreads, 0, s>>>(data, n, data, (TO*)nullptr);
+    return;
+  }
+  TO* sums = tmp;
+  k_scan_tiles<TO, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, data, sums);
+  scan_in_place<TO>(sums, tiles, tmp + tiles + 1, s);
+  k_scan_add<TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, sums);
+}
+
+template <typename TI, typename TO>
+void scan_exclusive(const TI* in, int64_t n, TO* out, TO* tmp, cudaStream_t s) {
+  int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    k_scan_tiles<TI, TO><<<1, kScanThreads, 0, s>>>(in, n, out, (TO*)nullptr);
+  } else {
+    TO* sums = tmp;
+    k_scan_tiles<TI, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, out, sums);
+    scan_in_place<TO>(sums, tiles, tmp + tiles + 1, s);
+    k_scan_add<TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums);
+  }
+}
+
+// bin_off[k] = first sorted position with key >= k, for k in [0, n_bins].
+__global__ void k_bin_offsets(const uint32_t* __restrict__ skey, int32_t N, uint32_t n_bins,
+                              int32_t* __restrict__ bin_off) {
+  int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int64_t prev = s > 0 ? (int64_t)skey[s - 1] : -1;
+  int64_t cur = skey[s];
+  for (int64_t k = prev + 1; k <= cur && k <= (int64_t)n_bins; ++k) bin_off[k] = s;
+  if (s == N - 1)
+    for (int64_t k = cur + 1; k <= (int64_t)n_bins; ++k) bin_off[k] = N;
+}
+
+__global__ void k_gather_u(const int32_t* __restrict__ perm, int32_t N,
+                           const double* __restrict__ ux, const double* __restrict__ uy,
+                           const double* __restrict__ uz, double* __restrict__ sx,
+                           double* __restrict__ sy, double* __restrict__ sz) {
+  int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= N) return;
+  int32_t n = perm[s];
+  sx[s] = ux[n];
+  sy[s] = uy[n];
+  sz[s] = uz[n];
+}
+
+// ---------------------------------------------------------------------------
+// a4 + a5: block-local neighbour search and weights.
+// ---------------------------------------------------------------------------
+struct PairParams {
+  int32_t nx, ny, nbx_b, nbx;  // map, cell blocks along RA, bins along RA
+  double lon0, lat0, dlon, dlat;
+  double cR2;       // chord^2 at R: 4 sin^2(R/2), FP64
+  float lo_thr;     // FP32 c^2 below this: inside for sure
+  float hi_thr;     // FP32 c^2 above this: outside for sure
+  float k_hi, k_lo; // 1 / (2 sigma^2) in rad^-2 as float-float
+};
+
+constexpr int kChunk = 128;  // candidates staged per round (= threads per CTA)
+
+__device__ __forceinline__ void unit_vec(double lon_deg, double lat_deg, double& x, double& y,
+                                         double& z) {
+  double sa, ca, sd, cd;
+  sincos(lon_deg * kDeg, &sa, &ca);
+  sincos(lat_deg * kDeg, &sd, &cd);
+  x = cd * ca;
+  y = cd * sa;
+  z = sd;
+}
+
+// Exact difference a - b = s + e of two floats (Knuth's TwoSum on a, -b).
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
+  s = __fsub_rn(a, b);
+  float v = __fsub_rn(s, a);
+  e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, v)), __fadd_rn(b, v));
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+
+// Gaussian weight of a pair from block-local float-float coordinates.
+//   chord c = |u_m - u_n| (float-float), d^2 = c^2 g(c^2/4) with
+//   g(h) = asin^2(sqrt h)/h = 1 + h/3 + 8h^2/45 + 4h^3/35 + 128h^4/1575 + ...
+//   (the power series of arcsin^2), w = exp(-d^2 / (2 sigma^2)).
+// Relative error ~3 ulp of FP32 for h <= 0.01.
+__device__ __forceinline__ float pair_weight(const float (&mh)[3], const float (&ml)[3],
+                                             const float (&nh)[3], const float (&nl)[3],
+                                             float k_hi, float k_lo) {
+  float h[3], l[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float s, e;
+    two_diff(mh[i], nh[i], s, e);
+    h[i] = s;
+    l[i] = __fadd_rn(e, __fsub_rn(ml[i], nl[i]));
+  }
+  float p[3], pe[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    p[i] = __fmul_rn(h[i], h[i]);
+    pe[i] = __fmaf_rn(h[i], h[i], -p[i]) + 2.0f * h[i] * l[i];
+  }
+  float s01, t01, S, t2;
+  two_sum(p[0], p[1], s01, t01);
+  two_sum(s01, p[2], S, t2);
+  float Slo = t01 + t2 + pe[0] + pe[1] + pe[2];
+  float ch = __fadd_rn(S, Slo);
+  float cl = __fsub_rn(Slo, __fsub_rn(ch, S));
+  float hh = 0.25f * ch;
+  float corr =
+      hh * (1.0f / 3.0f + hh * (8.0f / 45.0f + hh * (4.0f / 35.0f + hh * (128.0f / 1575.0f))));
+  float xl = cl + ch * corr;
+  float xh = __fadd_rn(ch, xl);
+  xl = __fsub_rn(xl, __fsub_rn(xh, ch));
+  float th = __fmul_rn(xh, k_hi);
+  float tl = __fmaf_rn(xh, k_hi, -th) + xh * k_lo + xl * k_hi;
+  return expf(-th) * (1.0f - tl);
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kChunk)
+    k_block_pairs(PairParams pp, const int4* __restrict__ win, const int32_t* __restrict__ bin_off,
+                  const int32_t* __restrict__ perm, const double* __restrict__ sx,
+                  const double* __restrict__ sy, const double* __restrict__ sz,
+                  int32_t* __restrict__ cnt, int32_t* __restrict__ kb,
+                  const int64_t* __restrict__ nb_off, const int64_t* __restrict__ cand_off,
+                  int32_t* __restrict__ nb_idx, int32_t* __restrict__ nb_loc,
+                  float* __restrict__ nb_w, float* __restrict__ wsum,
+                  int32_t* __restrict__ cand_idx) {
+  __shared__ float s_eh[3][kChunk];
+  __shared__ float s_el[3][kChunk];
+  __shared__ double s_u[3][kChunk];
+  __shared__ int32_t s_n[kChunk];
+  __shared__ uint32_t s_umask[kChunk / 32];
+
+  const int t = threadIdx.x;
+  const int b = blockIdx.x;
+  const int bbx = b % pp.nbx_b, bby = b / pp.nbx_b;
+  const int ix = bbx * HG_BX + (t % HG_BX), iy = bby * HG_BY + (t / HG_BX);
+  const bool active = ix < pp.nx && iy < pp.ny;
+  const int64_t m = (int64_t)iy * pp.nx + ix;
+
+  // Block-local frame: origin at the unit vector of the block's centre.
+  double bx0, by0, bz0;
+  unit_vec(pp.lon0 + ((double)bbx * HG_BX + 0.5 * (HG_BX - 1) - 0.5 * (pp.nx - 1)) * pp.dlon,
+           pp.lat0 + ((double)bby * HG_BY + 0.5 * (HG_BY - 1) - 0.5 * (pp.ny - 1)) * pp.dlat,
+           bx0, by0, bz0);
+  double um[3];
+  unit_vec(pp.lon0 + ((double)ix - 0.5 * (pp.nx - 1)) * pp.dlon,
+           pp.lat0 + ((double)iy - 0.5 * (pp.ny - 1)) * pp.dlat, um[0], um[1], um[2]);
+  float mh[3], ml[3];
+  {
+    double e[3] = {um[0] - bx0, um[1] - by0, um[2] - bz0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      mh[i] = __double2float_rn(e[i]);
+      ml[i] = __double2float_rn(e[i] - (double)mh[i]);
+    }
+  }
+
+  int32_t count = 0;
+  int64_t kcount = 0;  // union size so far (local index of the next candidate)
+  int64_t pos = 0;
+  float ws = 0.0f, wc = 0.0f;  // Neumaier-compensated sum of weights
+  int64_t cbase = 0;
+  if (FILL) {
+    if (active) pos = nb_off[m];
+    cbase = cand_off[b];
+  }
+  const int4 wb = win[b];  // by0, by1, bx0, bx1
+  for (int by = wb.x; by <= wb.y; ++by) {
+    const int32_t s_beg = bin_off[(int64_t)by * pp.nbx + wb.z];
+    const int32_t s_end = bin_off[(int64_t)by * pp.nbx + wb.w + 1];
+    for (int32_t base = s_beg; base < s_end; base += kChunk) {
+      const int32_t s = base + t;
+      const int nk = min(kChunk, s_end - base);
+      if (s < s_end) {
+        double u[3] = {sx[s], sy[s], sz[s]};
+        double e[3] = {u[0] - bx0, u[1] - by0, u[2] - bz0};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          float hv = __double2float_rn(e[i]);
+          s_eh[i][t] = hv;
+          s_el[i][t] = __double2float_rn(e[i] - (double)hv);
+          s_u[i][t] = u[i];
+        }
+        s_n[t] = perm[s];
+      }
+      if (t < kChunk / 32) s_umask[t] = 0u;
+      __syncthreads();
+
+      // Phase 1: membership of each staged candidate for this thread's cell.
+      uint32_t mask[kChunk / 32];
+#pragma unroll
+      for (int q = 0; q < kChunk / 32; ++q) {
+        uint32_t mm = 0u;
+        const int kend = active ? min(32, nk - 32 * q) : 0;
+        for (int r = 0; r < kend; ++r) {
+          const int k = 32 * q + r;
+          float dx = mh[0] - s_eh[0][k], dy = mh[1] - s_eh[1][k], dz = mh[2] - s_eh[2][k];
+          float c2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          bool in;
+          if (c2 <= pp.lo_thr) {
+            in = true;
+          } else if (c2 > pp.hi_thr) {
+            in = false;
+          } else {  // inside the FP32 error band: decide in FP64
+            double ex = um[0] - s_u[0][k], ey = um[1] - s_u[1][k], ez = um[2] - s_u[2][k];
+            in = ex * ex + ey * ey + ez * ez <= pp.cR2;
+          }
+          mm |= (uint32_t)in << r;
+        }
+        mask[q] = mm;
+      }
+#pragma unroll
+      for (int q = 0; q < kChunk / 32; ++q) {
+        uint32_t wmask = __reduce_or_sync(0xffffffffu, mask[q]);
+        if ((t & 31) == 0 && wmask) atomicOr(&s_umask[q], wmask);
+      }
+      __syncthreads();
+      uint32_t um4[kChunk / 32];
+      int ucount = 0;
+#pragma unroll
+      for (int q = 0; q < kChunk / 32; ++q) {
+        um4[q] = s_umask[q];
+        ucount += __popc(um4[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kChunk / 32; ++q) count += __popc(mask[q]);
+
+      if (FILL) {
+        // Candidate list of the block: the union, in staging order.
+        {
+          int q = t >> 5, r = t & 31;
+          if ((um4[q] >> r) & 1u) {
+            int before = __popc(um4[q] & ((1u << r) - 1u));
+            for (int j = 0; j < q; ++j) before += __popc(um4[j]);
+            cand_idx[cbase + kcount + before] = s_n[t];
+          }
+        }
+        // Pairs of this cell with their local index and weight.
+        int pre = 0;
+#pragma unroll
+        for (int q = 0; q < kChunk / 32; ++q) {
+          uint32_t mm = mask[q];
+          while (mm) {
+            int r = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            int k = q * 32 + r;
+            int loc = pre + __popc(um4[q] & ((1u << r) - 1u));
+            float nh[3] = {s_eh[0][k], s_eh[1][k], s_eh[2][k]};
+            float nl[3] = {s_el[0][k], s_el[1][k], s_el[2][k]};
+            float w = pair_weight(mh, ml, nh, nl, pp.k_hi, pp.k_lo);
+            nb_idx[pos] = s_n[k];
+            nb_loc[pos] = (int32_t)(kcount + loc);
+            nb_w[pos] = w;
+            ++pos;
+            float tt = ws + w;
+            wc += fabsf(ws) >= fabsf(w) ? (ws - tt) + w : (w - tt) + ws;
+            ws = tt;
+          }
+          pre += __popc(um4[q]);
+        }
+      }
+      kcount += ucount;
+      __syncthreads();
+    }
+  }
+  if (!FILL) {
+    if (active) cnt[m] = count;
+    if (t == 0) kb[b] = (int32_t)kcount;
+  } else {
+    if (active) wsum[m] = ws + wc;
+    // Pad the candidate list to a multiple of HG_KPAD with a valid sample
+    // index (its weight is zero in every cell).
+    int64_t padded = (kcount + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
+    int32_t filler = kcount > 0 ? cand_idx[cbase] : 0;
+    for (int64_t i = kcount + t; i < padded; i += kChunk) cand_idx[cbase + i] = filler;
+  }
+}
+
+__global__ void k_pad_counts(const int32_t* __restrict__ kb, int64_t n, int64_t* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ((int64_t)kb[i] + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
+}
+
+template <typename T>
+static cudaError_t dmalloc(T** p, int64_t n, int64_t* bytes) {
+  size_t sz = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+  *bytes += (int64_t)sz;
+  return cudaMalloc((void**)p, sz);
+}
+
+}  // namespace
+
+void free_plan_arrays(hegrid_plan* p) {
+  cudaFree(p->perm);
+  cudaFree(p->bin_off);
+  cudaFree(p->nb_off);
+  cudaFree(p->nb_idx);
+  cudaFree(p->nb_loc);
+  cudaFree(p->nb_w);
+  cudaFree(p->wsum);
+  cudaFree(p->cand_off);
+  cudaFree(p->cand_idx);
+  cudaFree(p->err_word);
+}
+
+// Temporary device buffers of plan_create, freed on every exit path.
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+  template <typename T>
+  cudaError_t get(T** p, int64_t n) {
+    size_t sz = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, sz);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+};
+
+hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
+                                int coords_on_device, cudaStream_t st) {
+  const int32_t N = (int32_t)p->N;
+  const hegrid_map_geom& g = p->geom;
+  Scratch sc;
+
+  // --- layout of the padded map (a2) -----------------------------------
+  const double half_rows = 0.5 * (double)(g.ny - 1) * g.dlat_deg;
+  const double lat_max = std::max(std::fabs(g.lat0_deg - half_rows), std::fabs(g.lat0_deg + half_rows));
+  if (lat_max + p->R_deg >= 90.0) {
+    set_error("map rows come within R of a pole");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  const double Hmax = std::asin(std::sin(p->R_rad) / std::cos(lat_max * kDeg)) / kDeg;
+  p->pady = (int32_t)std::ceil(p->R_deg / g.dlat_deg) + 1;
+  p->padx = (int32_t)std::ceil(Hmax / g.dlon_deg) + 1;
+  if ((double)(g.nx + 2 * p->padx) * g.dlon_deg >= 360.0) {
+    set_error("padded map is wider than 360 degrees of RA");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  const int B = p->bin_cells;
+  p->nbx = (g.nx + 2 * p->padx + B - 1) / B;
+  p->nby = (g.ny + 2 * p->pady + B - 1) / B;
+  p->n_bins = (int64_t)p->nbx * p->nby;
+  if (p->n_bins >= (int64_t)0x7fffffff) {
+    set_error("too many bins");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  p->nbx_b = (g.nx + HG_BX - 1) / HG_BX;
+  p->nby_b = (g.ny + HG_BY - 1) / HG_BY;
+  p->n_blocks = (int64_t)p->nbx_b * p->nby_b;
+
+  // --- coordinates on the device ---------------------------------------
+  const double* dlon = lon;
+  const double* dlat = lat;
+  if (!coords_on_device) {
+    double *a, *b;
+    HG_CUDA_TRY(sc.get(&a, N));
+    HG_CUDA_TRY(sc.get(&b, N));
+    HG_CUDA_TRY(cudaMemcpyAsync(a, lon, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    HG_CUDA_TRY(cudaMemcpyAsync(b, lat, sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    dlon = a;
+    dlat = b;
+  }
+
+  // --- a1 + a2 ------------------------------------------------------------
+  uint32_t *key0, *key1;
+  int32_t *val0, *val1;
+  double *ux, *uy, *uz, *sx, *sy, *sz;
+  HG_CUDA_TRY(sc.get(&key0, N));
+  HG_CUDA_TRY(sc.get(&key1, N));
+  HG_CUDA_TRY(sc.get(&val0, N));
+  HG_CUDA_TRY(sc.get(&val1, N));
+  HG_CUDA_TRY(sc.get(&ux, N));
+  HG_CUDA_TRY(sc.get(&uy, N));
+  HG_CUDA_TRY(sc.get(&uz, N));
+  HG_CUDA_TRY(sc.get(&sx, N));
+  HG_CUDA_TRY(sc.get(&sy, N));
+  HG_CUDA_TRY(sc.get(&sz, N));
+  KeyParams kp;
+  kp.lon0 = g.lon0_deg;
+  kp.lat0 = g.lat0_deg;
+  kp.dlon = g.dlon_deg;
+  kp.dlat = g.dlat_deg;
+  kp.cx = 0.5 * (double)g.nx + (double)p->padx;
+  kp.cy = 0.5 * (double)g.ny + (double)p->pady;
+  kp.wx = (double)(g.nx + 2 * p->padx);
+  kp.wy = (double)(g.ny + 2 * p->pady);
+  kp.bin_cells = B;
+  kp.nbx = p->nbx;
+  kp.n_bins = (uint32_t)p->n_bins;
+  k_prep<<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, key0, val0, ux, uy, uz);
+  HG_CUDA_TRY(cudaGetLastError());
+
+  // --- a3: radix sort ------------------------------------------------------
+  int bits = 1;
+  while (((uint64_t)1 << bits) <= (uint64_t)p->n_bins) ++bits;
+  const int passes = (bits + 7) / 8;
+  const int32_t n_tiles = (N + kSortTile - 1) / kSortTile;
+  const int64_t hist_n = (int64_t)256 * n_tiles;
+  int32_t *hist, *hoff, *stmp32;
+  HG_CUDA_TRY(sc.get(&hist, hist_n));
+  HG_CUDA_TRY(sc.get(&hoff, hist_n + 1));
+  HG_CUDA_TRY(sc.get(&stmp32, scan_tmp_elems(hist_n) + 8));
+  uint32_t *kin = key0, *kout = key1;
+  int32_t *vin = val0, *vout = val1;
+  for (int ps = 0; ps < passes; ++ps) {
+    k_radix_hist<<<n_tiles, kSortThreads, 0, st>>>(kin, N, 8 * ps, n_tiles, hist);
+    scan_exclusive<int32_t, int32_t>(hist, hist_n, hoff, stmp32, st);
+    k_radix_scatter<<<n_tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, 8 * ps, n_tiles,
+                                                       hoff);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  HG_CUDA_TRY(cudaGetLastError());
+  int64_t bytes = 0;
+  HG_CUDA_TRY(dmalloc(&p->perm, N, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->bin_off, p->n_bins + 1, &bytes));
+  HG_CUDA_TRY(cudaMemcpyAsync(p->perm, vin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
+  k_bin_offsets<<<(N + 255) / 256, 256, 0, st>>>(kin, N, (uint32_t)p->n_bins, p->bin_off);
+  k_gather_u<<<(N + 255) / 256, 256, 0, st>>>(p->perm, N, ux, uy, uz, sx, sy, sz);
+  HG_CUDA_TRY(cudaGetLastError());
+
+  // --- block windows (host) ------------------------------------------------
+  std::vector<int4> hwin(p->n_blocks);
+  const double eps_px = 1e-6;
+  const double sR = std::sin(p->R_rad);
+  for (int64_t b = 0; b < p->n_blocks; ++b) {
+    int bbx = (int)(b % p->nbx_b), bby = (int)(b / p->nbx_b);
+    int ix0 = bbx * HG_BX, ix1 = std::min(ix0 + HG_BX - 1, g.nx - 1);
+    int iy0 = bby * HG_BY, iy1 = std::min(iy0 + HG_BY - 1, g.ny - 1);
+    double la0 = g.lat0_deg + ((double)iy0 - 0.5 * (g.ny - 1)) * g.dlat_deg;
+    double la1 = g.lat0_deg + ((double)iy1 - 0.5 * (g.ny - 1)) * g.dlat_deg;
+    double lmax = std::max(std::fabs(la0), std::fabs(la1));
+    double Hb = std::asin(sR / std::cos(lmax * kDeg)) / kDeg;
+    double qy_lo = iy0 + p->pady + 0.5 - p->R_deg / g.dlat_deg - eps_px;
+    double qy_hi = iy1 + p->pady + 0.5 + p->R_deg / g.dlat_deg + eps_px;
+    double qx_lo = ix0 + p->padx + 0.5 - Hb / g.dlon_deg - eps_px;
+    double qx_hi = ix1 + p->padx + 0.5 + Hb / g.dlon_deg + eps_px;
+    int by0 = std::max(0, (int)std::floor(qy_lo) / B);
+    int by1 = std::min(p->nby - 1, (int)std::floor(qy_hi) / B);
+    int bx0 = std::max(0, (int)std::floor(qx_lo) / B);
+    int bx1 = std::min(p->nbx - 1, (int)std::floor(qx_hi) / B);
+    hwin[b] = make_int4(by0, by1, bx0, bx1);
+  }
+  int4* dwin;
+  HG_CUDA_TRY(sc.get(&dwin, p->n_blocks));
+  HG_CUDA_TRY(cudaMemcpyAsync(dwin, hwin.data(), sizeof(int4) * p->n_blocks,
+                              cudaMemcpyHostToDevice, st));
+
+  // --- a4: count pass --------------------------------------------------------
+  PairParams pp;
+  pp.nx = g.nx;
+  pp.ny = g.ny;
+  pp.nbx_b = p->nbx_b;
+  pp.nbx = p->nbx;
+  pp.lon0 = g.lon0_deg;
+  pp.lat0 = g.lat0_deg;
+  pp.dlon = g.dlon_deg;
+  pp.dlat = g.dlat_deg;
+  {
+    double s = std::sin(0.5 * p->R_rad);
+    pp.cR2 = 4.0 * s * s;
+    // Error band of the FP32 test (relative to c_R^2).  With E the largest
+    // |u - u_block| in the window and c the chord, the FP32 chord^2 from the
+    // rounded block-local coordinates is within 2^-24 (7 E/c + 8) of the exact
+    // value; the band is 2^-20 (8 + 8 E/c), 16x wider.
+    double cR = 2.0 * s;
+    double wx_cells = HG_BX + 2.0 * (Hmax / g.dlon_deg + 2.0 * B + 1.0);
+    double wy_cells = HG_BY + 2.0 * (p->R_deg / g.dlat_deg + 2.0 * B + 1.0);
+    double E = 0.5 * std::sqrt(wx_cells * wx_cells * g.dlon_deg * g.dlon_deg +
+                               wy_cells * wy_cells * g.dlat_deg * g.dlat_deg) * kDeg;
+    double band = std::ldexp(8.0 + 8.0 * E / cR, -20);
+    pp.lo_thr = std::nextafter((float)(pp.cR2 * (1.0 - band)), 0.0f);
+    pp.hi_thr = std::nextafter((float)(pp.cR2 * (1.0 + band)), 1.0f);
+    double k = 1.0 / (2.0 * p->sigma_rad * p->sigma_rad);
+    pp.k_hi = (float)k;
+    pp.k_lo = (float)(k - (double)pp.k_hi);
+  }
+  int32_t *cnt, *kb;
+  int64_t* kbp;
+  HG_CUDA_TRY(sc.get(&cnt, p->M + 1));
+  HG_CUDA_TRY(sc.get(&kb, p->n_blocks + 1));
+  HG_CUDA_TRY(sc.get(&kbp, p->n_blocks + 1));
+  HG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (p->M + 1), st));
+  HG_CUDA_TRY(cudaMemsetAsync(kb, 0, sizeof(int32_t) * (p->n_blocks + 1), st));
+  k_block_pairs<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
+      pp, dwin, p->bin_off, p->perm, sx, sy, sz, cnt, kb, nullptr, nullptr, nullptr, nullptr,
+      nullptr, nullptr, nullptr);
+  HG_CUDA_TRY(cudaGetLastError());
+  int64_t* stmp64;
+  HG_CUDA_TRY(sc.get(&stmp64, scan_tmp_elems(std::max(p->M, p->n_blocks) + 1) + 8));
+  HG_CUDA_TRY(dmalloc(&p->nb_off, p->M + 1, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->cand_off, p->n_blocks + 1, &bytes));
+  // exclusive scans over n+1 entries (last input 0): out[n] is the total
+  scan_exclusive<int32_t, int64_t>(cnt, p->M + 1, p->nb_off, stmp64, st);
+  k_pad_counts<<<(unsigned)((p->n_blocks + 1 + 255) / 256), 256, 0, st>>>(kb, p->n_blocks + 1, kbp);
+  scan_exclusive<int64_t, int64_t>(kbp, p->n_blocks + 1, p->cand_off, stmp64, st);
+  HG_CUDA_TRY(cudaGetLastError());
+
+  // The one host round trip of plan creation: the number of pairs and of
+  // candidate slots size the remaining arrays.
+  int64_t totals[2];
+  HG_CUDA_TRY(cudaMemcpyAsync(&totals[0], p->nb_off + p->M, sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, st));
+  HG_CUDA_TRY(cudaMemcpyAsync(&totals[1], p->cand_off + p->n_blocks, sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, st));
+  HG_CUDA_TRY(cudaStreamSynchronize(st));
+  p->P = totals[0];
+  p->n_cand = totals[1];
+  if (p->n_cand > (int64_t)0x7fffffff) {
+    set_error("too many candidate slots");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+
+  // --- a4 fill + a5 weights ------------------------------------------------
+  HG_CUDA_TRY(dmalloc(&p->nb_idx, p->P, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->nb_loc, p->P, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->nb_w, p->P, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->wsum, p->M, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->err_word, 4, &bytes));
+  HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
+  HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * p->M, st));
+  k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
+      pp, dwin, p->bin_off, p->perm, sx, sy, sz, nullptr, nullptr, p->nb_off, p->cand_off,
+      p->nb_idx, p->nb_loc, p->nb_w, p->wsum, p->cand_idx);
+  HG_CUDA_TRY(cudaGetLastError());
+  // scratch is freed by ~Scratch; make sure the kernels that use it are done
+  HG_CUDA_TRY(cudaStreamSynchronize(st));
+  p->bytes = bytes;
+  return HEGRID_OK;
+}
+
+}  // namespace hg
+
+// ===========================================================================
+// C ABI: plan lifetime, info, export
+// ===========================================================================
+extern "C" {
+
+const char* hegrid_last_error(void) { return hg::last_error(); }
+
+hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const double* lon_deg,
+                                 const double* lat_deg, int coords_on_device,
+                                 const hegrid_map_geom* geom, const hegrid_kernel* kern,
+                                 uint32_t flags, void* stream) {
+  hg::set_error("");
+  HG_ARG_CHECK(out != nullptr, "out is NULL");
+  *out = nullptr;
+  HG_ARG_CHECK(lon_deg && lat_deg && geom && kern, "NULL coordinates, geometry or kernel");
+  HG_ARG_CHECK(n_samples >= 1 && n_samples < (int64_t)0x7fffffff, "n_samples out of [1, 2^31)");
+  HG_ARG_CHECK(geom->nx >= 1 && geom->ny >= 1, "nx, ny must be >= 1");
+  HG_ARG_CHECK((int64_t)geom->nx * geom->ny < ((int64_t)1 << 40), "map too large");
+  HG_ARG_CHECK(geom->dlon_deg > 0 && geom->dlat_deg > 0, "cell size must be > 0");
+  HG_ARG_CHECK(std::isfinite(geom->lon0_deg) && std::isfinite(geom->lat0_deg),
+               "map centre must be finite");
+  HG_ARG_CHECK(kern->fwhm_deg > 0 && kern->support_sigmas > 0, "FWHM and support must be > 0");
+  uint32_t bc = flags & 0xffu;
+  hegrid_plan* p = new hegrid_plan();
+  std::memset(p, 0, sizeof(*p));
+  p->geom = *geom;
+  p->kern = *kern;
+  cudaGetDevice(&p->device);
+  p->N = n_samples;
+  p->M = (int64_t)geom->nx * geom->ny;
+  p->bin_cells = bc ? (int32_t)bc : 2;
+  double sigma_deg = kern->fwhm_deg / std::sqrt(8.0 * std::log(2.0));
+  p->sigma_rad = sigma_deg * hg::kDeg;
+  p->R_deg = kern->support_sigmas * sigma_deg;
+  p->R_rad = p->R_deg * hg::kDeg;
+  if (p->R_deg > 11.0) {
+    delete p;
+    hg::set_error("kernel radius above 11 degrees is not supported");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  hegrid_status s = hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream);
+  if (s != HEGRID_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    hg::free_plan_arrays(p);
+    delete p;
+    return s;
+  }
+  *out = p;
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_plan_destroy(hegrid_plan* plan) {
+  if (!plan) return HEGRID_OK;
+  cudaDeviceSynchronize();
+  hg::free_plan_arrays(plan);
+  delete plan;
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_plan_info(const hegrid_plan* plan, int64_t* n_pairs, int64_t* n_bins,
+                               int64_t* n_blocks, int64_t* n_cand, int64_t* bytes) {
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  if (n_pairs) *n_pairs = plan->P;
+  if (n_bins) *n_bins = plan->n_bins;
+  if (n_blocks) *n_blocks = plan->n_blocks;
+  if (n_cand) *n_cand = plan->n_cand;
+  if (bytes) *bytes = plan->bytes;
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t* bin_off,
+                                 int64_t* nb_off, int32_t* nb_idx, float* nb_w, float* weight) {
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  HG_CUDA_TRY(cudaDeviceSynchronize());
+  if (perm)
+    HG_CUDA_TRY(cudaMemcpy(perm, plan->perm, sizeof(int32_t) * plan->N, cudaMemcpyDeviceToHost));
+  if (bin_off)
+    HG_CUDA_TRY(cudaMemcpy(bin_off, plan->bin_off, sizeof(int32_t) * (plan->n_bins + 1),
+                           cudaMemcpyDeviceToHost));
+  if (weight)
+    HG_CUDA_TRY(cudaMemcpy(weight, plan->wsum, sizeof(float) * plan->M, cudaMemcpyDeviceToHost));
+  if (nb_off || nb_idx || nb_w) {
+    std::vector<int64_t> off(plan->M + 1);
+    HG_CUDA_TRY(cudaMemcpy(off.data(), plan->nb_off, sizeof(int64_t) * (plan->M + 1),
+                           cudaMemcpyDeviceToHost));
+    if (nb_off) std::memcpy(nb_off, off.data(), sizeof(int64_t) * (plan->M + 1));
+    if (nb_idx || nb_w) {
+      std::vector<int32_t> idx(plan->P);
+      std::vector<float> w(plan->P);
+      HG_CUDA_TRY(cudaMemcpy(idx.data(), plan->nb_idx, sizeof(int32_t) * plan->P,
+                             cudaMemcpyDeviceToHost));
+      HG_CUDA_TRY(
+          cudaMemcpy(w.data(), plan->nb_w, sizeof(float) * plan->P, cudaMemcpyDeviceToHost));
+      // canonical order: ascending sample index inside each cell
+      std::vector<int64_t> ord;
+      for (int64_t m = 0; m < plan->M; ++m) {
+        int64_t a = off[m], b = off[m + 1];
+        ord.resize(b - a);
+        for (int64_t i = 0; i < b - a; ++i) ord[i] = a + i;
+        std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return idx[x] < idx[y]; });
+        for (int64_t i = 0; i < b - a; ++i) {
+          if (nb_idx) nb_idx[a + i] = idx[ord[i]];
+          if (nb_w) nb_w[a + i] = w[ord[i]];
+        }
+      }
+    }
+  }
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_status_poll(const hegrid_plan* plan) {
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  int32_t w = 0;
+  HG_CUDA_TRY(cudaMemcpy(&w, plan->err_word, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (w != 0) {
+    hg::set_error("a bounded device-side wait timed out (error word " + std::to_string(w) + ")");
+    return HEGRID_ERR_TIMEOUT;
+  }
+  return HEGRID_OK;
+}
+
+}  // extern "C"
