@@ -7,8 +7,8 @@
 
 namespace hg {
 
-// Upper bound on mbarrier polls before a wait gives up (seconds of spinning).
-constexpr uint32_t kSpinLimit = 1u << 26;
+// A bounded wait gives up after this many nanoseconds of polling.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Error codes written to the plan's device error word.
 constexpr int32_t kErrWaitTimeout = 1;
@@ -52,11 +52,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Bounded wait on a phase of an mbarrier.  Returns false (and records the
-// timeout in *err) if the phase did not complete within kSpinLimit polls.
+// timeout in *err) if the phase did not complete within kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
   if (err) atomicExch(err, kErrWaitTimeout);
   return false;
 }
