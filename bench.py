@@ -1,0 +1,356 @@
+"""Throughput of the gridding hot path on the FAST-like drift-scan workload.
+
+One step = one pass of the whole path over one batch of synthetic input:
+plan creation (coordinate prep, bin keys, radix sort, bin offsets, neighbour
+lists, weights) followed by the grid step (accumulate + normalise) of every
+channel, then plan destruction.  Metric: sample x channel contributions per
+second, N * C / t_step, whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode tc_split|tc|fp32]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Under torchrun each rank runs an independent replica (the path shards by
+fields or channel slices with no exchange; one GPU per rank): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2207_04584_gb300 import workloads as W  # noqa: E402
+
+METRIC = "sample x channel contributions/s (N*C/t, plan + grid per step)"
+UNIT = "contrib/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
+                 "100", "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(wl, frac_rows=20, nthreads=0):
+    """Time the FP64 oracle on a bounded sample: every frac_rows-th map row,
+    all channels; extrapolate to the full map as t_index + t_cells * M / cells."""
+    import oracle
+    g = wl["geom"]
+    nx, ny = g["nx"], g["ny"]
+    rows = np.arange(0, ny, frac_rows)
+    cells = (rows[:, None] * nx + np.arange(nx)[None, :]).ravel()
+    t0 = time.perf_counter()
+    ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"], wl.get("support", 3.0))
+    t1 = time.perf_counter()
+    ix.grid(wl["values"], cells=cells, nthreads=nthreads)
+    t2 = time.perf_counter()
+    M = nx * ny
+    t_full = (t1 - t0) + (t2 - t1) * M / len(cells)
+    N, C = wl["values"].shape
+    cores = nthreads if nthreads > 0 else (os.cpu_count() or 1)
+    return {"value": N * C / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle (declination-strip index, OpenMP) on every {frac_rows}th "
+                      f"map row ({len(cells)} of {M} cells, all {C} channels); index build "
+                      f"{t1 - t0:.2f}s + cells {t2 - t1:.2f}s, extrapolated to the full map "
+                      f"({t_full:.1f}s)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    t_gen = time.perf_counter()
+    wl = W.config2()
+    t_gen = time.perf_counter() - t_gen
+    N, C = wl["values"].shape
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(wl, frac_rows=60)
+        if i >= args.warmup:
+            times.append(N * C / r["value"])
+    t = statistics.mean(times)
+    value = N * C / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "N": N, "C": C, "M": wl["geom"]["nx"] ** 2,
+                       "seed": W.SEED_BASE + 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
+                             "cores": os.cpu_count(), "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gen_s": t_gen}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "tc_split", "tc", "fp32"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--channels", type=int, default=1024)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    from paper_2207_04584_gb300 import hegrid as H
+    H.lib()
+
+    # ---- workload (config 2: FAST-like drift scan, FP32 values) ----------
+    t_gen = time.perf_counter()
+    pos = W.config2(with_values=False, C=args.channels)
+    N = len(pos["lon"])
+    C = args.channels
+    host_vals = torch.empty((N, C), dtype=torch.float32, pin_memory=True)
+    wl = W.config2(C=C, out=host_vals.numpy())
+    t_gen = time.perf_counter() - t_gen
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    lon_d = torch.from_numpy(wl["lon"]).to(dev)
+    lat_d = torch.from_numpy(wl["lat"]).to(dev)
+    vals_d = host_vals.to(dev)
+    map_d = torch.empty((M, C), device=dev)
+    w_d = torch.empty(M, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    modes = {"tc_split": H.HEGRID_MODE_TC_SPLIT, "tc": H.HEGRID_MODE_TC,
+             "fp32": H.HEGRID_MODE_FP32}
+    mode_name = args.mode
+    if mode_name == "auto":
+        mode_name = "tc_split"
+        try:
+            p = H.hegrid_plan_create(64, wl["lon"][:64].copy(), wl["lat"][:64].copy(), 0, g,
+                                     wl["fwhm_deg"], 3.0, 0, sh)
+            try:
+                H.hegrid_grid(p, vals_d, H.HEGRID_F32, C, C, map_d, C, w_d,
+                              H.HEGRID_MODE_TC_SPLIT, sh)
+            finally:
+                H.hegrid_plan_destroy(p)
+        except H.HegridError:
+            mode_name = "fp32"
+    mode = modes[mode_name]
+
+    ev = []
+
+    def step(record):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, 0, sh)
+        e1.record(stream)
+        H.hegrid_grid(plan, vals_d, H.HEGRID_F32, C, C, map_d, C, w_d, mode, sh)
+        e2.record(stream)
+        H.hegrid_plan_destroy(plan)
+        if record:
+            ev.append((e0, e1, e2))
+        return plan
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = H.hegrid_launch_count()
+    clocks = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    launches = (H.hegrid_launch_count() - launches0) // max(1, args.steps)
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if dist:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    t_plan = statistics.mean(a.elapsed_time(b) for a, b, c in ev) / 1e3
+    t_grid = statistics.mean(b.elapsed_time(c) for a, b, c in ev) / 1e3
+    value = world * N * C * args.steps / elapsed
+
+    # plan facts and accuracy on sampled cells (vs the FP64 oracle)
+    plan = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, 0, sh)
+    info = H.hegrid_plan_info(plan)
+    P = info["n_pairs"]
+    forms = {}
+    err = {}
+    for nm, md in modes.items():
+        try:
+            H.hegrid_grid(plan, vals_d, H.HEGRID_F32, C, C, map_d, C, w_d, md, sh)
+        except H.HegridError as e:
+            forms[nm] = {"unavailable": str(e)}
+            continue
+        torch.cuda.synchronize()
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        es.record(stream)
+        for _ in range(reps):
+            H.hegrid_grid(plan, vals_d, H.HEGRID_F32, C, C, map_d, C, w_d, md, sh)
+        ee.record(stream)
+        torch.cuda.synchronize()
+        tg = es.elapsed_time(ee) / 1e3 / reps
+        forms[nm] = {"grid_ms": tg * 1e3, "grid_contrib_per_s": N * C / tg,
+                     "pair_channel_per_s": P * C / tg}
+        if rank == 0:
+            import oracle
+            rng = np.random.default_rng(7)
+            cells = np.sort(rng.choice(M, 256, replace=False))
+            ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
+            ref, Wref = ix.grid(wl["values"], cells=cells)
+            got = map_d[torch.from_numpy(cells).to(dev)].cpu().numpy().astype(np.float64)
+            mask = Wref >= 1e-3 * Wref.max()
+            rms = np.sqrt(np.mean(ref[mask] ** 2, axis=0))
+            e = np.max(np.abs(got[mask] - ref[mask]), axis=0) / rms
+            err[nm] = {"max": float(e.max()), "median": float(np.median(e)),
+                       "cells": int(mask.sum())}
+    H.hegrid_plan_destroy(plan)
+
+    # ---- roofline of the dominant kernel (the grid step) ------------------
+    hbm, tc_peak, peak_kind = _peaks()
+    alg_bytes = N * C * 4 + M * C * 4 + M * 4
+    if mode == H.HEGRID_MODE_FP32:
+        clk_mhz = 2070.0
+        peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        achieved = 2.0 * P * C / t_grid / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived); "
+                        "achieved = 2 P C / grid-kernel time"}
+    else:
+        achieved = alg_bytes / t_grid / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "note": f"algorithmic bytes N*C*4 + M*C*4 + M*4 per grid launch; peak {peak_kind}"}
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
+        host_w = torch.empty(M, dtype=torch.float32, pin_memory=True)
+        lon_h, lat_h = np.ascontiguousarray(wl["lon"]), np.ascontiguousarray(wl["lat"])
+        n_chunks = 4
+        cc = C // n_chunks
+        chunks = [torch.empty((N, cc), dtype=torch.float32, pin_memory=True)
+                  for _ in range(n_chunks)]
+        for k in range(n_chunks):
+            chunks[k].copy_(host_vals[:, k * cc:(k + 1) * cc])
+
+        def e2e_step():
+            p = H.hegrid_plan_create(N, lon_h, lat_h, 0, g, wl["fwhm_deg"], 3.0, 0, sh)
+            H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, mode, host_map, C, host_w)
+            H.hegrid_plan_destroy(p)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - ts) / args.e2e_steps
+        e2e = {"value": world * N * C / te, "unit": UNIT,
+               "h2d_bytes_per_step": N * 16 + N * C * 4,
+               "d2h_bytes_per_step": M * C * 4 + M * 4, "ms_per_step": te * 1e3,
+               "path": "hegrid_plan_create(host coords) + hegrid_grid_stream(4 pinned channel "
+                       "chunks -> pinned host map)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl, frac_rows=20)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if mode_name == "fp32" else "bf16", "data": "synthetic",
+                "config": {"workload": "FAST-like 19-beam drift scan, 5x5 deg at (30,41), "
+                                       f"N={N}, C={C} FP32, 600x600 map at 0.5', FWHM 2.9', R=3 sigma",
+                           "mode": mode_name, "N": N, "C": C, "M": M, "pairs": P,
+                           "l2": "inputs larger than L2 (values 8 GB)",
+                           "parallelism": f"replicas x{world}"},
+                "plan_ms": t_plan * 1e3, "grid_ms": t_grid * 1e3,
+                "forms": forms, "err_vs_oracle": err, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "gen_s": t_gen}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

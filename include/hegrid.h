@@ -89,8 +89,8 @@ typedef struct {
  *
  * Errors: INVALID_ARG (N < 1, nx/ny < 1, cell size <= 0, FWHM <= 0, support
  * <= 0); UNSUPPORTED (a cell row within R of a pole, a padded map wider than
- * 360 deg, R > 11 deg, more than 65,535 candidate samples in one cell block);
- * OOM; CUDA.  On error *out is set to NULL.
+ * 360 deg, R > 11 deg, more than 2^31 candidate slots over all cell blocks); OOM; CUDA.
+ * On error *out is set to NULL.
  */
 hegrid_status hegrid_plan_create(hegrid_plan **out, int64_t n_samples, const double *lon_deg,
                                  const double *lat_deg, int coords_on_device,
@@ -184,6 +184,11 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
 
 /* Device-side error word of the plan (bounded waits that timed out). */
 hegrid_status hegrid_status_poll(const hegrid_plan *plan);
+
+/* Number of CUDA kernels this library has launched in this process (for
+ * profiling and launch accounting; counts launches recorded into graphs once,
+ * at capture). */
+int64_t hegrid_launch_count(void);
 
 /* Thread-local message describing the most recent failure ("" if none). */
 const char *hegrid_last_error(void);

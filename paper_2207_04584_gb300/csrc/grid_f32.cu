@@ -195,6 +195,7 @@ hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s) {
   int64_t grid = std::min<int64_t>(jt.n_items, (int64_t)sms * 2);
   if (grid < 1) return HEGRID_OK;
   k_grid_f32<<<(unsigned)grid, kThreads, sizeof(SmemF32), s>>>(jt);
+  count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   return HEGRID_OK;
 }

@@ -22,6 +22,9 @@ namespace hg {
 // Thread-local error message for hegrid_last_error().
 void set_error(const std::string& msg);
 
+// Process-wide count of kernel launches made by the library.
+void count_launch(int n = 1);
+
 #define HG_CUDA_TRY(expr)                                                           \
   do {                                                                              \
     cudaError_t _e = (expr);                                                        \

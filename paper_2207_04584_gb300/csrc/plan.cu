@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,6 +27,10 @@
 #include "hegrid_internal.cuh"
 
 namespace hg {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
@@ -220,12 +225,15 @@ void scan_in_place(TO* data, int64_t n, TO* tmp, cudaStream_t s) {
   int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles <= 1) {
     k_scan_tiles<TO, TO><<<1, kScanThreads, 0, s>>>(data, n, data, (TO*)nullptr);
+    count_launch();
     return;
   }
   TO* sums = tmp;
   k_scan_tiles<TO, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, data, sums);
+  count_launch();
   scan_in_place<TO>(sums, tiles, tmp + tiles + 1, s);
   k_scan_add<TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, sums);
+  count_launch();
 }
 
 template <typename TI, typename TO>
@@ -233,11 +241,14 @@ void scan_exclusive(const TI* in, int64_t n, TO* out, TO* tmp, cudaStream_t s) {
   int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles <= 1) {
     k_scan_tiles<TI, TO><<<1, kScanThreads, 0, s>>>(in, n, out, (TO*)nullptr);
+    count_launch();
   } else {
     TO* sums = tmp;
     k_scan_tiles<TI, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, out, sums);
+    count_launch();
     scan_in_place<TO>(sums, tiles, tmp + tiles + 1, s);
     k_scan_add<TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums);
+    count_launch();
   }
 }
 
@@ -617,6 +628,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   kp.nbx = p->nbx;
   kp.n_bins = (uint32_t)p->n_bins;
   k_prep<<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, key0, val0, ux, uy, uz);
+  count_launch();
   HG_CUDA_TRY(cudaGetLastError());
 
   // --- a3: radix sort ------------------------------------------------------
@@ -633,9 +645,11 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   int32_t *vin = val0, *vout = val1;
   for (int ps = 0; ps < passes; ++ps) {
     k_radix_hist<<<n_tiles, kSortThreads, 0, st>>>(kin, N, 8 * ps, n_tiles, hist);
+    count_launch();
     scan_exclusive<int32_t, int32_t>(hist, hist_n, hoff, stmp32, st);
     k_radix_scatter<<<n_tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, 8 * ps, n_tiles,
                                                        hoff);
+    count_launch();
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
@@ -645,7 +659,9 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(dmalloc(&p->bin_off, p->n_bins + 1, &bytes));
   HG_CUDA_TRY(cudaMemcpyAsync(p->perm, vin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
   k_bin_offsets<<<(N + 255) / 256, 256, 0, st>>>(kin, N, (uint32_t)p->n_bins, p->bin_off);
+  count_launch();
   k_gather_u<<<(N + 255) / 256, 256, 0, st>>>(p->perm, N, ux, uy, uz, sx, sy, sz);
+  count_launch();
   HG_CUDA_TRY(cudaGetLastError());
 
   // --- block windows (host) ------------------------------------------------
@@ -714,6 +730,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   k_block_pairs<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
       pp, dwin, p->bin_off, p->perm, sx, sy, sz, cnt, kb, nullptr, nullptr, nullptr, nullptr,
       nullptr, nullptr, nullptr);
+  count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   int64_t* stmp64;
   HG_CUDA_TRY(sc.get(&stmp64, scan_tmp_elems(std::max(p->M, p->n_blocks) + 1) + 8));
@@ -722,6 +739,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   // exclusive scans over n+1 entries (last input 0): out[n] is the total
   scan_exclusive<int32_t, int64_t>(cnt, p->M + 1, p->nb_off, stmp64, st);
   k_pad_counts<<<(unsigned)((p->n_blocks + 1 + 255) / 256), 256, 0, st>>>(kb, p->n_blocks + 1, kbp);
+  count_launch();
   scan_exclusive<int64_t, int64_t>(kbp, p->n_blocks + 1, p->cand_off, stmp64, st);
   HG_CUDA_TRY(cudaGetLastError());
 
@@ -752,6 +770,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
       pp, dwin, p->bin_off, p->perm, sx, sy, sz, nullptr, nullptr, p->nb_off, p->cand_off,
       p->nb_idx, p->nb_loc, p->nb_w, p->wsum, p->cand_idx);
+  count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   // scratch is freed by ~Scratch; make sure the kernels that use it are done
   HG_CUDA_TRY(cudaStreamSynchronize(st));
@@ -767,6 +786,8 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
 extern "C" {
 
 const char* hegrid_last_error(void) { return hg::last_error(); }
+
+int64_t hegrid_launch_count(void) { return hg::launch_count(); }
 
 hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const double* lon_deg,
                                  const double* lat_deg, int coords_on_device,

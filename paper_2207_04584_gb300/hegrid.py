@@ -29,7 +29,7 @@ HEGRID_MODE_FP32, HEGRID_MODE_TC, HEGRID_MODE_TC_SPLIT = 0, 1, 2
 EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_grid_batched",
             "hegrid_batch_create", "hegrid_batch_launch", "hegrid_batch_destroy",
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
-            "hegrid_last_error"]
+            "hegrid_launch_count", "hegrid_last_error"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -82,8 +82,9 @@ def lib():
     L.hegrid_plan_export.argtypes = [P, P, P, P, P, P, P]
     L.hegrid_status_poll.argtypes = [P]
     L.hegrid_last_error.restype = ctypes.c_char_p
+    L.hegrid_launch_count.restype = ctypes.c_int64
     for name in EXPORTED:
-        if name != "hegrid_last_error":
+        if name not in ("hegrid_last_error", "hegrid_launch_count"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -192,6 +193,10 @@ def hegrid_plan_export(plan, perm=None, bin_off=None, nb_off=None, nb_idx=None, 
     return _check(lib().hegrid_plan_export(plan, _ptr(perm), _ptr(bin_off), _ptr(nb_off),
                                            _ptr(nb_idx), _ptr(nb_w), _ptr(weight)),
                   "hegrid_plan_export")
+
+
+def hegrid_launch_count() -> int:
+    return int(lib().hegrid_launch_count())
 
 
 def hegrid_status_poll(plan):

@@ -125,12 +125,13 @@ def add_sources(values, lon, lat, src_lon, src_lat, src_fwhm_deg, spectra, cut_s
     """values[n, :] += profile_s(n) * spectra[s, :] for Gaussian sources.
 
     The source profile is a flat-sky Gaussian (RA offsets scaled by cos Dec);
-    it is truncated at ``cut_sigmas``.
+    it is truncated at ``cut_sigmas``.  Channel blocks are filled by threads.
     """
     sig = src_fwhm_deg / math.sqrt(8.0 * math.log(2.0))
     order = np.argsort(lat, kind="stable")
     lat_s = lat[order]
     rad = cut_sigmas * sig
+    foot = []
     for s in range(len(src_lon)):
         a = np.searchsorted(lat_s, src_lat[s] - rad)
         b = np.searchsorted(lat_s, src_lat[s] + rad, side="right")
@@ -143,9 +144,20 @@ def add_sources(values, lon, lat, src_lon, src_lat, src_fwhm_deg, spectra, cut_s
         keep = r2 <= rad * rad
         if not keep.any():
             continue
-        idx = idx[keep]
-        prof = np.exp(-0.5 * r2[keep] / (sig * sig)).astype(np.float32)
-        values[idx] += prof[:, None] * spectra[s][None, :]
+        foot.append((s, idx[keep], np.exp(-0.5 * r2[keep] / (sig * sig)).astype(np.float32)))
+    C = values.shape[1]
+    nblk = max(1, min(_threads(), C // 16))
+    edges = np.linspace(0, C, nblk + 1).astype(np.int64)
+
+    def work(i):
+        c0, c1 = int(edges[i]), int(edges[i + 1])
+        if c1 <= c0:
+            return
+        for s, idx, prof in foot:
+            values[idx, c0:c1] += prof[:, None] * spectra[s, c0:c1][None, :]
+
+    with _cf.ThreadPoolExecutor(nblk) as ex:
+        list(ex.map(work, range(nblk)))
 
 
 def one_over_f(rng, C, amplitude=1.0, mean=1.0):
