@@ -29,7 +29,7 @@ constexpr int kCT = 128;  // channels per tile
 struct __align__(128) SmemF32 {
   float V[2][kKC][kCT];   // staged sample rows
   float Wt[2][kKC][kCT];  // dense weight tile [k][cell column]
-  uint32_t pmask[2][8];   // per patch: bit k set if any cell of the patch has sample k
+  uint32_t pmask[2][kKC];  // per sample k: bit p set if any cell of patch p has it
   uint64_t bar[2];
 };
 
@@ -37,6 +37,14 @@ __device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
   int j = 0;
   while (j + 1 < jt.n_jobs && jt.job[j + 1].item_base <= item) ++j;
   return j;
+}
+
+// Block-local cell (lx, ly) -> tile column (inverse of col_to_cell).
+__device__ __forceinline__ int cell_to_col(int lx, int ly) {
+  int p = (ly >> 2) * 4 + (lx >> 2);
+  int py = ly & 3, px = lx & 3;
+  int cs = py >> 1, i = (py & 1) * 4 + px;
+  return p * 16 + cs * 8 + i;
 }
 
 // Tile column t (0..127) -> block-local cell (lx, ly): 8 patches of 4x4 cells,
@@ -77,18 +85,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kKC);
 
-    // this thread's cell as the owner of tile column `tid` (threads 0..127)
-    int64_t p_cur = 0, p_end = 0;
-    if (tid < HG_BLOCK_CELLS) {
-      int lx, ly;
-      col_to_cell(tid, lx, ly);
-      int ix = bbx * HG_BX + lx, iy = bby * HG_BY + ly;
-      if (ix < pv.nx && iy < pv.ny) {
-        int64_t m = (int64_t)iy * pv.nx + ix;
-        p_cur = pv.nb_off[m];
-        p_end = pv.nb_off[m + 1];
-      }
-    }
+    const int64_t sub0 = kb0 / kKC;  // first 32-candidate sub-chunk of the block
 
     auto issue = [&](int j) {
       int s = j & 1;
@@ -110,25 +107,22 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int j = 0; j < n_chunks; ++j) {
       const int s = j & 1;
       if (tid == 0 && j + 1 < n_chunks) issue(j + 1);
-      // weight tile for chunk j
-      if (tid < HG_BLOCK_CELLS) {
-#pragma unroll 8
-        for (int k = 0; k < kKC; ++k) S.Wt[s][k][tid] = 0.0f;
-        uint32_t km = 0;
-        const int32_t kend = (j + 1) * kKC;
-        while (p_cur < p_end) {
-          int32_t loc = pv.nb_loc[p_cur];
-          if (loc >= kend) break;
-          int k = loc - j * kKC;
-          S.Wt[s][k][tid] = pv.nb_w[p_cur];
-          km |= 1u << k;
-          ++p_cur;
+      // weight tile for chunk j: zero, then scatter the chunk's entries
+      {
+        float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][0]);
+        for (int i = tid; i < kKC * kCT / 4; i += kThreads) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tid < kKC) S.pmask[s][tid] = 0u;
+      }
+      __syncthreads();
+      {
+        const int64_t e0 = pv.sub_off[sub0 + j], e1 = pv.sub_off[sub0 + j + 1];
+        for (int64_t e = e0 + tid; e < e1; e += kThreads) {
+          const uint32_t ck = pv.ent_ck[e];
+          const int col = (int)(ck >> 6), k = (int)(ck & 31u);
+          const int tc = cell_to_col(col % HG_BX, col / HG_BX);
+          S.Wt[s][k][tc] = pv.ent_w[e];
+          atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
         }
-        // OR over the 16 columns of this patch (lanes 0-15 or 16-31)
-        uint32_t hm = __reduce_or_sync(0xffffffffu, (lane < 16) ? km : 0u);
-        uint32_t lm = __reduce_or_sync(0xffffffffu, (lane >= 16) ? km : 0u);
-        if (lane == 0) S.pmask[s][tid >> 4] = hm;
-        if (lane == 16) S.pmask[s][tid >> 4] = lm;
       }
       __syncthreads();
       const int timed_out = !mbar_wait(&S.bar[s], phase[s], pv.err_word);
@@ -139,11 +133,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         break;
       }
       phase[s] ^= 1u;
-      const uint32_t pm = S.pmask[s][patch];
+      const uint32_t* pm = S.pmask[s];
       const float* wrow = &S.Wt[s][0][patch * 16 + cs * 8];
       const float* vrow = &S.V[s][0][cg * 8];
       for (int k = 0; k < kKC; ++k) {
-        if (!((pm >> k) & 1u)) continue;
+        if (!((pm[k] >> patch) & 1u)) continue;
         float4 w0 = *reinterpret_cast<const float4*>(wrow + k * kCT);
         float4 w1 = *reinterpret_cast<const float4*>(wrow + k * kCT + 4);
         float4 v0 = *reinterpret_cast<const float4*>(vrow + k * kCT);

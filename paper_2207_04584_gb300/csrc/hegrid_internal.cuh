@@ -49,12 +49,12 @@ struct PlanView {
   int32_t nbx_b, nby_b;     // cell blocks along RA / Dec
   int64_t M;                // cells
   int64_t n_blocks;
-  const int64_t* nb_off;    // [M+1] pair offsets per cell
-  const int32_t* nb_loc;    // [P] local candidate index of each pair
-  const float* nb_w;        // [P] FP32 weight of each pair
   const float* wsum;        // [M] sum of FP32 weights per cell
-  const int64_t* cand_off;  // [n_blocks+1] candidate slots per block (padded)
+  const int64_t* cand_off;  // [n_blocks+1] candidate slots per block (padded to 64)
   const int32_t* cand_idx;  // [n_cand] original sample index per slot
+  const int64_t* sub_off;   // [n_cand/32+1] first entry of each 32-candidate sub-chunk
+  const uint16_t* ent_ck;   // [P] entry: (block-local cell << 6) | (candidate & 63)
+  const float* ent_w;       // [P] FP32 weight of the entry
   int32_t* err_word;        // device error word (bounded waits)
 };
 
@@ -70,13 +70,13 @@ struct hegrid_plan {
   // device arrays (owned)
   int32_t* perm;
   int32_t* bin_off;
-  int64_t* nb_off;
-  int32_t* nb_idx;
-  int32_t* nb_loc;
-  float* nb_w;
-  float* wsum;
   int64_t* cand_off;
+  int64_t* blk_pair_off;
   int32_t* cand_idx;
+  int64_t* sub_off;
+  uint16_t* ent_ck;
+  float* ent_w;
+  float* wsum;
   int32_t* err_word;
   int64_t bytes;
   hg::PlanView view() const {
@@ -87,12 +87,12 @@ struct hegrid_plan {
     v.nby_b = nby_b;
     v.M = M;
     v.n_blocks = n_blocks;
-    v.nb_off = nb_off;
-    v.nb_loc = nb_loc;
-    v.nb_w = nb_w;
     v.wsum = wsum;
     v.cand_off = cand_off;
     v.cand_idx = cand_idx;
+    v.sub_off = sub_off;
+    v.ent_ck = ent_ck;
+    v.ent_w = ent_w;
     v.err_word = err_word;
     return v;
   }

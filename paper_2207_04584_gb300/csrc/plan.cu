@@ -352,23 +352,33 @@ __device__ __forceinline__ float pair_weight(const float (&mh)[3], const float (
   return expf(-th) * (1.0f - tl);
 }
 
+// One CTA per 16x8 cell block; thread t owns block-local cell t (= ly*16 + lx).
+// The samples of the bins around the block are staged kChunk at a time.
+// COUNT pass: number of distinct candidates (K_b, the union of the cells'
+// neighbours) and number of pairs of the block.  FILL pass: the candidate list
+// (original sample indices, union order), the weight entries of the block in
+// candidate-major order (entry = 6-bit k within a 64-candidate chunk | 7-bit
+// cell, FP32 weight), the offsets of every 32-candidate sub-chunk, W[m].
 template <bool FILL>
 __global__ void __launch_bounds__(kChunk)
     k_block_pairs(PairParams pp, const int4* __restrict__ win, const int32_t* __restrict__ bin_off,
                   const int32_t* __restrict__ perm, const double* __restrict__ sx,
                   const double* __restrict__ sy, const double* __restrict__ sz,
-                  int32_t* __restrict__ cnt, int32_t* __restrict__ kb,
-                  const int64_t* __restrict__ nb_off, const int64_t* __restrict__ cand_off,
-                  int32_t* __restrict__ nb_idx, int32_t* __restrict__ nb_loc,
-                  float* __restrict__ nb_w, float* __restrict__ wsum,
-                  int32_t* __restrict__ cand_idx) {
+                  int32_t* __restrict__ kb, int32_t* __restrict__ kpairs,
+                  const int64_t* __restrict__ cand_off, const int64_t* __restrict__ blk_pair_off,
+                  int32_t* __restrict__ cand_idx, int64_t* __restrict__ sub_off,
+                  uint16_t* __restrict__ ent_ck, float* __restrict__ ent_w,
+                  float* __restrict__ wsum) {
   __shared__ float s_eh[3][kChunk];
   __shared__ float s_el[3][kChunk];
   __shared__ double s_u[3][kChunk];
   __shared__ int32_t s_n[kChunk];
   __shared__ uint32_t s_umask[kChunk / 32];
+  __shared__ int32_t s_cc[kChunk];   // cells containing staged candidate k
+  __shared__ int32_t s_cur[kChunk];  // write cursor per staged candidate
+  __shared__ int32_t s_wsum[kChunk / 32];
 
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
   const int bbx = b % pp.nbx_b, bby = b / pp.nbx_b;
   const int ix = bbx * HG_BX + (t % HG_BX), iy = bby * HG_BY + (t / HG_BX);
@@ -393,14 +403,15 @@ __global__ void __launch_bounds__(kChunk)
     }
   }
 
-  int32_t count = 0;
+  int32_t count = 0;   // pairs of this cell
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
-  int64_t pos = 0;
+  int64_t erun = 0;    // entries of the block so far
   float ws = 0.0f, wc = 0.0f;  // Neumaier-compensated sum of weights
-  int64_t cbase = 0;
+  int64_t cbase = 0, ebase = 0, sbase = 0;
   if (FILL) {
-    if (active) pos = nb_off[m];
     cbase = cand_off[b];
+    ebase = blk_pair_off[b];
+    sbase = cbase / 32;
   }
   const int4 wb = win[b];  // by0, by1, bx0, bx1
   for (int by = wb.x; by <= wb.y; ++by) {
@@ -422,6 +433,8 @@ __global__ void __launch_bounds__(kChunk)
         s_n[t] = perm[s];
       }
       if (t < kChunk / 32) s_umask[t] = 0u;
+      s_cc[t] = 0;
+      s_cur[t] = 0;
       __syncthreads();
 
       // Phase 1: membership of each staged candidate for this thread's cell.
@@ -450,7 +463,15 @@ __global__ void __launch_bounds__(kChunk)
 #pragma unroll
       for (int q = 0; q < kChunk / 32; ++q) {
         uint32_t wmask = __reduce_or_sync(0xffffffffu, mask[q]);
-        if ((t & 31) == 0 && wmask) atomicOr(&s_umask[q], wmask);
+        if (lane == 0 && wmask) atomicOr(&s_umask[q], wmask);
+        if (FILL) {
+          uint32_t mm = mask[q];
+          while (mm) {
+            int r = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            atomicAdd(&s_cc[32 * q + r], 1);
+          }
+        }
       }
       __syncthreads();
       uint32_t um4[kChunk / 32];
@@ -464,16 +485,37 @@ __global__ void __launch_bounds__(kChunk)
       for (int q = 0; q < kChunk / 32; ++q) count += __popc(mask[q]);
 
       if (FILL) {
-        // Candidate list of the block: the union, in staging order.
+        // exclusive prefix of the column counts over the staged candidates
+        const int cc = s_cc[t];
+        int incl = cc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        int wpre = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kChunk / 32; ++w) {
+          if (w < wid) wpre += s_wsum[w];
+          total += s_wsum[w];
+        }
+        const int pre_t = wpre + incl - cc;  // entries before candidate t
+        // candidate list and sub-chunk offsets (by the candidate's own thread)
         {
           int q = t >> 5, r = t & 31;
           if ((um4[q] >> r) & 1u) {
             int before = __popc(um4[q] & ((1u << r) - 1u));
             for (int j = 0; j < q; ++j) before += __popc(um4[j]);
-            cand_idx[cbase + kcount + before] = s_n[t];
+            const int64_t loc = kcount + before;
+            cand_idx[cbase + loc] = s_n[t];
+            if ((loc & 31) == 0) sub_off[sbase + loc / 32] = ebase + erun + pre_t;
           }
         }
-        // Pairs of this cell with their local index and weight.
+        // pre_t of every candidate, for the entry writes below
+        s_cc[t] = pre_t;
+        __syncthreads();
         int pre = 0;
 #pragma unroll
         for (int q = 0; q < kChunk / 32; ++q) {
@@ -482,35 +524,48 @@ __global__ void __launch_bounds__(kChunk)
             int r = __ffs(mm) - 1;
             mm &= mm - 1u;
             int k = q * 32 + r;
-            int loc = pre + __popc(um4[q] & ((1u << r) - 1u));
+            int loc = (int)((kcount + pre + __popc(um4[q] & ((1u << r) - 1u))) & 63);
             float nh[3] = {s_eh[0][k], s_eh[1][k], s_eh[2][k]};
             float nl[3] = {s_el[0][k], s_el[1][k], s_el[2][k]};
             float w = pair_weight(mh, ml, nh, nl, pp.k_hi, pp.k_lo);
-            nb_idx[pos] = s_n[k];
-            nb_loc[pos] = (int32_t)(kcount + loc);
-            nb_w[pos] = w;
-            ++pos;
+            int64_t e = ebase + erun + s_cc[k] + atomicAdd(&s_cur[k], 1);
+            ent_ck[e] = (uint16_t)((t << 6) | loc);
+            ent_w[e] = w;
             float tt = ws + w;
             wc += fabsf(ws) >= fabsf(w) ? (ws - tt) + w : (w - tt) + ws;
             ws = tt;
           }
           pre += __popc(um4[q]);
         }
+        erun += total;
       }
       kcount += ucount;
       __syncthreads();
     }
   }
   if (!FILL) {
-    if (active) cnt[m] = count;
-    if (t == 0) kb[b] = (int32_t)kcount;
+    // pairs of the block
+    int c = count;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) s_wsum[wid] = c;
+    __syncthreads();
+    if (t == 0) {
+      int tot = 0;
+      for (int w = 0; w < kChunk / 32; ++w) tot += s_wsum[w];
+      kpairs[b] = tot;
+      kb[b] = (int32_t)kcount;
+    }
   } else {
     if (active) wsum[m] = ws + wc;
     // Pad the candidate list to a multiple of HG_KPAD with a valid sample
-    // index (its weight is zero in every cell).
+    // index (its weight is zero in every cell); empty sub-chunks start at the
+    // block's end.
     int64_t padded = (kcount + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
     int32_t filler = kcount > 0 ? cand_idx[cbase] : 0;
     for (int64_t i = kcount + t; i < padded; i += kChunk) cand_idx[cbase + i] = filler;
+    for (int64_t j = (kcount + 31) / 32 + t; j < padded / 32; j += kChunk)
+      sub_off[sbase + j] = ebase + erun;
   }
 }
 
@@ -531,13 +586,13 @@ static cudaError_t dmalloc(T** p, int64_t n, int64_t* bytes) {
 void free_plan_arrays(hegrid_plan* p) {
   cudaFree(p->perm);
   cudaFree(p->bin_off);
-  cudaFree(p->nb_off);
-  cudaFree(p->nb_idx);
-  cudaFree(p->nb_loc);
-  cudaFree(p->nb_w);
-  cudaFree(p->wsum);
   cudaFree(p->cand_off);
+  cudaFree(p->blk_pair_off);
   cudaFree(p->cand_idx);
+  cudaFree(p->sub_off);
+  cudaFree(p->ent_ck);
+  cudaFree(p->ent_w);
+  cudaFree(p->wsum);
   cudaFree(p->err_word);
 }
 
@@ -720,33 +775,33 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     pp.k_hi = (float)k;
     pp.k_lo = (float)(k - (double)pp.k_hi);
   }
-  int32_t *cnt, *kb;
-  int64_t* kbp;
-  HG_CUDA_TRY(sc.get(&cnt, p->M + 1));
+  int32_t *kb, *kpairs;
+  int64_t *kbp, *kpp;
   HG_CUDA_TRY(sc.get(&kb, p->n_blocks + 1));
+  HG_CUDA_TRY(sc.get(&kpairs, p->n_blocks + 1));
   HG_CUDA_TRY(sc.get(&kbp, p->n_blocks + 1));
-  HG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (p->M + 1), st));
   HG_CUDA_TRY(cudaMemsetAsync(kb, 0, sizeof(int32_t) * (p->n_blocks + 1), st));
+  HG_CUDA_TRY(cudaMemsetAsync(kpairs, 0, sizeof(int32_t) * (p->n_blocks + 1), st));
   k_block_pairs<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-      pp, dwin, p->bin_off, p->perm, sx, sy, sz, cnt, kb, nullptr, nullptr, nullptr, nullptr,
+      pp, dwin, p->bin_off, p->perm, sx, sy, sz, kb, kpairs, nullptr, nullptr, nullptr, nullptr,
       nullptr, nullptr, nullptr);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   int64_t* stmp64;
-  HG_CUDA_TRY(sc.get(&stmp64, scan_tmp_elems(std::max(p->M, p->n_blocks) + 1) + 8));
-  HG_CUDA_TRY(dmalloc(&p->nb_off, p->M + 1, &bytes));
+  HG_CUDA_TRY(sc.get(&stmp64, scan_tmp_elems(p->n_blocks + 1) + 8));
   HG_CUDA_TRY(dmalloc(&p->cand_off, p->n_blocks + 1, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->blk_pair_off, p->n_blocks + 1, &bytes));
   // exclusive scans over n+1 entries (last input 0): out[n] is the total
-  scan_exclusive<int32_t, int64_t>(cnt, p->M + 1, p->nb_off, stmp64, st);
   k_pad_counts<<<(unsigned)((p->n_blocks + 1 + 255) / 256), 256, 0, st>>>(kb, p->n_blocks + 1, kbp);
   count_launch();
   scan_exclusive<int64_t, int64_t>(kbp, p->n_blocks + 1, p->cand_off, stmp64, st);
+  scan_exclusive<int32_t, int64_t>(kpairs, p->n_blocks + 1, p->blk_pair_off, stmp64, st);
   HG_CUDA_TRY(cudaGetLastError());
 
   // The one host round trip of plan creation: the number of pairs and of
   // candidate slots size the remaining arrays.
   int64_t totals[2];
-  HG_CUDA_TRY(cudaMemcpyAsync(&totals[0], p->nb_off + p->M, sizeof(int64_t),
+  HG_CUDA_TRY(cudaMemcpyAsync(&totals[0], p->blk_pair_off + p->n_blocks, sizeof(int64_t),
                               cudaMemcpyDeviceToHost, st));
   HG_CUDA_TRY(cudaMemcpyAsync(&totals[1], p->cand_off + p->n_blocks, sizeof(int64_t),
                               cudaMemcpyDeviceToHost, st));
@@ -759,17 +814,20 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   }
 
   // --- a4 fill + a5 weights ------------------------------------------------
-  HG_CUDA_TRY(dmalloc(&p->nb_idx, p->P, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->nb_loc, p->P, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->nb_w, p->P, &bytes));
+  const int64_t n_sub = p->n_cand / 32;
+  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->sub_off, n_sub + 1, &bytes));
   HG_CUDA_TRY(dmalloc(&p->wsum, p->M, &bytes));
   HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes));
   HG_CUDA_TRY(dmalloc(&p->err_word, 4, &bytes));
   HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * p->M, st));
+  HG_CUDA_TRY(cudaMemcpyAsync(p->sub_off + n_sub, p->blk_pair_off + p->n_blocks, sizeof(int64_t),
+                              cudaMemcpyDeviceToDevice, st));
   k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-      pp, dwin, p->bin_off, p->perm, sx, sy, sz, nullptr, nullptr, p->nb_off, p->cand_off,
-      p->nb_idx, p->nb_loc, p->nb_w, p->wsum, p->cand_idx);
+      pp, dwin, p->bin_off, p->perm, sx, sy, sz, nullptr, nullptr, p->cand_off, p->blk_pair_off,
+      p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   // scratch is freed by ~Scratch; make sure the kernels that use it are done
@@ -864,29 +922,49 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
   if (weight)
     HG_CUDA_TRY(cudaMemcpy(weight, plan->wsum, sizeof(float) * plan->M, cudaMemcpyDeviceToHost));
   if (nb_off || nb_idx || nb_w) {
-    std::vector<int64_t> off(plan->M + 1);
-    HG_CUDA_TRY(cudaMemcpy(off.data(), plan->nb_off, sizeof(int64_t) * (plan->M + 1),
+    // Rebuild the cell-major CSR from the block-local, candidate-major entries.
+    const int64_t nb = plan->n_blocks, nc = plan->n_cand, ns = nc / 32, P = plan->P, M = plan->M;
+    std::vector<int64_t> coff(nb + 1), soff(ns + 1);
+    std::vector<int32_t> cidx(std::max<int64_t>(nc, 1));
+    std::vector<uint16_t> ck(std::max<int64_t>(P, 1));
+    std::vector<float> w(std::max<int64_t>(P, 1));
+    HG_CUDA_TRY(cudaMemcpy(coff.data(), plan->cand_off, sizeof(int64_t) * (nb + 1),
                            cudaMemcpyDeviceToHost));
-    if (nb_off) std::memcpy(nb_off, off.data(), sizeof(int64_t) * (plan->M + 1));
-    if (nb_idx || nb_w) {
-      std::vector<int32_t> idx(plan->P);
-      std::vector<float> w(plan->P);
-      HG_CUDA_TRY(cudaMemcpy(idx.data(), plan->nb_idx, sizeof(int32_t) * plan->P,
-                             cudaMemcpyDeviceToHost));
-      HG_CUDA_TRY(
-          cudaMemcpy(w.data(), plan->nb_w, sizeof(float) * plan->P, cudaMemcpyDeviceToHost));
-      // canonical order: ascending sample index inside each cell
-      std::vector<int64_t> ord;
-      for (int64_t m = 0; m < plan->M; ++m) {
-        int64_t a = off[m], b = off[m + 1];
-        ord.resize(b - a);
-        for (int64_t i = 0; i < b - a; ++i) ord[i] = a + i;
-        std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return idx[x] < idx[y]; });
-        for (int64_t i = 0; i < b - a; ++i) {
-          if (nb_idx) nb_idx[a + i] = idx[ord[i]];
-          if (nb_w) nb_w[a + i] = w[ord[i]];
+    HG_CUDA_TRY(cudaMemcpy(soff.data(), plan->sub_off, sizeof(int64_t) * (ns + 1),
+                           cudaMemcpyDeviceToHost));
+    if (nc) HG_CUDA_TRY(cudaMemcpy(cidx.data(), plan->cand_idx, sizeof(int32_t) * nc,
+                                   cudaMemcpyDeviceToHost));
+    if (P) {
+      HG_CUDA_TRY(cudaMemcpy(ck.data(), plan->ent_ck, sizeof(uint16_t) * P, cudaMemcpyDeviceToHost));
+      HG_CUDA_TRY(cudaMemcpy(w.data(), plan->ent_w, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    }
+    const int nx = plan->geom.nx, nbx_b = plan->nbx_b;
+    auto cell_of = [&](int64_t b, int col) -> int64_t {
+      int64_t bbx = b % nbx_b, bby = b / nbx_b;
+      return (bby * HG_BY + col / HG_BX) * (int64_t)nx + bbx * HG_BX + (col % HG_BX);
+    };
+    std::vector<int64_t> off(M + 1, 0);
+    for (int64_t b = 0; b < nb; ++b)
+      for (int64_t e = soff[coff[b] / 32]; e < soff[coff[b + 1] / 32]; ++e)
+        off[cell_of(b, ck[e] >> 6) + 1]++;
+    for (int64_t m = 0; m < M; ++m) off[m + 1] += off[m];
+    std::vector<int64_t> cur(off.begin(), off.end() - 1);
+    std::vector<std::pair<int32_t, float>> pr(std::max<int64_t>(P, 1));
+    for (int64_t b = 0; b < nb; ++b) {
+      for (int64_t j = coff[b] / 32; j < coff[b + 1] / 32; ++j) {
+        const int64_t loc0 = 32 * j - coff[b];
+        for (int64_t e = soff[j]; e < soff[j + 1]; ++e) {
+          const int64_t m = cell_of(b, ck[e] >> 6);
+          const int64_t loc = loc0 + (ck[e] & 31);
+          pr[cur[m]++] = {cidx[coff[b] + loc], w[e]};
         }
       }
+    }
+    for (int64_t m = 0; m < M; ++m) std::sort(pr.begin() + off[m], pr.begin() + off[m + 1]);
+    if (nb_off) std::memcpy(nb_off, off.data(), sizeof(int64_t) * (M + 1));
+    for (int64_t i = 0; i < P; ++i) {
+      if (nb_idx) nb_idx[i] = pr[i].first;
+      if (nb_w) nb_w[i] = pr[i].second;
     }
   }
   return HEGRID_OK;
