@@ -1,0 +1,205 @@
+"""GPU parity of the tcgen05 tensor-core path against the FP64 oracle.
+
+Tolerances (error metric of the FP32 tests): split form 5e-5; the single
+BF16 form is reported and only bounded loosely.  For BF16/FP16-stored values
+the oracle runs on the stored values upcast exactly, so the error measures the
+computation only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import map_error
+from paper_2207_04584_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 5e-5
+TOL_SINGLE = 3e-2
+ARCMIN = 1.0 / 60.0
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_04584_gb300 import build
+    build.build()
+    from paper_2207_04584_gb300 import hegrid
+    hegrid.lib()
+    return hegrid
+
+
+def _plan(H, wl):
+    return H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
+                                np.ascontiguousarray(wl["lat"]), 0, wl["geom"], wl["fwhm_deg"],
+                                wl.get("support", 3.0), 0, torch.cuda.current_stream().cuda_stream)
+
+
+def _run(H, plan, vdev, dtype, C, ld, M, mode):
+    out = torch.full((M, C), -7.0, device="cuda")
+    wout = torch.full((M,), -7.0, device="cuda")
+    H.hegrid_grid(plan, vdev, dtype, C, ld, out, C, wout, mode,
+                  torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    H.hegrid_status_poll(plan)
+    return out.cpu().numpy(), wout.cpu().numpy()
+
+
+def _case(seed, n=6000, nx=40, ny=24, C=5, lon0=45.0, lat0=20.0, cell=ARCMIN, fwhm=3 * ARCMIN):
+    rng = np.random.default_rng(seed)
+    lon = lon0 + rng.uniform(-0.65 * nx * cell, 0.65 * nx * cell, n)
+    lat = lat0 + rng.uniform(-0.65 * ny * cell, 0.65 * ny * cell, n)
+    values = (rng.normal(1.0, 2.0, (n, C))).astype(np.float32)
+    return {"lon": lon % 360.0, "lat": lat, "values": values, "fwhm_deg": fwhm, "support": 3.0,
+            "geom": {"nx": nx, "ny": ny, "lon0": lon0, "lat0": lat0, "dlon": cell, "dlat": cell}}
+
+
+def _padded(values, mult):
+    n, C = values.shape
+    ld = (C + mult - 1) // mult * mult
+    v = np.zeros((n, ld), values.dtype)
+    v[:, :C] = values
+    return v, ld
+
+
+@pytest.mark.parametrize("mode,tol", [("split", TOL_SPLIT), ("single", TOL_SINGLE)])
+def test_tc_f32_config1(H, mode, tol):
+    wl = W.config1()
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    md = H.HEGRID_MODE_TC_SPLIT if mode == "split" else H.HEGRID_MODE_TC
+    plan = _plan(H, wl)
+    try:
+        got, gw = _run(H, plan, torch.from_numpy(wl["values"]).cuda(), H.HEGRID_F32, 4, 4, M, md)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, med, _ = map_error(got, ref, Wref)
+    print(f"tc {mode} config1: max err {err:.3e} median {med:.3e}")
+    assert err <= tol, err
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    has = Wref > 0
+    wtol = 2e-5 if mode == "split" else 1e-2
+    assert np.max(np.abs(gw[has] / Wref[has] - 1.0)) <= wtol
+
+
+@pytest.mark.parametrize("C", [1, 5, 256, 300])
+def test_tc_split_ragged_channels(H, C):
+    wl = _case(51, C=C)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    v, ld = _padded(wl["values"], 4)
+    plan = _plan(H, wl)
+    try:
+        got, _ = _run(H, plan, torch.from_numpy(v).cuda(), H.HEGRID_F32, C, ld, M,
+                      H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(got, ref, Wref)
+    assert err <= TOL_SPLIT, err
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+
+
+@pytest.mark.parametrize("kind", ["bf16", "f16", "bf16x2"])
+def test_tc_stored_dtypes(H, kind):
+    wl = _case(61, C=24)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    vt = torch.from_numpy(wl["values"])
+    if kind == "bf16":
+        dv = vt.to(torch.bfloat16)
+        ref_vals = dv.float().numpy()
+        dt = H.HEGRID_BF16
+    elif kind == "f16":
+        dv = vt.to(torch.float16)
+        ref_vals = dv.float().numpy()
+        dt = H.HEGRID_F16
+    else:
+        hi = vt.to(torch.bfloat16)
+        lo = (vt - hi.float()).to(torch.bfloat16)
+        dv = torch.stack([hi, lo], dim=-1).contiguous().view(torch.int32)
+        ref_vals = wl["values"]
+        dt = H.HEGRID_BF16X2
+    plan = _plan(H, wl)
+    try:
+        got, _ = _run(H, plan, dv.contiguous().cuda(), dt, 24, 24, M, H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(
+        np.ascontiguousarray(ref_vals))
+    err, _, _ = map_error(got, ref, Wref)
+    print(f"tc split {kind}: max err {err:.3e}")
+    assert err <= TOL_SPLIT, err
+
+
+def test_tc_constant_sky(H):
+    wl = W.config1(with_values=False)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    v = np.full((len(wl["lon"]), 8), 3.7, np.float32)
+    plan = _plan(H, wl)
+    try:
+        got, gw = _run(H, plan, torch.from_numpy(v).cuda(), H.HEGRID_F32, 8, 8, M,
+                       H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    has = gw > 0
+    assert np.max(np.abs(got[has] / np.float32(3.7) - 1.0)) <= 2e-5
+    assert np.all(np.isnan(got[~has]))
+
+
+def test_tc_matches_fp32_path(H):
+    """The two GPU forms agree with each other as well as with the oracle."""
+    wl = _case(71, n=8000, nx=48, ny=40, C=64)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    plan = _plan(H, wl)
+    try:
+        vd = torch.from_numpy(wl["values"]).cuda()
+        a, wa = _run(H, plan, vd, H.HEGRID_F32, 64, 64, M, H.HEGRID_MODE_FP32)
+        b, wb = _run(H, plan, vd, H.HEGRID_F32, 64, 64, M, H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    err, _, _ = map_error(b, a.astype(np.float64), wa)
+    assert err <= TOL_SPLIT
+
+
+def test_tc_config3_precision_table(H):
+    """Config 3: 16,384 channels on the config-1 geometry, per-dtype error."""
+    wl = W.config3()
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    C = wl["values"].shape[1]
+    vt = torch.from_numpy(wl["values"])
+    plan = _plan(H, wl)
+    ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
+    rng = np.random.default_rng(3)
+    cells = np.sort(rng.choice(M, 600, replace=False))
+    res = {}
+    try:
+        for kind, dv, dt, md, refv in [
+            ("bf16", vt.to(torch.bfloat16), H.HEGRID_BF16, H.HEGRID_MODE_TC_SPLIT, None),
+            ("bf16-single", vt.to(torch.bfloat16), H.HEGRID_BF16, H.HEGRID_MODE_TC, None),
+            ("f16", vt.to(torch.float16), H.HEGRID_F16, H.HEGRID_MODE_TC_SPLIT, None),
+            ("f32-split", vt, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT, wl["values"]),
+        ]:
+            out = torch.empty((M, C), device="cuda")
+            H.hegrid_grid(plan, dv.contiguous().cuda(), dt, C, C, out, C, None, md,
+                          torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            got = out[torch.from_numpy(cells).cuda()].cpu().numpy()
+            if refv is None:
+                refv = dv.float().numpy()
+            ref, Wref = ix.grid(np.ascontiguousarray(refv), cells=cells)
+            err, med, _ = map_error(got, ref, Wref)
+            res[kind] = (err, med)
+            del out
+    finally:
+        H.hegrid_plan_destroy(plan)
+    print("config3 per-dtype error (max, median):", res)
+    assert res["bf16"][0] <= TOL_SPLIT
+    assert res["f16"][0] <= TOL_SPLIT
+    assert res["f32-split"][0] <= TOL_SPLIT
