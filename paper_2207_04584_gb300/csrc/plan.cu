@@ -776,7 +776,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     pp.k_lo = (float)(k - (double)pp.k_hi);
   }
   int32_t *kb, *kpairs;
-  int64_t *kbp, *kpp;
+  int64_t* kbp;
   HG_CUDA_TRY(sc.get(&kb, p->n_blocks + 1));
   HG_CUDA_TRY(sc.get(&kpairs, p->n_blocks + 1));
   HG_CUDA_TRY(sc.get(&kbp, p->n_blocks + 1));
