@@ -10,8 +10,10 @@
 // Precision: values and weights are split into a high and a low 16-bit part
 // (BF16, or FP16 for F16 input); HEGRID_MODE_TC_SPLIT issues hi*hi + hi*lo +
 // lo*hi (the lo*lo term is below FP32 rounding), HEGRID_MODE_TC issues hi*hi.
-// W is accumulated by the same MMAs against a tile of ones, so the map is
-// normalised by the sum of exactly the quantised weights that produced S.
+// The main term and the two correction terms accumulate in separate TMEM
+// regions (a small term added into a large FP32 accumulator loses its low
+// bits), summed once in the epilogue.  W is the plan's compensated sum of
+// exactly the quantised weights (hi, or hi + lo) that produced S.
 //
 // CTA: 8 producer warps (values -> B tiles, entries -> A tiles, 2-stage
 // ring), warps 0-3 also run the epilogue (TMEM -> registers -> S / W ->
@@ -37,13 +39,12 @@ constexpr int kThreads = kProducers + 32;  // + the MMA warp
 constexpr int kK = 64;                     // candidates per chunk (one 128-byte row of BF16)
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
-constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
-constexpr uint32_t kWCol = 256;
+constexpr uint32_t kTmemCols = 512;        // main sums in [0,256), corrections in [256,512)
+constexpr uint32_t kCorrCol = 256;
 
 struct __align__(1024) TcSmem {
   uint8_t A[2][2][kM * 128];   // [stage][hi, lo]: weight tiles, K-major, 128B swizzle
   uint8_t B[2][2][kN * 128];   // [stage][hi, lo]: value tiles, K-major, 128B swizzle
-  uint8_t ones[2][16 * 128];   // [bf16, f16] all-ones B operand for W
   uint64_t full[2], empty[2], done, tfree;
   uint32_t tmem_base;
 };
@@ -101,12 +102,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     mbar_init(&S.tfree, 4);
     fence_mbar_init();
   }
-  // ones tiles (bf16 1.0 = 0x3f80, f16 1.0 = 0x3c00)
-  for (int i = tid; i < 16 * 128 / 4; i += kThreads) {
-    reinterpret_cast<uint32_t*>(S.ones[0])[i] = 0x3f803f80u;
-    reinterpret_cast<uint32_t*>(S.ones[1])[i] = 0x3c003c00u;
-  }
-  fence_proxy_async_smem();
   if (warp == kProducerWarps) {
     tmem_alloc(&S.tmem_base, kTmemCols);
     tmem_relinquish();
@@ -140,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         tc_fence_after();
         const uint32_t fmt = f16 ? 0u : 1u;
-        const uint32_t idS = idesc_f16(fmt, kM, kN), idW = idesc_f16(fmt, kM, 16);
+        const uint32_t idS = idesc_f16(fmt, kM, kN);
         for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
           const int s = g & 1;
           if (!mbar_wait(&S.full[s], (g >> 1) & 1u, err)) {
@@ -151,21 +146,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           if (lane == 0) {
             const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
             const uint32_t b_hi = smem_u32(S.B[s][0]), b_lo = smem_u32(S.B[s][1]);
-            const uint32_t on = smem_u32(S.ones[f16 ? 1 : 0]);
 #pragma unroll
             for (int kk = 0; kk < kK / 16; ++kk) {
               const uint32_t o = kk * 32;
-              const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-              tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_hi + o), idS, acc);
+              const uint32_t first = (j == 0 && kk == 0) ? 1u : 0u;
+              // main term and the two correction terms in separate accumulators
+              tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_hi + o), idS,
+                         1u - first);
               if (vsplit)
-                tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_lo + o), idS, 1u);
+                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw128(a_hi + o),
+                           smem_desc_k_sw128(b_lo + o), idS, 1u - first);
               if (split)
-                tc_mma_f16(tmem, smem_desc_k_sw128(a_lo + o), smem_desc_k_sw128(b_hi + o), idS, 1u);
-              tc_mma_f16(tmem + kWCol, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(on + o), idW,
-                         acc);
-              if (split)
-                tc_mma_f16(tmem + kWCol, smem_desc_k_sw128(a_lo + o), smem_desc_k_sw128(on + o),
-                           idW, 1u);
+                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw128(a_lo + o),
+                           smem_desc_k_sw128(b_hi + o), idS, vsplit ? 1u : 1u - first);
             }
             tc_commit(&S.empty[s]);
             if (j == n_chunks - 1) tc_commit(&S.done);
@@ -298,32 +291,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       ++n_tm;
       tc_fence_after();
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-      uint32_t r[32];
-      tmem_ld_32x32b_x32(tl + kWCol, r);
-      tmem_ld_wait();
-      const float W = __uint_as_float(r[0]);
-      const float inv_ok = W > 0.0f ? 1.0f : 0.0f;
+      const int wvar = f16 ? (split ? 4 : 3) : (split ? 2 : 1);
+      const float W = active ? pv.wsum[(int64_t)wvar * pv.M + m] : 0.0f;
+      const bool ok = W > 0.0f;
+      uint32_t r[32], rc[32];
 #pragma unroll 1
       for (int cb = 0; cb < kN / 32; ++cb) {
         tmem_ld_32x32b_x32(tl + cb * 32, r);
+        if (split) tmem_ld_32x32b_x32(tl + kCorrCol + cb * 32, rc);
         tmem_ld_wait();
         if (active) {
           const int64_t cbase = c0 + cb * 32;
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float sum = split ? __fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i]))
+                                    : __uint_as_float(r[i]);
+            v[i] = ok ? __fdiv_rn(sum, W) : qnan;
+          }
           if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              float4 o;
-              o.x = inv_ok != 0.0f ? __fdiv_rn(__uint_as_float(r[i + 0]), W) : qnan;
-              o.y = inv_ok != 0.0f ? __fdiv_rn(__uint_as_float(r[i + 1]), W) : qnan;
-              o.z = inv_ok != 0.0f ? __fdiv_rn(__uint_as_float(r[i + 2]), W) : qnan;
-              o.w = inv_ok != 0.0f ? __fdiv_rn(__uint_as_float(r[i + 3]), W) : qnan;
-              *reinterpret_cast<float4*>(out + cbase + i) = o;
-            }
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(out + cbase + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (cbase + i < C)
-                out[cbase + i] = inv_ok != 0.0f ? __fdiv_rn(__uint_as_float(r[i]), W) : qnan;
+              if (cbase + i < C) out[cbase + i] = v[i];
           }
         }
       }

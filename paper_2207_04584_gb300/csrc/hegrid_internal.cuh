@@ -19,6 +19,10 @@
 
 namespace hg {
 
+// W per cell is kept for each weight representation: 0 FP32, 1 BF16 hi,
+// 2 BF16 hi+lo, 3 FP16 hi, 4 FP16 hi+lo (wsum[v * M + m]).
+constexpr int kWsumVariants = 5;
+
 // Thread-local error message for hegrid_last_error().
 void set_error(const std::string& msg);
 
@@ -49,7 +53,7 @@ struct PlanView {
   int32_t nbx_b, nby_b;     // cell blocks along RA / Dec
   int64_t M;                // cells
   int64_t n_blocks;
-  const float* wsum;        // [M] sum of FP32 weights per cell
+  const float* wsum;        // [kWsumVariants * M] W per cell and weight representation
   const int64_t* cand_off;  // [n_blocks+1] candidate slots per block (padded to 64)
   const int32_t* cand_idx;  // [n_cand] original sample index per slot
   const int64_t* sub_off;   // [n_cand/32+1] first entry of each 32-candidate sub-chunk

@@ -14,6 +14,8 @@
 // its 128 cells.  The membership test runs in FP32 in a block-local frame with
 // a proven error band; pairs inside the band are decided in FP64.  Weights are
 // computed in float-float arithmetic from the same frame.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -281,6 +283,7 @@ __global__ void k_gather_u(const int32_t* __restrict__ perm, int32_t N,
 // ---------------------------------------------------------------------------
 struct PairParams {
   int32_t nx, ny, nbx_b, nbx;  // map, cell blocks along RA, bins along RA
+  int64_t M;
   double lon0, lat0, dlon, dlat;
   double cR2;       // chord^2 at R: 4 sin^2(R/2), FP64
   float lo_thr;     // FP32 c^2 below this: inside for sure
@@ -359,6 +362,17 @@ __device__ __forceinline__ float pair_weight(const float (&mh)[3], const float (
 // (original sample indices, union order), the weight entries of the block in
 // candidate-major order (entry = 6-bit k within a 64-candidate chunk | 7-bit
 // cell, FP32 weight), the offsets of every 32-candidate sub-chunk, W[m].
+// Neumaier-compensated running sum.
+struct CSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s + c; }
+};
+
 template <bool FILL>
 __global__ void __launch_bounds__(kChunk)
     k_block_pairs(PairParams pp, const int4* __restrict__ win, const int32_t* __restrict__ bin_off,
@@ -406,7 +420,10 @@ __global__ void __launch_bounds__(kChunk)
   int32_t count = 0;   // pairs of this cell
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
   int64_t erun = 0;    // entries of the block so far
-  float ws = 0.0f, wc = 0.0f;  // Neumaier-compensated sum of weights
+  // W of the cell for each weight representation the grid kernels use:
+  // FP32, BF16 hi, BF16 hi+lo, FP16 hi, FP16 hi+lo (so that every form
+  // normalises by the sum of exactly the weights it multiplied).
+  CSum wsv[kWsumVariants];
   int64_t cbase = 0, ebase = 0, sbase = 0;
   if (FILL) {
     cbase = cand_off[b];
@@ -531,9 +548,17 @@ __global__ void __launch_bounds__(kChunk)
             int64_t e = ebase + erun + s_cc[k] + atomicAdd(&s_cur[k], 1);
             ent_ck[e] = (uint16_t)((t << 6) | loc);
             ent_w[e] = w;
-            float tt = ws + w;
-            wc += fabsf(ws) >= fabsf(w) ? (ws - tt) + w : (w - tt) + ws;
-            ws = tt;
+            {
+              const float bh = __bfloat162float(__float2bfloat16_rn(w));
+              const float bl = __bfloat162float(__float2bfloat16_rn(w - bh));
+              const float hh = __half2float(__float2half_rn(w));
+              const float hl = __half2float(__float2half_rn(w - hh));
+              wsv[0].add(w);
+              wsv[1].add(bh);
+              wsv[2].add(bh + bl);
+              wsv[3].add(hh);
+              wsv[4].add(hh + hl);
+            }
           }
           pre += __popc(um4[q]);
         }
@@ -557,7 +582,9 @@ __global__ void __launch_bounds__(kChunk)
       kb[b] = (int32_t)kcount;
     }
   } else {
-    if (active) wsum[m] = ws + wc;
+    if (active)
+#pragma unroll
+      for (int v = 0; v < kWsumVariants; ++v) wsum[(int64_t)v * pp.M + m] = wsv[v].value();
     // Pad the candidate list to a multiple of HG_KPAD with a valid sample
     // index (its weight is zero in every cell); empty sub-chunks start at the
     // block's end.
@@ -750,6 +777,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   PairParams pp;
   pp.nx = g.nx;
   pp.ny = g.ny;
+  pp.M = p->M;
   pp.nbx_b = p->nbx_b;
   pp.nbx = p->nbx;
   pp.lon0 = g.lon0_deg;
@@ -818,11 +846,11 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P, &bytes));
   HG_CUDA_TRY(dmalloc(&p->ent_w, p->P, &bytes));
   HG_CUDA_TRY(dmalloc(&p->sub_off, n_sub + 1, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->wsum, p->M, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->wsum, kWsumVariants * p->M, &bytes));
   HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes));
   HG_CUDA_TRY(dmalloc(&p->err_word, 4, &bytes));
   HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
-  HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * p->M, st));
+  HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * kWsumVariants * p->M, st));
   HG_CUDA_TRY(cudaMemcpyAsync(p->sub_off + n_sub, p->blk_pair_off + p->n_blocks, sizeof(int64_t),
                               cudaMemcpyDeviceToDevice, st));
   k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
