@@ -7,13 +7,17 @@
 // candidate-major entries) and B = the sample values of the chunk (K-major, so
 // each channel row holds 64 samples).  FP32 accumulation lives in TMEM.
 //
-// Precision: values and weights are split into a high and a low 16-bit part
-// (BF16, or FP16 for F16 input); HEGRID_MODE_TC_SPLIT issues hi*hi + hi*lo +
-// lo*hi (the lo*lo term is below FP32 rounding), HEGRID_MODE_TC issues hi*hi.
-// The main term and the two correction terms accumulate in separate TMEM
-// regions (a small term added into a large FP32 accumulator loses its low
-// bits), summed once in the epilogue.  W is the plan's compensated sum of
-// exactly the quantised weights (hi, or hi + lo) that produced S.
+// Precision: values and weights are split into a high and a low 16-bit part;
+// HEGRID_MODE_TC_SPLIT issues hi*hi + hi*lo + lo*hi (the lo*lo term is below
+// FP32 rounding), HEGRID_MODE_TC issues hi*hi.  The 16-bit format is chosen
+// per 64-sample chunk: FP16 (11-bit halves, ~2^-22 residual) when every value
+// of the chunk lies in [2^-7, 2^15] in magnitude (zeros allowed) -- or, for
+// BF16 input, when FP16 holds every value exactly -- and BF16 (8-bit halves,
+// ~2^-17 residual, full FP32 range) otherwise.  Chunks of one block may mix
+// formats: each MMA carries its own instruction descriptor and all of them
+// accumulate in FP32.  W is accumulated by the same MMAs against a tile of
+// ones, so the map is normalised by the sum of exactly the quantised weights
+// that produced S.
 //
 // CTA: 8 producer warps (values -> B tiles, entries -> A tiles, 2-stage
 // ring), warps 0-3 also run the epilogue (TMEM -> registers -> S / W ->
@@ -39,12 +43,15 @@ constexpr int kThreads = kProducers + 32;  // + the MMA warp
 constexpr int kK = 64;                     // candidates per chunk (one 128-byte row of BF16)
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
-constexpr uint32_t kTmemCols = 512;        // main sums in [0,256), corrections in [256,512)
-constexpr uint32_t kCorrCol = 256;
+constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
+constexpr uint32_t kWCol = 256;
 
 struct __align__(1024) TcSmem {
   uint8_t A[2][2][kM * 128];   // [stage][hi, lo]: weight tiles, K-major, 128B swizzle
   uint8_t B[2][2][kN * 128];   // [stage][hi, lo]: value tiles, K-major, 128B swizzle
+  uint8_t ones[2][16 * 128];   // [bf16, f16] all-ones B operand for W
+  uint32_t red[2][kProducerWarps][3];  // per stage and warp: max|v|, min|v|>0, non-finite
+  uint32_t fmt16[2];                   // per stage: 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t full[2], empty[2], done, tfree;
   uint32_t tmem_base;
 };
@@ -75,6 +82,18 @@ __device__ __forceinline__ void split_f16(float x, uint16_t& hi, uint16_t& lo) {
   lo = __half_as_ushort(l);
 }
 
+// The value a raw element encodes (dtype of the input).
+__device__ __forceinline__ float value_of(uint32_t x, int32_t dtype) {
+  switch (dtype) {
+    case HEGRID_F32: return __uint_as_float(x);
+    case HEGRID_BF16X2:
+      return __bfloat162float(__ushort_as_bfloat16((uint16_t)(x & 0xffffu))) +
+             __bfloat162float(__ushort_as_bfloat16((uint16_t)(x >> 16)));
+    case HEGRID_BF16: return __bfloat162float(__ushort_as_bfloat16((uint16_t)x));
+    default: return __half2float(__ushort_as_half((uint16_t)x));
+  }
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
                                              uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
@@ -102,6 +121,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     mbar_init(&S.tfree, 4);
     fence_mbar_init();
   }
+  // ones tiles (bf16 1.0 = 0x3f80, f16 1.0 = 0x3c00)
+  for (int i = tid; i < 16 * 128 / 4; i += kThreads) {
+    reinterpret_cast<uint32_t*>(S.ones[0])[i] = 0x3f803f80u;
+    reinterpret_cast<uint32_t*>(S.ones[1])[i] = 0x3c003c00u;
+  }
+  fence_proxy_async_smem();
   if (warp == kProducerWarps) {
     tmem_alloc(&S.tmem_base, kTmemCols);
     tmem_relinquish();
@@ -124,7 +149,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kK);
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
-    const bool f16 = J.dtype == HEGRID_F16;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
 
     if (warp == kProducerWarps) {
@@ -134,8 +158,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           bail = true;
         }
         tc_fence_after();
-        const uint32_t fmt = f16 ? 0u : 1u;
-        const uint32_t idS = idesc_f16(fmt, kM, kN);
+        const uint32_t idS16 = idesc_f16(0u, kM, kN), idW16 = idesc_f16(0u, kM, 16);
+        const uint32_t idSbf = idesc_f16(1u, kM, kN), idWbf = idesc_f16(1u, kM, 16);
         for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
           const int s = g & 1;
           if (!mbar_wait(&S.full[s], (g >> 1) & 1u, err)) {
@@ -144,21 +168,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           }
           tc_fence_after();
           if (lane == 0) {
+            const bool h = S.fmt16[s] != 0u;
+            const uint32_t idS = h ? idS16 : idSbf, idW = h ? idW16 : idWbf;
             const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
             const uint32_t b_hi = smem_u32(S.B[s][0]), b_lo = smem_u32(S.B[s][1]);
+            const uint32_t on = smem_u32(S.ones[h ? 1 : 0]);
 #pragma unroll
             for (int kk = 0; kk < kK / 16; ++kk) {
               const uint32_t o = kk * 32;
-              const uint32_t first = (j == 0 && kk == 0) ? 1u : 0u;
-              // main term and the two correction terms in separate accumulators
-              tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_hi + o), idS,
-                         1u - first);
+              const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+              tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_hi + o), idS, acc);
               if (vsplit)
-                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw128(a_hi + o),
-                           smem_desc_k_sw128(b_lo + o), idS, 1u - first);
+                tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_lo + o), idS, 1u);
               if (split)
-                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw128(a_lo + o),
-                           smem_desc_k_sw128(b_hi + o), idS, vsplit ? 1u : 1u - first);
+                tc_mma_f16(tmem, smem_desc_k_sw128(a_lo + o), smem_desc_k_sw128(b_hi + o), idS, 1u);
+              tc_mma_f16(tmem + kWCol, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(on + o), idW,
+                         acc);
+              if (split)
+                tc_mma_f16(tmem + kWCol, smem_desc_k_sw128(a_lo + o), smem_desc_k_sw128(on + o),
+                           idW, 1u);
             }
             tc_commit(&S.empty[s]);
             if (j == n_chunks - 1) tc_commit(&S.done);
@@ -182,57 +210,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         bail = true;
         break;
       }
-      // B tiles: row tid holds 64 samples of channel c.  All 64 loads are
-      // issued before any conversion (memory-level parallelism).
+      // Values of this thread's channel row: all 64 loads issued first.
+      const int32_t* ci = pv.cand_idx + kb0 + (int64_t)j * kK;
+      uint32_t raw[kK];
+      if (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) {
+        const uint32_t* vp = static_cast<const uint32_t*>(J.values);
+#pragma unroll
+        for (int k = 0; k < kK; ++k)
+          raw[k] = cvalid ? __ldg(vp + (int64_t)__ldg(ci + k) * J.ld_values + c) : 0u;
+      } else {
+        const uint16_t* vp = static_cast<const uint16_t*>(J.values);
+#pragma unroll
+        for (int k = 0; k < kK; ++k)
+          raw[k] = cvalid ? (uint32_t)__ldg(vp + (int64_t)__ldg(ci + k) * J.ld_values + c) : 0u;
+      }
+      // Range of the chunk's values (decides the 16-bit format of the chunk).
       {
-        const int32_t* ci = pv.cand_idx + kb0 + (int64_t)j * kK;
-        uint32_t raw[kK];
-        if (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) {
-          const uint32_t* vp = static_cast<const uint32_t*>(J.values);
+        float amax = 0.0f, amin = __int_as_float(0x7f800000);
+        uint32_t bad = 0u;
 #pragma unroll
-          for (int k = 0; k < kK; ++k)
-            raw[k] = cvalid ? __ldg(vp + (int64_t)__ldg(ci + k) * J.ld_values + c) : 0u;
-        } else {
-          const uint16_t* vp = static_cast<const uint16_t*>(J.values);
-#pragma unroll
-          for (int k = 0; k < kK; ++k)
-            raw[k] = cvalid ? (uint32_t)__ldg(vp + (int64_t)__ldg(ci + k) * J.ld_values + c) : 0u;
+        for (int k = 0; k < kK; ++k) {
+          const float a = fabsf(value_of(raw[k], J.dtype));
+          bad |= (a <= 3.0e38f) ? 0u : 1u;  // NaN or Inf
+          amax = fmaxf(amax, a);
+          if (a > 0.0f) amin = fminf(amin, a);
         }
-        const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
-#pragma unroll
-        for (int q = 0; q < kK / 8; ++q) {
-          uint32_t h2[4], l2[4];
-#pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            uint16_t h0, l0, h1, l1;
-            const uint32_t x0 = raw[q * 8 + e], x1 = raw[q * 8 + e + 1];
-            if (J.dtype == HEGRID_F32) {
-              if (vsplit) {
-                split_bf16(__uint_as_float(x0), h0, l0);
-                split_bf16(__uint_as_float(x1), h1, l1);
-              } else {
-                h0 = __bfloat16_as_ushort(__float2bfloat16_rn(__uint_as_float(x0)));
-                h1 = __bfloat16_as_ushort(__float2bfloat16_rn(__uint_as_float(x1)));
-                l0 = l1 = 0;
-              }
-            } else if (J.dtype == HEGRID_BF16X2) {
-              h0 = (uint16_t)(x0 & 0xffffu);
-              l0 = (uint16_t)(x0 >> 16);
-              h1 = (uint16_t)(x1 & 0xffffu);
-              l1 = (uint16_t)(x1 >> 16);
-            } else {
-              h0 = (uint16_t)x0;
-              h1 = (uint16_t)x1;
-              l0 = l1 = 0;
-            }
-            h2[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            l2[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-          }
-          st_shared_v4(bh + sw128(tid, q), h2[0], h2[1], h2[2], h2[3]);
-          if (vsplit) st_shared_v4(bl + sw128(tid, q), l2[0], l2[1], l2[2], l2[3]);
+        const uint32_t wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+        const uint32_t wmin = __reduce_min_sync(0xffffffffu, __float_as_uint(amin));
+        const uint32_t wbad = __reduce_or_sync(0xffffffffu, bad);
+        if (lane == 0) {
+          S.red[s][warp][0] = wmax;
+          S.red[s][warp][1] = wmin;
+          S.red[s][warp][2] = wbad;
         }
       }
-      // A tiles: zero, then scatter the chunk's weight entries
+      // A tiles: zero (the scatter follows the barrier)
       {
         uint4* ah = reinterpret_cast<uint4*>(S.A[s][0]);
         uint4* al = reinterpret_cast<uint4*>(S.A[s][1]);
@@ -243,6 +255,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
       }
       named_bar_producers();
+      bool h16;
+      {
+        uint32_t mx = 0u, mn = 0x7f800000u, bd = 0u;
+#pragma unroll
+        for (int w = 0; w < kProducerWarps; ++w) {
+          mx = max(mx, S.red[s][w][0]);
+          mn = min(mn, S.red[s][w][1]);
+          bd |= S.red[s][w][2];
+        }
+        const float fmx = __uint_as_float(mx), fmn = __uint_as_float(mn);
+        if (J.dtype == HEGRID_F16) {
+          h16 = true;
+        } else if (bd) {
+          h16 = false;
+        } else if (J.dtype == HEGRID_BF16) {
+          h16 = fmx <= 32768.0f && (mn == 0x7f800000u || fmn >= 6.103515625e-05f);
+        } else {
+          h16 = fmx <= 32768.0f && (fmx == 0.0f || fmx >= 0.0078125f);
+        }
+        if (tid == 0) S.fmt16[s] = h16 ? 1u : 0u;
+      }
+      // B tiles: row tid holds the 64 samples of channel c
+      {
+        const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
+#pragma unroll
+        for (int q = 0; q < kK / 8; ++q) {
+          uint32_t h2[4], l2[4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            uint16_t h0, l0, h1, l1;
+            const uint32_t x0 = raw[q * 8 + e], x1 = raw[q * 8 + e + 1];
+            if (J.dtype == HEGRID_F16 || (J.dtype == HEGRID_BF16 && !h16)) {
+              h0 = (uint16_t)x0;  // stored format already matches the chunk format
+              h1 = (uint16_t)x1;
+              l0 = l1 = 0;
+            } else {
+              const float v0 = value_of(x0, J.dtype), v1 = value_of(x1, J.dtype);
+              if (h16) {
+                split_f16(v0, h0, l0);
+                split_f16(v1, h1, l1);
+              } else {
+                split_bf16(v0, h0, l0);
+                split_bf16(v1, h1, l1);
+              }
+            }
+            h2[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            l2[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+          }
+          st_shared_v4(bh + sw128(tid, q), h2[0], h2[1], h2[2], h2[3]);
+          if (vsplit) st_shared_v4(bl + sw128(tid, q), l2[0], l2[1], l2[2], l2[3]);
+        }
+      }
+      // A tiles: scatter the chunk's weight entries
       {
         const int64_t e0 = pv.sub_off[sub0 + 2 * j], e1 = pv.sub_off[sub0 + 2 * j + 2];
         uint8_t* ah = S.A[s][0];
@@ -252,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           const int r = (int)(ck >> 6), k = (int)(ck & 63u);
           const float w = pv.ent_w[e];
           uint16_t hi, lo;
-          if (f16)
+          if (h16)
             split_f16(w, hi, lo);
           else
             split_bf16(w, hi, lo);
@@ -291,28 +356,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       ++n_tm;
       tc_fence_after();
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-      const int wvar = f16 ? (split ? 4 : 3) : (split ? 2 : 1);
-      const float W = active ? pv.wsum[(int64_t)wvar * pv.M + m] : 0.0f;
+      uint32_t r[32];
+      tmem_ld_32x32b_x32(tl + kWCol, r);
+      tmem_ld_wait();
+      const float W = __uint_as_float(r[0]);
       const bool ok = W > 0.0f;
-      uint32_t r[32], rc[32];
 #pragma unroll 1
       for (int cb = 0; cb < kN / 32; ++cb) {
         tmem_ld_32x32b_x32(tl + cb * 32, r);
-        if (split) tmem_ld_32x32b_x32(tl + kCorrCol + cb * 32, rc);
         tmem_ld_wait();
         if (active) {
           const int64_t cbase = c0 + cb * 32;
           float v[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float sum = split ? __fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i]))
-                                    : __uint_as_float(r[i]);
-            v[i] = ok ? __fdiv_rn(sum, W) : qnan;
-          }
+          for (int i = 0; i < 32; ++i) v[i] = ok ? __fdiv_rn(__uint_as_float(r[i]), W) : qnan;
           if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(out + cbase + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+              *reinterpret_cast<float4*>(out + cbase + i) =
+                  make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)

@@ -203,3 +203,42 @@ def test_tc_config3_precision_table(H):
     assert res["bf16"][0] <= TOL_SPLIT
     assert res["f16"][0] <= TOL_SPLIT
     assert res["f32-split"][0] <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("scale", [1e6, 1e-5])
+def test_tc_split_bf16_fallback_range(H, scale):
+    """Values outside the FP16 window take the BF16 split (full FP32 range)."""
+    wl = _case(81, C=16)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    vals = (wl["values"].astype(np.float64) * scale).astype(np.float32)
+    plan = _plan(H, wl)
+    try:
+        got, _ = _run(H, plan, torch.from_numpy(vals).cuda(), H.HEGRID_F32, 16, 16, M,
+                      H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(vals)
+    err, _, _ = map_error(got, ref, Wref)
+    print(f"bf16 fallback scale {scale}: {err:.3e}")
+    assert err <= TOL_SPLIT, err
+
+
+def test_tc_split_mixed_chunk_formats(H):
+    """A few huge samples force BF16 in their chunks; the rest stay FP16."""
+    wl = _case(82, C=16)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    vals = wl["values"].copy()
+    rng = np.random.default_rng(5)
+    hot = rng.choice(len(vals), 40, replace=False)
+    vals[hot] *= 1e5
+    plan = _plan(H, wl)
+    try:
+        got, _ = _run(H, plan, torch.from_numpy(vals).cuda(), H.HEGRID_F32, 16, 16, M,
+                      H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(vals)
+    err, _, _ = map_error(got, ref, Wref)
+    assert err <= TOL_SPLIT, err
