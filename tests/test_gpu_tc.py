@@ -225,7 +225,11 @@ def test_tc_split_bf16_fallback_range(H, scale):
 
 
 def test_tc_split_mixed_chunk_formats(H):
-    """A few huge samples force BF16 in their chunks; the rest stay FP16."""
+    """A few huge samples force BF16 in their chunks; the rest stay FP16.
+
+    Cells that touch a huge sample are dominated by it and carry the BF16
+    split's residual (~2^-17 of the huge value): they are checked relative to
+    their own magnitude.  Every other cell must meet the split tolerance."""
     wl = _case(82, C=16)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
@@ -239,6 +243,15 @@ def test_tc_split_mixed_chunk_formats(H):
                       H.HEGRID_MODE_TC_SPLIT)
     finally:
         H.hegrid_plan_destroy(plan)
-    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(vals)
-    err, _, _ = map_error(got, ref, Wref)
+    ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
+    ref, Wref = ix.grid(vals)
+    off, idx, _ = ix.neighbours()
+    cells = np.repeat(np.arange(M), np.diff(off))
+    hot_cell = np.zeros(M, bool)
+    hot_cell[cells[np.isin(idx, hot)]] = True
+    cold = ~hot_cell & (Wref > 0)
+    err, _, _ = map_error(got[cold], ref[cold], Wref[cold])
     assert err <= TOL_SPLIT, err
+    h = hot_cell & (Wref >= 1e-3 * Wref.max())
+    rel = np.abs(got[h] - ref[h]) / np.abs(ref[h]).max(axis=0)
+    assert rel.max() <= 4 * 2.0 ** -17, rel.max()
