@@ -146,6 +146,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--channels", type=int, default=1024)
+    ap.add_argument("--lean", action="store_true",
+                    help="timed steps only (no per-form timings, accuracy check, e2e or CPU "
+                         "baseline): the command used for profiler captures")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -251,7 +254,7 @@ def main():
     P = info["n_pairs"]
     forms = {}
     err = {}
-    for nm, md in modes.items():
+    for nm, md in ([] if args.lean else modes.items()):
         try:
             H.hegrid_grid(plan, vals_d, H.HEGRID_F32, C, C, map_d, C, w_d, md, sh)
         except H.HegridError as e:
@@ -301,7 +304,7 @@ def main():
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not args.lean:
         host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
         host_w = torch.empty(M, dtype=torch.float32, pin_memory=True)
         lon_h, lat_h = np.ascontiguousarray(wl["lon"]), np.ascontiguousarray(wl["lat"])
@@ -331,7 +334,7 @@ def main():
                        "chunks -> pinned host map)"}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not args.lean:
         cpu = cpu_oracle_sample(wl, frac_rows=20)
 
     if rank == 0:
