@@ -1,11 +1,11 @@
 // Plain FP32 form of the cell update (Algorithm 1's accumulate and normalise
 // steps, Eq. 1) on CUDA cores.
 //
-// A persistent CTA pulls work items (field, 16x8 cell block, 128-channel tile)
-// from a device queue.  For each K chunk of 32 candidate samples of the block:
-//   * one thread stages the 32 sample rows (FP32, channel-contiguous) into
-//     shared memory with bulk async copies (TMA engine) completing on an
-//     mbarrier, double-buffered;
+// A persistent CTA takes work items (field, 16x8 cell block, 128-channel tile)
+// in a fixed stride.  For each K chunk of 32 candidate samples of the block:
+//   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) into shared
+//     memory with bulk async copies (TMA engine, one row per lane) completing
+//     on an mbarrier, double-buffered;
 //   * each of 128 threads scatters its cell's pairs that fall in the chunk
 //     into a dense 32 x 128 weight tile and ORs a per-patch occupancy mask;
 //   * each warp owns a 4x4-cell patch and 128 channels; a thread accumulates
@@ -87,13 +87,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int64_t sub0 = kb0 / kKC;  // first 32-candidate sub-chunk of the block
 
+    // Stage the 32 sample rows of chunk j: warp 0, one row per lane.
     auto issue = [&](int j) {
-      int s = j & 1;
-      mbar_arrive_expect_tx(&S.bar[s], row_bytes * kKC);
-      for (int k = 0; k < kKC; ++k) {
-        int32_t n = pv.cand_idx[kb0 + (int64_t)j * kKC + k];
-        bulk_g2s(&S.V[s][k][0], vals + (int64_t)n * J.ld_values + c0, row_bytes, &S.bar[s]);
-      }
+      const int s = j & 1;
+      if (lane == 0) mbar_arrive_expect_tx(&S.bar[s], row_bytes * kKC);
+      __syncwarp();
+      const int32_t n = pv.cand_idx[kb0 + (int64_t)j * kKC + lane];
+      bulk_g2s(&S.V[s][lane][0], vals + (int64_t)n * J.ld_values + c0, row_bytes, &S.bar[s]);
     };
 
     float acc[8][8];
@@ -103,10 +103,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int e = 0; e < 8; ++e) acc[i][e] = 0.0f;
 
     const int patch = warp, cs = lane >> 4, cg = lane & 15;
-    if (tid == 0 && n_chunks > 0) issue(0);
+    if (warp == 0 && n_chunks > 0) issue(0);
     for (int j = 0; j < n_chunks; ++j) {
       const int s = j & 1;
-      if (tid == 0 && j + 1 < n_chunks) issue(j + 1);
+      if (warp == 0 && j + 1 < n_chunks) issue(j + 1);
       // weight tile for chunk j: zero, then scatter the chunk's entries
       {
         float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][0]);

@@ -2,29 +2,34 @@
 // tcgen05: per 16x8 cell block b and 256-channel tile, the sums
 //     S[cell, c] = sum_k T[cell, k] V[k, c]
 // run as dense MMAs over the block's candidate samples k (sorted spatially by
-// the plan, 64 per chunk):  D[128 cells x 256 ch] (+)= A[128 x 16] * B[16 x 256]
+// the plan, 32 per chunk):  D[128 cells x 256 ch] (+)= A[128 x 16] * B[16 x 256]
 // with A = the block's weight tile (built in shared memory from the plan's
 // candidate-major entries) and B = the sample values of the chunk (K-major, so
-// each channel row holds 64 samples).  FP32 accumulation lives in TMEM.
+// each channel row holds the chunk's samples).  FP32 accumulation in TMEM.
 //
 // Precision: values and weights are split into a high and a low 16-bit part;
 // HEGRID_MODE_TC_SPLIT issues hi*hi + hi*lo + lo*hi (the lo*lo term is below
 // FP32 rounding), HEGRID_MODE_TC issues hi*hi.  The 16-bit format is chosen
-// per 64-sample chunk: FP16 (11-bit halves, ~2^-22 residual) when every value
-// of the chunk lies in [2^-7, 2^15] in magnitude (zeros allowed) -- or, for
-// BF16 input, when FP16 holds every value exactly -- and BF16 (8-bit halves,
-// ~2^-17 residual, full FP32 range) otherwise.  Chunks of one block may mix
-// formats: each MMA carries its own instruction descriptor and all of them
-// accumulate in FP32.  W is accumulated by the same MMAs against a tile of
-// ones, so the map is normalised by the sum of exactly the quantised weights
-// that produced S.
+// per chunk: FP16 (11-bit halves, ~2^-22 residual) when every value of the
+// chunk lies in [2^-7, 2^15] in magnitude (zeros allowed) -- or, for BF16
+// input, when FP16 holds every value exactly -- and BF16 (8-bit halves, ~2^-17
+// residual, full FP32 range) otherwise.  Chunks of one block may mix formats:
+// each MMA carries its own instruction descriptor and all accumulate in FP32.
+// W is accumulated by the same MMAs against a tile of ones, so the map is
+// normalised by the sum of exactly the quantised weights that produced S.
 //
-// CTA: 8 producer warps (values -> B tiles, entries -> A tiles, 2-stage
-// ring), warps 0-3 also run the epilogue (TMEM -> registers -> S / W ->
-// global), and warp 8 allocates TMEM and issues the MMAs (one lane).
-// Stages are handed over with mbarriers; MMA completion is signalled by
-// tcgen05.commit.  Every wait is bounded (global timer) and reports a timeout
-// through the plan's error word.
+// Warp roles (one CTA per SM, persistent over work items):
+//   warp 9      stages the chunk's 32 sample rows (raw, as stored) into a
+//               3-deep shared-memory ring with bulk async copies (TMA
+//               engine), one row per lane;
+//   warps 0-7   convert a staged chunk into the B tiles (row = channel),
+//               scatter the chunk's weight entries into the A tiles (2-deep
+//               ring), and warps 0-3 run the epilogue (TMEM -> registers ->
+//               S / W -> global);
+//   warp 8      allocates TMEM and issues the MMAs (one lane).
+// Hand-offs use mbarriers; MMA completion is signalled by tcgen05.commit.
+// Every wait is bounded (global timer) and reports a timeout through the
+// plan's error word.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -39,32 +44,54 @@ namespace {
 
 constexpr int kProducerWarps = 8;
 constexpr int kProducers = kProducerWarps * 32;
-constexpr int kThreads = kProducers + 32;  // + the MMA warp
-constexpr int kK = 64;                     // candidates per chunk (one 128-byte row of BF16)
+constexpr int kMmaWarp = 8;
+constexpr int kTmaWarp = 9;
+constexpr int kThreads = 10 * 32;
+constexpr int kK = 32;                     // candidates per chunk (64-byte rows of 16-bit values)
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
+constexpr int kStages = 2;                 // A/B tile ring
+constexpr int kRawStages = 3;              // staged sample rows ring
+constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst case)
 constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
 constexpr uint32_t kWCol = 256;
+constexpr int kBand = 8;                   // blocks per band of the work order
 
 struct __align__(1024) TcSmem {
-  uint8_t A[2][2][kM * 128];   // [stage][hi, lo]: weight tiles, K-major, 128B swizzle
-  uint8_t B[2][2][kN * 128];   // [stage][hi, lo]: value tiles, K-major, 128B swizzle
-  uint8_t ones[2][16 * 128];   // [bf16, f16] all-ones B operand for W
-  uint32_t red[2][kProducerWarps][3];  // per stage and warp: max|v|, min|v|>0, non-finite
-  uint32_t fmt16[2];                   // per stage: 1 = FP16 tiles, 0 = BF16 tiles
-  uint64_t full[2], empty[2], done, tfree;
+  uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
+  uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
+  uint8_t ones[2][16 * 64];            // [bf16, f16] all-ones B operand for W
+  uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
+  uint32_t red[kStages][kProducerWarps][3];  // max|v|, min|v|>0, non-finite
+  uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
+  uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+  uint64_t ab_full[kStages], ab_empty[kStages], done, tfree;
   uint32_t tmem_base;
 };
 
-// Byte offset of 16-byte chunk q of row r in a K-major, 128B-swizzled tile.
-__device__ __forceinline__ uint32_t sw128(int r, int q) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
+// Byte offset of 16-byte chunk q (0..3) of row r in a K-major, 64B-swizzled tile.
+__device__ __forceinline__ uint32_t sw64(int r, int q) {
+  return (uint32_t)(r * 64 + ((q ^ ((r >> 1) & 3)) << 4));
 }
 
 __device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
   int j = 0;
   while (j + 1 < jt.n_jobs && jt.job[j + 1].item_base <= item) ++j;
   return j;
+}
+
+// Work order inside a job: channel tiles slowest, then cell blocks in bands
+// of kBand block columns, so concurrently running CTAs share candidates in L2.
+__device__ __forceinline__ void item_coords(const GridJob& J, int64_t local, int64_t& b,
+                                            int64_t& ct) {
+  const int64_t nb = J.pv.n_blocks;
+  ct = local / nb;
+  const int64_t bo = local - ct * nb;
+  const int64_t per_band = (int64_t)kBand * J.pv.nby_b;
+  const int64_t band = bo / per_band;
+  const int64_t t = bo - band * per_band;
+  const int64_t bw = min((int64_t)kBand, (int64_t)J.pv.nbx_b - band * kBand);
+  b = (t / bw) * J.pv.nbx_b + band * kBand + (t % bw);
 }
 
 // Split x into hi + lo 16-bit floats (round to nearest for both parts).
@@ -113,21 +140,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   int32_t* err = jt.job[0].pv.err_word;
 
   if (tid == 0) {
-    mbar_init(&S.full[0], kProducerWarps);
-    mbar_init(&S.full[1], kProducerWarps);
-    mbar_init(&S.empty[0], 1);
-    mbar_init(&S.empty[1], 1);
+    for (int i = 0; i < kRawStages; ++i) {
+      mbar_init(&S.raw_full[i], 1);
+      mbar_init(&S.raw_empty[i], kProducerWarps);
+    }
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&S.ab_full[i], kProducerWarps);
+      mbar_init(&S.ab_empty[i], 1);
+    }
     mbar_init(&S.done, 1);
     mbar_init(&S.tfree, 4);
     fence_mbar_init();
   }
   // ones tiles (bf16 1.0 = 0x3f80, f16 1.0 = 0x3c00)
-  for (int i = tid; i < 16 * 128 / 4; i += kThreads) {
+  for (int i = tid; i < 16 * 64 / 4; i += kThreads) {
     reinterpret_cast<uint32_t*>(S.ones[0])[i] = 0x3f803f80u;
     reinterpret_cast<uint32_t*>(S.ones[1])[i] = 0x3c003c00u;
   }
   fence_proxy_async_smem();
-  if (warp == kProducerWarps) {
+  if (warp == kMmaWarp) {
     tmem_alloc(&S.tmem_base, kTmemCols);
     tmem_relinquish();
   }
@@ -137,32 +168,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   const uint32_t tmem = S.tmem_base;
 
   bool bail = false;
-  uint32_t g = 0;        // chunks produced / consumed so far (stage = g & 1)
-  uint32_t n_tm = 0;     // items that used TMEM so far
+  uint32_t g = 0;     // chunks through the A/B ring so far
+  uint32_t gr = 0;    // chunks through the raw ring so far
+  uint32_t n_tm = 0;  // items that used TMEM so far
 
   for (int64_t item = blockIdx.x; item < jt.n_items && !bail; item += gridDim.x) {
     const GridJob& J = jt.job[find_job(jt, item)];
     const PlanView& pv = J.pv;
-    const int64_t local = item - J.item_base;
-    const int64_t b = local / J.n_ctiles;
-    const int64_t c0 = (local % J.n_ctiles) * kN;
+    int64_t b, ct;
+    item_coords(J, item - J.item_base, b, ct);
+    const int64_t c0 = ct * kN;
+    const int64_t C = J.C;
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kK);
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
+    const int eb = (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) ? 4 : 2;
 
-    if (warp == kProducerWarps) {
+    if (warp == kTmaWarp) {
+      // ---------------- row stager ----------------
+      const int64_t cw = C - c0 < kN ? C - c0 : kN;
+      const uint32_t row_bytes = (uint32_t)((cw * eb + 15) / 16 * 16);
+      const uint8_t* vals = static_cast<const uint8_t*>(J.values);
+      for (int j = 0; j < n_chunks; ++j, ++gr) {
+        const int r = gr % kRawStages;
+        const uint32_t u = gr / kRawStages;
+        if (u >= 1 && !mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err)) {
+          bail = true;
+          break;
+        }
+        if (lane == 0) mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * kK);
+        __syncwarp();
+        const int64_t n = pv.cand_idx[kb0 + (int64_t)j * kK + lane];
+        bulk_g2s(&S.raw[r][lane * kRawPitch], vals + (n * J.ld_values + c0) * eb, row_bytes,
+                 &S.raw_full[r]);
+      }
+      continue;
+    }
+
+    if (warp == kMmaWarp) {
       // ---------------- MMA issuer ----------------
       if (n_chunks > 0) {
-        if (n_tm > 0 && !mbar_wait(&S.tfree, (n_tm - 1) & 1u, err)) {
-          bail = true;
-        }
+        if (n_tm > 0 && !mbar_wait(&S.tfree, (n_tm - 1) & 1u, err)) bail = true;
         tc_fence_after();
         const uint32_t idS16 = idesc_f16(0u, kM, kN), idW16 = idesc_f16(0u, kM, 16);
         const uint32_t idSbf = idesc_f16(1u, kM, kN), idWbf = idesc_f16(1u, kM, 16);
         for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
-          const int s = g & 1;
-          if (!mbar_wait(&S.full[s], (g >> 1) & 1u, err)) {
+          const int s = g % kStages;
+          if (!mbar_wait(&S.ab_full[s], (g / kStages) & 1u, err)) {
             bail = true;
             break;
           }
@@ -177,18 +230,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
             for (int kk = 0; kk < kK / 16; ++kk) {
               const uint32_t o = kk * 32;
               const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-              tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_hi + o), idS, acc);
+              tc_mma_f16(tmem, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_hi + o), idS, acc);
               if (vsplit)
-                tc_mma_f16(tmem, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(b_lo + o), idS, 1u);
+                tc_mma_f16(tmem, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_lo + o), idS, 1u);
               if (split)
-                tc_mma_f16(tmem, smem_desc_k_sw128(a_lo + o), smem_desc_k_sw128(b_hi + o), idS, 1u);
-              tc_mma_f16(tmem + kWCol, smem_desc_k_sw128(a_hi + o), smem_desc_k_sw128(on + o), idW,
+                tc_mma_f16(tmem, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(b_hi + o), idS, 1u);
+              tc_mma_f16(tmem + kWCol, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(on + o), idW,
                          acc);
               if (split)
-                tc_mma_f16(tmem + kWCol, smem_desc_k_sw128(a_lo + o), smem_desc_k_sw128(on + o),
+                tc_mma_f16(tmem + kWCol, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(on + o),
                            idW, 1u);
             }
-            tc_commit(&S.empty[s]);
+            tc_commit(&S.ab_empty[s]);
             if (j == n_chunks - 1) tc_commit(&S.done);
           }
           __syncwarp();
@@ -199,38 +252,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     }
 
     // ---------------- producers (warps 0-7) ----------------
-    const int64_t C = J.C;
     const int64_t c = c0 + tid;  // this thread's channel = B row `tid`
     const bool cvalid = c < C;
     const int64_t sub0 = kb0 / 32;
-    for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
-      const int s = g & 1;
-      const uint32_t u = g >> 1;
-      if (u >= 1 && !mbar_wait(&S.empty[s], (u - 1) & 1u, err)) {
+    for (int j = 0; j < n_chunks && !bail; ++j, ++g, ++gr) {
+      const int s = g % kStages;
+      const int rs = gr % kRawStages;
+      if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) {
         bail = true;
         break;
       }
-      // Values of this thread's channel row: all 64 loads issued first.
-      const int32_t* ci = pv.cand_idx + kb0 + (int64_t)j * kK;
-      uint32_t raw[kK];
-      if (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) {
-        const uint32_t* vp = static_cast<const uint32_t*>(J.values);
-#pragma unroll
-        for (int k = 0; k < kK; ++k)
-          raw[k] = cvalid ? __ldg(vp + (int64_t)__ldg(ci + k) * J.ld_values + c) : 0u;
-      } else {
-        const uint16_t* vp = static_cast<const uint16_t*>(J.values);
-#pragma unroll
-        for (int k = 0; k < kK; ++k)
-          raw[k] = cvalid ? (uint32_t)__ldg(vp + (int64_t)__ldg(ci + k) * J.ld_values + c) : 0u;
+      if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) {
+        bail = true;
+        break;
       }
+      // Channel column `tid` of the staged rows.
+      uint32_t x[kK];
+      {
+        const uint8_t* rb = S.raw[rs];
+        if (eb == 4) {
+#pragma unroll
+          for (int k = 0; k < kK; ++k)
+            x[k] = cvalid ? *reinterpret_cast<const uint32_t*>(rb + k * kRawPitch + tid * 4) : 0u;
+        } else {
+#pragma unroll
+          for (int k = 0; k < kK; ++k)
+            x[k] = cvalid ? (uint32_t) * reinterpret_cast<const uint16_t*>(rb + k * kRawPitch +
+                                                                         tid * 2)
+                          : 0u;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
       // Range of the chunk's values (decides the 16-bit format of the chunk).
       {
         float amax = 0.0f, amin = __int_as_float(0x7f800000);
         uint32_t bad = 0u;
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
-          const float a = fabsf(value_of(raw[k], J.dtype));
+          const float a = fabsf(value_of(x[k], J.dtype));
           bad |= (a <= 3.0e38f) ? 0u : 1u;  // NaN or Inf
           amax = fmaxf(amax, a);
           if (a > 0.0f) amin = fminf(amin, a);
@@ -249,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         uint4* ah = reinterpret_cast<uint4*>(S.A[s][0]);
         uint4* al = reinterpret_cast<uint4*>(S.A[s][1]);
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = tid; i < kM * 128 / 16; i += kProducers) {
+        for (int i = tid; i < kM * 64 / 16; i += kProducers) {
           ah[i] = z;
           if (split) al[i] = z;
         }
@@ -276,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         if (tid == 0) S.fmt16[s] = h16 ? 1u : 0u;
       }
-      // B tiles: row tid holds the 64 samples of channel c
+      // B tiles: row tid holds the chunk's 32 samples of channel c
       {
         const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
@@ -285,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
             uint16_t h0, l0, h1, l1;
-            const uint32_t x0 = raw[q * 8 + e], x1 = raw[q * 8 + e + 1];
+            const uint32_t x0 = x[q * 8 + e], x1 = x[q * 8 + e + 1];
             if (J.dtype == HEGRID_F16 || (J.dtype == HEGRID_BF16 && !h16)) {
               h0 = (uint16_t)x0;  // stored format already matches the chunk format
               h1 = (uint16_t)x1;
@@ -303,32 +363,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
             h2[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
             l2[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
           }
-          st_shared_v4(bh + sw128(tid, q), h2[0], h2[1], h2[2], h2[3]);
-          if (vsplit) st_shared_v4(bl + sw128(tid, q), l2[0], l2[1], l2[2], l2[3]);
+          st_shared_v4(bh + sw64(tid, q), h2[0], h2[1], h2[2], h2[3]);
+          if (vsplit) st_shared_v4(bl + sw64(tid, q), l2[0], l2[1], l2[2], l2[3]);
         }
       }
       // A tiles: scatter the chunk's weight entries
       {
-        const int64_t e0 = pv.sub_off[sub0 + 2 * j], e1 = pv.sub_off[sub0 + 2 * j + 2];
+        const int64_t e0 = pv.sub_off[sub0 + j], e1 = pv.sub_off[sub0 + j + 1];
         uint8_t* ah = S.A[s][0];
         uint8_t* al = S.A[s][1];
         for (int64_t e = e0 + tid; e < e1; e += kProducers) {
           const uint32_t ck = pv.ent_ck[e];
-          const int r = (int)(ck >> 6), k = (int)(ck & 63u);
+          const int r = (int)(ck >> 6), k = (int)(ck & 31u);
           const float w = pv.ent_w[e];
           uint16_t hi, lo;
           if (h16)
             split_f16(w, hi, lo);
           else
             split_bf16(w, hi, lo);
-          const uint32_t off = sw128(r, k >> 3) + (k & 7) * 2;
+          const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
           *reinterpret_cast<uint16_t*>(ah + off) = hi;
           if (split) *reinterpret_cast<uint16_t*>(al + off) = lo;
         }
       }
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.full[s]);
+      if (lane == 0) mbar_arrive(&S.ab_full[s]);
     }
     if (bail) break;
 
@@ -391,12 +451,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     }
   }
 
-  // drain: make sure no MMA is still writing TMEM before it is freed
-  if (warp == kProducerWarps && n_tm > 0 && !bail) mbar_wait(&S.done, (n_tm - 1) & 1u, nullptr);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kProducerWarps) tmem_dealloc(tmem, kTmemCols);
+  if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace

@@ -167,6 +167,18 @@ __device__ __forceinline__ uint64_t smem_desc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// Same for a K-major operand with 64-byte swizzle (rows of 64 bytes, 8-row
+// groups of 512 bytes): layout type 4 (SWIZZLE_64B), SBO 512 bytes.
+__device__ __forceinline__ uint64_t smem_desc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3fffu);
+  d |= (uint64_t)1u << 16;                       // LBO (ignored)
+  d |= (uint64_t)((512u >> 4) & 0x3fffu) << 32;  // SBO
+  d |= (uint64_t)1u << 46;                       // version
+  d |= (uint64_t)4u << 61;                       // SWIZZLE_64B
+  return d;
+}
+
 // Instruction descriptor for kind::f16: FP32 accumulate, A/B format
 // (0 = F16, 1 = BF16), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_fmt, uint32_t M, uint32_t N) {
