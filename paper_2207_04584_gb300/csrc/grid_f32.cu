@@ -25,6 +25,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kKC = 32;   // candidates per K chunk
 constexpr int kCT = 128;  // channels per tile
+constexpr int kPre = 6;   // weight entries prefetched per thread and chunk
 
 struct __align__(128) SmemF32 {
   float V[2][kKC][kCT];   // staged sample rows
@@ -104,9 +105,25 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int patch = warp, cs = lane >> 4, cg = lane & 15;
     if (warp == 0 && n_chunks > 0) issue(0);
+    int64_t e_lo = 0, e_hi = 0;
+    if (n_chunks > 0) {
+      e_lo = pv.sub_off[sub0];
+      e_hi = pv.sub_off[sub0 + 1];
+    }
     for (int j = 0; j < n_chunks; ++j) {
       const int s = j & 1;
       if (warp == 0 && j + 1 < n_chunks) issue(j + 1);
+      // The chunk's weight entries, loaded before the tile is cleared so the
+      // loads' latency overlaps the clearing and the barrier.
+      uint32_t pck[kPre];
+      float pw[kPre];
+#pragma unroll
+      for (int i = 0; i < kPre; ++i) {
+        const int64_t e = e_lo + tid + (int64_t)i * kThreads;
+        pck[i] = e < e_hi ? (uint32_t)__ldg(pv.ent_ck + e) : 0xffffffffu;
+        pw[i] = e < e_hi ? __ldg(pv.ent_w + e) : 0.0f;
+      }
+      const int64_t e_next = j + 1 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 2) : 0;
       // weight tile for chunk j: zero, then scatter the chunk's entries
       {
         float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][0]);
@@ -115,14 +132,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       __syncthreads();
       {
-        const int64_t e0 = pv.sub_off[sub0 + j], e1 = pv.sub_off[sub0 + j + 1];
-        for (int64_t e = e0 + tid; e < e1; e += kThreads) {
-          const uint32_t ck = pv.ent_ck[e];
+        auto put = [&](uint32_t ck, float w) {
           const int col = (int)(ck >> 6), k = (int)(ck & 31u);
           const int tc = cell_to_col(col % HG_BX, col / HG_BX);
-          S.Wt[s][k][tc] = pv.ent_w[e];
+          S.Wt[s][k][tc] = w;
           atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
-        }
+        };
+#pragma unroll
+        for (int i = 0; i < kPre; ++i)
+          if (pck[i] != 0xffffffffu) put(pck[i], pw[i]);
+        for (int64_t e = e_lo + tid + (int64_t)kPre * kThreads; e < e_hi; e += kThreads)
+          put(pv.ent_ck[e], pv.ent_w[e]);
+        e_lo = e_hi;
+        e_hi = e_next;
       }
       __syncthreads();
       const int timed_out = !mbar_wait(&S.bar[s], phase[s], pv.err_word);

@@ -56,6 +56,7 @@ constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst c
 constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
 constexpr uint32_t kWCol = 256;
 constexpr int kBand = 8;                   // blocks per band of the work order
+constexpr int kPre = 8;                    // weight entries prefetched per producer thread
 
 struct __align__(1024) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
@@ -255,9 +256,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int64_t c = c0 + tid;  // this thread's channel = B row `tid`
     const bool cvalid = c < C;
     const int64_t sub0 = kb0 / 32;
+    int64_t e_lo = 0, e_hi = 0;
+    if (n_chunks > 0) {
+      e_lo = pv.sub_off[sub0];
+      e_hi = pv.sub_off[sub0 + 1];
+    }
     for (int j = 0; j < n_chunks && !bail; ++j, ++g, ++gr) {
       const int s = g % kStages;
       const int rs = gr % kRawStages;
+      // The chunk's weight entries: loads issued before the stage waits so
+      // their latency overlaps them (kPre per thread; the rest follow below).
+      uint32_t pck[kPre];
+      float pw[kPre];
+#pragma unroll
+      for (int i = 0; i < kPre; ++i) {
+        const int64_t e = e_lo + tid + (int64_t)i * kProducers;
+        pck[i] = e < e_hi ? (uint32_t)__ldg(pv.ent_ck + e) : 0xffffffffu;
+        pw[i] = e < e_hi ? __ldg(pv.ent_w + e) : 0.0f;
+      }
+      const int64_t e_next = j + 1 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 2) : 0;
       if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) {
         bail = true;
         break;
@@ -369,13 +386,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       }
       // A tiles: scatter the chunk's weight entries
       {
-        const int64_t e0 = pv.sub_off[sub0 + j], e1 = pv.sub_off[sub0 + j + 1];
         uint8_t* ah = S.A[s][0];
         uint8_t* al = S.A[s][1];
-        for (int64_t e = e0 + tid; e < e1; e += kProducers) {
-          const uint32_t ck = pv.ent_ck[e];
+        auto put = [&](uint32_t ck, float w) {
           const int r = (int)(ck >> 6), k = (int)(ck & 31u);
-          const float w = pv.ent_w[e];
           uint16_t hi, lo;
           if (h16)
             split_f16(w, hi, lo);
@@ -384,8 +398,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
           *reinterpret_cast<uint16_t*>(ah + off) = hi;
           if (split) *reinterpret_cast<uint16_t*>(al + off) = lo;
-        }
+        };
+#pragma unroll
+        for (int i = 0; i < kPre; ++i)
+          if (pck[i] != 0xffffffffu) put(pck[i], pw[i]);
+        for (int64_t e = e_lo + tid + (int64_t)kPre * kProducers; e < e_hi; e += kProducers)
+          put(pv.ent_ck[e], pv.ent_w[e]);
       }
+      e_lo = e_hi;
+      e_hi = e_next;
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.ab_full[s]);
