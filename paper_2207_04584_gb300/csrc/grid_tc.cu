@@ -20,7 +20,7 @@
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warp 9      stages the chunk's 32 sample rows (raw, as stored) into a
-//               3-deep shared-memory ring with bulk async copies (TMA
+//               4-deep shared-memory ring with bulk async copies (TMA
 //               engine), one row per lane;
 //   warps 0-7   convert a staged chunk into the B tiles (row = channel),
 //               scatter the chunk's weight entries into the A tiles (2-deep
@@ -51,14 +51,14 @@ constexpr int kK = 32;                     // candidates per chunk (64-byte rows
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
-constexpr int kRawStages = 3;              // staged sample rows ring
+constexpr int kRawStages = 4;              // staged sample rows ring
 constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst case)
 constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
 constexpr uint32_t kWCol = 256;
 constexpr int kBand = 8;                   // blocks per band of the work order
 constexpr int kPre = 8;                    // weight entries prefetched per producer thread
 
-struct __align__(1024) TcSmem {
+struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
   uint8_t ones[2][16 * 64];            // [bf16, f16] all-ones B operand for W
@@ -135,8 +135,9 @@ __device__ __forceinline__ void named_bar_producers() {
 
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
   extern __shared__ unsigned char smem_raw[];
+  // 64B-swizzled tiles need 512-byte alignment (the swizzle atom)
   TcSmem& S = *reinterpret_cast<TcSmem*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+      (reinterpret_cast<uintptr_t>(smem_raw) + 511) & ~(uintptr_t)511);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* err = jt.job[0].pv.err_word;
 
@@ -191,16 +192,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       const int64_t cw = C - c0 < kN ? C - c0 : kN;
       const uint32_t row_bytes = (uint32_t)((cw * eb + 15) / 16 * 16);
       const uint8_t* vals = static_cast<const uint8_t*>(J.values);
+      int64_t n_next = n_chunks > 0 ? __ldg(pv.cand_idx + kb0 + lane) : 0;
       for (int j = 0; j < n_chunks; ++j, ++gr) {
         const int r = gr % kRawStages;
         const uint32_t u = gr / kRawStages;
+        const int64_t n = n_next;  // this lane's row, loaded one chunk ahead
+        if (j + 1 < n_chunks) n_next = __ldg(pv.cand_idx + kb0 + (int64_t)(j + 1) * kK + lane);
         if (u >= 1 && !mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err)) {
           bail = true;
           break;
         }
         if (lane == 0) mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * kK);
         __syncwarp();
-        const int64_t n = pv.cand_idx[kb0 + (int64_t)j * kK + lane];
         bulk_g2s(&S.raw[r][lane * kRawPitch], vals + (n * J.ld_values + c0) * eb, row_bytes,
                  &S.raw_full[r]);
       }
@@ -484,7 +487,7 @@ int tc_channel_tile() { return kN; }
 
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s) {
   static int sms = 0;
-  const size_t smem = sizeof(TcSmem) + 1024;
+  const size_t smem = sizeof(TcSmem) + 512;
   if (!sms) {
     int dev;
     cudaGetDevice(&dev);
