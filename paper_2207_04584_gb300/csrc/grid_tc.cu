@@ -63,7 +63,7 @@ struct __align__(512) TcSmem {
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
   uint8_t ones[2][16 * 64];            // [bf16, f16] all-ones B operand for W
   uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
-  uint32_t red[kStages][kProducerWarps][3];  // max|v|, min|v|>0, non-finite
+  uint32_t red[kStages][kProducerWarps][2];  // max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t raw_full[kRawStages], raw_empty[kRawStages];
   uint64_t ab_full[kStages], ab_empty[kStages], done, tfree;
@@ -110,18 +110,6 @@ __device__ __forceinline__ void split_f16(float x, uint16_t& hi, uint16_t& lo) {
   lo = __half_as_ushort(l);
 }
 
-// The value a raw element encodes (dtype of the input).
-__device__ __forceinline__ float value_of(uint32_t x, int32_t dtype) {
-  switch (dtype) {
-    case HEGRID_F32: return __uint_as_float(x);
-    case HEGRID_BF16X2:
-      return __bfloat162float(__ushort_as_bfloat16((uint16_t)(x & 0xffffu))) +
-             __bfloat162float(__ushort_as_bfloat16((uint16_t)(x >> 16)));
-    case HEGRID_BF16: return __bfloat162float(__ushort_as_bfloat16((uint16_t)x));
-    default: return __half2float(__ushort_as_half((uint16_t)x));
-  }
-}
-
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
                                              uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
@@ -131,6 +119,186 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 __device__ __forceinline__ void named_bar_producers() {
   asm volatile("bar.sync 1, %0;" ::"r"(kProducers) : "memory");
+}
+
+// Per-value 16-bit split of two FP32 values: hi = RN(v), lo = RN(v - hi), in
+// FP16 or BF16, packed two per 32-bit word.
+__device__ __forceinline__ void split2(float v0, float v1, bool h16, uint32_t& hi, uint32_t& lo) {
+  if (h16) {
+    const __half2 h = __float22half2_rn(make_float2(v0, v1));
+    const float2 f = __half22float2(h);
+    const __half2 l = __float22half2_rn(make_float2(v0 - f.x, v1 - f.y));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __nv_bfloat162 h = __float22bfloat162_rn(make_float2(v0, v1));
+    const float2 f = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(v0 - f.x, v1 - f.y));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uint_as_float(b16 << 16); }
+
+// Producer side of one work item (warps 0-7): for every chunk, convert the
+// staged rows into the B tiles and scatter the weight entries into the A
+// tiles.  DT is the stored value type; SPLIT selects the hi/lo form.
+// Returns false if a bounded wait gave up.
+template <int DT, bool SPLIT>
+__device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_t kb0, int n_chunks,
+                                          int64_t c0, uint32_t& g, uint32_t& gr, int32_t* err) {
+  constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
+  constexpr bool kVsplit = SPLIT && kWide;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const PlanView& pv = J.pv;
+  const bool cvalid = c0 + tid < J.C;  // this thread's channel = B row `tid`
+  const int64_t sub0 = kb0 / 32;
+  int64_t e_lo = pv.sub_off[sub0];
+  int64_t e_hi = pv.sub_off[sub0 + 1];
+  constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
+  constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
+  constexpr uint32_t kBits2m14 = 0x38800000u;    // 2^-14 (smallest normal FP16)
+  constexpr uint32_t kInf = 0x7f800000u;
+  for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
+    const int s = g % kStages;
+    const int rs = gr % kRawStages;
+    // The chunk's weight entries (streaming loads, issued before the stage
+    // waits so that their latency overlaps them).
+    uint32_t pck[kPre];
+    float pw[kPre];
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      const int64_t e = e_lo + tid + (int64_t)i * kProducers;
+      pck[i] = e < e_hi ? (uint32_t)__ldcs(pv.ent_ck + e) : 0xffffffffu;
+      pw[i] = e < e_hi ? __ldcs(pv.ent_w + e) : 0.0f;
+    }
+    const int64_t e_next = j + 1 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 2) : 0;
+    if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
+    if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
+    // Channel column `tid` of the staged rows.
+    uint32_t x[kK];
+    {
+      const uint8_t* rb = S.raw[rs];
+#pragma unroll
+      for (int k = 0; k < kK; ++k) {
+        if (kWide)
+          x[k] = cvalid ? *reinterpret_cast<const uint32_t*>(rb + k * kRawPitch + tid * 4) : 0u;
+        else
+          x[k] = cvalid ? (uint32_t)*reinterpret_cast<const uint16_t*>(rb + k * kRawPitch + tid * 2)
+                        : 0u;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
+    // Range of the chunk's values (decides the 16-bit format of the chunk):
+    // max |v| and, for BF16 input, min nonzero |v|, as float bit patterns.
+    if (DT != HEGRID_F16) {
+      uint32_t mx = 0u, mn = kInf;
+#pragma unroll
+      for (int k = 0; k < kK; ++k) {
+        uint32_t a;
+        if (DT == HEGRID_F32)
+          a = x[k] & 0x7fffffffu;
+        else  // BF16 and BF16X2: the (high) BF16 part
+          a = (x[k] << 16) & 0x7fffffffu;
+        mx = max(mx, a);
+        if (DT == HEGRID_BF16) mn = min(mn, a == 0u ? kInf : a);
+      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (DT == HEGRID_BF16) mn = __reduce_min_sync(0xffffffffu, mn);
+      if (lane == 0) {
+        S.red[s][warp][0] = mx;
+        S.red[s][warp][1] = mn;
+      }
+    }
+    // A tiles: zero (the scatter follows the barrier)
+    {
+      uint4* ah = reinterpret_cast<uint4*>(S.A[s][0]);
+      uint4* al = reinterpret_cast<uint4*>(S.A[s][1]);
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int i = tid; i < kM * 64 / 16; i += kProducers) {
+        ah[i] = z;
+        if (SPLIT) al[i] = z;
+      }
+    }
+    named_bar_producers();
+    bool h16 = true;
+    if (DT != HEGRID_F16) {
+      uint32_t mx = 0u, mn = kInf;
+#pragma unroll
+      for (int w = 0; w < kProducerWarps; ++w) {
+        mx = max(mx, S.red[s][w][0]);
+        mn = min(mn, S.red[s][w][1]);
+      }
+      if (DT == HEGRID_BF16)
+        h16 = mx <= kBits32768 && (mn == kInf || mn >= kBits2m14);
+      else  // NaN / Inf give mx >= kInf > 2^15
+        h16 = mx <= kBits32768 && (mx == 0u || mx >= kBits2m7);
+    }
+    if (tid == 0) S.fmt16[s] = h16 ? 1u : 0u;
+    // B tiles: row tid holds the chunk's 32 samples of channel c0 + tid
+    {
+      const uint32_t bh = smem_u32(S.B[s][0]) + 0u, bl = smem_u32(S.B[s][1]);
+#pragma unroll
+      for (int q = 0; q < kK / 8; ++q) {
+        uint32_t h2[4], l2[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const uint32_t x0 = x[q * 8 + 2 * e], x1 = x[q * 8 + 2 * e + 1];
+          if (DT == HEGRID_F32) {
+            split2(__uint_as_float(x0), __uint_as_float(x1), h16, h2[e], l2[e]);
+          } else if (DT == HEGRID_BF16X2) {
+            const float v0 = bf16_bits_to_float(x0 & 0xffffu) + bf16_bits_to_float(x0 >> 16);
+            const float v1 = bf16_bits_to_float(x1 & 0xffffu) + bf16_bits_to_float(x1 >> 16);
+            split2(v0, v1, h16, h2[e], l2[e]);
+          } else if (DT == HEGRID_BF16) {
+            if (h16) {  // exact in FP16 (checked above)
+              const __half2 h = __float22half2_rn(
+                  make_float2(bf16_bits_to_float(x0), bf16_bits_to_float(x1)));
+              h2[e] = *reinterpret_cast<const uint32_t*>(&h);
+            } else {
+              h2[e] = x0 | (x1 << 16);
+            }
+            l2[e] = 0u;
+          } else {  // F16
+            h2[e] = x0 | (x1 << 16);
+            l2[e] = 0u;
+          }
+        }
+        st_shared_v4(bh + sw64(tid, q), h2[0], h2[1], h2[2], h2[3]);
+        if (kVsplit) st_shared_v4(bl + sw64(tid, q), l2[0], l2[1], l2[2], l2[3]);
+      }
+    }
+    // A tiles: scatter the chunk's weight entries
+    {
+      uint8_t* ah = S.A[s][0];
+      uint8_t* al = S.A[s][1];
+      auto put = [&](uint32_t ck, float w) {
+        const int r = (int)(ck >> 6), k = (int)(ck & 31u);
+        uint16_t hi, lo;
+        if (h16)
+          split_f16(w, hi, lo);
+        else
+          split_bf16(w, hi, lo);
+        const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
+        *reinterpret_cast<uint16_t*>(ah + off) = hi;
+        if (SPLIT) *reinterpret_cast<uint16_t*>(al + off) = lo;
+      };
+#pragma unroll
+      for (int i = 0; i < kPre; ++i)
+        if (pck[i] != 0xffffffffu) put(pck[i], pw[i]);
+      for (int64_t e = e_lo + tid + (int64_t)kPre * kProducers; e < e_hi; e += kProducers)
+        put(__ldcs(pv.ent_ck + e), __ldcs(pv.ent_w + e));
+    }
+    e_lo = e_hi;
+    e_hi = e_next;
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.ab_full[s]);
+  }
+  return true;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
@@ -256,163 +424,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     }
 
     // ---------------- producers (warps 0-7) ----------------
-    const int64_t c = c0 + tid;  // this thread's channel = B row `tid`
-    const bool cvalid = c < C;
-    const int64_t sub0 = kb0 / 32;
-    int64_t e_lo = 0, e_hi = 0;
-    if (n_chunks > 0) {
-      e_lo = pv.sub_off[sub0];
-      e_hi = pv.sub_off[sub0 + 1];
-    }
-    for (int j = 0; j < n_chunks && !bail; ++j, ++g, ++gr) {
-      const int s = g % kStages;
-      const int rs = gr % kRawStages;
-      // The chunk's weight entries: loads issued before the stage waits so
-      // their latency overlaps them (kPre per thread; the rest follow below).
-      uint32_t pck[kPre];
-      float pw[kPre];
-#pragma unroll
-      for (int i = 0; i < kPre; ++i) {
-        const int64_t e = e_lo + tid + (int64_t)i * kProducers;
-        pck[i] = e < e_hi ? (uint32_t)__ldg(pv.ent_ck + e) : 0xffffffffu;
-        pw[i] = e < e_hi ? __ldg(pv.ent_w + e) : 0.0f;
-      }
-      const int64_t e_next = j + 1 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 2) : 0;
-      if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) {
-        bail = true;
-        break;
-      }
-      if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) {
-        bail = true;
-        break;
-      }
-      // Channel column `tid` of the staged rows.
-      uint32_t x[kK];
-      {
-        const uint8_t* rb = S.raw[rs];
-        if (eb == 4) {
-#pragma unroll
-          for (int k = 0; k < kK; ++k)
-            x[k] = cvalid ? *reinterpret_cast<const uint32_t*>(rb + k * kRawPitch + tid * 4) : 0u;
-        } else {
-#pragma unroll
-          for (int k = 0; k < kK; ++k)
-            x[k] = cvalid ? (uint32_t) * reinterpret_cast<const uint16_t*>(rb + k * kRawPitch +
-                                                                         tid * 2)
-                          : 0u;
+    {
+      bool ok = true;
+      if (split) {
+        switch (J.dtype) {
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+        }
+      } else {
+        switch (J.dtype) {
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
         }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
-      // Range of the chunk's values (decides the 16-bit format of the chunk).
-      {
-        float amax = 0.0f, amin = __int_as_float(0x7f800000);
-        uint32_t bad = 0u;
-#pragma unroll
-        for (int k = 0; k < kK; ++k) {
-          const float a = fabsf(value_of(x[k], J.dtype));
-          bad |= (a <= 3.0e38f) ? 0u : 1u;  // NaN or Inf
-          amax = fmaxf(amax, a);
-          if (a > 0.0f) amin = fminf(amin, a);
-        }
-        const uint32_t wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
-        const uint32_t wmin = __reduce_min_sync(0xffffffffu, __float_as_uint(amin));
-        const uint32_t wbad = __reduce_or_sync(0xffffffffu, bad);
-        if (lane == 0) {
-          S.red[s][warp][0] = wmax;
-          S.red[s][warp][1] = wmin;
-          S.red[s][warp][2] = wbad;
-        }
-      }
-      // A tiles: zero (the scatter follows the barrier)
-      {
-        uint4* ah = reinterpret_cast<uint4*>(S.A[s][0]);
-        uint4* al = reinterpret_cast<uint4*>(S.A[s][1]);
-        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = tid; i < kM * 64 / 16; i += kProducers) {
-          ah[i] = z;
-          if (split) al[i] = z;
-        }
-      }
-      named_bar_producers();
-      bool h16;
-      {
-        uint32_t mx = 0u, mn = 0x7f800000u, bd = 0u;
-#pragma unroll
-        for (int w = 0; w < kProducerWarps; ++w) {
-          mx = max(mx, S.red[s][w][0]);
-          mn = min(mn, S.red[s][w][1]);
-          bd |= S.red[s][w][2];
-        }
-        const float fmx = __uint_as_float(mx), fmn = __uint_as_float(mn);
-        if (J.dtype == HEGRID_F16) {
-          h16 = true;
-        } else if (bd) {
-          h16 = false;
-        } else if (J.dtype == HEGRID_BF16) {
-          h16 = fmx <= 32768.0f && (mn == 0x7f800000u || fmn >= 6.103515625e-05f);
-        } else {
-          h16 = fmx <= 32768.0f && (fmx == 0.0f || fmx >= 0.0078125f);
-        }
-        if (tid == 0) S.fmt16[s] = h16 ? 1u : 0u;
-      }
-      // B tiles: row tid holds the chunk's 32 samples of channel c
-      {
-        const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
-#pragma unroll
-        for (int q = 0; q < kK / 8; ++q) {
-          uint32_t h2[4], l2[4];
-#pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            uint16_t h0, l0, h1, l1;
-            const uint32_t x0 = x[q * 8 + e], x1 = x[q * 8 + e + 1];
-            if (J.dtype == HEGRID_F16 || (J.dtype == HEGRID_BF16 && !h16)) {
-              h0 = (uint16_t)x0;  // stored format already matches the chunk format
-              h1 = (uint16_t)x1;
-              l0 = l1 = 0;
-            } else {
-              const float v0 = value_of(x0, J.dtype), v1 = value_of(x1, J.dtype);
-              if (h16) {
-                split_f16(v0, h0, l0);
-                split_f16(v1, h1, l1);
-              } else {
-                split_bf16(v0, h0, l0);
-                split_bf16(v1, h1, l1);
-              }
-            }
-            h2[e / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            l2[e / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
-          }
-          st_shared_v4(bh + sw64(tid, q), h2[0], h2[1], h2[2], h2[3]);
-          if (vsplit) st_shared_v4(bl + sw64(tid, q), l2[0], l2[1], l2[2], l2[3]);
-        }
-      }
-      // A tiles: scatter the chunk's weight entries
-      {
-        uint8_t* ah = S.A[s][0];
-        uint8_t* al = S.A[s][1];
-        auto put = [&](uint32_t ck, float w) {
-          const int r = (int)(ck >> 6), k = (int)(ck & 31u);
-          uint16_t hi, lo;
-          if (h16)
-            split_f16(w, hi, lo);
-          else
-            split_bf16(w, hi, lo);
-          const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
-          *reinterpret_cast<uint16_t*>(ah + off) = hi;
-          if (split) *reinterpret_cast<uint16_t*>(al + off) = lo;
-        };
-#pragma unroll
-        for (int i = 0; i < kPre; ++i)
-          if (pck[i] != 0xffffffffu) put(pck[i], pw[i]);
-        for (int64_t e = e_lo + tid + (int64_t)kPre * kProducers; e < e_hi; e += kProducers)
-          put(pv.ent_ck[e], pv.ent_w[e]);
-      }
-      e_lo = e_hi;
-      e_hi = e_next;
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.ab_full[s]);
+      bail = !ok;
     }
     if (bail) break;
 
