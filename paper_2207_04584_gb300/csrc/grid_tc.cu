@@ -154,8 +154,19 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
   const PlanView& pv = J.pv;
   const bool cvalid = c0 + tid < J.C;  // this thread's channel = B row `tid`
   const int64_t sub0 = kb0 / 32;
+  // Weight entries are software-pipelined one chunk ahead: while chunk j is
+  // converted, the loads of chunk j+1's entries are in flight.
   int64_t e_lo = pv.sub_off[sub0];
   int64_t e_hi = pv.sub_off[sub0 + 1];
+  int64_t e_nx = n_chunks > 1 ? pv.sub_off[sub0 + 2] : e_hi;
+  uint32_t pck[kPre];
+  float pw[kPre];
+#pragma unroll
+  for (int i = 0; i < kPre; ++i) {
+    const int64_t e = e_lo + tid + (int64_t)i * kProducers;
+    pck[i] = e < e_hi ? (uint32_t)__ldcs(pv.ent_ck + e) : 0xffffffffu;
+    pw[i] = e < e_hi ? __ldcs(pv.ent_w + e) : 0.0f;
+  }
   constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
   constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
   constexpr uint32_t kBits2m14 = 0x38800000u;    // 2^-14 (smallest normal FP16)
@@ -163,17 +174,16 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
   for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
     const int s = g % kStages;
     const int rs = gr % kRawStages;
-    // The chunk's weight entries (streaming loads, issued before the stage
-    // waits so that their latency overlaps them).
-    uint32_t pck[kPre];
-    float pw[kPre];
+    // Next chunk's entries (streaming loads, consumed one iteration later).
+    uint32_t nck[kPre];
+    float nw[kPre];
 #pragma unroll
     for (int i = 0; i < kPre; ++i) {
-      const int64_t e = e_lo + tid + (int64_t)i * kProducers;
-      pck[i] = e < e_hi ? (uint32_t)__ldcs(pv.ent_ck + e) : 0xffffffffu;
-      pw[i] = e < e_hi ? __ldcs(pv.ent_w + e) : 0.0f;
+      const int64_t e = e_hi + tid + (int64_t)i * kProducers;
+      nck[i] = e < e_nx ? (uint32_t)__ldcs(pv.ent_ck + e) : 0xffffffffu;
+      nw[i] = e < e_nx ? __ldcs(pv.ent_w + e) : 0.0f;
     }
-    const int64_t e_next = j + 1 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 2) : 0;
+    const int64_t e_nx2 = j + 2 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 3) : e_nx;
     if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
     // Channel column `tid` of the staged rows.
@@ -293,7 +303,13 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         put(__ldcs(pv.ent_ck + e), __ldcs(pv.ent_w + e));
     }
     e_lo = e_hi;
-    e_hi = e_next;
+    e_hi = e_nx;
+    e_nx = e_nx2;
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      pck[i] = nck[i];
+      pw[i] = nw[i];
+    }
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.ab_full[s]);
@@ -486,12 +502,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(out + cbase + i) =
-                  make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+              __stcs(reinterpret_cast<float4*>(out + cbase + i),
+                     make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (cbase + i < C) out[cbase + i] = v[i];
+              if (cbase + i < C) __stcs(out + cbase + i, v[i]);
           }
         }
       }
