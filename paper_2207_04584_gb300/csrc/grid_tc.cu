@@ -117,6 +117,22 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                : "memory");
 }
 
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u16(uint32_t addr) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_shared_u16(uint32_t addr, uint16_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+
 __device__ __forceinline__ void named_bar_producers() {
   asm volatile("bar.sync 1, %0;" ::"r"(kProducers) : "memory");
 }
@@ -189,14 +205,13 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     // Channel column `tid` of the staged rows.
     uint32_t x[kK];
     {
-      const uint8_t* rb = S.raw[rs];
+      const uint32_t rb = smem_u32(S.raw[rs]);
 #pragma unroll
       for (int k = 0; k < kK; ++k) {
         if (kWide)
-          x[k] = cvalid ? *reinterpret_cast<const uint32_t*>(rb + k * kRawPitch + tid * 4) : 0u;
+          x[k] = cvalid ? ld_shared_u32(rb + k * kRawPitch + tid * 4) : 0u;
         else
-          x[k] = cvalid ? (uint32_t)*reinterpret_cast<const uint16_t*>(rb + k * kRawPitch + tid * 2)
-                        : 0u;
+          x[k] = cvalid ? ld_shared_u16(rb + k * kRawPitch + tid * 2) : 0u;
       }
     }
     __syncwarp();
@@ -224,13 +239,11 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     }
     // A tiles: zero (the scatter follows the barrier)
     {
-      uint4* ah = reinterpret_cast<uint4*>(S.A[s][0]);
-      uint4* al = reinterpret_cast<uint4*>(S.A[s][1]);
-      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
 #pragma unroll
       for (int i = tid; i < kM * 64 / 16; i += kProducers) {
-        ah[i] = z;
-        if (SPLIT) al[i] = z;
+        st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
+        if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
       }
     }
     named_bar_producers();
@@ -283,8 +296,7 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     }
     // A tiles: scatter the chunk's weight entries
     {
-      uint8_t* ah = S.A[s][0];
-      uint8_t* al = S.A[s][1];
+      const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
       auto put = [&](uint32_t ck, float w) {
         const int r = (int)(ck >> 6), k = (int)(ck & 31u);
         uint16_t hi, lo;
@@ -293,8 +305,8 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         else
           split_bf16(w, hi, lo);
         const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
-        *reinterpret_cast<uint16_t*>(ah + off) = hi;
-        if (SPLIT) *reinterpret_cast<uint16_t*>(al + off) = lo;
+        st_shared_u16(ah + off, hi);
+        if (SPLIT) st_shared_u16(al + off, lo);
       };
 #pragma unroll
       for (int i = 0; i < kPre; ++i)
@@ -319,9 +331,10 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
 
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
   extern __shared__ unsigned char smem_raw[];
-  // 64B-swizzled tiles need 512-byte alignment (the swizzle atom)
-  TcSmem& S = *reinterpret_cast<TcSmem*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 511) & ~(uintptr_t)511);
+  // 64B-swizzled tiles need 512-byte alignment (the swizzle atom); offsetting
+  // smem_raw (not an integer round trip) keeps the shared address space.
+  const uint32_t pad = (512u - (smem_u32(smem_raw) & 511u)) & 511u;
+  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw + pad);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* err = jt.job[0].pv.err_word;
 
