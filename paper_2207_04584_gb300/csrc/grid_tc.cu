@@ -19,14 +19,14 @@
 // normalised by the sum of exactly the quantised weights that produced S.
 //
 // Warp roles (one CTA per SM, persistent over work items):
-//   warp 9      stages the chunk's 32 sample rows (raw, as stored) into a
+//   warp 17     stages the chunk's 32 sample rows (raw, as stored) into a
 //               4-deep shared-memory ring with bulk async copies (TMA
 //               engine), one row per lane;
-//   warps 0-7   convert a staged chunk into the B tiles (row = channel),
-//               scatter the chunk's weight entries into the A tiles (2-deep
-//               ring), and warps 0-3 run the epilogue (TMEM -> registers ->
-//               S / W -> global);
-//   warp 8      allocates TMEM and issues the MMAs (one lane).
+//   warps 0-15  convert a staged chunk into the B tiles (row = channel, two
+//               threads per row), scatter the chunk's weight entries into the
+//               A tiles (2-deep ring), and warps 0-3 run the epilogue (TMEM ->
+//               registers -> S / W -> global);
+//   warp 16     allocates TMEM and issues the MMAs (one lane).
 // Hand-offs use mbarriers; MMA completion is signalled by tcgen05.commit.
 // Every wait is bounded (global timer) and reports a timeout through the
 // plan's error word.
@@ -42,11 +42,11 @@
 namespace hg {
 namespace {
 
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
-constexpr int kMmaWarp = 8;
-constexpr int kTmaWarp = 9;
-constexpr int kThreads = 10 * 32;
+constexpr int kMmaWarp = kProducerWarps;
+constexpr int kTmaWarp = kProducerWarps + 1;
+constexpr int kThreads = (kProducerWarps + 2) * 32;
 constexpr int kK = 32;                     // candidates per chunk (64-byte rows of 16-bit values)
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
@@ -56,7 +56,9 @@ constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst c
 constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
 constexpr uint32_t kWCol = 256;
 constexpr int kBand = 8;                   // blocks per band of the work order
-constexpr int kPre = 8;                    // weight entries prefetched per producer thread
+constexpr int kPre = 4;                    // weight entries prefetched per producer thread
+constexpr int kHalves = kProducers / kN;   // producer threads per B row
+constexpr int kKT = kK / kHalves;          // samples of a row converted per thread
 
 struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
@@ -157,7 +159,7 @@ __device__ __forceinline__ void split2(float v0, float v1, bool h16, uint32_t& h
 
 __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uint_as_float(b16 << 16); }
 
-// Producer side of one work item (warps 0-7): for every chunk, convert the
+// Producer side of one work item (warps 0-15): for every chunk, convert the
 // staged rows into the B tiles and scatter the weight entries into the A
 // tiles.  DT is the stored value type; SPLIT selects the hi/lo form.
 // Returns false if a bounded wait gave up.
@@ -167,8 +169,9 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row = tid % kN, kh = tid / kN;  // B row (channel c0 + row), half of the chunk
   const PlanView& pv = J.pv;
-  const bool cvalid = c0 + tid < J.C;  // this thread's channel = B row `tid`
+  const bool cvalid = c0 + row < J.C;
   const int64_t sub0 = kb0 / 32;
   // Weight entries are software-pipelined one chunk ahead: while chunk j is
   // converted, the loads of chunk j+1's entries are in flight.
@@ -202,16 +205,16 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     const int64_t e_nx2 = j + 2 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 3) : e_nx;
     if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
-    // Channel column `tid` of the staged rows.
-    uint32_t x[kK];
+    // Channel column `row` of this thread's half of the staged rows.
+    uint32_t x[kKT];
     {
-      const uint32_t rb = smem_u32(S.raw[rs]);
+      const uint32_t rb = smem_u32(S.raw[rs]) + kh * kKT * kRawPitch;
 #pragma unroll
-      for (int k = 0; k < kK; ++k) {
+      for (int k = 0; k < kKT; ++k) {
         if (kWide)
-          x[k] = cvalid ? ld_shared_u32(rb + k * kRawPitch + tid * 4) : 0u;
+          x[k] = cvalid ? ld_shared_u32(rb + k * kRawPitch + row * 4) : 0u;
         else
-          x[k] = cvalid ? ld_shared_u16(rb + k * kRawPitch + tid * 2) : 0u;
+          x[k] = cvalid ? ld_shared_u16(rb + k * kRawPitch + row * 2) : 0u;
       }
     }
     __syncwarp();
@@ -221,7 +224,7 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     if (DT != HEGRID_F16) {
       uint32_t mx = 0u, mn = kInf;
 #pragma unroll
-      for (int k = 0; k < kK; ++k) {
+      for (int k = 0; k < kKT; ++k) {
         uint32_t a;
         if (DT == HEGRID_F32)
           a = x[k] & 0x7fffffffu;
@@ -261,15 +264,17 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         h16 = mx <= kBits32768 && (mx == 0u || mx >= kBits2m7);
     }
     if (tid == 0) S.fmt16[s] = h16 ? 1u : 0u;
-    // B tiles: row tid holds the chunk's 32 samples of channel c0 + tid
+    // B tiles: row `row` holds the chunk's samples of channel c0 + row; this
+    // thread writes its half (16-byte chunks kh*kKT/8 ...).
     {
-      const uint32_t bh = smem_u32(S.B[s][0]) + 0u, bl = smem_u32(S.B[s][1]);
+      const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
-      for (int q = 0; q < kK / 8; ++q) {
+      for (int qq = 0; qq < kKT / 8; ++qq) {
+        const int q = kh * (kKT / 8) + qq;
         uint32_t h2[4], l2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const uint32_t x0 = x[q * 8 + 2 * e], x1 = x[q * 8 + 2 * e + 1];
+          const uint32_t x0 = x[qq * 8 + 2 * e], x1 = x[qq * 8 + 2 * e + 1];
           if (DT == HEGRID_F32) {
             split2(__uint_as_float(x0), __uint_as_float(x1), h16, h2[e], l2[e]);
           } else if (DT == HEGRID_BF16X2) {
@@ -290,8 +295,8 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
             l2[e] = 0u;
           }
         }
-        st_shared_v4(bh + sw64(tid, q), h2[0], h2[1], h2[2], h2[3]);
-        if (kVsplit) st_shared_v4(bl + sw64(tid, q), l2[0], l2[1], l2[2], l2[3]);
+        st_shared_v4(bh + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
+        if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
       }
     }
     // A tiles: scatter the chunk's weight entries
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       continue;
     }
 
-    // ---------------- producers (warps 0-7) ----------------
+    // ---------------- producers (warps 0-15) ----------------
     {
       bool ok = true;
       if (split) {
