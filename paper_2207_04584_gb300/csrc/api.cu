@@ -220,14 +220,15 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
     if (scomp) cudaStreamSynchronize(scomp);
     if (sout) cudaStreamSynchronize(sout);
     for (int i = 0; i < 2; ++i) {
-      cudaFree(dv[i]);
-      cudaFree(dm[i]);
+      if (dv[i]) cudaFreeAsync(dv[i], scomp);
+      if (dm[i]) cudaFreeAsync(dm[i], scomp);
       if (ev_in[i]) cudaEventDestroy(ev_in[i]);
       if (ev_k[i]) cudaEventDestroy(ev_k[i]);
       if (ev_out[i]) cudaEventDestroy(ev_out[i]);
       if (ev_free[i]) cudaEventDestroy(ev_free[i]);
     }
-    cudaFree(dw);
+    if (dw) cudaFreeAsync(dw, scomp);
+    if (scomp) cudaStreamSynchronize(scomp);
     if (sin) cudaStreamDestroy(sin);
     if (scomp) cudaStreamDestroy(scomp);
     if (sout) cudaStreamDestroy(sout);
@@ -242,17 +243,23 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
       return st;                                                               \
     }                                                                          \
   } while (0)
+  HG_STREAM_TRY(cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking));
   for (int i = 0; i < 2; ++i) {
-    HG_STREAM_TRY(cudaMalloc(&dv[i], vbytes));
-    HG_STREAM_TRY(cudaMalloc((void**)&dm[i], mbytes));
+    HG_STREAM_TRY(hg::pool_alloc(&dv[i], vbytes, scomp));
+    HG_STREAM_TRY(hg::pool_alloc((void**)&dm[i], mbytes, scomp));
     HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming));
     HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_k[i], cudaEventDisableTiming));
     HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_out[i], cudaEventDisableTiming));
     HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_free[i], cudaEventDisableTiming));
   }
-  HG_STREAM_TRY(cudaMalloc((void**)&dw, sizeof(float) * M));
+  HG_STREAM_TRY(hg::pool_alloc((void**)&dw, sizeof(float) * M, scomp));
+  // the buffers are allocated on the compute stream; the copy-in stream starts after that
+  cudaEvent_t ev_alloc = nullptr;
+  HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming));
+  HG_STREAM_TRY(cudaEventRecord(ev_alloc, scomp));
   HG_STREAM_TRY(cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking));
-  HG_STREAM_TRY(cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking));
+  HG_STREAM_TRY(cudaStreamWaitEvent(sin, ev_alloc, 0));
+  cudaEventDestroy(ev_alloc);
   HG_STREAM_TRY(cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking));
   for (int k = 0; k < n_chunks; ++k) {
     const int r = k & 1;

@@ -29,6 +29,10 @@ void set_error(const std::string& msg);
 // Process-wide count of kernel launches made by the library.
 void count_launch(int n = 1);
 
+// Stream-ordered allocation from the library's per-device pool (freed blocks
+// are kept for reuse); release with cudaFreeAsync.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+
 #define HG_CUDA_TRY(expr)                                                           \
   do {                                                                              \
     cudaError_t _e = (expr);                                                        \

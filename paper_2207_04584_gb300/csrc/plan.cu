@@ -601,38 +601,67 @@ __global__ void k_pad_counts(const int32_t* __restrict__ kb, int64_t n, int64_t*
   if (i < n) out[i] = ((int64_t)kb[i] + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
 }
 
-template <typename T>
-static cudaError_t dmalloc(T** p, int64_t n, int64_t* bytes) {
-  size_t sz = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
-  *bytes += (int64_t)sz;
-  return cudaMalloc((void**)p, sz);
+// Device memory of plans comes from a library-owned, stream-ordered pool per
+// device whose release threshold keeps freed blocks for reuse, so repeated plan
+// creation does not pay for cudaMalloc/cudaFree.
+static cudaMemPool_t plan_pool() {
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
 }
 
 }  // namespace
 
-void free_plan_arrays(hegrid_plan* p) {
-  cudaFree(p->perm);
-  cudaFree(p->bin_off);
-  cudaFree(p->cand_off);
-  cudaFree(p->blk_pair_off);
-  cudaFree(p->cand_idx);
-  cudaFree(p->sub_off);
-  cudaFree(p->ent_ck);
-  cudaFree(p->ent_w);
-  cudaFree(p->wsum);
-  cudaFree(p->err_word);
+cudaError_t pool_alloc(void** p, size_t sz, cudaStream_t st) {
+  cudaMemPool_t pool = plan_pool();
+  if (!pool) return cudaMalloc(p, sz);
+  return cudaMallocFromPoolAsync(p, sz, pool, st);
 }
 
-// Temporary device buffers of plan_create, freed on every exit path.
+namespace {
+
+template <typename T>
+static cudaError_t dmalloc(T** p, int64_t n, int64_t* bytes, cudaStream_t st) {
+  size_t sz = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+  *bytes += (int64_t)sz;
+  return pool_alloc((void**)p, sz, st);
+}
+
+}  // namespace
+
+void free_plan_arrays(hegrid_plan* p, cudaStream_t st) {
+  void* arrays[] = {p->perm, p->bin_off, p->cand_off, p->blk_pair_off, p->cand_idx,
+                    p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->err_word};
+  for (void* a : arrays)
+    if (a) cudaFreeAsync(a, st);
+}
+
+// Temporary device buffers of plan_create, released (stream-ordered) on every
+// exit path.
 struct Scratch {
+  cudaStream_t st;
   std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
   ~Scratch() {
-    for (void* q : ptrs) cudaFree(q);
+    for (void* q : ptrs) cudaFreeAsync(q, st);
   }
   template <typename T>
   cudaError_t get(T** p, int64_t n) {
     size_t sz = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc((void**)p, sz);
+    cudaError_t e = pool_alloc((void**)p, sz, st);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
@@ -642,7 +671,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
                                 int coords_on_device, cudaStream_t st) {
   const int32_t N = (int32_t)p->N;
   const hegrid_map_geom& g = p->geom;
-  Scratch sc;
+  Scratch sc(st);
 
   // --- layout of the padded map (a2) -----------------------------------
   const double half_rows = 0.5 * (double)(g.ny - 1) * g.dlat_deg;
@@ -737,8 +766,8 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   }
   HG_CUDA_TRY(cudaGetLastError());
   int64_t bytes = 0;
-  HG_CUDA_TRY(dmalloc(&p->perm, N, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->bin_off, p->n_bins + 1, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->perm, N, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->bin_off, p->n_bins + 1, &bytes, st));
   HG_CUDA_TRY(cudaMemcpyAsync(p->perm, vin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
   k_bin_offsets<<<(N + 255) / 256, 256, 0, st>>>(kin, N, (uint32_t)p->n_bins, p->bin_off);
   count_launch();
@@ -817,8 +846,8 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(cudaGetLastError());
   int64_t* stmp64;
   HG_CUDA_TRY(sc.get(&stmp64, scan_tmp_elems(p->n_blocks + 1) + 8));
-  HG_CUDA_TRY(dmalloc(&p->cand_off, p->n_blocks + 1, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->blk_pair_off, p->n_blocks + 1, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->cand_off, p->n_blocks + 1, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->blk_pair_off, p->n_blocks + 1, &bytes, st));
   // exclusive scans over n+1 entries (last input 0): out[n] is the total
   k_pad_counts<<<(unsigned)((p->n_blocks + 1 + 255) / 256), 256, 0, st>>>(kb, p->n_blocks + 1, kbp);
   count_launch();
@@ -843,12 +872,12 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
 
   // --- a4 fill + a5 weights ------------------------------------------------
   const int64_t n_sub = p->n_cand / 32;
-  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->sub_off, n_sub + 1, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->wsum, kWsumVariants * p->M, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes));
-  HG_CUDA_TRY(dmalloc(&p->err_word, 4, &bytes));
+  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->sub_off, n_sub + 1, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->wsum, kWsumVariants * p->M, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->err_word, 4, &bytes, st));
   HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * kWsumVariants * p->M, st));
   HG_CUDA_TRY(cudaMemcpyAsync(p->sub_off + n_sub, p->blk_pair_off + p->n_blocks, sizeof(int64_t),
@@ -858,8 +887,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
       p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
-  // scratch is freed by ~Scratch; make sure the kernels that use it are done
-  HG_CUDA_TRY(cudaStreamSynchronize(st));
+  // scratch is released by ~Scratch, ordered after these kernels on `st`
   p->bytes = bytes;
   return HEGRID_OK;
 }
@@ -911,7 +939,8 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
   hegrid_status s = hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream);
   if (s != HEGRID_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
-    hg::free_plan_arrays(p);
+    hg::free_plan_arrays(p, (cudaStream_t)stream);
+    cudaStreamSynchronize((cudaStream_t)stream);
     delete p;
     return s;
   }
@@ -922,7 +951,7 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
 hegrid_status hegrid_plan_destroy(hegrid_plan* plan) {
   if (!plan) return HEGRID_OK;
   cudaDeviceSynchronize();
-  hg::free_plan_arrays(plan);
+  hg::free_plan_arrays(plan, nullptr);
   delete plan;
   return HEGRID_OK;
 }
