@@ -84,6 +84,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device=None):
+    """The largest of x over all ranks (x itself when not distributed)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, elapsed_max):
+    """Whole-job throughput of independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return world * units_per_rank / elapsed_max
+
+
 def cpu_oracle_sample(wl, frac_rows=20, nthreads=0):
     """Time the FP64 oracle on a bounded sample: every frac_rows-th map row,
     all channels; extrapolate to the full map as t_index + t_cells * M / cells."""
@@ -239,14 +255,10 @@ def main():
     if dist:
         dist.barrier()
     launches = (H.hegrid_launch_count() - launches0) // max(1, args.steps)
-    elapsed = t0.elapsed_time(t1) / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, dist, dev)
     t_plan = statistics.mean(a.elapsed_time(b) for a, b, c in ev) / 1e3
     t_grid = statistics.mean(b.elapsed_time(c) for a, b, c in ev) / 1e3
-    value = world * N * C * args.steps / elapsed
+    value = job_value(N * C * args.steps, world, elapsed)
 
     # plan facts and accuracy on sampled cells (vs the FP64 oracle)
     plan = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, 0, sh)

@@ -1,0 +1,156 @@
+"""GPU tests of the batching and streaming runtime (many fields in one
+persistent launch, the CUDA-graph batch, host-chunk streaming with
+copy/compute overlap) against single-field calls and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import map_error
+from paper_2207_04584_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_SPLIT = 5e-5
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_04584_gb300 import build
+    build.build()
+    from paper_2207_04584_gb300 import hegrid
+    hegrid.lib()
+    return hegrid
+
+
+def _fields(n_fields=6, seed=W.SEED_BASE + 4):
+    """A scaled-down config-4 batch: uneven N, map sizes, channels, dtypes."""
+    fields, _ = W.config4_fields(seed=seed, n_fields=n_fields, max_bytes=4e9,
+                                 n_range=(2e3, 3e4), side_choices=(24, 40, 64),
+                                 c_range=(4, 96))
+    return [W.field_samples(f) for f in fields]
+
+
+def _plan(H, wl):
+    return H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
+                                np.ascontiguousarray(wl["lat"]), 0, wl["geom"], wl["fwhm_deg"],
+                                3.0, 0, torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_values(wl, dtype_name):
+    v = torch.from_numpy(wl["values"])
+    C = v.shape[1]
+    if dtype_name == "bf16":
+        ld = (C + 7) // 8 * 8
+        d = torch.zeros((v.shape[0], ld), dtype=torch.bfloat16)
+        d[:, :C] = v.to(torch.bfloat16)
+        ref = d[:, :C].float().numpy()
+    else:
+        ld = (C + 3) // 4 * 4
+        d = torch.zeros((v.shape[0], ld), dtype=torch.float32)
+        d[:, :C] = v
+        ref = wl["values"]
+    return d.cuda(), ld, np.ascontiguousarray(ref)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_uneven_fields(H, use_graph):
+    wls = _fields()
+    plans, args, refs, outs = [], [], [], []
+    n_f32 = 0
+    try:
+        for wl in wls:
+            plans.append(_plan(H, wl))
+            C = wl["values"].shape[1]
+            M = wl["geom"]["nx"] * wl["geom"]["ny"]
+            dv, ld, refv = _dev_values(wl, wl["dtype"])
+            out = torch.full((M, C), -7.0, device="cuda")
+            wout = torch.full((M,), -7.0, device="cuda")
+            mode = H.HEGRID_MODE_TC_SPLIT
+            if wl["dtype"] == "f32":
+                mode = H.HEGRID_MODE_FP32 if n_f32 % 2 == 0 else H.HEGRID_MODE_TC_SPLIT
+                n_f32 += 1
+            dt = H.HEGRID_BF16 if wl["dtype"] == "bf16" else H.HEGRID_F32
+            args.append({"values": dv, "dtype": dt, "n_channels": C, "ld_values": ld,
+                         "map_out": out, "ld_map": C, "weight_out": wout, "mode": mode})
+            outs.append((out, wout, dv))
+            refs.append(refv)
+        s = torch.cuda.current_stream().cuda_stream
+        if use_graph:
+            batch = H.hegrid_batch_create(plans, args, s)
+            try:
+                for _ in range(2):  # replays are idempotent
+                    for o, w, _ in outs:
+                        o.fill_(-7.0)
+                    H.hegrid_batch_launch(batch, s)
+                    torch.cuda.synchronize()
+            finally:
+                H.hegrid_batch_destroy(batch)
+        else:
+            H.hegrid_grid_batched(plans, args, s)
+            torch.cuda.synchronize()
+        for p in plans:
+            H.hegrid_status_poll(p)
+        for wl, a, (o, w, _), refv in zip(wls, args, outs, refs):
+            ref, Wref = oracle.Index(wl["lon"], wl["lat"], wl["geom"], wl["fwhm_deg"]).grid(refv)
+            got = o.cpu().numpy()
+            err, _, _ = map_error(got, ref, Wref)
+            tol = TOL_F32 if a["mode"] == H.HEGRID_MODE_FP32 else TOL_SPLIT
+            assert err <= tol, (wl["name"], a["mode"], err)
+            assert np.array_equal(np.isnan(got), np.isnan(ref))
+    finally:
+        for p in plans:
+            H.hegrid_plan_destroy(p)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tc_split"])
+def test_stream_host_chunks(H, mode):
+    """Config-5 shape at small scale: channel chunks in pinned host memory."""
+    wl = W.config5(size_deg=0.4, target_n=60000)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    n_chunks, cc = 5, 12
+    chunks = [W.config5_chunk(wl, k, C_chunk=cc) for k in range(n_chunks)]
+    host = [torch.from_numpy(c).pin_memory() for c in chunks]
+    hmap = torch.full((M, n_chunks * cc + 3), -7.0).pin_memory()
+    hw = torch.zeros(M).pin_memory()
+    md = H.HEGRID_MODE_FP32 if mode == "fp32" else H.HEGRID_MODE_TC_SPLIT
+    plan = _plan(H, wl)
+    try:
+        H.hegrid_grid_stream(plan, host, cc, H.HEGRID_F32, md, hmap, n_chunks * cc + 3, hw)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    allv = np.ascontiguousarray(np.concatenate(chunks, axis=1))
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(allv)
+    got = hmap.numpy()
+    err, _, _ = map_error(got[:, :n_chunks * cc], ref, Wref)
+    assert err <= (TOL_F32 if mode == "fp32" else TOL_SPLIT), err
+    assert np.all(got[:, n_chunks * cc:] == -7.0)
+    assert np.allclose(hw.numpy(), Wref, rtol=2e-5, atol=0)
+
+
+def test_stream_matches_device_call(H):
+    """Streaming the channels in chunks gives the device call's map bit for bit
+    (same kernels, same per-chunk tiles)."""
+    wl = W.config1(n=8000, C=64, nx=48, ny=48)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    plan = _plan(H, wl)
+    try:
+        s = torch.cuda.current_stream().cuda_stream
+        out = torch.empty((M, 64), device="cuda")
+        H.hegrid_grid(plan, torch.from_numpy(wl["values"]).cuda(), H.HEGRID_F32, 64, 64, out, 64,
+                      None, H.HEGRID_MODE_FP32, s)
+        torch.cuda.synchronize()
+        chunks = [torch.from_numpy(np.ascontiguousarray(wl["values"][:, k * 16:(k + 1) * 16]))
+                  .pin_memory() for k in range(4)]
+        hmap = torch.empty((M, 64)).pin_memory()
+        H.hegrid_grid_stream(plan, chunks, 16, H.HEGRID_F32, H.HEGRID_MODE_FP32, hmap, 64)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    a, b = out.cpu().numpy(), hmap.numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
