@@ -77,14 +77,19 @@ hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStrea
   return HEGRID_OK;
 }
 
+// wait_ready: make `s` wait for each plan's creation (false inside a graph
+// capture, where the caller has synchronised the plans on the host instead).
 hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args* args,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool wait_ready = true) {
   HG_ARG_CHECK(n >= 0, "n must be >= 0");
   HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
   std::vector<GridJob> f32, tc;
   for (int i = 0; i < n; ++i) {
     hegrid_status st = check_args(plans[i], args[i]);
     if (st != HEGRID_OK) return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (wait_ready) HG_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ready, 0));
     if (args[i].mode == HEGRID_MODE_FP32)
       f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
     else
@@ -140,6 +145,8 @@ hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const*
     hegrid_status st = hg::check_args(plans ? plans[i] : nullptr, args[i]);
     if (st != HEGRID_OK) return st;
   }
+  // the plans must be complete before their launches are recorded
+  for (int i = 0; i < n; ++i) HG_CUDA_TRY(cudaEventSynchronize(plans[i]->ready));
   cudaStream_t cap;
   HG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   hegrid_batch* b = new hegrid_batch();
@@ -148,7 +155,7 @@ hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const*
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   hegrid_status st = HEGRID_OK;
   if (e == cudaSuccess) {
-    st = hg::grid_many(n, plans, args, cap);
+    st = hg::grid_many(n, plans, args, cap, false);
     cudaError_t e2 = cudaStreamEndCapture(cap, &b->graph);
     if (st == HEGRID_OK && e2 != cudaSuccess) e = e2;
   }

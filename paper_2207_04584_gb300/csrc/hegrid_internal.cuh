@@ -87,6 +87,10 @@ struct hegrid_plan {
   float* wsum;
   int32_t* err_word;
   int64_t bytes;
+  // Recorded on the creation stream after the last plan kernel.  The plan's
+  // memory comes from a stream-ordered pool, so every other stream must wait
+  // on this event before touching it.
+  cudaEvent_t ready;
   hg::PlanView view() const {
     hg::PlanView v;
     v.nx = geom.nx;

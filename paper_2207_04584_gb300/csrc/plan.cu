@@ -887,6 +887,8 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
       p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming));
+  HG_CUDA_TRY(cudaEventRecord(p->ready, st));
   // scratch is released by ~Scratch, ordered after these kernels on `st`
   p->bytes = bytes;
   return HEGRID_OK;
@@ -941,6 +943,7 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
     cudaStreamSynchronize((cudaStream_t)stream);
     hg::free_plan_arrays(p, (cudaStream_t)stream);
     cudaStreamSynchronize((cudaStream_t)stream);
+    if (p->ready) cudaEventDestroy(p->ready);
     delete p;
     return s;
   }
@@ -952,6 +955,8 @@ hegrid_status hegrid_plan_destroy(hegrid_plan* plan) {
   if (!plan) return HEGRID_OK;
   cudaDeviceSynchronize();
   hg::free_plan_arrays(plan, nullptr);
+  cudaStreamSynchronize(nullptr);
+  if (plan->ready) cudaEventDestroy(plan->ready);
   delete plan;
   return HEGRID_OK;
 }
@@ -1029,6 +1034,7 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
 
 hegrid_status hegrid_status_poll(const hegrid_plan* plan) {
   HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  HG_CUDA_TRY(cudaEventSynchronize(plan->ready));
   int32_t w = 0;
   HG_CUDA_TRY(cudaMemcpy(&w, plan->err_word, sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (w != 0) {
