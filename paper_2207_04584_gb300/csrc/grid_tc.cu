@@ -15,8 +15,11 @@
 // input, when FP16 holds every value exactly -- and BF16 (8-bit halves, ~2^-17
 // residual, full FP32 range) otherwise.  Chunks of one block may mix formats:
 // each MMA carries its own instruction descriptor and all accumulate in FP32.
-// W is accumulated by the same MMAs against a tile of ones, so the map is
-// normalised by the sum of exactly the quantised weights that produced S.
+// The tensor core's FP32 accumulation is not round-to-nearest: its error grows
+// with the number of MMAs added into one accumulator, so the main term and the
+// two small correction terms accumulate in separate TMEM regions and are added
+// once, in the epilogue.  W is summed by the producers in shared memory from
+// exactly the quantised weights that entered the MMAs.
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warp 17     stages the chunk's 32 sample rows (raw, as stored) into a
@@ -53,8 +56,8 @@ constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kRawStages = 4;              // staged sample rows ring
 constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst case)
-constexpr uint32_t kTmemCols = 512;        // S in [0,256), W in [256,272)
-constexpr uint32_t kWCol = 256;
+constexpr uint32_t kTmemCols = 512;        // main term in [0,256), corrections in [256,512)
+constexpr uint32_t kCorrCol = 256;
 constexpr int kBand = 8;                   // blocks per band of the work order
 constexpr int kPre = 4;                    // weight entries prefetched per producer thread
 constexpr int kHalves = kProducers / kN;   // producer threads per B row
@@ -63,7 +66,7 @@ constexpr int kKT = kK / kHalves;          // samples of a row converted per thr
 struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
-  uint8_t ones[2][16 * 64];            // [bf16, f16] all-ones B operand for W
+  float wacc[2][kM];                   // W of each cell, per item parity
   uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
   uint32_t red[kStages][kProducerWarps][2];  // max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
@@ -165,7 +168,8 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uin
 // Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT>
 __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_t kb0, int n_chunks,
-                                          int64_t c0, uint32_t& g, uint32_t& gr, int32_t* err) {
+                                          int64_t c0, uint32_t& g, uint32_t& gr, uint32_t par,
+                                          int32_t* err) {
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -248,6 +252,9 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
         if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
       }
+      // W of this item starts at zero (the other parity belongs to the
+      // previous item's epilogue)
+      if (j == 0 && tid < kM) S.wacc[par][tid] = 0.0f;
     }
     named_bar_producers();
     bool h16 = true;
@@ -305,13 +312,19 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
       auto put = [&](uint32_t ck, float w) {
         const int r = (int)(ck >> 6), k = (int)(ck & 31u);
         uint16_t hi, lo;
-        if (h16)
+        float wq;  // the weight exactly as the MMAs see it
+        if (h16) {
           split_f16(w, hi, lo);
-        else
+          wq = SPLIT ? __half2float(__ushort_as_half(hi)) + __half2float(__ushort_as_half(lo))
+                     : __half2float(__ushort_as_half(hi));
+        } else {
           split_bf16(w, hi, lo);
+          wq = SPLIT ? bf16_bits_to_float(hi) + bf16_bits_to_float(lo) : bf16_bits_to_float(hi);
+        }
         const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
         st_shared_u16(ah + off, hi);
         if (SPLIT) st_shared_u16(al + off, lo);
+        atomicAdd(&S.wacc[par][r], wq);
       };
 #pragma unroll
       for (int i = 0; i < kPre; ++i)
@@ -334,7 +347,7 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
+__global__ void __maxnreg__(112) k_grid_tc(const __grid_constant__ JobTable jt) {
   extern __shared__ unsigned char smem_raw[];
   // 64B-swizzled tiles need 512-byte alignment (the swizzle atom); offsetting
   // smem_raw (not an integer round trip) keeps the shared address space.
@@ -356,12 +369,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     mbar_init(&S.tfree, 4);
     fence_mbar_init();
   }
-  // ones tiles (bf16 1.0 = 0x3f80, f16 1.0 = 0x3c00)
-  for (int i = tid; i < 16 * 64 / 4; i += kThreads) {
-    reinterpret_cast<uint32_t*>(S.ones[0])[i] = 0x3f803f80u;
-    reinterpret_cast<uint32_t*>(S.ones[1])[i] = 0x3c003c00u;
-  }
-  fence_proxy_async_smem();
   if (warp == kMmaWarp) {
     tmem_alloc(&S.tmem_base, kTmemCols);
     tmem_relinquish();
@@ -417,8 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       if (n_chunks > 0) {
         if (n_tm > 0 && !mbar_wait(&S.tfree, (n_tm - 1) & 1u, err)) bail = true;
         tc_fence_after();
-        const uint32_t idS16 = idesc_f16(0u, kM, kN), idW16 = idesc_f16(0u, kM, 16);
-        const uint32_t idSbf = idesc_f16(1u, kM, kN), idWbf = idesc_f16(1u, kM, 16);
+        const uint32_t idS16 = idesc_f16(0u, kM, kN), idSbf = idesc_f16(1u, kM, kN);
         for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
           const int s = g % kStages;
           if (!mbar_wait(&S.ab_full[s], (g / kStages) & 1u, err)) {
@@ -428,24 +434,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           tc_fence_after();
           if (lane == 0) {
             const bool h = S.fmt16[s] != 0u;
-            const uint32_t idS = h ? idS16 : idSbf, idW = h ? idW16 : idWbf;
+            const uint32_t idS = h ? idS16 : idSbf;
             const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
             const uint32_t b_hi = smem_u32(S.B[s][0]), b_lo = smem_u32(S.B[s][1]);
-            const uint32_t on = smem_u32(S.ones[h ? 1 : 0]);
 #pragma unroll
             for (int kk = 0; kk < kK / 16; ++kk) {
               const uint32_t o = kk * 32;
               const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
               tc_mma_f16(tmem, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_hi + o), idS, acc);
               if (vsplit)
-                tc_mma_f16(tmem, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_lo + o), idS, 1u);
+                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw64(a_hi + o),
+                           smem_desc_k_sw64(b_lo + o), idS, acc);
               if (split)
-                tc_mma_f16(tmem, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(b_hi + o), idS, 1u);
-              tc_mma_f16(tmem + kWCol, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(on + o), idW,
-                         acc);
-              if (split)
-                tc_mma_f16(tmem + kWCol, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(on + o),
-                           idW, 1u);
+                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw64(a_lo + o),
+                           smem_desc_k_sw64(b_hi + o), idS, vsplit ? 1u : acc);
             }
             tc_commit(&S.ab_empty[s]);
             if (j == n_chunks - 1) tc_commit(&S.done);
@@ -462,20 +464,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       bool ok = true;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
         }
       }
       bail = !ok;
+      // every producer's W atomics of this item are done before the epilogue
+      if (!bail && n_chunks > 0) named_bar_producers();
     }
     if (bail) break;
 
@@ -503,28 +507,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       ++n_tm;
       tc_fence_after();
       const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-      uint32_t r[32];
-      tmem_ld_32x32b_x32(tl + kWCol, r);
-      tmem_ld_wait();
-      const float W = __uint_as_float(r[0]);
+      const float W = S.wacc[(n_tm - 1) & 1u][row];
       const bool ok = W > 0.0f;
+      uint32_t r[16], rc[16];
 #pragma unroll 1
-      for (int cb = 0; cb < kN / 32; ++cb) {
-        tmem_ld_32x32b_x32(tl + cb * 32, r);
+      for (int cb = 0; cb < kN / 16; ++cb) {
+        tmem_ld_32x32b_x16(tl + cb * 16, r);
+        if (split) tmem_ld_32x32b_x16(tl + kCorrCol + cb * 16, rc);
         tmem_ld_wait();
         if (active) {
-          const int64_t cbase = c0 + cb * 32;
-          float v[32];
+          const int64_t cbase = c0 + cb * 16;
+          float v[16];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = ok ? __fdiv_rn(__uint_as_float(r[i]), W) : qnan;
-          if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
+          for (int i = 0; i < 16; ++i) {
+            const float sum = split ? __fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i]))
+                                    : __uint_as_float(r[i]);
+            v[i] = ok ? __fdiv_rn(sum, W) : qnan;
+          }
+          if (cbase + 16 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
+            for (int i = 0; i < 16; i += 4)
               __stcs(reinterpret_cast<float4*>(out + cbase + i),
                      make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
           } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
+            for (int i = 0; i < 16; ++i)
               if (cbase + i < C) __stcs(out + cbase + i, v[i]);
           }
         }
