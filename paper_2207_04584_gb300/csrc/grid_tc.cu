@@ -347,7 +347,7 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
   return true;
 }
 
-__global__ void __maxnreg__(104) k_grid_tc(const __grid_constant__ JobTable jt) {
+__global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
   extern __shared__ unsigned char smem_raw[];
   // 64B-swizzled tiles need 512-byte alignment (the swizzle atom); offsetting
   // smem_raw (not an integer round trip) keeps the shared address space.
