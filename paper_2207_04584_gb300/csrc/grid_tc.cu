@@ -15,21 +15,24 @@
 // input, when FP16 holds every value exactly -- and BF16 (8-bit halves, ~2^-17
 // residual, full FP32 range) otherwise.  Chunks of one block may mix formats:
 // each MMA carries its own instruction descriptor and all accumulate in FP32.
-// The tensor core's FP32 accumulation is not round-to-nearest: its error grows
-// with the number of MMAs added into one accumulator, so the main term and the
-// two small correction terms accumulate in separate TMEM regions and are added
-// once, in the epilogue.  W is summed by the producers in shared memory from
-// exactly the quantised weights that entered the MMAs.
+// The tensor core's FP32 accumulate loses about 2^-22 of the running sum per
+// MMA (measured; it grows with the number of MMAs added into one accumulator),
+// so a block's sum is built in segments of kSeg chunks: segment 0 accumulates
+// into a "total" TMEM region, later segments into a "segment" region that the
+// drain warps add into the total with FP32 round-to-nearest adds (tcgen05
+// ld/st).  W is summed by the producers in shared memory from exactly the
+// quantised weights that entered the MMAs.
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warp 17     stages the chunk's 32 sample rows (raw, as stored) into a
 //               4-deep shared-memory ring with bulk async copies (TMA
 //               engine), one row per lane;
 //   warps 0-15  convert a staged chunk into the B tiles (row = channel, two
-//               threads per row), scatter the chunk's weight entries into the
-//               A tiles (2-deep ring), and warps 0-3 run the epilogue (TMEM ->
-//               registers -> S / W -> global);
-//   warp 16     allocates TMEM and issues the MMAs (one lane).
+//               threads per row) and scatter the chunk's weight entries into
+//               the A tiles (2-deep ring);
+//   warp 16     allocates TMEM and issues the MMAs (one lane);
+//   warps 18-21 drain finished segments into the running total and run the
+//               epilogue (TMEM -> registers -> S / W -> global).
 // Hand-offs use mbarriers; MMA completion is signalled by tcgen05.commit.
 // Every wait is bounded (global timer) and reports a timeout through the
 // plan's error word.
@@ -49,15 +52,17 @@ constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
 constexpr int kMmaWarp = kProducerWarps;
 constexpr int kTmaWarp = kProducerWarps + 1;
-constexpr int kThreads = (kProducerWarps + 2) * 32;
+constexpr int kDrainWarp0 = kProducerWarps + 2;  // 4 warps: drains and epilogue
+constexpr int kThreads = (kProducerWarps + 6) * 32;
 constexpr int kK = 32;                     // candidates per chunk (64-byte rows of 16-bit values)
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kRawStages = 4;              // staged sample rows ring
 constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst case)
-constexpr uint32_t kTmemCols = 512;        // main term in [0,256), corrections in [256,512)
-constexpr uint32_t kCorrCol = 256;
+constexpr uint32_t kTmemCols = 512;        // segment sums in [0,256), running total in [256,512)
+constexpr uint32_t kTotCol = 256;
+constexpr int kSeg = 16;                   // chunks per accumulation segment
 constexpr int kBand = 8;                   // blocks per band of the work order
 constexpr int kPre = 4;                    // weight entries prefetched per producer thread
 constexpr int kHalves = kProducers / kN;   // producer threads per B row
@@ -66,12 +71,13 @@ constexpr int kKT = kK / kHalves;          // samples of a row converted per thr
 struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
-  float wacc[2][kM];                   // W of each cell, per item parity
+  float wacc[4][kM];                   // W of each cell, per item (mod 4)
   uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
   uint32_t red[kStages][kProducerWarps][2];  // max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t raw_full[kRawStages], raw_empty[kRawStages];
-  uint64_t ab_full[kStages], ab_empty[kStages], done, tfree;
+  uint64_t ab_full[kStages], ab_empty[kStages];
+  uint64_t segdone, segfree, totfree, wready[4];
   uint32_t tmem_base;
 };
 
@@ -365,8 +371,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       mbar_init(&S.ab_full[i], kProducerWarps);
       mbar_init(&S.ab_empty[i], 1);
     }
-    mbar_init(&S.done, 1);
-    mbar_init(&S.tfree, 4);
+    mbar_init(&S.segdone, 1);
+    mbar_init(&S.segfree, 4);
+    mbar_init(&S.totfree, 4);
+    for (int i = 0; i < 4; ++i) mbar_init(&S.wready[i], 1);
     fence_mbar_init();
   }
   if (warp == kMmaWarp) {
@@ -382,6 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   uint32_t g = 0;     // chunks through the A/B ring so far
   uint32_t gr = 0;    // chunks through the raw ring so far
   uint32_t n_tm = 0;  // items that used TMEM so far
+  uint32_t n_sg = 0;  // accumulation segments so far (segdone / segfree phases)
 
   for (int64_t item = blockIdx.x; item < jt.n_items && !bail; item += gridDim.x) {
     const GridJob& J = jt.job[find_job(jt, item)];
@@ -392,6 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int64_t C = J.C;
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kK);
+    const int n_seg = (n_chunks + kSeg - 1) / kSeg;
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
     const int eb = (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) ? 4 : 2;
@@ -421,71 +431,67 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
 
     if (warp == kMmaWarp) {
       // ---------------- MMA issuer ----------------
-      if (n_chunks > 0) {
-        if (n_tm > 0 && !mbar_wait(&S.tfree, (n_tm - 1) & 1u, err)) bail = true;
-        tc_fence_after();
-        const uint32_t idS16 = idesc_f16(0u, kM, kN), idSbf = idesc_f16(1u, kM, kN);
-        for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
-          const int s = g % kStages;
-          if (!mbar_wait(&S.ab_full[s], (g / kStages) & 1u, err)) {
-            bail = true;
-            break;
+      if (n_chunks == 0) continue;
+      const uint32_t idS16 = idesc_f16(0u, kM, kN), idSbf = idesc_f16(1u, kM, kN);
+      uint32_t dcol = kTotCol;
+      for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
+        const int s = g % kStages;
+        const int q = j / kSeg;
+        const bool seg_start = j % kSeg == 0;
+        const bool seg_end = j % kSeg == kSeg - 1 || j == n_chunks - 1;
+        if (seg_start) {
+          // segment 0 writes the total (free once the previous epilogue read
+          // it); later segments write the segment region (free once drained)
+          // (the drains acknowledge every segment in order, so waiting for the
+          // previous one also means the segment region has been drained)
+          if (q == 0) {
+            dcol = kTotCol;
+            if (n_tm > 0 && !mbar_wait(&S.totfree, (n_tm - 1) & 1u, err)) bail = true;
+          } else {
+            dcol = 0;
+            if (!mbar_wait(&S.segfree, (n_sg - 1) & 1u, err)) bail = true;
           }
           tc_fence_after();
-          if (lane == 0) {
-            const bool h = S.fmt16[s] != 0u;
-            const uint32_t idS = h ? idS16 : idSbf;
-            const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
-            const uint32_t b_hi = smem_u32(S.B[s][0]), b_lo = smem_u32(S.B[s][1]);
-#pragma unroll
-            for (int kk = 0; kk < kK / 16; ++kk) {
-              const uint32_t o = kk * 32;
-              const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-              tc_mma_f16(tmem, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_hi + o), idS, acc);
-              if (vsplit)
-                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw64(a_hi + o),
-                           smem_desc_k_sw64(b_lo + o), idS, acc);
-              if (split)
-                tc_mma_f16(tmem + kCorrCol, smem_desc_k_sw64(a_lo + o),
-                           smem_desc_k_sw64(b_hi + o), idS, vsplit ? 1u : acc);
-            }
-            tc_commit(&S.ab_empty[s]);
-            if (j == n_chunks - 1) tc_commit(&S.done);
-          }
-          __syncwarp();
+          if (bail) break;
         }
-        ++n_tm;
+        if (!mbar_wait(&S.ab_full[s], (g / kStages) & 1u, err)) {
+          bail = true;
+          break;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          // all producers have added this item's weights to W (they arrived on
+          // ab_full after their scatter); pass that on to the epilogue
+          if (j == n_chunks - 1) mbar_arrive(&S.wready[n_tm & 3u]);
+          const bool h = S.fmt16[s] != 0u;
+          const uint32_t idS = h ? idS16 : idSbf;
+          const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
+          const uint32_t b_hi = smem_u32(S.B[s][0]), b_lo = smem_u32(S.B[s][1]);
+          const uint32_t d = tmem + dcol;
+#pragma unroll
+          for (int kk = 0; kk < kK / 16; ++kk) {
+            const uint32_t o = kk * 32;
+            const uint32_t acc = (!seg_start || kk > 0) ? 1u : 0u;
+            tc_mma_f16(d, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_hi + o), idS, acc);
+            if (vsplit)
+              tc_mma_f16(d, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_lo + o), idS, 1u);
+            if (split)
+              tc_mma_f16(d, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(b_hi + o), idS, 1u);
+          }
+          tc_commit(&S.ab_empty[s]);
+          if (seg_end) tc_commit(&S.segdone);
+        }
+        __syncwarp();
+        if (seg_end) ++n_sg;
       }
+      ++n_tm;
       continue;
     }
 
-    // ---------------- producers (warps 0-15) ----------------
-    {
-      bool ok = true;
-      if (split) {
-        switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-        }
-      } else {
-        switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, n_tm & 1u, err); break;
-        }
-      }
-      bail = !ok;
-      // every producer's W atomics of this item are done before the epilogue
-      if (!bail && n_chunks > 0) named_bar_producers();
-    }
-    if (bail) break;
-
-    // ---------------- epilogue (warps 0-3) ----------------
-    if (warp < 4) {
-      const int row = warp * 32 + lane;
+    if (warp >= kDrainWarp0) {
+      // ---------------- drains and epilogue ----------------
+      const int quarter = warp & 3;  // TMEM lane quarter this warp may access
+      const int row = quarter * 32 + lane;
       const int bbx = (int)(b % pv.nbx_b), bby = (int)(b / pv.nbx_b);
       const int ix = bbx * HG_BX + (row % HG_BX), iy = bby * HG_BY + (row / HG_BX);
       const bool active = ix < pv.nx && iy < pv.ny;
@@ -500,30 +506,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         continue;
       }
-      if (!mbar_wait(&S.done, (n_tm & 1u), err)) {
+      const uint32_t lrow = (uint32_t)(quarter * 32) << 16;
+      const uint32_t tseg = tmem + lrow, ttot = tmem + lrow + kTotCol;
+      for (int q = 0; q < n_seg; ++q) {
+        if (!mbar_wait(&S.segdone, n_sg & 1u, err)) {
+          bail = true;
+          break;
+        }
+        ++n_sg;
+        tc_fence_after();
+        if (q > 0) {
+          // total += segment, FP32 round-to-nearest
+          uint32_t a[16], t[16];
+#pragma unroll 1
+          for (int cb = 0; cb < kN / 16; ++cb) {
+            tmem_ld_32x32b_x16(tseg + cb * 16, a);
+            tmem_ld_32x32b_x16(ttot + cb * 16, t);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              t[i] = __float_as_uint(__fadd_rn(__uint_as_float(t[i]), __uint_as_float(a[i])));
+            tmem_st_32x32b_x16(ttot + cb * 16, t);
+          }
+          tmem_st_wait();
+        }
+        // acknowledge the segment (segment 0 needs no work)
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.segfree);
+      }
+      if (bail) break;
+      // epilogue: map = total / W
+      if (!mbar_wait(&S.wready[n_tm & 3u], (n_tm >> 2) & 1u, err)) {
         bail = true;
         break;
       }
-      ++n_tm;
-      tc_fence_after();
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-      const float W = S.wacc[(n_tm - 1) & 1u][row];
+      const float W = S.wacc[n_tm & 3u][row];
       const bool ok = W > 0.0f;
-      uint32_t r[16], rc[16];
+      uint32_t t[16];
 #pragma unroll 1
       for (int cb = 0; cb < kN / 16; ++cb) {
-        tmem_ld_32x32b_x16(tl + cb * 16, r);
-        if (split) tmem_ld_32x32b_x16(tl + kCorrCol + cb * 16, rc);
+        tmem_ld_32x32b_x16(ttot + cb * 16, t);
         tmem_ld_wait();
         if (active) {
           const int64_t cbase = c0 + cb * 16;
           float v[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float sum = split ? __fadd_rn(__uint_as_float(r[i]), __uint_as_float(rc[i]))
-                                    : __uint_as_float(r[i]);
-            v[i] = ok ? __fdiv_rn(sum, W) : qnan;
-          }
+          for (int i = 0; i < 16; ++i) v[i] = ok ? __fdiv_rn(__uint_as_float(t[i]), W) : qnan;
           if (cbase + 16 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
             for (int i = 0; i < 16; i += 4)
@@ -539,8 +568,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       if (active && c0 == 0 && J.weight_out) J.weight_out[m] = W;
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.tfree);
-    } else if (n_chunks > 0) {
+      if (lane == 0) mbar_arrive(&S.totfree);
+      ++n_tm;
+      continue;
+    }
+
+    // ---------------- producers (warps 0-15) ----------------
+    if (n_chunks == 0) continue;
+    {
+      bool ok = true;
+      const uint32_t par = n_tm & 3u;
+      if (split) {
+        switch (J.dtype) {
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+        }
+      } else {
+        switch (J.dtype) {
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+        }
+      }
+      bail = !ok;
       ++n_tm;
     }
   }
