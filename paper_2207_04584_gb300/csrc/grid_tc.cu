@@ -62,7 +62,10 @@ constexpr int kRawStages = 4;              // staged sample rows ring
 constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst case)
 constexpr uint32_t kTmemCols = 512;        // segment sums in [0,256), running total in [256,512)
 constexpr uint32_t kTotCol = 256;
-constexpr int kSeg = 16;                   // chunks per accumulation segment
+#ifndef HG_TC_SEG
+#define HG_TC_SEG 16
+#endif
+constexpr int kSeg = HG_TC_SEG;            // chunks per accumulation segment
 constexpr int kBand = 8;                   // blocks per band of the work order
 constexpr int kPre = 4;                    // weight entries prefetched per producer thread
 constexpr int kHalves = kProducers / kN;   // producer threads per B row
@@ -517,16 +520,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         tc_fence_after();
         if (q > 0) {
           // total += segment, FP32 round-to-nearest
-          uint32_t a[16], t[16];
+          uint32_t a[32], t[32];
 #pragma unroll 1
-          for (int cb = 0; cb < kN / 16; ++cb) {
-            tmem_ld_32x32b_x16(tseg + cb * 16, a);
-            tmem_ld_32x32b_x16(ttot + cb * 16, t);
+          for (int cb = 0; cb < kN / 32; ++cb) {
+            tmem_ld_32x32b_x32(tseg + cb * 32, a);
+            tmem_ld_32x32b_x32(ttot + cb * 32, t);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
+            for (int i = 0; i < 32; ++i)
               t[i] = __float_as_uint(__fadd_rn(__uint_as_float(t[i]), __uint_as_float(a[i])));
-            tmem_st_32x32b_x16(ttot + cb * 16, t);
+            tmem_st_32x32b_x32(ttot + cb * 32, t);
           }
           tmem_st_wait();
         }
