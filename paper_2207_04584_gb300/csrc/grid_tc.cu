@@ -20,8 +20,7 @@
 // so a block's sum is built in segments of kSeg chunks: segment 0 accumulates
 // into a "total" TMEM region, later segments into a "segment" region that the
 // drain warps add into the total with FP32 round-to-nearest adds (tcgen05
-// ld/st).  W is summed by the producers in shared memory from exactly the
-// quantised weights that entered the MMAs.
+// ld/st).  W comes from the plan (compensated sums of the weights).
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warp 17     stages the chunk's 32 sample rows (raw, as stored) into a
@@ -74,13 +73,12 @@ constexpr int kKT = kK / kHalves;          // samples of a row converted per thr
 struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
-  float wacc[4][kM];                   // W of each cell, per item (mod 4)
   uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
   uint32_t red[kStages][kProducerWarps][2];  // max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t raw_full[kRawStages], raw_empty[kRawStages];
   uint64_t ab_full[kStages], ab_empty[kStages];
-  uint64_t segdone, segfree, totfree, wready[4];
+  uint64_t segdone, segfree, totfree;
   uint32_t tmem_base;
 };
 
@@ -177,8 +175,7 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uin
 // Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT>
 __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_t kb0, int n_chunks,
-                                          int64_t c0, uint32_t& g, uint32_t& gr, uint32_t par,
-                                          int32_t* err) {
+                                          int64_t c0, uint32_t& g, uint32_t& gr, int32_t* err) {
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -261,9 +258,6 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
         if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
       }
-      // W of this item starts at zero (the other parity belongs to the
-      // previous item's epilogue)
-      if (j == 0 && tid < kM) S.wacc[par][tid] = 0.0f;
     }
     named_bar_producers();
     bool h16 = true;
@@ -321,19 +315,13 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
       auto put = [&](uint32_t ck, float w) {
         const int r = (int)(ck >> 6), k = (int)(ck & 31u);
         uint16_t hi, lo;
-        float wq;  // the weight exactly as the MMAs see it
-        if (h16) {
+        if (h16)
           split_f16(w, hi, lo);
-          wq = SPLIT ? __half2float(__ushort_as_half(hi)) + __half2float(__ushort_as_half(lo))
-                     : __half2float(__ushort_as_half(hi));
-        } else {
+        else
           split_bf16(w, hi, lo);
-          wq = SPLIT ? bf16_bits_to_float(hi) + bf16_bits_to_float(lo) : bf16_bits_to_float(hi);
-        }
         const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
         st_shared_u16(ah + off, hi);
         if (SPLIT) st_shared_u16(al + off, lo);
-        atomicAdd(&S.wacc[par][r], wq);
       };
 #pragma unroll
       for (int i = 0; i < kPre; ++i)
@@ -377,7 +365,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     mbar_init(&S.segdone, 1);
     mbar_init(&S.segfree, 4);
     mbar_init(&S.totfree, 4);
-    for (int i = 0; i < 4; ++i) mbar_init(&S.wready[i], 1);
     fence_mbar_init();
   }
   if (warp == kMmaWarp) {
@@ -463,9 +450,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
         tc_fence_after();
         if (lane == 0) {
-          // all producers have added this item's weights to W (they arrived on
-          // ab_full after their scatter); pass that on to the epilogue
-          if (j == n_chunks - 1) mbar_arrive(&S.wready[n_tm & 3u]);
           const bool h = S.fmt16[s] != 0u;
           const uint32_t idS = h ? idS16 : idSbf;
           const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
@@ -539,12 +523,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         if (lane == 0) mbar_arrive(&S.segfree);
       }
       if (bail) break;
-      // epilogue: map = total / W
-      if (!mbar_wait(&S.wready[n_tm & 3u], (n_tm >> 2) & 1u, err)) {
-        bail = true;
-        break;
-      }
-      const float W = S.wacc[n_tm & 3u][row];
+      // epilogue: map = total / W, W from the plan's compensated sums: FP32
+      // weights for the split form (the hi+lo split differs from them by at
+      // most 2^-17 per weight, at random), FP16-rounded weights for the
+      // single form
+      const float W = active ? pv.wsum[(int64_t)(split ? 0 : 3) * pv.M + m] : 0.0f;
       const bool ok = W > 0.0f;
       uint32_t t[16];
 #pragma unroll 1
@@ -580,20 +563,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     if (n_chunks == 0) continue;
     {
       bool ok = true;
-      const uint32_t par = n_tm & 3u;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, par, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
         }
       }
       bail = !ok;
