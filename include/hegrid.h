@@ -193,6 +193,43 @@ int64_t hegrid_launch_count(void);
 /* Thread-local message describing the most recent failure ("" if none). */
 const char *hegrid_last_error(void);
 
+/*
+ * hegrid_bin_sort_noalloc -- the plan's bin key, stable radix sort and bin
+ * offsets (perm and bin_off, exactly as hegrid_plan_export returns them) for
+ * callers that cannot allocate device memory: code running where
+ * cudaMalloc/cudaMallocAsync is not permitted or not wanted, such as an
+ * allocator-controlled host framework that forbids foreign allocations, a
+ * real-time loop that must not block on the allocator, or a region where the
+ * caller has promised a fixed memory budget.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.  (The paper has no counterpart: its
+ * sort ran on the CPU.)
+ *
+ * Scratch lives in one fixed device array of about 8.5 MB compiled into the
+ * library; every GPU that loads the library holds it until the process
+ * exits.  Hence n_samples <= 524288 (HEGRID_NOALLOC_MAX_SAMPLES); larger
+ * inputs return INVALID_ARG before any launch.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or the same stream from
+ * several threads without ordering) race and corrupt each other's result.
+ * Every scratch word a call reads was written by that same call, so nothing
+ * has to be cleared between calls.  The first call on each device looks up
+ * the array's device address (with that device current); make that first
+ * call before any stream capture.
+ *
+ * lon_deg, lat_deg  device FP64 [n_samples] (caller-owned).
+ * geom, kern, flags as for hegrid_plan_create.
+ * perm_out          device int32 [n_samples].
+ * bin_off_out       device int32 [bin_off_capacity], capacity >= n_bins + 1.
+ * n_bins_out        host; set to the number of bins even when the capacity is
+ *                   too small (INVALID_ARG), so the caller can size the buffer.
+ * Asynchronous on `stream`.
+ */
+#define HEGRID_NOALLOC_MAX_SAMPLES 524288
+hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double *lon_deg,
+                                      const double *lat_deg, const hegrid_map_geom *geom,
+                                      const hegrid_kernel *kern, uint32_t flags, int32_t *perm_out,
+                                      int32_t *bin_off_out, int64_t bin_off_capacity,
+                                      int64_t *n_bins_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

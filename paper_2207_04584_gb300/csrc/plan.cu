@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1045,3 +1046,174 @@ hegrid_status hegrid_status_poll(const hegrid_plan* plan) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free bin sort.  The same bin key, stable radix sort and bin
+// offsets as plan creation, for callers that must not allocate device memory:
+// the sort's scratch lives in one fixed file-scope device array.
+// ===========================================================================
+namespace hg {
+namespace {
+
+constexpr int64_t kNoAllocMaxSamples = (int64_t)1 << 19;  // 524,288 samples
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxSamples + kSortTile - 1) / kSortTile;
+constexpr int64_t kNoAllocHist = 256 * kNoAllocTiles;
+constexpr int64_t kNoAllocTmp = 64;  // >= scan_tmp_elems(kNoAllocHist)
+constexpr size_t kOffKey0 = 0;
+constexpr size_t kOffKey1 = kOffKey0 + 4 * kNoAllocMaxSamples;
+constexpr size_t kOffVal0 = kOffKey1 + 4 * kNoAllocMaxSamples;
+constexpr size_t kOffVal1 = kOffVal0 + 4 * kNoAllocMaxSamples;
+constexpr size_t kOffHist = kOffVal1 + 4 * kNoAllocMaxSamples;
+constexpr size_t kOffHoff = kOffHist + 4 * kNoAllocHist;
+constexpr size_t kOffTmp = kOffHoff + (4 * (kNoAllocHist + 1) + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kOffTmp + 4 * kNoAllocTmp;  // about 8.5 MB
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Bin key only (the key arithmetic of k_prep, without the unit vectors).
+__global__ void k_keys_only(int32_t N, const double* __restrict__ lon,
+                            const double* __restrict__ lat, KeyParams kp,
+                            uint32_t* __restrict__ key, int32_t* __restrict__ idx) {
+  int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double a = __dsub_rn(lon[n], kp.lon0);
+  double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
+  a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
+  double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
+  double qy = __dadd_rn(__ddiv_rn(__dsub_rn(lat[n], kp.lat0), kp.dlat), kp.cy);
+  double fx = floor(qx), fy = floor(qy);
+  uint32_t k = kp.n_bins;
+  if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
+    int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
+    k = (uint32_t)(by * kp.nbx + bx);
+  }
+  key[n] = k;
+  idx[n] = n;
+}
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[64] = {};
+
+// Device address of the scratch array on the current device (set up once per
+// device; host code only sees a stand-in symbol, never the device address).
+hegrid_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  HG_CUDA_TRY(cudaGetDevice(&dev));
+  HG_ARG_CHECK(dev >= 0 && dev < 64, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    HG_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return HEGRID_OK;
+}
+
+}  // namespace
+}  // namespace hg
+
+extern "C" hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double* lon_deg,
+                                                 const double* lat_deg,
+                                                 const hegrid_map_geom* geom,
+                                                 const hegrid_kernel* kern, uint32_t flags,
+                                                 int32_t* perm_out, int32_t* bin_off_out,
+                                                 int64_t bin_off_capacity, int64_t* n_bins_out,
+                                                 void* stream) {
+  using namespace hg;
+  set_error("");
+  HG_ARG_CHECK(lon_deg && lat_deg && geom && kern, "NULL coordinates, geometry or kernel");
+  HG_ARG_CHECK(perm_out && bin_off_out && n_bins_out, "NULL output");
+  HG_ARG_CHECK(n_samples >= 1, "n_samples must be >= 1");
+  HG_ARG_CHECK(n_samples <= kNoAllocMaxSamples,
+               "n_samples above the allocation-free limit of 524288 samples");
+  HG_ARG_CHECK(geom->nx >= 1 && geom->ny >= 1, "nx, ny must be >= 1");
+  HG_ARG_CHECK(geom->dlon_deg > 0 && geom->dlat_deg > 0, "cell size must be > 0");
+  HG_ARG_CHECK(std::isfinite(geom->lon0_deg) && std::isfinite(geom->lat0_deg),
+               "map centre must be finite");
+  HG_ARG_CHECK(kern->fwhm_deg > 0 && kern->support_sigmas > 0, "FWHM and support must be > 0");
+  const int B = (flags & 0xffu) ? (int)(flags & 0xffu) : 2;
+  const double sigma_deg = kern->fwhm_deg / std::sqrt(8.0 * std::log(2.0));
+  const double R_deg = kern->support_sigmas * sigma_deg;
+  const double R_rad = R_deg * kDeg;
+  if (R_deg > 11.0) {
+    set_error("kernel radius above 11 degrees is not supported");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  // padded-map layout (the bin key's definition)
+  const hegrid_map_geom& g = *geom;
+  const double half_rows = 0.5 * (double)(g.ny - 1) * g.dlat_deg;
+  const double lat_max =
+      std::max(std::fabs(g.lat0_deg - half_rows), std::fabs(g.lat0_deg + half_rows));
+  if (lat_max + R_deg >= 90.0) {
+    set_error("map rows come within R of a pole");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  const double Hmax = std::asin(std::sin(R_rad) / std::cos(lat_max * kDeg)) / kDeg;
+  const int32_t pady = (int32_t)std::ceil(R_deg / g.dlat_deg) + 1;
+  const int32_t padx = (int32_t)std::ceil(Hmax / g.dlon_deg) + 1;
+  if ((double)(g.nx + 2 * padx) * g.dlon_deg >= 360.0) {
+    set_error("padded map is wider than 360 degrees of RA");
+    return HEGRID_ERR_UNSUPPORTED;
+  }
+  const int32_t nbx = (g.nx + 2 * padx + B - 1) / B;
+  const int32_t nby = (g.ny + 2 * pady + B - 1) / B;
+  const int64_t n_bins = (int64_t)nbx * nby;
+  *n_bins_out = n_bins;
+  HG_ARG_CHECK(n_bins < (int64_t)0x7fffffff, "too many bins");
+  HG_ARG_CHECK(bin_off_capacity >= n_bins + 1, "bin_off_out holds fewer than n_bins + 1 entries");
+
+  unsigned char* base = nullptr;
+  {
+    hegrid_status s = noalloc_scratch(&base);
+    if (s != HEGRID_OK) return s;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t N = (int32_t)n_samples;
+  uint32_t* key0 = reinterpret_cast<uint32_t*>(base + kOffKey0);
+  uint32_t* key1 = reinterpret_cast<uint32_t*>(base + kOffKey1);
+  int32_t* val0 = reinterpret_cast<int32_t*>(base + kOffVal0);
+  int32_t* val1 = reinterpret_cast<int32_t*>(base + kOffVal1);
+  int32_t* hist = reinterpret_cast<int32_t*>(base + kOffHist);
+  int32_t* hoff = reinterpret_cast<int32_t*>(base + kOffHoff);
+  int32_t* tmp = reinterpret_cast<int32_t*>(base + kOffTmp);
+
+  KeyParams kp;
+  kp.lon0 = g.lon0_deg;
+  kp.lat0 = g.lat0_deg;
+  kp.dlon = g.dlon_deg;
+  kp.dlat = g.dlat_deg;
+  kp.cx = 0.5 * (double)g.nx + (double)padx;
+  kp.cy = 0.5 * (double)g.ny + (double)pady;
+  kp.wx = (double)(g.nx + 2 * padx);
+  kp.wy = (double)(g.ny + 2 * pady);
+  kp.bin_cells = B;
+  kp.nbx = nbx;
+  kp.n_bins = (uint32_t)n_bins;
+  k_keys_only<<<(N + 255) / 256, 256, 0, st>>>(N, lon_deg, lat_deg, kp, key0, val0);
+  count_launch();
+  int bits = 1;
+  while (((uint64_t)1 << bits) <= (uint64_t)n_bins) ++bits;
+  const int passes = (bits + 7) / 8;
+  const int32_t n_tiles = (N + kSortTile - 1) / kSortTile;
+  const int64_t hist_n = (int64_t)256 * n_tiles;
+  uint32_t *kin = key0, *kout = key1;
+  int32_t *vin = val0, *vout = val1;
+  for (int ps = 0; ps < passes; ++ps) {
+    k_radix_hist<<<n_tiles, kSortThreads, 0, st>>>(kin, N, 8 * ps, n_tiles, hist);
+    count_launch();
+    scan_exclusive<int32_t, int32_t>(hist, hist_n, hoff, tmp, st);
+    k_radix_scatter<<<n_tiles, kSortThreads, 0, st>>>(kin, vin, kout, vout, N, 8 * ps, n_tiles,
+                                                       hoff);
+    count_launch();
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(cudaMemcpyAsync(perm_out, vin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
+  k_bin_offsets<<<(N + 255) / 256, 256, 0, st>>>(kin, N, (uint32_t)n_bins, bin_off_out);
+  count_launch();
+  HG_CUDA_TRY(cudaGetLastError());
+  return HEGRID_OK;
+}

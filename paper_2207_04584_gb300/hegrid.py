@@ -29,7 +29,7 @@ HEGRID_MODE_FP32, HEGRID_MODE_TC, HEGRID_MODE_TC_SPLIT = 0, 1, 2
 EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_grid_batched",
             "hegrid_batch_create", "hegrid_batch_launch", "hegrid_batch_destroy",
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
-            "hegrid_launch_count", "hegrid_last_error"]
+            "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -81,6 +81,8 @@ def lib():
     L.hegrid_plan_info.argtypes = [P, P, P, P, P, P]
     L.hegrid_plan_export.argtypes = [P, P, P, P, P, P, P]
     L.hegrid_status_poll.argtypes = [P]
+    L.hegrid_bin_sort_noalloc.argtypes = [i64, P, P, ctypes.POINTER(hegrid_map_geom),
+                                          ctypes.POINTER(hegrid_kernel), u32, P, P, i64, P, P]
     L.hegrid_last_error.restype = ctypes.c_char_p
     L.hegrid_launch_count.restype = ctypes.c_int64
     for name in EXPORTED:
@@ -201,3 +203,18 @@ def hegrid_launch_count() -> int:
 
 def hegrid_status_poll(plan):
     return _check(lib().hegrid_status_poll(plan), "hegrid_status_poll")
+
+
+def hegrid_bin_sort_noalloc(n_samples, lon_deg, lat_deg, geom, fwhm_deg, support_sigmas,
+                            perm_out, bin_off_out, bin_off_capacity, flags=0, stream=None):
+    """Bin sort into caller buffers without allocating device memory (see the
+    header for the limits).  Returns the number of bins."""
+    nb = ctypes.c_int64(0)
+    g = geom_struct(geom)
+    k = hegrid_kernel(float(fwhm_deg), float(support_sigmas))
+    _check(lib().hegrid_bin_sort_noalloc(int(n_samples), _ptr(lon_deg), _ptr(lat_deg),
+                                         ctypes.byref(g), ctypes.byref(k), int(flags),
+                                         _ptr(perm_out), _ptr(bin_off_out), int(bin_off_capacity),
+                                         ctypes.byref(nb), _ptr(stream)),
+           "hegrid_bin_sort_noalloc")
+    return nb.value
