@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       {
         auto put = [&](uint32_t ck, float w) {
-          const int col = (int)(ck >> 6), k = (int)(ck & 31u);
+          int col, k;
+          tile_rk(ck, col, k);
           const int tc = cell_to_col(col % HG_BX, col / HG_BX);
           S.Wt[s][k][tc] = w;
           atomicOr(&S.pmask[s][k], 1u << (tc >> 4));

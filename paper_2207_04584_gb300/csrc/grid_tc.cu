@@ -20,15 +20,17 @@
 // so a block's sum is built in segments of kSeg chunks: segment 0 accumulates
 // into a "total" TMEM region, later segments into a "segment" region that the
 // drain warps add into the total with FP32 round-to-nearest adds (tcgen05
-// ld/st).  W comes from the plan (compensated sums of the weights).
+// ld/st).  Weights enter the A tiles scaled by 2^15 (exact), which keeps the
+// low FP16 half of their split a normal number; W comes from the plan
+// (compensated sums of the weights) and is scaled to match.
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warp 17     stages the chunk's 32 sample rows (raw, as stored) into a
 //               4-deep shared-memory ring with bulk async copies (TMA
 //               engine), one row per lane;
 //   warps 0-15  convert a staged chunk into the B tiles (row = channel, two
-//               threads per row) and scatter the chunk's weight entries into
-//               the A tiles (2-deep ring);
+//               threads per row) and store the chunk's weight entries into the
+//               A tiles at the tile offsets the plan precomputed (2-deep ring);
 //   warp 16     allocates TMEM and issues the MMAs (one lane);
 //   warps 18-21 drain finished segments into the running total and run the
 //               epilogue (TMEM -> registers -> S / W -> global).
@@ -74,7 +76,7 @@ struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
   uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
-  uint32_t red[kStages][kProducerWarps][2];  // max|v|, min|v|>0 (float bits)
+  uint32_t red[3][2];                        // range slots: max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t raw_full[kRawStages], raw_empty[kRawStages];
   uint64_t ab_full[kStages], ab_empty[kStages];
@@ -105,21 +107,6 @@ __device__ __forceinline__ void item_coords(const GridJob& J, int64_t local, int
   const int64_t t = bo - band * per_band;
   const int64_t bw = min((int64_t)kBand, (int64_t)J.pv.nbx_b - band * kBand);
   b = (t / bw) * J.pv.nbx_b + band * kBand + (t % bw);
-}
-
-// Split x into hi + lo 16-bit floats (round to nearest for both parts).
-__device__ __forceinline__ void split_bf16(float x, uint16_t& hi, uint16_t& lo) {
-  __nv_bfloat16 h = __float2bfloat16_rn(x);
-  __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  hi = __bfloat16_as_ushort(h);
-  lo = __bfloat16_as_ushort(l);
-}
-
-__device__ __forceinline__ void split_f16(float x, uint16_t& hi, uint16_t& lo) {
-  __half h = __float2half_rn(x);
-  __half l = __float2half_rn(x - __half2float(h));
-  hi = __half_as_ushort(h);
-  lo = __half_as_ushort(l);
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
@@ -171,30 +158,38 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uin
 
 // Producer side of one work item (warps 0-15): for every chunk, convert the
 // staged rows into the B tiles and scatter the weight entries into the A
-// tiles.  DT is the stored value type; SPLIT selects the hi/lo form.
+// tiles.  DT is the stored value type; SPLIT selects the hi/lo form.  rslot
+// rotates over the three range-reduction slots (see below).
 // Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT>
 __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_t kb0, int n_chunks,
-                                          int64_t c0, uint32_t& g, uint32_t& gr, int32_t* err) {
+                                             int64_t c0, uint32_t& g, uint32_t& gr,
+                                             uint32_t& rslot, int32_t* err) {
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr uint32_t kNone = 0xffffu;  // no entry in this prefetch slot
+  constexpr uint32_t kLoTile = kM * 64;  // A[s][1] follows A[s][0]
+  const int tid = threadIdx.x, lane = tid & 31;
   const int row = tid % kN, kh = tid / kN;  // B row (channel c0 + row), half of the chunk
   const PlanView& pv = J.pv;
   const bool cvalid = c0 + row < J.C;
-  const int64_t sub0 = kb0 / 32;
+  // The block's entries, indexed relative to its first one.
+  const int64_t* __restrict__ so = pv.sub_off + kb0 / 32;
+  const int64_t ebase = so[0];
+  const uint16_t* __restrict__ eck = pv.ent_ck + ebase;
+  const float* __restrict__ ew = pv.ent_w + ebase;
   // Weight entries are software-pipelined one chunk ahead: while chunk j is
   // converted, the loads of chunk j+1's entries are in flight.
-  int64_t e_lo = pv.sub_off[sub0];
-  int64_t e_hi = pv.sub_off[sub0 + 1];
-  int64_t e_nx = n_chunks > 1 ? pv.sub_off[sub0 + 2] : e_hi;
+  int e_lo = 0;
+  int e_hi = (int)(so[1] - ebase);
+  int e_nx = n_chunks > 1 ? (int)(so[2] - ebase) : e_hi;
   uint32_t pck[kPre];
   float pw[kPre];
 #pragma unroll
   for (int i = 0; i < kPre; ++i) {
-    const int64_t e = e_lo + tid + (int64_t)i * kProducers;
-    pck[i] = e < e_hi ? (uint32_t)__ldcs(pv.ent_ck + e) : 0xffffffffu;
-    pw[i] = e < e_hi ? __ldcs(pv.ent_w + e) : 0.0f;
+    const int e = e_lo + tid + i * kProducers;
+    pck[i] = e < e_hi ? (uint32_t)__ldcs(eck + e) : kNone;
+    pw[i] = e < e_hi ? __ldcs(ew + e) : 0.0f;
   }
   constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
   constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
@@ -208,11 +203,11 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     float nw[kPre];
 #pragma unroll
     for (int i = 0; i < kPre; ++i) {
-      const int64_t e = e_hi + tid + (int64_t)i * kProducers;
-      nck[i] = e < e_nx ? (uint32_t)__ldcs(pv.ent_ck + e) : 0xffffffffu;
-      nw[i] = e < e_nx ? __ldcs(pv.ent_w + e) : 0.0f;
+      const int e = e_hi + tid + i * kProducers;
+      nck[i] = e < e_nx ? (uint32_t)__ldcs(eck + e) : kNone;
+      nw[i] = e < e_nx ? __ldcs(ew + e) : 0.0f;
     }
-    const int64_t e_nx2 = j + 2 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 3) : e_nx;
+    const int e_nx2 = j + 2 < n_chunks ? (int)(__ldg(so + j + 3) - ebase) : e_nx;
     if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
     // Channel column `row` of this thread's half of the staged rows.
@@ -230,24 +225,26 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
     // Range of the chunk's values (decides the 16-bit format of the chunk):
-    // max |v| and, for BF16 input, min nonzero |v|, as float bit patterns.
+    // max |v| and, for BF16 input, min nonzero |v|, as float bit patterns,
+    // combined over the producers in slot rslot (warp maxima, shared atomics).
     if (DT != HEGRID_F16) {
-      uint32_t mx = 0u, mn = kInf;
+      float fmx = 0.0f;
+      uint32_t mn = kInf;
 #pragma unroll
       for (int k = 0; k < kKT; ++k) {
-        uint32_t a;
-        if (DT == HEGRID_F32)
-          a = x[k] & 0x7fffffffu;
-        else  // BF16 and BF16X2: the (high) BF16 part
-          a = (x[k] << 16) & 0x7fffffffu;
-        mx = max(mx, a);
-        if (DT == HEGRID_BF16) mn = min(mn, a == 0u ? kInf : a);
+        if (DT == HEGRID_F32) {
+          fmx = fmaxf(fmx, fabsf(__uint_as_float(x[k])));  // NaN is dropped, Inf kept
+        } else {  // BF16 and BF16X2: the (high) BF16 part
+          const uint32_t a = (x[k] << 16) & 0x7fffffffu;
+          fmx = fmaxf(fmx, __uint_as_float(a));
+          if (DT == HEGRID_BF16) mn = min(mn, a == 0u ? kInf : a);
+        }
       }
-      mx = __reduce_max_sync(0xffffffffu, mx);
+      const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fmx));
       if (DT == HEGRID_BF16) mn = __reduce_min_sync(0xffffffffu, mn);
       if (lane == 0) {
-        S.red[s][warp][0] = mx;
-        S.red[s][warp][1] = mn;
+        atomicMax(&S.red[rslot][0], mx);
+        if (DT == HEGRID_BF16) atomicMin(&S.red[rslot][1], mn);
       }
     }
     // A tiles: zero (the scatter follows the barrier)
@@ -262,18 +259,21 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     named_bar_producers();
     bool h16 = true;
     if (DT != HEGRID_F16) {
-      uint32_t mx = 0u, mn = kInf;
-#pragma unroll
-      for (int w = 0; w < kProducerWarps; ++w) {
-        mx = max(mx, S.red[s][w][0]);
-        mn = min(mn, S.red[s][w][1]);
-      }
+      const uint32_t mx = S.red[rslot][0], mn = S.red[rslot][1];
       if (DT == HEGRID_BF16)
         h16 = mx <= kBits32768 && (mn == kInf || mn >= kBits2m14);
-      else  // NaN / Inf give mx >= kInf > 2^15
+      else  // Inf gives mx >= kInf > 2^15
         h16 = mx <= kBits32768 && (mx == 0u || mx >= kBits2m7);
     }
-    if (tid == 0) S.fmt16[s] = h16 ? 1u : 0u;
+    if (tid == 0) {
+      S.fmt16[s] = h16 ? 1u : 0u;
+      // Slot (rslot + 2) % 3 was last read before this chunk's barrier and is
+      // next written after the following one: reset it for that chunk.
+      const uint32_t rr = rslot == 0u ? 2u : rslot - 1u;
+      S.red[rr][0] = 0u;
+      S.red[rr][1] = kInf;
+    }
+    rslot = rslot == 2u ? 0u : rslot + 1u;
     // B tiles: row `row` holds the chunk's samples of channel c0 + row; this
     // thread writes its half (16-byte chunks kh*kKT/8 ...).
     {
@@ -309,25 +309,30 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
       }
     }
-    // A tiles: scatter the chunk's weight entries
+    // A tiles: the chunk's weight entries, scaled by kTcWeightScale and split
+    // into the chunk's 16-bit format, stored at their precomputed offsets.
     {
-      const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
-      auto put = [&](uint32_t ck, float w) {
-        const int r = (int)(ck >> 6), k = (int)(ck & 31u);
-        uint16_t hi, lo;
-        if (h16)
-          split_f16(w, hi, lo);
-        else
-          split_bf16(w, hi, lo);
-        const uint32_t off = sw64(r, k >> 3) + (k & 7) * 2;
-        st_shared_u16(ah + off, hi);
-        if (SPLIT) st_shared_u16(al + off, lo);
-      };
+      const uint32_t ah = smem_u32(S.A[s][0]);
 #pragma unroll
-      for (int i = 0; i < kPre; ++i)
-        if (pck[i] != 0xffffffffu) put(pck[i], pw[i]);
-      for (int64_t e = e_lo + tid + (int64_t)kPre * kProducers; e < e_hi; e += kProducers)
-        put(__ldcs(pv.ent_ck + e), __ldcs(pv.ent_w + e));
+      for (int i = 0; i < kPre; i += 2) {
+        uint32_t h2, l2;
+        split2(pw[i] * kTcWeightScale, pw[i + 1] * kTcWeightScale, h16, h2, l2);
+        if (pck[i] != kNone) {
+          st_shared_u16(ah + pck[i], (uint16_t)(h2 & 0xffffu));
+          if (SPLIT) st_shared_u16(ah + kLoTile + pck[i], (uint16_t)(l2 & 0xffffu));
+        }
+        if (pck[i + 1] != kNone) {
+          st_shared_u16(ah + pck[i + 1], (uint16_t)(h2 >> 16));
+          if (SPLIT) st_shared_u16(ah + kLoTile + pck[i + 1], (uint16_t)(l2 >> 16));
+        }
+      }
+      for (int e = e_lo + tid + kPre * kProducers; e < e_hi; e += kProducers) {
+        const uint32_t off = __ldcs(eck + e);
+        uint32_t h2, l2;
+        split2(__ldcs(ew + e) * kTcWeightScale, 0.0f, h16, h2, l2);
+        st_shared_u16(ah + off, (uint16_t)(h2 & 0xffffu));
+        if (SPLIT) st_shared_u16(ah + kLoTile + off, (uint16_t)(l2 & 0xffffu));
+      }
     }
     e_lo = e_hi;
     e_hi = e_nx;
@@ -362,6 +367,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       mbar_init(&S.ab_full[i], kProducerWarps);
       mbar_init(&S.ab_empty[i], 1);
     }
+    for (int i = 0; i < 3; ++i) {
+      S.red[i][0] = 0u;
+      S.red[i][1] = 0x7f800000u;
+    }
     mbar_init(&S.segdone, 1);
     mbar_init(&S.segfree, 4);
     mbar_init(&S.totfree, 4);
@@ -381,6 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   uint32_t gr = 0;    // chunks through the raw ring so far
   uint32_t n_tm = 0;  // items that used TMEM so far
   uint32_t n_sg = 0;  // accumulation segments so far (segdone / segfree phases)
+  uint32_t rslot = 0; // producers: range-reduction slot of the next chunk
 
   for (int64_t item = blockIdx.x; item < jt.n_items && !bail; item += gridDim.x) {
     const GridJob& J = jt.job[find_job(jt, item)];
@@ -525,9 +535,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       if (bail) break;
       // epilogue: map = total / W, W from the plan's compensated sums: FP32
       // weights for the split form (the hi+lo split differs from them by at
-      // most 2^-17 per weight, at random), FP16-rounded weights for the
-      // single form
-      const float W = active ? pv.wsum[(int64_t)(split ? 0 : 3) * pv.M + m] : 0.0f;
+      // most 2^-22 per weight in FP16 chunks, 2^-17 in BF16 chunks, at
+      // random), FP16-rounded weights for the single form; both x 2^15
+      const float Wm = active ? pv.wsum[(int64_t)(split ? 0 : 1) * pv.M + m] : 0.0f;
+      const float W = Wm * kTcWeightScale;
       const bool ok = W > 0.0f;
       uint32_t t[16];
 #pragma unroll 1
@@ -551,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           }
         }
       }
-      if (active && c0 == 0 && J.weight_out) J.weight_out[m] = W;
+      if (active && c0 == 0 && J.weight_out) J.weight_out[m] = Wm;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.totfree);
@@ -565,17 +576,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       bool ok = true;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
         }
       }
       bail = !ok;

@@ -19,9 +19,27 @@
 
 namespace hg {
 
-// W per cell is kept for each weight representation: 0 FP32, 1 BF16 hi,
-// 2 BF16 hi+lo, 3 FP16 hi, 4 FP16 hi+lo (wsum[v * M + m]).
-constexpr int kWsumVariants = 5;
+// W per cell is kept for each weight representation the grid kernels
+// multiply by: 0 the FP32 weights (FP32 form, tensor-core split form), 1 the
+// weights rounded to FP16 (tensor-core single form) (wsum[v * M + m]).
+constexpr int kWsumVariants = 2;
+
+// The tensor-core forms multiply weights scaled by this power of two (exact),
+// so that the low FP16 half of a weight split stays a normal number down to
+// weights of about 2^-17; W is scaled to match.
+constexpr float kTcWeightScale = 32768.0f;
+
+// Weight entries address a K-major, 64-byte-swizzled 128 x 32 tile of 16-bit
+// values (one block's cells x one 32-candidate sub-chunk): byte offset of
+// (cell r, candidate k), and back.  The tensor-core kernel stores weights at
+// this offset directly; the FP32 kernel decodes (r, k).
+__host__ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
+  return (uint32_t)(r * 64 + ((((k >> 3) ^ ((r >> 1) & 3)) << 4) | ((k & 7) << 1)));
+}
+__host__ __device__ __forceinline__ void tile_rk(uint32_t off, int& r, int& k) {
+  r = (int)(off >> 6);
+  k = (int)(((((off >> 4) & 3u) ^ ((uint32_t)(r >> 1) & 3u)) << 3) | ((off >> 1) & 7u));
+}
 
 // Thread-local error message for hegrid_last_error().
 void set_error(const std::string& msg);
@@ -61,7 +79,7 @@ struct PlanView {
   const int64_t* cand_off;  // [n_blocks+1] candidate slots per block (padded to 64)
   const int32_t* cand_idx;  // [n_cand] original sample index per slot
   const int64_t* sub_off;   // [n_cand/32+1] first entry of each 32-candidate sub-chunk
-  const uint16_t* ent_ck;   // [P] entry: (block-local cell << 6) | (candidate & 63)
+  const uint16_t* ent_ck;   // [P] entry: tile_off(block-local cell, candidate & 31)
   const float* ent_w;       // [P] FP32 weight of the entry
   int32_t* err_word;        // device error word (bounded waits)
 };

@@ -361,8 +361,9 @@ __device__ __forceinline__ float pair_weight(const float (&mh)[3], const float (
 // COUNT pass: number of distinct candidates (K_b, the union of the cells'
 // neighbours) and number of pairs of the block.  FILL pass: the candidate list
 // (original sample indices, union order), the weight entries of the block in
-// candidate-major order (entry = 6-bit k within a 64-candidate chunk | 7-bit
-// cell, FP32 weight), the offsets of every 32-candidate sub-chunk, W[m].
+// candidate-major order (entry = tile_off(cell, candidate & 31), FP32
+// weight; the cells of one candidate in increasing order), the offsets of
+// every 32-candidate sub-chunk, W[m].
 // Neumaier-compensated running sum.
 struct CSum {
   float s = 0.0f, c = 0.0f;
@@ -374,6 +375,18 @@ struct CSum {
   __device__ __forceinline__ float value() const { return s + c; }
 };
 
+// 32 x 32 bit-matrix transpose across a warp: bit j of lane i's word becomes
+// bit i of lane j's word (five rounds of swapping off-diagonal sub-blocks).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  uint32_t lo = 0x0000ffffu;  // bits j with (j & s) == 0
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1, lo ^= lo << s) {
+    const uint32_t p = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? ((x & ~lo) | ((p & ~lo) >> s)) : ((x & lo) | ((p & lo) << s));
+  }
+  return x;
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(kChunk)
     k_block_pairs(PairParams pp, const int4* __restrict__ win, const int32_t* __restrict__ bin_off,
@@ -384,14 +397,24 @@ __global__ void __launch_bounds__(kChunk)
                   int32_t* __restrict__ cand_idx, int64_t* __restrict__ sub_off,
                   uint16_t* __restrict__ ent_ck, float* __restrict__ ent_w,
                   float* __restrict__ wsum) {
+  constexpr int kQ = kChunk / 32;
   __shared__ float s_eh[3][kChunk];
   __shared__ float s_el[3][kChunk];
   __shared__ double s_u[3][kChunk];
   __shared__ int32_t s_n[kChunk];
-  __shared__ uint32_t s_umask[kChunk / 32];
-  __shared__ int32_t s_cc[kChunk];   // cells containing staged candidate k
-  __shared__ int32_t s_cur[kChunk];  // write cursor per staged candidate
-  __shared__ int32_t s_wsum[kChunk / 32];
+  __shared__ uint32_t s_umask[kQ];
+  __shared__ int32_t s_red[kQ];
+  // FILL only: cell coordinates, candidate-major cell masks (bit i of
+  // s_cm[k][w]: cell 32 w + i has staged candidate k), entries before each
+  // staged candidate, candidate index within its 32-candidate sub-chunk.
+  __shared__ float s_mh[3][FILL ? kChunk : 1];
+  __shared__ float s_ml[3][FILL ? kChunk : 1];
+  __shared__ uint32_t s_cm[FILL ? kChunk : 1][kQ];
+  __shared__ int32_t s_pre[FILL ? kChunk + 1 : 1];
+  __shared__ int32_t s_loc[FILL ? kChunk : 1];
+  __shared__ int32_t s_base[FILL ? kChunk : 1][kQ];  // first entry of (candidate, cell word)
+  __shared__ uint16_t s_ent[FILL ? 32 * kChunk : 1];  // (cell << 5 | candidate) of a group
+  __shared__ float s_w[FILL ? 32 * kChunk : 1];       // weights of a group's entries
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
@@ -415,15 +438,20 @@ __global__ void __launch_bounds__(kChunk)
     for (int i = 0; i < 3; ++i) {
       mh[i] = __double2float_rn(e[i]);
       ml[i] = __double2float_rn(e[i] - (double)mh[i]);
+      if (FILL) {
+        s_mh[i][t] = mh[i];
+        s_ml[i][t] = ml[i];
+      }
     }
   }
 
   int32_t count = 0;   // pairs of this cell
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
   int64_t erun = 0;    // entries of the block so far
-  // W of the cell for each weight representation the grid kernels use:
-  // FP32, BF16 hi, BF16 hi+lo, FP16 hi, FP16 hi+lo (so that every form
-  // normalises by the sum of exactly the weights it multiplied).
+  // W of the cell for each weight representation the grid kernels use
+  // (FP32; FP16-rounded as the tensor-core single form rounds them), so
+  // that every form normalises by the sum of exactly the weights it
+  // multiplied.
   CSum wsv[kWsumVariants];
   int64_t cbase = 0, ebase = 0, sbase = 0;
   if (FILL) {
@@ -450,15 +478,13 @@ __global__ void __launch_bounds__(kChunk)
         }
         s_n[t] = perm[s];
       }
-      if (t < kChunk / 32) s_umask[t] = 0u;
-      s_cc[t] = 0;
-      s_cur[t] = 0;
+      if (t < kQ) s_umask[t] = 0u;
       __syncthreads();
 
       // Phase 1: membership of each staged candidate for this thread's cell.
-      uint32_t mask[kChunk / 32];
+      uint32_t mask[kQ];
 #pragma unroll
-      for (int q = 0; q < kChunk / 32; ++q) {
+      for (int q = 0; q < kQ; ++q) {
         uint32_t mm = 0u;
         const int kend = active ? min(32, nk - 32 * q) : 0;
         for (int r = 0; r < kend; ++r) {
@@ -479,89 +505,112 @@ __global__ void __launch_bounds__(kChunk)
         mask[q] = mm;
       }
 #pragma unroll
-      for (int q = 0; q < kChunk / 32; ++q) {
+      for (int q = 0; q < kQ; ++q) {
         uint32_t wmask = __reduce_or_sync(0xffffffffu, mask[q]);
         if (lane == 0 && wmask) atomicOr(&s_umask[q], wmask);
-        if (FILL) {
-          uint32_t mm = mask[q];
-          while (mm) {
-            int r = __ffs(mm) - 1;
-            mm &= mm - 1u;
-            atomicAdd(&s_cc[32 * q + r], 1);
-          }
-        }
+        if (FILL) s_cm[32 * q + lane][wid] = transpose32(mask[q], lane);
       }
       __syncthreads();
-      uint32_t um4[kChunk / 32];
+      uint32_t um4[kQ];
       int ucount = 0;
 #pragma unroll
-      for (int q = 0; q < kChunk / 32; ++q) {
+      for (int q = 0; q < kQ; ++q) {
         um4[q] = s_umask[q];
         ucount += __popc(um4[q]);
       }
 #pragma unroll
-      for (int q = 0; q < kChunk / 32; ++q) count += __popc(mask[q]);
+      for (int q = 0; q < kQ; ++q) count += __popc(mask[q]);
 
       if (FILL) {
-        // exclusive prefix of the column counts over the staged candidates
-        const int cc = s_cc[t];
+        // entries of staged candidate t (per cell word and in all) and their
+        // exclusive prefix over the staged candidates
+        int cw[kQ], cc = 0;
+#pragma unroll
+        for (int w = 0; w < kQ; ++w) {
+          cw[w] = __popc(s_cm[t][w]);
+          cc += cw[w];
+        }
         int incl = cc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           int y = __shfl_up_sync(0xffffffffu, incl, o);
           if (lane >= o) incl += y;
         }
-        if (lane == 31) s_wsum[wid] = incl;
+        if (lane == 31) s_red[wid] = incl;
         __syncthreads();
         int wpre = 0, total = 0;
 #pragma unroll
-        for (int w = 0; w < kChunk / 32; ++w) {
-          if (w < wid) wpre += s_wsum[w];
-          total += s_wsum[w];
+        for (int w = 0; w < kQ; ++w) {
+          if (w < wid) wpre += s_red[w];
+          total += s_red[w];
         }
-        const int pre_t = wpre + incl - cc;  // entries before candidate t
-        // candidate list and sub-chunk offsets (by the candidate's own thread)
+        const int pre_t = wpre + incl - cc;
+        s_pre[t] = pre_t;
+        if (t == 0) s_pre[kChunk] = total;
         {
-          int q = t >> 5, r = t & 31;
-          if ((um4[q] >> r) & 1u) {
-            int before = __popc(um4[q] & ((1u << r) - 1u));
-            for (int j = 0; j < q; ++j) before += __popc(um4[j]);
-            const int64_t loc = kcount + before;
-            cand_idx[cbase + loc] = s_n[t];
-            if ((loc & 31) == 0) sub_off[sbase + loc / 32] = ebase + erun + pre_t;
+          // entry of (cell 32 w + i, candidate t) = s_base[t][w] + (cells of
+          // word w below i that have t)
+          int acc = pre_t;
+#pragma unroll
+          for (int w = 0; w < kQ; ++w) {
+            s_base[t][w] = acc;
+            acc += cw[w];
           }
         }
-        // pre_t of every candidate, for the entry writes below
-        s_cc[t] = pre_t;
-        __syncthreads();
-        int pre = 0;
+        // candidate list and sub-chunk offsets (by the candidate's own thread)
+        if (cc > 0) {
+          int before = 0;
 #pragma unroll
-        for (int q = 0; q < kChunk / 32; ++q) {
+          for (int q = 0; q < kQ; ++q)
+            before += __popc(q < wid ? um4[q] : q == wid ? um4[q] & ((1u << lane) - 1u) : 0u);
+          const int64_t loc = kcount + before;
+          cand_idx[cbase + loc] = s_n[t];
+          if ((loc & 31) == 0) sub_off[sbase + loc / 32] = ebase + erun + pre_t;
+          s_loc[t] = (int)(loc & 31);
+        }
+        __syncthreads();
+        const uint32_t lt = (1u << lane) - 1u;
+        // The staged candidates in groups of 32 (at most 32 x 128 entries):
+        // list the group's (cell, candidate) pairs in entry order, compute
+        // the weights one entry per thread (coalesced writes), then add them
+        // into W of each cell in candidate order.
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const int g0 = s_pre[32 * q], gT = s_pre[32 * q + 32] - g0;
+          if (gT == 0) continue;
           uint32_t mm = mask[q];
           while (mm) {
-            int r = __ffs(mm) - 1;
+            const int r = __ffs(mm) - 1;
             mm &= mm - 1u;
-            int k = q * 32 + r;
-            int loc = (int)((kcount + pre + __popc(um4[q] & ((1u << r) - 1u))) & 63);
-            float nh[3] = {s_eh[0][k], s_eh[1][k], s_eh[2][k]};
-            float nl[3] = {s_el[0][k], s_el[1][k], s_el[2][k]};
-            float w = pair_weight(mh, ml, nh, nl, pp.k_hi, pp.k_lo);
-            int64_t e = ebase + erun + s_cc[k] + atomicAdd(&s_cur[k], 1);
-            ent_ck[e] = (uint16_t)((t << 6) | loc);
-            ent_w[e] = w;
-            {
-              const float bh = __bfloat162float(__float2bfloat16_rn(w));
-              const float bl = __bfloat162float(__float2bfloat16_rn(w - bh));
-              const float hh = __half2float(__float2half_rn(w));
-              const float hl = __half2float(__float2half_rn(w - hh));
-              wsv[0].add(w);
-              wsv[1].add(bh);
-              wsv[2].add(bh + bl);
-              wsv[3].add(hh);
-              wsv[4].add(hh + hl);
-            }
+            const int k = 32 * q + r;
+            const int pos = s_base[k][wid] + __popc(s_cm[k][wid] & lt) - g0;
+            s_ent[pos] = (uint16_t)((t << 5) | r);
           }
-          pre += __popc(um4[q]);
+          __syncthreads();
+          for (int e = t; e < gT; e += kChunk) {
+            const int ent = s_ent[e];
+            const int cell = ent >> 5, k = 32 * q + (ent & 31);
+            const float ch[3] = {s_mh[0][cell], s_mh[1][cell], s_mh[2][cell]};
+            const float cl[3] = {s_ml[0][cell], s_ml[1][cell], s_ml[2][cell]};
+            const float nh[3] = {s_eh[0][k], s_eh[1][k], s_eh[2][k]};
+            const float nl[3] = {s_el[0][k], s_el[1][k], s_el[2][k]};
+            const float wgt = pair_weight(ch, cl, nh, nl, pp.k_hi, pp.k_lo);
+            const int64_t pos = ebase + erun + g0 + e;
+            ent_ck[pos] = (uint16_t)tile_off(cell, s_loc[k]);
+            ent_w[pos] = wgt;
+            s_w[e] = wgt;
+          }
+          __syncthreads();
+          mm = mask[q];
+          while (mm) {
+            const int r = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            const int k = 32 * q + r;
+            const float wgt = s_w[s_base[k][wid] + __popc(s_cm[k][wid] & lt) - g0];
+            wsv[0].add(wgt);
+            wsv[1].add(__half2float(__float2half_rn(wgt * kTcWeightScale)) *
+                       (1.0f / kTcWeightScale));
+          }
         }
         erun += total;
       }
@@ -574,11 +623,11 @@ __global__ void __launch_bounds__(kChunk)
     int c = count;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) s_wsum[wid] = c;
+    if (lane == 0) s_red[wid] = c;
     __syncthreads();
     if (t == 0) {
       int tot = 0;
-      for (int w = 0; w < kChunk / 32; ++w) tot += s_wsum[w];
+      for (int w = 0; w < kQ; ++w) tot += s_red[w];
       kpairs[b] = tot;
       kb[b] = (int32_t)kcount;
     }
@@ -1009,7 +1058,7 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
     std::vector<int64_t> off(M + 1, 0);
     for (int64_t b = 0; b < nb; ++b)
       for (int64_t e = soff[coff[b] / 32]; e < soff[coff[b + 1] / 32]; ++e)
-        off[cell_of(b, ck[e] >> 6) + 1]++;
+        off[cell_of(b, (int)(ck[e] >> 6)) + 1]++;
     for (int64_t m = 0; m < M; ++m) off[m + 1] += off[m];
     std::vector<int64_t> cur(off.begin(), off.end() - 1);
     std::vector<std::pair<int32_t, float>> pr(std::max<int64_t>(P, 1));
@@ -1017,8 +1066,10 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
       for (int64_t j = coff[b] / 32; j < coff[b + 1] / 32; ++j) {
         const int64_t loc0 = 32 * j - coff[b];
         for (int64_t e = soff[j]; e < soff[j + 1]; ++e) {
-          const int64_t m = cell_of(b, ck[e] >> 6);
-          const int64_t loc = loc0 + (ck[e] & 31);
+          int r, k;
+          hg::tile_rk(ck[e], r, k);
+          const int64_t m = cell_of(b, r);
+          const int64_t loc = loc0 + k;
           pr[cur[m]++] = {cidx[coff[b] + loc], w[e]};
         }
       }
