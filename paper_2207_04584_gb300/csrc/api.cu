@@ -1,9 +1,12 @@
 // C ABI of the grid step: validation, work-item tables, batched launches,
 // CUDA-graph batches and host-chunk streaming.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -54,8 +57,50 @@ GridJob make_job(const hegrid_plan* plan, const hegrid_grid_args& a, int64_t cti
   j.map = a.map_out;
   j.ld_map = a.ld_map;
   j.weight_out = a.weight_out;
+  j.n_rows = plan->N;
   j.n_ctiles = (a.n_channels + ctile - 1) / ctile;
   return j;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// Encode j.rows for the tensor-core kernel (channel tile width `tile`).
+hegrid_status encode_rows_map(GridJob& j, int tile) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return HEGRID_ERR_CUDA;
+  }
+  const bool wide = j.dtype == HEGRID_F32 || j.dtype == HEGRID_BF16X2;
+  const int eb = wide ? 4 : 2;
+  // The values as a 2-D array of raw 2- or 4-byte words: C channels (inner,
+  // channels past C read as zero) x N sample rows, rows ld_values apart.
+  cuuint64_t dims[2] = {(cuuint64_t)j.C, (cuuint64_t)j.n_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)j.ld_values * eb};
+  cuuint32_t box[2] = {(cuuint32_t)tile, 1u}, estr[2] = {1u, 1u};
+  CUresult r = enc(&j.rows, wide ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                   2, const_cast<void*>(j.values), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return HEGRID_ERR_CUDA;
+  }
+  return HEGRID_OK;
 }
 
 // Launch all jobs of one kernel family, kMaxJobs per launch.
@@ -92,8 +137,11 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
     if (wait_ready) HG_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ready, 0));
     if (args[i].mode == HEGRID_MODE_FP32)
       f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
-    else
+    else {
       tc.push_back(make_job(plans[i], args[i], tc_channel_tile()));
+      hegrid_status st = encode_rows_map(tc.back(), tc_channel_tile());
+      if (st != HEGRID_OK) return st;
+    }
   }
   if (!f32.empty()) {
     hegrid_status st = launch_family(f32, false, s);

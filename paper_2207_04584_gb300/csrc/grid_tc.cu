@@ -59,8 +59,10 @@ constexpr int kK = 32;                     // candidates per chunk (64-byte rows
 constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
-constexpr int kRawStages = 4;              // staged sample rows ring
-constexpr int kRawPitch = kN * 4;          // bytes per staged row (FP32 worst case)
+constexpr int kRawStages = 3;              // staged sample rows + weight entries ring
+constexpr int kEntCap = 1792;              // weight entries staged per chunk (more: read from global)
+constexpr int kEntStage = kEntCap - 8;     // entries copied (leaves room for 16-byte alignment)
+constexpr int kRawPitch = kN * 4;          // bytes per staged row slot (4-byte elements)
 constexpr uint32_t kTmemCols = 512;        // segment sums in [0,256), running total in [256,512)
 constexpr uint32_t kTotCol = 256;
 #ifndef HG_TC_SEG
@@ -68,17 +70,28 @@ constexpr uint32_t kTotCol = 256;
 #endif
 constexpr int kSeg = HG_TC_SEG;            // chunks per accumulation segment
 constexpr int kBand = 8;                   // blocks per band of the work order
-constexpr int kPre = 4;                    // weight entries prefetched per producer thread
 constexpr int kHalves = kProducers / kN;   // producer threads per B row
 constexpr int kKT = kK / kHalves;          // samples of a row converted per thread
+
+// Where a staged chunk's weight entries are: e_lo is the global index of its
+// first entry, n the number of entries, ns how many were staged; entry i < ns
+// sits at byte ck_off + 2 i of eck[] and w_off + 4 i of ew[].
+struct EntInfo {
+  int64_t e_lo;
+  int32_t n, ns;
+  uint32_t ck_off, w_off;
+};
 
 struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
   uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
+  uint8_t eck[kRawStages][kEntCap * 2];     // staged entry tile offsets (16-byte aligned window)
+  uint8_t ew[kRawStages][kEntCap * 4];      // staged entry weights (16-byte aligned window)
+  EntInfo einfo[kRawStages];
   uint32_t red[3][2];                        // range slots: max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
-  uint64_t raw_full[kRawStages], raw_empty[kRawStages];
+  uint64_t raw_full[kRawStages], raw_empty[kRawStages], ent_empty[kRawStages];
   uint64_t ab_full[kStages], ab_empty[kStages];
   uint64_t segdone, segfree, totfree;
   uint32_t tmem_base;
@@ -157,40 +170,22 @@ __device__ __forceinline__ void split2(float v0, float v1, bool h16, uint32_t& h
 __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uint_as_float(b16 << 16); }
 
 // Producer side of one work item (warps 0-15): for every chunk, convert the
-// staged rows into the B tiles and scatter the weight entries into the A
-// tiles.  DT is the stored value type; SPLIT selects the hi/lo form.  rslot
+// staged rows into the B tiles and store the staged weight entries into the
+// A tiles.  DT is the stored value type; SPLIT selects the hi/lo form.  rslot
 // rotates over the three range-reduction slots (see below).
 // Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT>
-__device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_t kb0, int n_chunks,
+__device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_chunks,
                                              int64_t c0, uint32_t& g, uint32_t& gr,
                                              uint32_t& rslot, int32_t* err) {
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
-  constexpr uint32_t kNone = 0xffffu;  // no entry in this prefetch slot
   constexpr uint32_t kLoTile = kM * 64;  // A[s][1] follows A[s][0]
+  constexpr int kPitch = kWide ? kRawPitch : kRawPitch / 2;  // staged rows are packed
   const int tid = threadIdx.x, lane = tid & 31;
   const int row = tid % kN, kh = tid / kN;  // B row (channel c0 + row), half of the chunk
   const PlanView& pv = J.pv;
   const bool cvalid = c0 + row < J.C;
-  // The block's entries, indexed relative to its first one.
-  const int64_t* __restrict__ so = pv.sub_off + kb0 / 32;
-  const int64_t ebase = so[0];
-  const uint16_t* __restrict__ eck = pv.ent_ck + ebase;
-  const float* __restrict__ ew = pv.ent_w + ebase;
-  // Weight entries are software-pipelined one chunk ahead: while chunk j is
-  // converted, the loads of chunk j+1's entries are in flight.
-  int e_lo = 0;
-  int e_hi = (int)(so[1] - ebase);
-  int e_nx = n_chunks > 1 ? (int)(so[2] - ebase) : e_hi;
-  uint32_t pck[kPre];
-  float pw[kPre];
-#pragma unroll
-  for (int i = 0; i < kPre; ++i) {
-    const int e = e_lo + tid + i * kProducers;
-    pck[i] = e < e_hi ? (uint32_t)__ldcs(eck + e) : kNone;
-    pw[i] = e < e_hi ? __ldcs(ew + e) : 0.0f;
-  }
   constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
   constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
   constexpr uint32_t kBits2m14 = 0x38800000u;    // 2^-14 (smallest normal FP16)
@@ -198,28 +193,18 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
   for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
     const int s = g % kStages;
     const int rs = gr % kRawStages;
-    // Next chunk's entries (streaming loads, consumed one iteration later).
-    uint32_t nck[kPre];
-    float nw[kPre];
-#pragma unroll
-    for (int i = 0; i < kPre; ++i) {
-      const int e = e_hi + tid + i * kProducers;
-      nck[i] = e < e_nx ? (uint32_t)__ldcs(eck + e) : kNone;
-      nw[i] = e < e_nx ? __ldcs(ew + e) : 0.0f;
-    }
-    const int e_nx2 = j + 2 < n_chunks ? (int)(__ldg(so + j + 3) - ebase) : e_nx;
     if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
     // Channel column `row` of this thread's half of the staged rows.
     uint32_t x[kKT];
     {
-      const uint32_t rb = smem_u32(S.raw[rs]) + kh * kKT * kRawPitch;
+      const uint32_t rb = smem_u32(S.raw[rs]) + kh * kKT * kPitch;
 #pragma unroll
       for (int k = 0; k < kKT; ++k) {
         if (kWide)
-          x[k] = cvalid ? ld_shared_u32(rb + k * kRawPitch + row * 4) : 0u;
+          x[k] = cvalid ? ld_shared_u32(rb + k * kPitch + row * 4) : 0u;
         else
-          x[k] = cvalid ? ld_shared_u16(rb + k * kRawPitch + row * 2) : 0u;
+          x[k] = cvalid ? ld_shared_u16(rb + k * kPitch + row * 2) : 0u;
       }
     }
     __syncwarp();
@@ -228,18 +213,19 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
     // max |v| and, for BF16 input, min nonzero |v|, as float bit patterns,
     // combined over the producers in slot rslot (warp maxima, shared atomics).
     if (DT != HEGRID_F16) {
-      float fmx = 0.0f;
+      float fm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       uint32_t mn = kInf;
 #pragma unroll
       for (int k = 0; k < kKT; ++k) {
         if (DT == HEGRID_F32) {
-          fmx = fmaxf(fmx, fabsf(__uint_as_float(x[k])));  // NaN is dropped, Inf kept
+          fm[k & 3] = fmaxf(fm[k & 3], fabsf(__uint_as_float(x[k])));  // NaN dropped, Inf kept
         } else {  // BF16 and BF16X2: the (high) BF16 part
           const uint32_t a = (x[k] << 16) & 0x7fffffffu;
-          fmx = fmaxf(fmx, __uint_as_float(a));
+          fm[k & 3] = fmaxf(fm[k & 3], __uint_as_float(a));
           if (DT == HEGRID_BF16) mn = min(mn, a == 0u ? kInf : a);
         }
       }
+      const float fmx = fmaxf(fmaxf(fm[0], fm[1]), fmaxf(fm[2], fm[3]));
       const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fmx));
       if (DT == HEGRID_BF16) mn = __reduce_min_sync(0xffffffffu, mn);
       if (lane == 0) {
@@ -309,39 +295,41 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int64_
         if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
       }
     }
-    // A tiles: the chunk's weight entries, scaled by kTcWeightScale and split
-    // into the chunk's 16-bit format, stored at their precomputed offsets.
+    // A tiles: the chunk's weight entries (staged in shared memory by the
+    // row stager; any beyond the staging capacity come from global memory),
+    // scaled by kTcWeightScale, split into the chunk's 16-bit format and
+    // stored at their precomputed tile offsets; two entries per step.
     {
+      const EntInfo ei = S.einfo[rs];
       const uint32_t ah = smem_u32(S.A[s][0]);
-#pragma unroll
-      for (int i = 0; i < kPre; i += 2) {
-        uint32_t h2, l2;
-        split2(pw[i] * kTcWeightScale, pw[i + 1] * kTcWeightScale, h16, h2, l2);
-        if (pck[i] != kNone) {
-          st_shared_u16(ah + pck[i], (uint16_t)(h2 & 0xffffu));
-          if (SPLIT) st_shared_u16(ah + kLoTile + pck[i], (uint16_t)(l2 & 0xffffu));
+      const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
+      auto entry = [&](int i, uint32_t& off, float& w) {
+        if (i < ei.ns) {
+          off = ld_shared_u16(eck + 2 * i);
+          w = __uint_as_float(ld_shared_u32(ew + 4 * i));
+        } else {
+          off = __ldg(pv.ent_ck + ei.e_lo + i);
+          w = __ldg(pv.ent_w + ei.e_lo + i);
         }
-        if (pck[i + 1] != kNone) {
-          st_shared_u16(ah + pck[i + 1], (uint16_t)(h2 >> 16));
-          if (SPLIT) st_shared_u16(ah + kLoTile + pck[i + 1], (uint16_t)(l2 >> 16));
+      };
+      for (int i = tid; i < ei.n; i += 2 * kProducers) {
+        const int i1 = i + kProducers;
+        uint32_t o0, o1 = 0u;
+        float w0, w1 = 0.0f;
+        entry(i, o0, w0);
+        if (i1 < ei.n) entry(i1, o1, w1);
+        uint32_t h2, l2;
+        split2(w0 * kTcWeightScale, w1 * kTcWeightScale, h16, h2, l2);
+        st_shared_u16(ah + o0, (uint16_t)(h2 & 0xffffu));
+        if (SPLIT) st_shared_u16(ah + kLoTile + o0, (uint16_t)(l2 & 0xffffu));
+        if (i1 < ei.n) {
+          st_shared_u16(ah + o1, (uint16_t)(h2 >> 16));
+          if (SPLIT) st_shared_u16(ah + kLoTile + o1, (uint16_t)(l2 >> 16));
         }
       }
-      for (int e = e_lo + tid + kPre * kProducers; e < e_hi; e += kProducers) {
-        const uint32_t off = __ldcs(eck + e);
-        uint32_t h2, l2;
-        split2(__ldcs(ew + e) * kTcWeightScale, 0.0f, h16, h2, l2);
-        st_shared_u16(ah + off, (uint16_t)(h2 & 0xffffu));
-        if (SPLIT) st_shared_u16(ah + kLoTile + off, (uint16_t)(l2 & 0xffffu));
-      }
     }
-    e_lo = e_hi;
-    e_hi = e_nx;
-    e_nx = e_nx2;
-#pragma unroll
-    for (int i = 0; i < kPre; ++i) {
-      pck[i] = nck[i];
-      pw[i] = nw[i];
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.ent_empty[rs]);
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.ab_full[s]);
@@ -362,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     for (int i = 0; i < kRawStages; ++i) {
       mbar_init(&S.raw_full[i], 1);
       mbar_init(&S.raw_empty[i], kProducerWarps);
+      mbar_init(&S.ent_empty[i], kProducerWarps);
     }
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&S.ab_full[i], kProducerWarps);
@@ -407,24 +396,63 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int eb = (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) ? 4 : 2;
 
     if (warp == kTmaWarp) {
-      // ---------------- row stager ----------------
-      const int64_t cw = C - c0 < kN ? C - c0 : kN;
-      const uint32_t row_bytes = (uint32_t)((cw * eb + 15) / 16 * 16);
-      const uint8_t* vals = static_cast<const uint8_t*>(J.values);
-      int64_t n_next = n_chunks > 0 ? __ldg(pv.cand_idx + kb0 + lane) : 0;
+      // ---------------- row and entry stager ----------------
+      // Per chunk: the 32 sample rows (eight four-row tensor gathers of the
+      // channel tile; channels past C arrive as zeros) and the chunk's
+      // weight entries (two bulk copies of 16-byte aligned windows), all
+      // completing on raw_full.  Candidate indices are loaded two chunks
+      // ahead, sub-chunk offsets 31 chunks at a time.
+      const uint32_t row_bytes = (uint32_t)(kN * eb);
+      const void* tmap = &J.rows;
+      const int64_t* __restrict__ so = pv.sub_off + kb0 / kK;
+      int32_t nA = n_chunks > 0 ? __ldg(pv.cand_idx + kb0 + lane) : 0;
+      int32_t nB = n_chunks > 1 ? __ldg(pv.cand_idx + kb0 + kK + lane) : 0;
+      int64_t sob = 0;
       for (int j = 0; j < n_chunks; ++j, ++gr) {
         const int r = gr % kRawStages;
         const uint32_t u = gr / kRawStages;
-        const int64_t n = n_next;  // this lane's row, loaded one chunk ahead
-        if (j + 1 < n_chunks) n_next = __ldg(pv.cand_idx + kb0 + (int64_t)(j + 1) * kK + lane);
-        if (u >= 1 && !mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err)) {
+        const int jb = j % 31;
+        if (jb == 0) sob = j + lane <= n_chunks ? __ldg(so + j + lane) : 0;
+        const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb);
+        const int64_t e_hi = __shfl_sync(0xffffffffu, sob, jb + 1);
+        const int32_t n = nA;  // this lane's row
+        nA = nB;
+        if (j + 2 < n_chunks) nB = __ldg(pv.cand_idx + kb0 + (int64_t)(j + 2) * kK + lane);
+        if (u >= 1 && !(mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err) &&
+                        mbar_wait(&S.ent_empty[r], (u - 1) & 1u, err))) {
           bail = true;
           break;
         }
-        if (lane == 0) mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * kK);
+        const int ne = (int)(e_hi - e_lo);
+        const int ns = ne < kEntStage ? ne : kEntStage;
+        const int64_t a0 = (e_lo * 2) & ~(int64_t)15, b0 = (e_lo * 4) & ~(int64_t)15;
+        const uint32_t abytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 2 + 15) & ~(int64_t)15) - a0) : 0u;
+        const uint32_t wbytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 4 + 15) & ~(int64_t)15) - b0) : 0u;
+        if (lane == 0) {
+          EntInfo ei;
+          ei.e_lo = e_lo;
+          ei.n = ne;
+          ei.ns = ns;
+          ei.ck_off = (uint32_t)(e_lo * 2 - a0);
+          ei.w_off = (uint32_t)(e_lo * 4 - b0);
+          S.einfo[r] = ei;
+          mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * kK + abytes + wbytes);
+        }
         __syncwarp();
-        bulk_g2s(&S.raw[r][lane * kRawPitch], vals + (n * J.ld_values + c0) * eb, row_bytes,
-                 &S.raw_full[r]);
+        {
+          const int q4 = (lane & 7) * 4;
+          const int32_t r0 = __shfl_sync(0xffffffffu, n, q4), r1 = __shfl_sync(0xffffffffu, n, q4 + 1);
+          const int32_t r2 = __shfl_sync(0xffffffffu, n, q4 + 2), r3 = __shfl_sync(0xffffffffu, n, q4 + 3);
+          if (lane < 8)
+            tma_gather4(&S.raw[r][lane * 4 * row_bytes], tmap, (int32_t)c0, r0, r1, r2, r3,
+                        &S.raw_full[r]);
+        }
+        if (lane == 0 && abytes)
+          bulk_g2s(S.eck[r], reinterpret_cast<const uint8_t*>(pv.ent_ck) + a0, abytes,
+                   &S.raw_full[r]);
+        if (lane == 1 && wbytes)
+          bulk_g2s(S.ew[r], reinterpret_cast<const uint8_t*>(pv.ent_w) + b0, wbytes,
+                   &S.raw_full[r]);
       }
       continue;
     }
@@ -576,17 +604,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       bool ok = true;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, kb0, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
         }
       }
       bail = !ok;

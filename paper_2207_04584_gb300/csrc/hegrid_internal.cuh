@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of libhegrid.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -134,6 +135,9 @@ struct hegrid_plan {
 namespace hg {
 
 struct GridJob {
+  // Tensor map of the values (rows = samples, 256-channel boxes one row
+  // high) for the tensor-core kernel's row gathers; unused by the FP32 kernel.
+  CUtensorMap rows;
   PlanView pv;
   const void* values;
   int32_t dtype;
@@ -142,6 +146,7 @@ struct GridJob {
   float* map;
   int64_t ld_map;
   float* weight_out;
+  int64_t n_rows;     // samples (rows of the values)
   int64_t n_ctiles;   // channel tiles
   int64_t item_base;  // first work item of this job in the queue
 };

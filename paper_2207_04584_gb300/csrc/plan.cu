@@ -922,8 +922,10 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
 
   // --- a4 fill + a5 weights ------------------------------------------------
   const int64_t n_sub = p->n_cand / 32;
-  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P, &bytes, st));
-  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P, &bytes, st));
+  // (+16 bytes: the tensor-core kernel stages entries in 16-byte aligned
+  // windows that may reach past the last entry)
+  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P + 8, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P + 4, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->sub_off, n_sub + 1, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->wsum, kWsumVariants * p->M, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes, st));

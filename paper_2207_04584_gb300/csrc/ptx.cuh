@@ -87,6 +87,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
       : "memory");
 }
 
+// Tensor gather of four rows (TMA, tile::gather4): box (width x 1) of the
+// 2-D tensor map at column x of rows r0..r3, stored as four consecutive
+// box rows at dst_smem; completes on `bar`.  x times the element size must be
+// a multiple of 16 bytes.
+__device__ __forceinline__ void tma_gather4(void* dst_smem, const void* tmap, int32_t x, int32_t r0,
+                                            int32_t r1, int32_t r2, int32_t r3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst_smem)),
+      "l"(tmap), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Make generic-proxy writes to shared memory visible to the async proxy
 // (tensor cores, TMA).
 __device__ __forceinline__ void fence_proxy_async_smem() {
