@@ -42,6 +42,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "hegrid_internal.cuh"
 #include "ptx.cuh"
@@ -66,7 +67,7 @@ constexpr int kRawPitch = kN * 4;          // bytes per staged row slot (4-byte 
 constexpr uint32_t kTmemCols = 512;        // segment sums in [0,256), running total in [256,512)
 constexpr uint32_t kTotCol = 256;
 #ifndef HG_TC_SEG
-#define HG_TC_SEG 16
+#define HG_TC_SEG 32
 #endif
 constexpr int kSeg = HG_TC_SEG;            // chunks per accumulation segment
 constexpr int kBand = 8;                   // blocks per band of the work order
@@ -150,9 +151,10 @@ __device__ __forceinline__ void named_bar_producers() {
 }
 
 // Per-value 16-bit split of two FP32 values: hi = RN(v), lo = RN(v - hi), in
-// FP16 or BF16, packed two per 32-bit word.
-__device__ __forceinline__ void split2(float v0, float v1, bool h16, uint32_t& hi, uint32_t& lo) {
-  if (h16) {
+// FP16 (H16) or BF16, packed two per 32-bit word.
+template <bool H16>
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  if (H16) {
     const __half2 h = __float22half2_rn(make_float2(v0, v1));
     const float2 f = __half22float2(h);
     const __half2 l = __float22half2_rn(make_float2(v0 - f.x, v1 - f.y));
@@ -185,7 +187,6 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
   const int tid = threadIdx.x, lane = tid & 31;
   const int row = tid % kN, kh = tid / kN;  // B row (channel c0 + row), half of the chunk
   const PlanView& pv = J.pv;
-  const bool cvalid = c0 + row < J.C;
   constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
   constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
   constexpr uint32_t kBits2m14 = 0x38800000u;    // 2^-14 (smallest normal FP16)
@@ -195,16 +196,17 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
     const int rs = gr % kRawStages;
     if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
-    // Channel column `row` of this thread's half of the staged rows.
+    // Channel column `row` of this thread's half of the staged rows (the
+    // gathers fill channels past C with zeros).
     uint32_t x[kKT];
     {
       const uint32_t rb = smem_u32(S.raw[rs]) + kh * kKT * kPitch;
 #pragma unroll
       for (int k = 0; k < kKT; ++k) {
         if (kWide)
-          x[k] = cvalid ? ld_shared_u32(rb + k * kPitch + row * 4) : 0u;
+          x[k] = ld_shared_u32(rb + k * kPitch + row * 4);
         else
-          x[k] = cvalid ? ld_shared_u16(rb + k * kPitch + row * 2) : 0u;
+          x[k] = ld_shared_u16(rb + k * kPitch + row * 2);
       }
     }
     __syncwarp();
@@ -242,6 +244,7 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
         if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
       }
     }
+    const EntInfo ei = S.einfo[rs];
     named_bar_producers();
     bool h16 = true;
     if (DT != HEGRID_F16) {
@@ -260,74 +263,85 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
       S.red[rr][1] = kInf;
     }
     rslot = rslot == 2u ? 0u : rslot + 1u;
-    // B tiles: row `row` holds the chunk's samples of channel c0 + row; this
-    // thread writes its half (16-byte chunks kh*kKT/8 ...).
-    {
-      const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
+    // The tiles in the chunk's format (one branch for the whole chunk).
+    auto tiles = [&](auto fmt) {
+      constexpr bool H16 = decltype(fmt)::value;
+      // B tiles: row `row` holds the chunk's samples of channel c0 + row; this
+      // thread writes its half (16-byte chunks kh*kKT/8 ...).
+      {
+        const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
-      for (int qq = 0; qq < kKT / 8; ++qq) {
-        const int q = kh * (kKT / 8) + qq;
-        uint32_t h2[4], l2[4];
+        for (int qq = 0; qq < kKT / 8; ++qq) {
+          const int q = kh * (kKT / 8) + qq;
+          uint32_t h2[4], l2[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const uint32_t x0 = x[qq * 8 + 2 * e], x1 = x[qq * 8 + 2 * e + 1];
-          if (DT == HEGRID_F32) {
-            split2(__uint_as_float(x0), __uint_as_float(x1), h16, h2[e], l2[e]);
-          } else if (DT == HEGRID_BF16X2) {
-            const float v0 = bf16_bits_to_float(x0 & 0xffffu) + bf16_bits_to_float(x0 >> 16);
-            const float v1 = bf16_bits_to_float(x1 & 0xffffu) + bf16_bits_to_float(x1 >> 16);
-            split2(v0, v1, h16, h2[e], l2[e]);
-          } else if (DT == HEGRID_BF16) {
-            if (h16) {  // exact in FP16 (checked above)
-              const __half2 h = __float22half2_rn(
-                  make_float2(bf16_bits_to_float(x0), bf16_bits_to_float(x1)));
-              h2[e] = *reinterpret_cast<const uint32_t*>(&h);
-            } else {
+          for (int e = 0; e < 4; ++e) {
+            const uint32_t x0 = x[qq * 8 + 2 * e], x1 = x[qq * 8 + 2 * e + 1];
+            if (DT == HEGRID_F32) {
+              split2<H16>(__uint_as_float(x0), __uint_as_float(x1), h2[e], l2[e]);
+            } else if (DT == HEGRID_BF16X2) {
+              const float v0 = bf16_bits_to_float(x0 & 0xffffu) + bf16_bits_to_float(x0 >> 16);
+              const float v1 = bf16_bits_to_float(x1 & 0xffffu) + bf16_bits_to_float(x1 >> 16);
+              split2<H16>(v0, v1, h2[e], l2[e]);
+            } else if (DT == HEGRID_BF16) {
+              if (H16) {  // exact in FP16 (checked above)
+                const __half2 h = __float22half2_rn(
+                    make_float2(bf16_bits_to_float(x0), bf16_bits_to_float(x1)));
+                h2[e] = *reinterpret_cast<const uint32_t*>(&h);
+              } else {
+                h2[e] = x0 | (x1 << 16);
+              }
+              l2[e] = 0u;
+            } else {  // F16
               h2[e] = x0 | (x1 << 16);
+              l2[e] = 0u;
             }
-            l2[e] = 0u;
-          } else {  // F16
-            h2[e] = x0 | (x1 << 16);
-            l2[e] = 0u;
           }
-        }
-        st_shared_v4(bh + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
-        if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
-      }
-    }
-    // A tiles: the chunk's weight entries (staged in shared memory by the
-    // row stager; any beyond the staging capacity come from global memory),
-    // scaled by kTcWeightScale, split into the chunk's 16-bit format and
-    // stored at their precomputed tile offsets; two entries per step.
-    {
-      const EntInfo ei = S.einfo[rs];
-      const uint32_t ah = smem_u32(S.A[s][0]);
-      const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
-      auto entry = [&](int i, uint32_t& off, float& w) {
-        if (i < ei.ns) {
-          off = ld_shared_u16(eck + 2 * i);
-          w = __uint_as_float(ld_shared_u32(ew + 4 * i));
-        } else {
-          off = __ldg(pv.ent_ck + ei.e_lo + i);
-          w = __ldg(pv.ent_w + ei.e_lo + i);
-        }
-      };
-      for (int i = tid; i < ei.n; i += 2 * kProducers) {
-        const int i1 = i + kProducers;
-        uint32_t o0, o1 = 0u;
-        float w0, w1 = 0.0f;
-        entry(i, o0, w0);
-        if (i1 < ei.n) entry(i1, o1, w1);
-        uint32_t h2, l2;
-        split2(w0 * kTcWeightScale, w1 * kTcWeightScale, h16, h2, l2);
-        st_shared_u16(ah + o0, (uint16_t)(h2 & 0xffffu));
-        if (SPLIT) st_shared_u16(ah + kLoTile + o0, (uint16_t)(l2 & 0xffffu));
-        if (i1 < ei.n) {
-          st_shared_u16(ah + o1, (uint16_t)(h2 >> 16));
-          if (SPLIT) st_shared_u16(ah + kLoTile + o1, (uint16_t)(l2 >> 16));
+          st_shared_v4(bh + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
+          if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
         }
       }
-    }
+      // A tiles: the chunk's weight entries (staged in shared memory by the
+      // row stager; any beyond the staging capacity come from global memory),
+      // scaled by kTcWeightScale, split into the chunk's 16-bit format and
+      // stored at their precomputed tile offsets; two entries per step.
+      {
+        const uint32_t ah = smem_u32(S.A[s][0]);
+        const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
+        auto entry = [&](int i, uint32_t& off, float& w) {
+          if (i < ei.ns) {
+            off = ld_shared_u16(eck + 2 * i);
+            w = __uint_as_float(ld_shared_u32(ew + 4 * i));
+          } else {
+            off = __ldg(pv.ent_ck + ei.e_lo + i);
+            w = __ldg(pv.ent_w + ei.e_lo + i);
+          }
+        };
+        auto put2 = [&](int i0) {
+          const int i1 = i0 + kProducers;
+          uint32_t o0 = 0u, o1 = 0u;
+          float w0 = 0.0f, w1 = 0.0f;
+          if (i0 < ei.n) entry(i0, o0, w0);
+          if (i1 < ei.n) entry(i1, o1, w1);
+          uint32_t h2, l2;
+          split2<H16>(w0 * kTcWeightScale, w1 * kTcWeightScale, h2, l2);
+          if (i0 < ei.n) {
+            st_shared_u16(ah + o0, (uint16_t)(h2 & 0xffffu));
+            if (SPLIT) st_shared_u16(ah + kLoTile + o0, (uint16_t)(l2 & 0xffffu));
+          }
+          if (i1 < ei.n) {
+            st_shared_u16(ah + o1, (uint16_t)(h2 >> 16));
+            if (SPLIT) st_shared_u16(ah + kLoTile + o1, (uint16_t)(l2 >> 16));
+          }
+        };
+        put2(tid);
+        for (int i = tid + 2 * kProducers; i < ei.n; i += 2 * kProducers) put2(i);
+      }
+    };
+    if (h16)
+      tiles(std::true_type{});
+    else
+      tiles(std::false_type{});
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.ent_empty[rs]);
     fence_proxy_async_smem();
@@ -568,25 +582,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       const float Wm = active ? pv.wsum[(int64_t)(split ? 0 : 1) * pv.M + m] : 0.0f;
       const float W = Wm * kTcWeightScale;
       const bool ok = W > 0.0f;
-      uint32_t t[16];
+      // 32 columns per step: each lane writes whole 128-byte lines of its row
+      uint32_t t[32];
 #pragma unroll 1
-      for (int cb = 0; cb < kN / 16; ++cb) {
-        tmem_ld_32x32b_x16(ttot + cb * 16, t);
+      for (int cb = 0; cb < kN / 32; ++cb) {
+        tmem_ld_32x32b_x32(ttot + cb * 32, t);
         tmem_ld_wait();
         if (active) {
-          const int64_t cbase = c0 + cb * 16;
-          float v[16];
+          const int64_t cbase = c0 + cb * 32;
+          if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = ok ? __fdiv_rn(__uint_as_float(t[i]), W) : qnan;
-          if (cbase + 16 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
-#pragma unroll
-            for (int i = 0; i < 16; i += 4)
+            for (int i = 0; i < 32; i += 4)
               __stcs(reinterpret_cast<float4*>(out + cbase + i),
-                     make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+                     ok ? make_float4(__fdiv_rn(__uint_as_float(t[i]), W),
+                                      __fdiv_rn(__uint_as_float(t[i + 1]), W),
+                                      __fdiv_rn(__uint_as_float(t[i + 2]), W),
+                                      __fdiv_rn(__uint_as_float(t[i + 3]), W))
+                        : make_float4(qnan, qnan, qnan, qnan));
           } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (cbase + i < C) __stcs(out + cbase + i, v[i]);
+            for (int i = 0; i < 32; ++i)
+              if (cbase + i < C) __stcs(out + cbase + i, ok ? __fdiv_rn(__uint_as_float(t[i]), W) : qnan);
           }
         }
       }
