@@ -165,7 +165,8 @@ hegrid_status hegrid_grid_stream(hegrid_plan *plan, const void *const *host_chun
                                  int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,
                                  float *host_map, int64_t ld_host_map, float *host_weight);
 
-/* Plan sizes: pairs P, bins, cell blocks, candidate slots, device bytes held. */
+/* Plan sizes: pairs P, bins, cell blocks, candidate slots in use (padded to 64
+ * per block), device bytes held.  Waits until the plan has been built. */
 hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_t *n_bins,
                                int64_t *n_blocks, int64_t *n_cand, int64_t *bytes);
 

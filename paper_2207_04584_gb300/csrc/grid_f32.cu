@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const float* __restrict__ vals = static_cast<const float*>(J.values);
     const int bbx = (int)(b % pv.nbx_b), bby = (int)(b / pv.nbx_b);
     const int64_t kb0 = pv.cand_off[b];
-    const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kKC);
+    const int n_chunks = pv.cand_cnt[b] / kKC;
 
     const int64_t sub0 = kb0 / kKC;  // first 32-candidate sub-chunk of the block
 

@@ -209,8 +209,34 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
           x[k] = ld_shared_u16(rb + k * kPitch + row * 2);
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
+    // A tiles: zero (the scatter follows the barrier).  Independent of the
+    // loads above and below, so their latencies overlap.
+    {
+      const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
+#pragma unroll
+      for (int i = tid; i < kM * 64 / 16; i += kProducers) {
+        st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
+        if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
+      }
+    }
+    // The chunk's weight entries (staged in shared memory by the row stager;
+    // any beyond the staging capacity come from global memory): entries tid
+    // and tid + kProducers now, the rest (if any) after the barrier.
+    const EntInfo ei = S.einfo[rs];
+    const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
+    auto entry = [&](int i, uint32_t& off, float& w) {
+      if (i < ei.ns) {
+        off = ld_shared_u16(eck + 2 * i);
+        w = __uint_as_float(ld_shared_u32(ew + 4 * i));
+      } else {
+        off = __ldg(pv.ent_ck + ei.e_lo + i);
+        w = __ldg(pv.ent_w + ei.e_lo + i);
+      }
+    };
+    uint32_t o0 = 0u, o1 = 0u;
+    float w0 = 0.0f, w1 = 0.0f;
+    if (tid < ei.n) entry(tid, o0, w0);
+    if (tid + kProducers < ei.n) entry(tid + kProducers, o1, w1);
     // Range of the chunk's values (decides the 16-bit format of the chunk):
     // max |v| and, for BF16 input, min nonzero |v|, as float bit patterns,
     // combined over the producers in slot rslot (warp maxima, shared atomics).
@@ -235,16 +261,9 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
         if (DT == HEGRID_BF16) atomicMin(&S.red[rslot][1], mn);
       }
     }
-    // A tiles: zero (the scatter follows the barrier)
-    {
-      const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
-#pragma unroll
-      for (int i = tid; i < kM * 64 / 16; i += kProducers) {
-        st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
-        if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
-      }
-    }
-    const EntInfo ei = S.einfo[rs];
+    // the values are in registers: release the staged rows
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
     named_bar_producers();
     bool h16 = true;
     if (DT != HEGRID_F16) {
@@ -301,41 +320,31 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
           if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
         }
       }
-      // A tiles: the chunk's weight entries (staged in shared memory by the
-      // row stager; any beyond the staging capacity come from global memory),
-      // scaled by kTcWeightScale, split into the chunk's 16-bit format and
-      // stored at their precomputed tile offsets; two entries per step.
+      // A tiles: the chunk's weight entries, scaled by kTcWeightScale, split
+      // into the chunk's 16-bit format and stored at their precomputed tile
+      // offsets; two entries per step.
       {
         const uint32_t ah = smem_u32(S.A[s][0]);
-        const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
-        auto entry = [&](int i, uint32_t& off, float& w) {
-          if (i < ei.ns) {
-            off = ld_shared_u16(eck + 2 * i);
-            w = __uint_as_float(ld_shared_u32(ew + 4 * i));
-          } else {
-            off = __ldg(pv.ent_ck + ei.e_lo + i);
-            w = __ldg(pv.ent_w + ei.e_lo + i);
-          }
-        };
-        auto put2 = [&](int i0) {
-          const int i1 = i0 + kProducers;
-          uint32_t o0 = 0u, o1 = 0u;
-          float w0 = 0.0f, w1 = 0.0f;
-          if (i0 < ei.n) entry(i0, o0, w0);
-          if (i1 < ei.n) entry(i1, o1, w1);
+        auto put2 = [&](int i0, uint32_t p0, float v0, uint32_t p1, float v1) {
           uint32_t h2, l2;
-          split2<H16>(w0 * kTcWeightScale, w1 * kTcWeightScale, h2, l2);
+          split2<H16>(v0 * kTcWeightScale, v1 * kTcWeightScale, h2, l2);
           if (i0 < ei.n) {
-            st_shared_u16(ah + o0, (uint16_t)(h2 & 0xffffu));
-            if (SPLIT) st_shared_u16(ah + kLoTile + o0, (uint16_t)(l2 & 0xffffu));
+            st_shared_u16(ah + p0, (uint16_t)(h2 & 0xffffu));
+            if (SPLIT) st_shared_u16(ah + kLoTile + p0, (uint16_t)(l2 & 0xffffu));
           }
-          if (i1 < ei.n) {
-            st_shared_u16(ah + o1, (uint16_t)(h2 >> 16));
-            if (SPLIT) st_shared_u16(ah + kLoTile + o1, (uint16_t)(l2 >> 16));
+          if (i0 + kProducers < ei.n) {
+            st_shared_u16(ah + p1, (uint16_t)(h2 >> 16));
+            if (SPLIT) st_shared_u16(ah + kLoTile + p1, (uint16_t)(l2 >> 16));
           }
         };
-        put2(tid);
-        for (int i = tid + 2 * kProducers; i < ei.n; i += 2 * kProducers) put2(i);
+        put2(tid, o0, w0, o1, w1);
+        for (int i = tid + 2 * kProducers; i < ei.n; i += 2 * kProducers) {
+          uint32_t p0 = 0u, p1 = 0u;
+          float v0 = 0.0f, v1 = 0.0f;
+          entry(i, p0, v0);
+          if (i + kProducers < ei.n) entry(i + kProducers, p1, v1);
+          put2(i, p0, v0, p1, v1);
+        }
       }
     };
     if (h16)
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int64_t c0 = ct * kN;
     const int64_t C = J.C;
     const int64_t kb0 = pv.cand_off[b];
-    const int n_chunks = (int)((pv.cand_off[b + 1] - kb0) / kK);
+    const int n_chunks = pv.cand_cnt[b] / kK;
     const int n_seg = (n_chunks + kSeg - 1) / kSeg;
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);

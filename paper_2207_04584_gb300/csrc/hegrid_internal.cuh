@@ -77,9 +77,11 @@ struct PlanView {
   int64_t M;                // cells
   int64_t n_blocks;
   const float* wsum;        // [kWsumVariants * M] W per cell and weight representation
-  const int64_t* cand_off;  // [n_blocks+1] candidate slots per block (padded to 64)
+  const int64_t* cand_off;  // [n_blocks+1] first candidate slot of each block (multiple of 64)
+  const int32_t* cand_cnt;  // [n_blocks] candidates of each block, padded to a multiple of 64
   const int32_t* cand_idx;  // [n_cand] original sample index per slot
-  const int64_t* sub_off;   // [n_cand/32+1] first entry of each 32-candidate sub-chunk
+  const int64_t* sub_off;   // [slots/32+1] first entry of each 32-candidate sub-chunk
+                            // (a block's last sub-chunk is followed by its end sentinel)
   const uint16_t* ent_ck;   // [P] entry: tile_off(block-local cell, candidate & 31)
   const float* ent_w;       // [P] FP32 weight of the entry
   int32_t* err_word;        // device error word (bounded waits)
@@ -91,7 +93,9 @@ struct hegrid_plan {
   hegrid_map_geom geom;
   hegrid_kernel kern;
   int device;
-  int64_t N, M, P, n_bins, n_blocks, n_cand;
+  int64_t N, M, n_bins, n_blocks;
+  int64_t P_ub, slots;  // entries and candidate slots reserved (upper bounds)
+  int64_t P, n_cand;    // pairs and used candidate slots (-1 until read back)
   int32_t bin_cells, padx, pady, nbx, nby, nbx_b, nby_b;
   double sigma_rad, R_rad, R_deg;
   // device arrays (owned)
@@ -99,6 +103,8 @@ struct hegrid_plan {
   int32_t* bin_off;
   int64_t* cand_off;
   int64_t* blk_pair_off;
+  int32_t* cand_cnt;
+  unsigned long long* totals;  // device: pairs, used candidate slots
   int32_t* cand_idx;
   int64_t* sub_off;
   uint16_t* ent_ck;
@@ -120,6 +126,7 @@ struct hegrid_plan {
     v.n_blocks = n_blocks;
     v.wsum = wsum;
     v.cand_off = cand_off;
+    v.cand_cnt = cand_cnt;
     v.cand_idx = cand_idx;
     v.sub_off = sub_off;
     v.ent_ck = ent_ck;

@@ -5,7 +5,7 @@
 //   a2  bin key of the padded map (replaces the HEALPix pixel index)
 //   a3  stable LSD radix sort of (key, index) and bin-range offsets (the LUT)
 //   a4  per-cell neighbour lists (Algorithm 1's ring/pixel search and its
-//       d <= R test), two passes: count, then fill
+//       d <= R test), one pass into ranges reserved by upper bounds
 //   a5  FP32 weights of every in-radius pair, computed once and shared by all
 //       channels, plus W[m] = sum of the weights
 //
@@ -357,13 +357,13 @@ __device__ __forceinline__ float pair_weight(const float (&mh)[3], const float (
 }
 
 // One CTA per 16x8 cell block; thread t owns block-local cell t (= ly*16 + lx).
-// The samples of the bins around the block are staged kChunk at a time.
-// COUNT pass: number of distinct candidates (K_b, the union of the cells'
-// neighbours) and number of pairs of the block.  FILL pass: the candidate list
-// (original sample indices, union order), the weight entries of the block in
-// candidate-major order (entry = tile_off(cell, candidate & 31), FP32
-// weight; the cells of one candidate in increasing order), the offsets of
-// every 32-candidate sub-chunk, W[m].
+// The samples of the bins around the block are staged kChunk at a time and
+// tested against the block's cells.  The block writes, inside the slot and
+// entry ranges its upper bounds reserved: the candidate list (original sample
+// indices, union order, padded to HG_KPAD), its padded length, the weight
+// entries in 32-candidate sub-chunks (entry = tile_off(cell, candidate & 31),
+// FP32 weight; cell-major inside each sub-chunk), the offsets of every
+// sub-chunk plus an end sentinel, and W[m].
 // Neumaier-compensated running sum.
 struct CSum {
   float s = 0.0f, c = 0.0f;
@@ -387,16 +387,30 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
   return x;
 }
 
-template <bool FILL>
+// Position of the (j+1)-th set bit of x (j < popc(x)).
+__device__ __forceinline__ int select_bit(uint32_t x, int j) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const int c = __popc(x & ((1u << w) - 1u));
+    if (j >= c) {
+      j -= c;
+      pos += w;
+      x >>= w;
+    }
+  }
+  return pos;
+}
+
 __global__ void __launch_bounds__(kChunk)
     k_block_pairs(PairParams pp, const int4* __restrict__ win, const int32_t* __restrict__ bin_off,
                   const int32_t* __restrict__ perm, const double* __restrict__ sx,
                   const double* __restrict__ sy, const double* __restrict__ sz,
-                  int32_t* __restrict__ kb, int32_t* __restrict__ kpairs,
                   const int64_t* __restrict__ cand_off, const int64_t* __restrict__ blk_pair_off,
-                  int32_t* __restrict__ cand_idx, int64_t* __restrict__ sub_off,
-                  uint16_t* __restrict__ ent_ck, float* __restrict__ ent_w,
-                  float* __restrict__ wsum) {
+                  int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand_idx,
+                  int64_t* __restrict__ sub_off, uint16_t* __restrict__ ent_ck,
+                  float* __restrict__ ent_w, float* __restrict__ wsum,
+                  unsigned long long* __restrict__ totals) {
   constexpr int kQ = kChunk / 32;
   __shared__ float s_eh[3][kChunk];
   __shared__ float s_el[3][kChunk];
@@ -404,17 +418,17 @@ __global__ void __launch_bounds__(kChunk)
   __shared__ int32_t s_n[kChunk];
   __shared__ uint32_t s_umask[kQ];
   __shared__ int32_t s_red[kQ];
-  // FILL only: cell coordinates, candidate-major cell masks (bit i of
+  // Cell coordinates, candidate-major cell masks (bit i of
   // s_cm[k][w]: cell 32 w + i has staged candidate k), entries before each
   // staged candidate, candidate index within its 32-candidate sub-chunk.
-  __shared__ float s_mh[3][FILL ? kChunk : 1];
-  __shared__ float s_ml[3][FILL ? kChunk : 1];
-  __shared__ uint32_t s_cm[FILL ? kChunk : 1][kQ];
-  __shared__ int32_t s_pre[FILL ? kChunk + 1 : 1];
-  __shared__ int32_t s_loc[FILL ? kChunk : 1];
-  __shared__ int32_t s_base[FILL ? kChunk : 1][kQ];  // first entry of (candidate, cell word)
-  __shared__ uint16_t s_ent[FILL ? 32 * kChunk : 1];  // (cell << 5 | candidate) of a group
-  __shared__ float s_w[FILL ? 32 * kChunk : 1];       // weights of a group's entries
+  __shared__ float s_mh[3][kChunk];
+  __shared__ float s_ml[3][kChunk];
+  __shared__ uint32_t s_cm[kChunk][kQ];
+  __shared__ int32_t s_pre[kChunk + 1];
+  __shared__ int32_t s_loc[kChunk];
+  __shared__ int32_t s_gred[kQ];                     // per-warp partial sums of a group
+  __shared__ uint16_t s_ent[32 * kChunk];  // (cell << 5 | candidate) of a group
+  __shared__ float s_w[32 * kChunk];       // weights of a group's entries
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
@@ -438,14 +452,11 @@ __global__ void __launch_bounds__(kChunk)
     for (int i = 0; i < 3; ++i) {
       mh[i] = __double2float_rn(e[i]);
       ml[i] = __double2float_rn(e[i] - (double)mh[i]);
-      if (FILL) {
-        s_mh[i][t] = mh[i];
-        s_ml[i][t] = ml[i];
-      }
+      s_mh[i][t] = mh[i];
+      s_ml[i][t] = ml[i];
     }
   }
 
-  int32_t count = 0;   // pairs of this cell
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
   int64_t erun = 0;    // entries of the block so far
   // W of the cell for each weight representation the grid kernels use
@@ -453,12 +464,7 @@ __global__ void __launch_bounds__(kChunk)
   // that every form normalises by the sum of exactly the weights it
   // multiplied.
   CSum wsv[kWsumVariants];
-  int64_t cbase = 0, ebase = 0, sbase = 0;
-  if (FILL) {
-    cbase = cand_off[b];
-    ebase = blk_pair_off[b];
-    sbase = cbase / 32;
-  }
+  const int64_t cbase = cand_off[b], ebase = blk_pair_off[b], sbase = cbase / 32;
   const int4 wb = win[b];  // by0, by1, bx0, bx1
   for (int by = wb.x; by <= wb.y; ++by) {
     const int32_t s_beg = bin_off[(int64_t)by * pp.nbx + wb.z];
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kChunk)
       for (int q = 0; q < kQ; ++q) {
         uint32_t wmask = __reduce_or_sync(0xffffffffu, mask[q]);
         if (lane == 0 && wmask) atomicOr(&s_umask[q], wmask);
-        if (FILL) s_cm[32 * q + lane][wid] = transpose32(mask[q], lane);
+        s_cm[32 * q + lane][wid] = transpose32(mask[q], lane);
       }
       __syncthreads();
       uint32_t um4[kQ];
@@ -518,18 +524,12 @@ __global__ void __launch_bounds__(kChunk)
         um4[q] = s_umask[q];
         ucount += __popc(um4[q]);
       }
+      {
+        // entries of staged candidate t and their exclusive prefix over the
+        // staged candidates
+        int cc = 0;
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) count += __popc(mask[q]);
-
-      if (FILL) {
-        // entries of staged candidate t (per cell word and in all) and their
-        // exclusive prefix over the staged candidates
-        int cw[kQ], cc = 0;
-#pragma unroll
-        for (int w = 0; w < kQ; ++w) {
-          cw[w] = __popc(s_cm[t][w]);
-          cc += cw[w];
-        }
+        for (int w = 0; w < kQ; ++w) cc += __popc(s_cm[t][w]);
         int incl = cc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -547,16 +547,6 @@ __global__ void __launch_bounds__(kChunk)
         const int pre_t = wpre + incl - cc;
         s_pre[t] = pre_t;
         if (t == 0) s_pre[kChunk] = total;
-        {
-          // entry of (cell 32 w + i, candidate t) = s_base[t][w] + (cells of
-          // word w below i that have t)
-          int acc = pre_t;
-#pragma unroll
-          for (int w = 0; w < kQ; ++w) {
-            s_base[t][w] = acc;
-            acc += cw[w];
-          }
-        }
         // candidate list and sub-chunk offsets (by the candidate's own thread)
         if (cc > 0) {
           int before = 0;
@@ -569,22 +559,50 @@ __global__ void __launch_bounds__(kChunk)
           s_loc[t] = (int)(loc & 31);
         }
         __syncthreads();
-        const uint32_t lt = (1u << lane) - 1u;
         // The staged candidates in groups of 32 (at most 32 x 128 entries):
         // list the group's (cell, candidate) pairs in entry order, compute
         // the weights one entry per thread (coalesced writes), then add them
-        // into W of each cell in candidate order.
+        // into W of each cell in candidate order.  Within a group, entries
+        // are cell-major on each side of the 32-candidate sub-chunk boundary
+        // that may fall inside it (candidate r_split starts a new
+        // sub-chunk), so every sub-chunk's entries stay contiguous.
+        int ubefore = 0;  // union candidates of the staged chunk before group q
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
           const int g0 = s_pre[32 * q], gT = s_pre[32 * q + 32] - g0;
+          const uint32_t uq = um4[q];
+          const int jb = (int)((32 - ((kcount + ubefore) & 31)) & 31);
+          ubefore += __popc(uq);
           if (gT == 0) continue;
-          uint32_t mm = mask[q];
-          while (mm) {
-            const int r = __ffs(mm) - 1;
-            mm &= mm - 1u;
-            const int k = 32 * q + r;
-            const int pos = s_base[k][wid] + __popc(s_cm[k][wid] & lt) - g0;
-            s_ent[pos] = (uint16_t)((t << 5) | r);
+          const int r_split = jb < __popc(uq) ? select_bit(uq, jb) : 32;
+          const uint32_t amask = r_split >= 32 ? 0xffffffffu : ((1u << r_split) - 1u);
+          const int cA = __popc(mask[q] & amask), cB = __popc(mask[q] & ~amask);
+          // exclusive prefix of (cA, cB) over the cells, packed in 16-bit halves
+          const int v = cA | (cB << 16);
+          int inc = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+          }
+          if (lane == 31) s_gred[wid] = inc;
+          __syncthreads();
+          int wp = 0, tot = 0;
+#pragma unroll
+          for (int w = 0; w < kQ; ++w) {
+            if (w < wid) wp += s_gred[w];
+            tot += s_gred[w];
+          }
+          const int ex = wp + inc - v;
+          const int a0 = ex & 0xffff, b0 = (tot & 0xffff) + (ex >> 16);
+          {
+            int pa = a0, pb = b0;
+            uint32_t mm = mask[q];
+            while (mm) {
+              const int r = __ffs(mm) - 1;
+              mm &= mm - 1u;
+              s_ent[r < r_split ? pa++ : pb++] = (uint16_t)((t << 5) | r);
+            }
           }
           __syncthreads();
           for (int e = t; e < gT; e += kChunk) {
@@ -601,16 +619,16 @@ __global__ void __launch_bounds__(kChunk)
             s_w[e] = wgt;
           }
           __syncthreads();
-          mm = mask[q];
-          while (mm) {
-            const int r = __ffs(mm) - 1;
-            mm &= mm - 1u;
-            const int k = 32 * q + r;
-            const float wgt = s_w[s_base[k][wid] + __popc(s_cm[k][wid] & lt) - g0];
-            wsv[0].add(wgt);
-            wsv[1].add(__half2float(__float2half_rn(wgt * kTcWeightScale)) *
-                       (1.0f / kTcWeightScale));
-          }
+          auto addw = [&](int e0, int n) {
+            for (int e = e0; e < e0 + n; ++e) {
+              const float wgt = s_w[e];
+              wsv[0].add(wgt);
+              wsv[1].add(__half2float(__float2half_rn(wgt * kTcWeightScale)) *
+                         (1.0f / kTcWeightScale));
+            }
+          };
+          addw(a0, cA);
+          addw(b0, cB);
         }
         erun += total;
       }
@@ -618,37 +636,71 @@ __global__ void __launch_bounds__(kChunk)
       __syncthreads();
     }
   }
-  if (!FILL) {
-    // pairs of the block
-    int c = count;
+  if (active)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) s_red[wid] = c;
-    __syncthreads();
-    if (t == 0) {
-      int tot = 0;
-      for (int w = 0; w < kQ; ++w) tot += s_red[w];
-      kpairs[b] = tot;
-      kb[b] = (int32_t)kcount;
-    }
-  } else {
-    if (active)
-#pragma unroll
-      for (int v = 0; v < kWsumVariants; ++v) wsum[(int64_t)v * pp.M + m] = wsv[v].value();
-    // Pad the candidate list to a multiple of HG_KPAD with a valid sample
-    // index (its weight is zero in every cell); empty sub-chunks start at the
-    // block's end.
-    int64_t padded = (kcount + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
-    int32_t filler = kcount > 0 ? cand_idx[cbase] : 0;
-    for (int64_t i = kcount + t; i < padded; i += kChunk) cand_idx[cbase + i] = filler;
-    for (int64_t j = (kcount + 31) / 32 + t; j < padded / 32; j += kChunk)
-      sub_off[sbase + j] = ebase + erun;
+    for (int v = 0; v < kWsumVariants; ++v) wsum[(int64_t)v * pp.M + m] = wsv[v].value();
+  // Pad the candidate list to a multiple of HG_KPAD with a valid sample index
+  // (its weight is zero in every cell); empty sub-chunks and the end
+  // sentinel point at the block's end.
+  const int64_t padded = (kcount + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
+  const int32_t filler = kcount > 0 ? cand_idx[cbase] : 0;
+  for (int64_t i = kcount + t; i < padded; i += kChunk) cand_idx[cbase + i] = filler;
+  for (int64_t j = (kcount + 31) / 32 + t; j <= padded / 32; j += kChunk)
+    sub_off[sbase + j] = ebase + erun;
+  if (t == 0) {
+    cand_cnt[b] = (int32_t)padded;
+    atomicAdd(&totals[0], (unsigned long long)erun);
+    atomicAdd(&totals[1], (unsigned long long)padded);
   }
 }
 
-__global__ void k_pad_counts(const int32_t* __restrict__ kb, int64_t n, int64_t* __restrict__ out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = ((int64_t)kb[i] + HG_KPAD - 1) / HG_KPAD * HG_KPAD;
+// Upper bounds per block, for the slot and entry ranges the pair kernel fills:
+// candidates <= the samples of the block's bin window (+ HG_KPAD padding + one
+// sub-chunk for the end sentinel); pairs <= sum over the block's cells of the
+// samples in each cell's own bin window (the bins that can hold a sample
+// within R of the cell, the same construction as the block window).
+struct BoundParams {
+  int32_t nx, ny, nbx_b, nbx, nby, bin_cells, padx, pady;
+  double lat0, dlat, dlon, R_deg, sinR, eps_px;
+};
+
+__global__ void __launch_bounds__(kChunk)
+    k_block_bounds(BoundParams bp, const int4* __restrict__ win,
+                   const int32_t* __restrict__ bin_off, int64_t* __restrict__ slots_ub,
+                   int64_t* __restrict__ pairs_ub) {
+  __shared__ long long s_sum[kChunk / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int b = blockIdx.x;
+  const int bbx = b % bp.nbx_b, bby = b / bp.nbx_b;
+  const int ix = bbx * HG_BX + (t % HG_BX), iy = bby * HG_BY + (t / HG_BX);
+  long long cnt = 0;
+  if (ix < bp.nx && iy < bp.ny) {
+    const double lat = bp.lat0 + ((double)iy - 0.5 * (bp.ny - 1)) * bp.dlat;
+    const double H = asin(bp.sinR / cos(fabs(lat) * kDeg)) / kDeg;
+    const double qy_lo = iy + bp.pady + 0.5 - bp.R_deg / bp.dlat - bp.eps_px;
+    const double qy_hi = iy + bp.pady + 0.5 + bp.R_deg / bp.dlat + bp.eps_px;
+    const double qx_lo = ix + bp.padx + 0.5 - H / bp.dlon - bp.eps_px;
+    const double qx_hi = ix + bp.padx + 0.5 + H / bp.dlon + bp.eps_px;
+    const int B = bp.bin_cells;
+    const int by0 = max(0, (int)floor(qy_lo) / B), by1 = min(bp.nby - 1, (int)floor(qy_hi) / B);
+    const int bx0 = max(0, (int)floor(qx_lo) / B), bx1 = min(bp.nbx - 1, (int)floor(qx_hi) / B);
+    for (int by = by0; by <= by1; ++by)
+      cnt += bin_off[(int64_t)by * bp.nbx + bx1 + 1] - bin_off[(int64_t)by * bp.nbx + bx0];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s_sum[wid] = cnt;
+  __syncthreads();
+  if (t == 0) {
+    long long tot = 0;
+    for (int w = 0; w < kChunk / 32; ++w) tot += s_sum[w];
+    pairs_ub[b] = tot;
+    const int4 wb = win[b];
+    long long ws = 0;
+    for (int by = wb.x; by <= wb.y; ++by)
+      ws += bin_off[(int64_t)by * bp.nbx + wb.w + 1] - bin_off[(int64_t)by * bp.nbx + wb.z];
+    slots_ub[b] = (ws + HG_KPAD - 1) / HG_KPAD * HG_KPAD + HG_KPAD;
+  }
 }
 
 // Device memory of plans comes from a library-owned, stream-ordered pool per
@@ -693,8 +745,8 @@ static cudaError_t dmalloc(T** p, int64_t n, int64_t* bytes, cudaStream_t st) {
 }  // namespace
 
 void free_plan_arrays(hegrid_plan* p, cudaStream_t st) {
-  void* arrays[] = {p->perm, p->bin_off, p->cand_off, p->blk_pair_off, p->cand_idx,
-                    p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->err_word};
+  void* arrays[] = {p->perm,   p->bin_off, p->cand_off, p->blk_pair_off, p->cand_cnt, p->cand_idx,
+                    p->sub_off, p->ent_ck,  p->ent_w,    p->wsum,         p->totals,   p->err_word};
   for (void* a : arrays)
     if (a) cudaFreeAsync(a, st);
 }
@@ -852,7 +904,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(cudaMemcpyAsync(dwin, hwin.data(), sizeof(int4) * p->n_blocks,
                               cudaMemcpyHostToDevice, st));
 
-  // --- a4: count pass --------------------------------------------------------
+  // --- a4 parameters -------------------------------------------------------
   PairParams pp;
   pp.nx = g.nx;
   pp.ny = g.ny;
@@ -882,63 +934,77 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     pp.k_hi = (float)k;
     pp.k_lo = (float)(k - (double)pp.k_hi);
   }
-  int32_t *kb, *kpairs;
-  int64_t* kbp;
-  HG_CUDA_TRY(sc.get(&kb, p->n_blocks + 1));
-  HG_CUDA_TRY(sc.get(&kpairs, p->n_blocks + 1));
-  HG_CUDA_TRY(sc.get(&kbp, p->n_blocks + 1));
-  HG_CUDA_TRY(cudaMemsetAsync(kb, 0, sizeof(int32_t) * (p->n_blocks + 1), st));
-  HG_CUDA_TRY(cudaMemsetAsync(kpairs, 0, sizeof(int32_t) * (p->n_blocks + 1), st));
-  k_block_pairs<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-      pp, dwin, p->bin_off, p->perm, sx, sy, sz, kb, kpairs, nullptr, nullptr, nullptr, nullptr,
-      nullptr, nullptr, nullptr);
-  count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  // --- a4 upper bounds: slot and entry ranges per block ---------------------
+  int64_t *slots_ub, *pairs_ub;
+  HG_CUDA_TRY(sc.get(&slots_ub, p->n_blocks + 1));
+  HG_CUDA_TRY(sc.get(&pairs_ub, p->n_blocks + 1));
+  HG_CUDA_TRY(cudaMemsetAsync(slots_ub + p->n_blocks, 0, sizeof(int64_t), st));
+  HG_CUDA_TRY(cudaMemsetAsync(pairs_ub + p->n_blocks, 0, sizeof(int64_t), st));
+  {
+    BoundParams bp;
+    bp.nx = g.nx;
+    bp.ny = g.ny;
+    bp.nbx_b = p->nbx_b;
+    bp.nbx = p->nbx;
+    bp.nby = p->nby;
+    bp.bin_cells = B;
+    bp.padx = p->padx;
+    bp.pady = p->pady;
+    bp.lat0 = g.lat0_deg;
+    bp.dlat = g.dlat_deg;
+    bp.dlon = g.dlon_deg;
+    bp.R_deg = p->R_deg;
+    bp.sinR = sR;
+    bp.eps_px = eps_px;
+    k_block_bounds<<<(unsigned)p->n_blocks, kChunk, 0, st>>>(bp, dwin, p->bin_off, slots_ub,
+                                                             pairs_ub);
+    count_launch();
+  }
   int64_t* stmp64;
   HG_CUDA_TRY(sc.get(&stmp64, scan_tmp_elems(p->n_blocks + 1) + 8));
   HG_CUDA_TRY(dmalloc(&p->cand_off, p->n_blocks + 1, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->blk_pair_off, p->n_blocks + 1, &bytes, st));
   // exclusive scans over n+1 entries (last input 0): out[n] is the total
-  k_pad_counts<<<(unsigned)((p->n_blocks + 1 + 255) / 256), 256, 0, st>>>(kb, p->n_blocks + 1, kbp);
-  count_launch();
-  scan_exclusive<int64_t, int64_t>(kbp, p->n_blocks + 1, p->cand_off, stmp64, st);
-  scan_exclusive<int32_t, int64_t>(kpairs, p->n_blocks + 1, p->blk_pair_off, stmp64, st);
+  scan_exclusive<int64_t, int64_t>(slots_ub, p->n_blocks + 1, p->cand_off, stmp64, st);
+  scan_exclusive<int64_t, int64_t>(pairs_ub, p->n_blocks + 1, p->blk_pair_off, stmp64, st);
   HG_CUDA_TRY(cudaGetLastError());
 
-  // The one host round trip of plan creation: the number of pairs and of
-  // candidate slots size the remaining arrays.
+  // The one host round trip of plan creation: the bounds' totals size the
+  // candidate-slot and entry arrays.
   int64_t totals[2];
   HG_CUDA_TRY(cudaMemcpyAsync(&totals[0], p->blk_pair_off + p->n_blocks, sizeof(int64_t),
                               cudaMemcpyDeviceToHost, st));
   HG_CUDA_TRY(cudaMemcpyAsync(&totals[1], p->cand_off + p->n_blocks, sizeof(int64_t),
                               cudaMemcpyDeviceToHost, st));
   HG_CUDA_TRY(cudaStreamSynchronize(st));
-  p->P = totals[0];
-  p->n_cand = totals[1];
-  if (p->n_cand > (int64_t)0x7fffffff) {
+  p->P_ub = totals[0];
+  p->slots = totals[1];
+  if (p->slots > (int64_t)0x7fffffff) {
     set_error("too many candidate slots");
     return HEGRID_ERR_UNSUPPORTED;
   }
 
   // --- a4 fill + a5 weights ------------------------------------------------
-  const int64_t n_sub = p->n_cand / 32;
+  const int64_t n_sub = p->slots / 32;
   // (+16 bytes: the tensor-core kernel stages entries in 16-byte aligned
   // windows that may reach past the last entry)
-  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P + 8, &bytes, st));
-  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P + 4, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->ent_ck, p->P_ub + 8, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->ent_w, p->P_ub + 4, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->sub_off, n_sub + 1, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->wsum, kWsumVariants * p->M, &bytes, st));
-  HG_CUDA_TRY(dmalloc(&p->cand_idx, p->n_cand, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->cand_idx, p->slots, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->cand_cnt, p->n_blocks, &bytes, st));
+  HG_CUDA_TRY(dmalloc(&p->totals, 2, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->err_word, 4, &bytes, st));
   HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
+  HG_CUDA_TRY(cudaMemsetAsync(p->totals, 0, 2 * sizeof(unsigned long long), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * kWsumVariants * p->M, st));
-  HG_CUDA_TRY(cudaMemcpyAsync(p->sub_off + n_sub, p->blk_pair_off + p->n_blocks, sizeof(int64_t),
-                              cudaMemcpyDeviceToDevice, st));
-  k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-      pp, dwin, p->bin_off, p->perm, sx, sy, sz, nullptr, nullptr, p->cand_off, p->blk_pair_off,
-      p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum);
+  k_block_pairs<<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
+      pp, dwin, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
+      p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
+  p->P = -1;  // exact totals: read on first use (plan_totals)
   HG_CUDA_TRY(cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming));
   HG_CUDA_TRY(cudaEventRecord(p->ready, st));
   // scratch is released by ~Scratch, ordered after these kernels on `st`
@@ -1013,13 +1079,29 @@ hegrid_status hegrid_plan_destroy(hegrid_plan* plan) {
   return HEGRID_OK;
 }
 
+// Exact pairs and used candidate slots, counted by the pair kernel (waits for
+// the plan to be built).
+static hegrid_status plan_totals(const hegrid_plan* plan, int64_t* P, int64_t* n_cand) {
+  HG_CUDA_TRY(cudaEventSynchronize(plan->ready));
+  unsigned long long t[2];
+  HG_CUDA_TRY(cudaMemcpy(t, plan->totals, sizeof(t), cudaMemcpyDeviceToHost));
+  *P = (int64_t)t[0];
+  *n_cand = (int64_t)t[1];
+  return HEGRID_OK;
+}
+
 hegrid_status hegrid_plan_info(const hegrid_plan* plan, int64_t* n_pairs, int64_t* n_bins,
                                int64_t* n_blocks, int64_t* n_cand, int64_t* bytes) {
   HG_ARG_CHECK(plan != nullptr, "plan is NULL");
-  if (n_pairs) *n_pairs = plan->P;
+  int64_t P = 0, nc = 0;
+  if (n_pairs || n_cand) {
+    hegrid_status st = plan_totals(plan, &P, &nc);
+    if (st != HEGRID_OK) return st;
+  }
+  if (n_pairs) *n_pairs = P;
   if (n_bins) *n_bins = plan->n_bins;
   if (n_blocks) *n_blocks = plan->n_blocks;
-  if (n_cand) *n_cand = plan->n_cand;
+  if (n_cand) *n_cand = nc;
   if (bytes) *bytes = plan->bytes;
   return HEGRID_OK;
 }
@@ -1036,21 +1118,27 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
   if (weight)
     HG_CUDA_TRY(cudaMemcpy(weight, plan->wsum, sizeof(float) * plan->M, cudaMemcpyDeviceToHost));
   if (nb_off || nb_idx || nb_w) {
-    // Rebuild the cell-major CSR from the block-local, candidate-major entries.
-    const int64_t nb = plan->n_blocks, nc = plan->n_cand, ns = nc / 32, P = plan->P, M = plan->M;
+    // Rebuild the cell-major CSR from the blocks' sub-chunk entries.
+    int64_t P = 0, nc_used = 0;
+    hegrid_status st = plan_totals(plan, &P, &nc_used);
+    if (st != HEGRID_OK) return st;
+    const int64_t nb = plan->n_blocks, ns = plan->slots / 32, M = plan->M, PU = plan->P_ub;
     std::vector<int64_t> coff(nb + 1), soff(ns + 1);
-    std::vector<int32_t> cidx(std::max<int64_t>(nc, 1));
-    std::vector<uint16_t> ck(std::max<int64_t>(P, 1));
-    std::vector<float> w(std::max<int64_t>(P, 1));
+    std::vector<int32_t> cnt(std::max<int64_t>(nb, 1));
+    std::vector<int32_t> cidx(std::max<int64_t>(plan->slots, 1));
+    std::vector<uint16_t> ck(std::max<int64_t>(PU, 1));
+    std::vector<float> w(std::max<int64_t>(PU, 1));
     HG_CUDA_TRY(cudaMemcpy(coff.data(), plan->cand_off, sizeof(int64_t) * (nb + 1),
+                           cudaMemcpyDeviceToHost));
+    HG_CUDA_TRY(cudaMemcpy(cnt.data(), plan->cand_cnt, sizeof(int32_t) * nb,
                            cudaMemcpyDeviceToHost));
     HG_CUDA_TRY(cudaMemcpy(soff.data(), plan->sub_off, sizeof(int64_t) * (ns + 1),
                            cudaMemcpyDeviceToHost));
-    if (nc) HG_CUDA_TRY(cudaMemcpy(cidx.data(), plan->cand_idx, sizeof(int32_t) * nc,
-                                   cudaMemcpyDeviceToHost));
-    if (P) {
-      HG_CUDA_TRY(cudaMemcpy(ck.data(), plan->ent_ck, sizeof(uint16_t) * P, cudaMemcpyDeviceToHost));
-      HG_CUDA_TRY(cudaMemcpy(w.data(), plan->ent_w, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    HG_CUDA_TRY(cudaMemcpy(cidx.data(), plan->cand_idx, sizeof(int32_t) * plan->slots,
+                           cudaMemcpyDeviceToHost));
+    if (PU) {
+      HG_CUDA_TRY(cudaMemcpy(ck.data(), plan->ent_ck, sizeof(uint16_t) * PU, cudaMemcpyDeviceToHost));
+      HG_CUDA_TRY(cudaMemcpy(w.data(), plan->ent_w, sizeof(float) * PU, cudaMemcpyDeviceToHost));
     }
     const int nx = plan->geom.nx, nbx_b = plan->nbx_b;
     auto cell_of = [&](int64_t b, int col) -> int64_t {
@@ -1059,13 +1147,20 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
     };
     std::vector<int64_t> off(M + 1, 0);
     for (int64_t b = 0; b < nb; ++b)
-      for (int64_t e = soff[coff[b] / 32]; e < soff[coff[b + 1] / 32]; ++e)
-        off[cell_of(b, (int)(ck[e] >> 6)) + 1]++;
+      for (int64_t e = soff[coff[b] / 32]; e < soff[(coff[b] + cnt[b]) / 32]; ++e) {
+        int r, k;
+        hg::tile_rk(ck[e], r, k);
+        off[cell_of(b, r) + 1]++;
+      }
     for (int64_t m = 0; m < M; ++m) off[m + 1] += off[m];
+    if (off[M] != P) {
+      hg::set_error("plan export: entry count does not match the pair total");
+      return HEGRID_ERR_CUDA;
+    }
     std::vector<int64_t> cur(off.begin(), off.end() - 1);
     std::vector<std::pair<int32_t, float>> pr(std::max<int64_t>(P, 1));
     for (int64_t b = 0; b < nb; ++b) {
-      for (int64_t j = coff[b] / 32; j < coff[b + 1] / 32; ++j) {
+      for (int64_t j = coff[b] / 32; j < (coff[b] + cnt[b]) / 32; ++j) {
         const int64_t loc0 = 32 * j - coff[b];
         for (int64_t e = soff[j]; e < soff[j + 1]; ++e) {
           int r, k;
