@@ -183,6 +183,59 @@ hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_
 hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t *bin_off,
                                  int64_t *nb_off, int32_t *nb_idx, float *nb_w, float *weight);
 
+/*
+ * Autotuning of launch shapes on the caller's own data (the paper tunes its
+ * block size and stream count by sweeps, Sec. 5.3; here the library times the
+ * candidates and keeps the fastest).
+ *
+ * hegrid_autotune -- time the grid step of `plan` for `mode` over a fixed set
+ * of launch shapes and store the fastest in the plan; later hegrid_grid,
+ * hegrid_grid_batched, hegrid_batch_create and hegrid_grid_stream calls on
+ * this plan use it.  Shapes: the work order's band width in cell-block
+ * columns (which blocks run concurrently and so share sample rows in L2),
+ * and for the tensor-core modes the accumulation segment length (16 or 32
+ * chunks; both keep the split form inside its error bound).  values,
+ * dtype, n_channels, ld_values as for hegrid_grid; the maps computed while
+ * timing go to a scratch buffer (stream-ordered pool) and are discarded.
+ * Synchronises `stream`.  report (may be NULL) receives every shape timed
+ * (milliseconds per grid call, mean of 2 after 1 warm-up) and the index of
+ * the one kept.
+ */
+#define HEGRID_TUNE_MAX 16
+typedef struct {
+  int32_t band; /* blocks per band (0: the channel tiles of a block back to back) */
+  int32_t seg;  /* chunks per accumulation segment (tensor-core modes) */
+  float ms;     /* time per grid call */
+} hegrid_tune_point;
+typedef struct {
+  int32_t n, best;
+  hegrid_tune_point pt[HEGRID_TUNE_MAX];
+} hegrid_tune_report;
+hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtype dtype,
+                              int64_t n_channels, int64_t ld_values, uint32_t mode, void *stream,
+                              hegrid_tune_report *report);
+
+/*
+ * hegrid_plan_set_tuning -- set the launch shape hegrid_autotune would keep
+ * (for instance one found in an earlier run).  band: blocks per band, >= 1
+ * (0: default; FP32 mode also -1: the channel tiles of a block back to back);
+ * seg: chunks per accumulation segment for the tensor-core modes, 1..32
+ * (0: default; longer segments would exceed the split form's error bound).
+ * INVALID_ARG otherwise.
+ */
+hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t band, int32_t seg);
+
+/*
+ * hegrid_autotune_bins -- time hegrid_plan_create (plus destroy) for bin edges
+ * of 1..4 map cells (the plan_create flags) on the given samples and return
+ * the fastest in *best_bin_cells; ms[4] (may be NULL) receives the times.
+ * Arguments as for hegrid_plan_create.  Synchronises the device.
+ */
+hegrid_status hegrid_autotune_bins(int64_t n_samples, const double *lon_deg, const double *lat_deg,
+                                   int coords_on_device, const hegrid_map_geom *geom,
+                                   const hegrid_kernel *kern, void *stream,
+                                   int32_t *best_bin_cells, float *ms);
+
 /* Device-side error word of the plan (bounded waits that timed out). */
 hegrid_status hegrid_status_poll(const hegrid_plan *plan);
 

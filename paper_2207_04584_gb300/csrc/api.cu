@@ -59,6 +59,13 @@ GridJob make_job(const hegrid_plan* plan, const hegrid_grid_args& a, int64_t cti
   j.weight_out = a.weight_out;
   j.n_rows = plan->N;
   j.n_ctiles = (a.n_channels + ctile - 1) / ctile;
+  if (a.mode == HEGRID_MODE_FP32) {
+    j.band = plan->tune_f32_band;
+    j.seg = 1;
+  } else {
+    j.band = plan->tune_tc_band > 0 ? plan->tune_tc_band : tc_default_band();
+    j.seg = plan->tune_tc_seg > 0 ? plan->tune_tc_seg : tc_default_seg();
+  }
   return j;
 }
 
@@ -348,6 +355,167 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
   HG_STREAM_TRY(cudaStreamSynchronize(scomp));
 #undef HG_STREAM_TRY
   cleanup();
+  return HEGRID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning
+// ---------------------------------------------------------------------------
+hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtype dtype,
+                              int64_t n_channels, int64_t ld_values, uint32_t mode, void* stream,
+                              hegrid_tune_report* report) {
+  hg::set_error("");
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool tc = mode != HEGRID_MODE_FP32;
+  // candidate shapes
+  std::vector<hegrid_tune_point> pts;
+  auto add = [&](int band, int seg) {
+    band = std::min(band, plan->nbx_b);
+    for (const auto& q : pts)
+      if (q.band == band && q.seg == seg) return;
+    hegrid_tune_point q;
+    q.band = band;
+    q.seg = seg;
+    q.ms = -1.0f;
+    pts.push_back(q);
+  };
+  const int bands[] = {2, 4, 8, 16, 1 << 30};
+  if (tc) {
+    for (int seg : {16, 32})
+      for (int b : bands) add(b, seg);
+  } else {
+    add(0, 1);
+    for (int b : bands) add(b, 1);
+  }
+  // scratch map (discarded)
+  float* scratch = nullptr;
+  const size_t map_bytes = sizeof(float) * (size_t)plan->M * (size_t)std::max<int64_t>(n_channels, 1);
+  HG_CUDA_TRY(hg::pool_alloc((void**)&scratch, map_bytes, s));
+  hegrid_grid_args a;
+  a.values = values;
+  a.dtype = dtype;
+  a.n_channels = n_channels;
+  a.ld_values = ld_values;
+  a.map_out = scratch;
+  a.ld_map = n_channels;
+  a.weight_out = nullptr;
+  a.mode = mode;
+  const int32_t keep[3] = {plan->tune_f32_band, plan->tune_tc_band, plan->tune_tc_seg};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  hegrid_status st = HEGRID_OK;
+  auto fail = [&](hegrid_status code) {
+    plan->tune_f32_band = keep[0];
+    plan->tune_tc_band = keep[1];
+    plan->tune_tc_seg = keep[2];
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(scratch, s);
+    return code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    hg::set_error("cudaEventCreate failed");
+    return fail(HEGRID_ERR_CUDA);
+  }
+  hegrid_plan* pl[1] = {plan};
+  int best = -1;
+  for (size_t i = 0; i < pts.size(); ++i) {
+    if (tc) {
+      plan->tune_tc_band = pts[i].band;
+      plan->tune_tc_seg = pts[i].seg;
+    } else {
+      plan->tune_f32_band = pts[i].band > 0 ? pts[i].band : -1;
+    }
+    constexpr int kReps = 2;
+    if ((st = hg::grid_many(1, pl, &a, s)) != HEGRID_OK) return fail(st);
+    if (cudaEventRecord(e0, s) != cudaSuccess) return fail(HEGRID_ERR_CUDA);
+    for (int r = 0; r < kReps; ++r)
+      if ((st = hg::grid_many(1, pl, &a, s)) != HEGRID_OK) return fail(st);
+    float ms = 0.0f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      hg::set_error("timing the autotune candidates failed");
+      return fail(HEGRID_ERR_CUDA);
+    }
+    pts[i].ms = ms / kReps;
+    if (best < 0 || pts[i].ms < pts[best].ms) best = (int)i;
+  }
+  if (tc) {
+    plan->tune_tc_band = pts[best].band;
+    plan->tune_tc_seg = pts[best].seg;
+  } else {
+    plan->tune_f32_band = pts[best].band > 0 ? pts[best].band : -1;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(scratch, s);
+  if (report) {
+    report->n = (int32_t)std::min<size_t>(pts.size(), HEGRID_TUNE_MAX);
+    report->best = best;
+    for (int i = 0; i < report->n; ++i) report->pt[i] = pts[i];
+  }
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t band, int32_t seg) {
+  hg::set_error("");
+  HG_ARG_CHECK(plan != nullptr, "plan is NULL");
+  if (mode == HEGRID_MODE_FP32) {
+    HG_ARG_CHECK(band >= -1, "band must be >= -1 for HEGRID_MODE_FP32");
+    plan->tune_f32_band = band;
+  } else {
+    HG_ARG_CHECK(mode == HEGRID_MODE_TC || mode == HEGRID_MODE_TC_SPLIT, "unknown mode");
+    HG_ARG_CHECK(band >= 0, "band must be >= 0");
+    HG_ARG_CHECK(seg >= 0 && seg <= 32, "seg must be in [0, 32]");
+    plan->tune_tc_band = band;
+    plan->tune_tc_seg = seg;
+  }
+  return HEGRID_OK;
+}
+
+hegrid_status hegrid_autotune_bins(int64_t n_samples, const double* lon_deg, const double* lat_deg,
+                                   int coords_on_device, const hegrid_map_geom* geom,
+                                   const hegrid_kernel* kern, void* stream,
+                                   int32_t* best_bin_cells, float* ms) {
+  hg::set_error("");
+  HG_ARG_CHECK(best_bin_cells != nullptr, "best_bin_cells is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  HG_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    hg::set_error("cudaEventCreate failed");
+    return HEGRID_ERR_CUDA;
+  }
+  float best_ms = 0.0f;
+  int best = 0;
+  hegrid_status st = HEGRID_OK;
+  for (int B = 1; B <= 4 && st == HEGRID_OK; ++B) {
+    float tmin = -1.0f;
+    for (int rep = 0; rep < 3 && st == HEGRID_OK; ++rep) {  // first: warm-up
+      hegrid_plan* p = nullptr;
+      cudaEventRecord(e0, s);
+      st = hegrid_plan_create(&p, n_samples, lon_deg, lat_deg, coords_on_device, geom, kern,
+                              (uint32_t)B, stream);
+      cudaEventRecord(e1, s);
+      if (st != HEGRID_OK) break;
+      float t = 0.0f;
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t, e0, e1);
+      hegrid_plan_destroy(p);
+      if (rep > 0 && (tmin < 0.0f || t < tmin)) tmin = t;
+    }
+    if (st != HEGRID_OK) break;
+    if (ms) ms[B - 1] = tmin;
+    if (best == 0 || tmin < best_ms) {
+      best = B;
+      best_ms = tmin;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != HEGRID_OK) return st;
+  *best_bin_cells = best;
   return HEGRID_OK;
 }
 

@@ -2,7 +2,9 @@
 // steps, Eq. 1) on CUDA cores.
 //
 // A persistent CTA takes work items (field, 16x8 cell block, 128-channel tile)
-// in a fixed stride.  For each K chunk of 32 candidate samples of the block:
+// in a fixed stride, in the job's work order (the channel tiles of a block
+// back to back, or channel tiles slowest with the blocks in bands of block
+// columns).  For each K chunk of 32 candidate samples of the block:
 //   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) into shared
 //     memory with bulk async copies (TMA engine, one row per lane) completing
 //     on an mbarrier, double-buffered;
@@ -76,8 +78,20 @@ __global__ void __launch_bounds__(kThreads, 2)
     const GridJob& J = jt.job[find_job(jt, item)];
     const PlanView& pv = J.pv;
     const int64_t local = item - J.item_base;
-    const int64_t b = local / J.n_ctiles;
-    const int64_t ct = local % J.n_ctiles;
+    int64_t b, ct;
+    if (J.band <= 0) {  // channel tiles of a block back to back
+      b = local / J.n_ctiles;
+      ct = local % J.n_ctiles;
+    } else {  // channel tiles slowest, blocks in bands of J.band block columns
+      const int64_t nb = J.pv.n_blocks;
+      ct = local / nb;
+      const int64_t bo = local - ct * nb;
+      const int64_t per_band = (int64_t)J.band * J.pv.nby_b;
+      const int64_t band = bo / per_band;
+      const int64_t t = bo - band * per_band;
+      const int64_t bw = min((int64_t)J.band, (int64_t)J.pv.nbx_b - band * J.band);
+      b = (t / bw) * J.pv.nbx_b + band * J.band + (t % bw);
+    }
     const int64_t c0 = ct * kCT;
     const int cw = (int)(J.C - c0 < kCT ? J.C - c0 : kCT);
     const uint32_t row_bytes = (uint32_t)(((cw + 3) & ~3) * 4);

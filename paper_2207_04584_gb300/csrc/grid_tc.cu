@@ -17,7 +17,7 @@
 // each MMA carries its own instruction descriptor and all accumulate in FP32.
 // The tensor core's FP32 accumulate loses about 2^-22 of the running sum per
 // MMA (measured; it grows with the number of MMAs added into one accumulator),
-// so a block's sum is built in segments of kSeg chunks: segment 0 accumulates
+// so a block's sum is built in segments of J.seg chunks: segment 0 accumulates
 // into a "total" TMEM region, later segments into a "segment" region that the
 // drain warps add into the total with FP32 round-to-nearest adds (tcgen05
 // ld/st).  Weights enter the A tiles scaled by 2^15 (exact), which keeps the
@@ -66,11 +66,8 @@ constexpr int kEntStage = kEntCap - 8;     // entries copied (leaves room for 16
 constexpr int kRawPitch = kN * 4;          // bytes per staged row slot (4-byte elements)
 constexpr uint32_t kTmemCols = 512;        // segment sums in [0,256), running total in [256,512)
 constexpr uint32_t kTotCol = 256;
-#ifndef HG_TC_SEG
-#define HG_TC_SEG 32
-#endif
-constexpr int kSeg = HG_TC_SEG;            // chunks per accumulation segment
-constexpr int kBand = 8;                   // blocks per band of the work order
+constexpr int kDefaultSeg = 32;            // chunks per accumulation segment
+constexpr int kDefaultBand = 8;            // blocks per band of the work order
 constexpr int kHalves = kProducers / kN;   // producer threads per B row
 constexpr int kKT = kK / kHalves;          // samples of a row converted per thread
 
@@ -110,16 +107,17 @@ __device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
 }
 
 // Work order inside a job: channel tiles slowest, then cell blocks in bands
-// of kBand block columns, so concurrently running CTAs share candidates in L2.
+// of J.band block columns, so concurrently running CTAs share candidates in L2.
 __device__ __forceinline__ void item_coords(const GridJob& J, int64_t local, int64_t& b,
                                             int64_t& ct) {
   const int64_t nb = J.pv.n_blocks;
   ct = local / nb;
   const int64_t bo = local - ct * nb;
-  const int64_t per_band = (int64_t)kBand * J.pv.nby_b;
+  const int64_t kBand = J.band;
+  const int64_t per_band = kBand * J.pv.nby_b;
   const int64_t band = bo / per_band;
   const int64_t t = bo - band * per_band;
-  const int64_t bw = min((int64_t)kBand, (int64_t)J.pv.nbx_b - band * kBand);
+  const int64_t bw = min(kBand, (int64_t)J.pv.nbx_b - band * kBand);
   b = (t / bw) * J.pv.nbx_b + band * kBand + (t % bw);
 }
 
@@ -413,6 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int64_t C = J.C;
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = pv.cand_cnt[b] / kK;
+    const int kSeg = J.seg;
     const int n_seg = (n_chunks + kSeg - 1) / kSeg;
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
@@ -656,6 +655,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
 }  // namespace
 
 int tc_channel_tile() { return kN; }
+int tc_default_band() { return kDefaultBand; }
+int tc_default_seg() { return kDefaultSeg; }
 
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s) {
   static int sms = 0;

@@ -112,6 +112,9 @@ struct hegrid_plan {
   float* wsum;
   int32_t* err_word;
   int64_t bytes;
+  // Launch shapes chosen by hegrid_autotune (0: defaults): FP32 band, tensor
+  // core band and segment length.
+  int32_t tune_f32_band, tune_tc_band, tune_tc_seg;
   // Recorded on the creation stream after the last plan kernel.  The plan's
   // memory comes from a stream-ordered pool, so every other stream must wait
   // on this event before touching it.
@@ -154,6 +157,10 @@ struct GridJob {
   int64_t ld_map;
   float* weight_out;
   int64_t n_rows;     // samples (rows of the values)
+  // Launch shape (see hegrid_autotune): blocks per band of the work order
+  // (0: channel tiles fastest, FP32 kernel only) and chunks per accumulation
+  // segment (tensor-core kernel).
+  int32_t band, seg;
   int64_t n_ctiles;   // channel tiles
   int64_t item_base;  // first work item of this job in the queue
 };
@@ -170,5 +177,7 @@ hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s);
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s);
 int f32_channel_tile();
 int tc_channel_tile();
+int tc_default_band();
+int tc_default_seg();
 
 }  // namespace hg

@@ -29,7 +29,8 @@ HEGRID_MODE_FP32, HEGRID_MODE_TC, HEGRID_MODE_TC_SPLIT = 0, 1, 2
 EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_grid_batched",
             "hegrid_batch_create", "hegrid_batch_launch", "hegrid_batch_destroy",
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
-            "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc"]
+            "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc",
+            "hegrid_autotune", "hegrid_autotune_bins", "hegrid_plan_set_tuning"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -47,6 +48,18 @@ class hegrid_grid_args(ctypes.Structure):
                 ("ld_values", ctypes.c_int64), ("map_out", ctypes.c_void_p),
                 ("ld_map", ctypes.c_int64), ("weight_out", ctypes.c_void_p),
                 ("mode", ctypes.c_uint32)]
+
+
+HEGRID_TUNE_MAX = 16
+
+
+class hegrid_tune_point(ctypes.Structure):
+    _fields_ = [("band", ctypes.c_int32), ("seg", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+class hegrid_tune_report(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("best", ctypes.c_int32),
+                ("pt", hegrid_tune_point * HEGRID_TUNE_MAX)]
 
 
 class HegridError(RuntimeError):
@@ -83,6 +96,11 @@ def lib():
     L.hegrid_status_poll.argtypes = [P]
     L.hegrid_bin_sort_noalloc.argtypes = [i64, P, P, ctypes.POINTER(hegrid_map_geom),
                                           ctypes.POINTER(hegrid_kernel), u32, P, P, i64, P, P]
+    L.hegrid_autotune.argtypes = [P, P, c_int, i64, i64, u32, P, ctypes.POINTER(hegrid_tune_report)]
+    L.hegrid_autotune_bins.argtypes = [i64, P, P, c_int, ctypes.POINTER(hegrid_map_geom),
+                                       ctypes.POINTER(hegrid_kernel), P,
+                                       ctypes.POINTER(ctypes.c_int32), P]
+    L.hegrid_plan_set_tuning.argtypes = [P, u32, ctypes.c_int32, ctypes.c_int32]
     L.hegrid_last_error.restype = ctypes.c_char_p
     L.hegrid_launch_count.restype = ctypes.c_int64
     for name in EXPORTED:
@@ -218,3 +236,32 @@ def hegrid_bin_sort_noalloc(n_samples, lon_deg, lat_deg, geom, fwhm_deg, support
                                          ctypes.byref(nb), _ptr(stream)),
            "hegrid_bin_sort_noalloc")
     return nb.value
+
+
+def hegrid_autotune(plan, values, dtype, n_channels, ld_values, mode, stream=None):
+    """Time the grid step's launch shapes for `mode`, keep the fastest in the
+    plan; returns the report as a dict."""
+    r = hegrid_tune_report()
+    _check(lib().hegrid_autotune(plan, _ptr(values), int(dtype), int(n_channels), int(ld_values),
+                                 int(mode), _ptr(stream), ctypes.byref(r)), "hegrid_autotune")
+    pts = [{"band": r.pt[i].band, "seg": r.pt[i].seg, "ms": r.pt[i].ms} for i in range(r.n)]
+    return {"points": pts, "best": r.best}
+
+
+def hegrid_autotune_bins(n_samples, lon_deg, lat_deg, coords_on_device, geom, fwhm_deg,
+                         support_sigmas=3.0, stream=None):
+    """Fastest plan bin edge (1..4 cells) and the time of each."""
+    best = ctypes.c_int32(0)
+    ms = (ctypes.c_float * 4)()
+    g = geom_struct(geom)
+    k = hegrid_kernel(float(fwhm_deg), float(support_sigmas))
+    _check(lib().hegrid_autotune_bins(int(n_samples), _ptr(lon_deg), _ptr(lat_deg),
+                                      int(coords_on_device), ctypes.byref(g), ctypes.byref(k),
+                                      _ptr(stream), ctypes.byref(best), ms),
+           "hegrid_autotune_bins")
+    return best.value, list(ms)
+
+
+def hegrid_plan_set_tuning(plan, mode, band, seg=0):
+    return _check(lib().hegrid_plan_set_tuning(plan, int(mode), int(band), int(seg)),
+                  "hegrid_plan_set_tuning")

@@ -1,0 +1,125 @@
+"""GPU tests of the autotuner: the shapes it times are valid, the one it keeps
+is used by later calls, and maps computed with it still match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import map_error
+from paper_2207_04584_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_SPLIT = 5e-5
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_04584_gb300 import build
+    build.build()
+    from paper_2207_04584_gb300 import hegrid
+    hegrid.lib()
+    return hegrid
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tc_split"])
+def test_autotune_keeps_fastest_and_matches_oracle(H, mode):
+    wl = W.config1(n=12000, C=40, nx=64, ny=64)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    C = wl["values"].shape[1]
+    s = torch.cuda.current_stream().cuda_stream
+    md = H.HEGRID_MODE_FP32 if mode == "fp32" else H.HEGRID_MODE_TC_SPLIT
+    plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, g, wl["fwhm_deg"], 3.0,
+                                0, s)
+    try:
+        v = torch.from_numpy(wl["values"]).cuda()
+        rep = H.hegrid_autotune(plan, v, H.HEGRID_F32, C, C, md, s)
+        pts = rep["points"]
+        assert 2 <= len(pts) <= H.HEGRID_TUNE_MAX
+        assert all(p["ms"] > 0 for p in pts)
+        best = pts[rep["best"]]
+        assert best["ms"] == min(p["ms"] for p in pts)
+        if mode == "tc_split":
+            assert {p["seg"] for p in pts} == {16, 32}
+        out = torch.full((M, C), -7.0, device="cuda")
+        wout = torch.full((M,), -7.0, device="cuda")
+        H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, wout, md, s)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
+    assert err <= (TOL_F32 if mode == "fp32" else TOL_SPLIT), err
+
+
+@pytest.mark.parametrize("mode,band,seg", [("tc_split", 1, 16), ("tc_split", 3, 32),
+                                            ("tc_split", 1 << 20, 1), ("tc", 2, 7),
+                                            ("fp32", -1, 0), ("fp32", 1, 0), ("fp32", 5, 0)])
+def test_every_shape_matches_oracle(H, mode, band, seg):
+    """Every launch shape the tuner can keep gives the same map as the oracle."""
+    wl = W.config1(n=8000, C=16, nx=70, ny=30)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    C = wl["values"].shape[1]
+    s = torch.cuda.current_stream().cuda_stream
+    md = {"fp32": H.HEGRID_MODE_FP32, "tc": H.HEGRID_MODE_TC,
+          "tc_split": H.HEGRID_MODE_TC_SPLIT}[mode]
+    plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, g, wl["fwhm_deg"], 3.0,
+                                0, s)
+    try:
+        H.hegrid_plan_set_tuning(plan, md, band, seg)
+        v = torch.from_numpy(wl["values"]).cuda()
+        out = torch.full((M, C), -7.0, device="cuda")
+        H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, None, md, s)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
+    tol = {"fp32": TOL_F32, "tc_split": TOL_SPLIT, "tc": 3e-2}[mode]  # single: reported, loose
+    assert err <= tol, err
+
+
+def test_set_tuning_rejects_bad_shapes(H):
+    wl = W.config1(n=2000, C=4, nx=20, ny=20)
+    s = torch.cuda.current_stream().cuda_stream
+    plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, wl["geom"],
+                                wl["fwhm_deg"], 3.0, 0, s)
+    try:
+        for md, band, seg in ((H.HEGRID_MODE_TC_SPLIT, 4, 33), (H.HEGRID_MODE_TC, -1, 16),
+                              (H.HEGRID_MODE_FP32, -2, 0), (9, 4, 16)):
+            with pytest.raises(H.HegridError) as e:
+                H.hegrid_plan_set_tuning(plan, md, band, seg)
+            assert e.value.status == H.HEGRID_ERR_INVALID_ARG
+    finally:
+        H.hegrid_plan_destroy(plan)
+
+
+def test_autotune_bins_plan_matches_oracle(H):
+    wl = W.config1(n=10000, C=4, nx=50, ny=40)
+    g = wl["geom"]
+    s = torch.cuda.current_stream().cuda_stream
+    best, ms = H.hegrid_autotune_bins(len(wl["lon"]), wl["lon"], wl["lat"], 0, g, wl["fwhm_deg"],
+                                      3.0, s)
+    assert 1 <= best <= 4
+    assert all(t > 0 for t in ms) and ms[best - 1] == min(ms)
+    plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, g, wl["fwhm_deg"], 3.0,
+                                best, s)
+    try:
+        M = g["nx"] * g["ny"]
+        C = wl["values"].shape[1]
+        v = torch.from_numpy(wl["values"]).cuda()
+        out = torch.full((M, C), -7.0, device="cuda")
+        H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, None, H.HEGRID_MODE_FP32, s)
+        torch.cuda.synchronize()
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
+    assert err <= TOL_F32, err
