@@ -15,6 +15,7 @@ fields or channel slices with no exchange; one GPU per rank): weak scaling.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -94,6 +95,37 @@ def max_over_ranks(x, dist, device=None):
     return float(t.item())
 
 
+# DRAM traffic per grid launch on the bench workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; see the capture summary named
+# below).  Used only while the kernel's sources hash to the value the capture
+# was taken on: a changed kernel reports null.
+TRAFFIC = {
+    "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
+                              "paper_2207_04584_gb300/csrc/ptx.cuh",
+                              "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
+                  "sha256": None, "bytes": None, "capture": None},
+    "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
+                               "paper_2207_04584_gb300/csrc/ptx.cuh",
+                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
+                   "sha256": None, "bytes": None, "capture": None},
+}
+
+
+def sources_sha256(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    t = TRAFFIC.get(kernel)
+    if not t or not t["sha256"] or sources_sha256(t["sources"]) != t["sha256"]:
+        return None
+    return t["bytes"]
+
+
 def job_value(units_per_rank, world, elapsed_max):
     """Whole-job throughput of independent replicas: all ranks' units over
     the slowest rank's time."""
@@ -162,6 +194,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--channels", type=int, default=1024)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (default launch shapes, bin edge 2)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (no per-form timings, accuracy check, e2e or CPU "
                          "baseline): the command used for profiler captures")
@@ -220,6 +254,31 @@ def main():
             mode_name = "fp32"
     mode = modes[mode_name]
 
+    # ---- autotuning, outside the timed region: the plan's bin edge and the
+    # grid step's launch shape, applied to every plan the steps create -----
+    tune = {}
+    if not args.no_tune:
+        t_tune = time.perf_counter()
+        bin_cells, bin_ms = H.hegrid_autotune_bins(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, sh)
+        p = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, bin_cells, sh)
+        try:
+            rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, C, mode, sh)
+        finally:
+            H.hegrid_plan_destroy(p)
+        best = rep["points"][rep["best"]]
+        tune = {"bin_cells": bin_cells, "band": best["band"], "seg": best["seg"],
+                "plan_ms_by_bin": [round(x, 3) for x in bin_ms],
+                "grid_ms_by_shape": [[q["band"], q["seg"], round(q["ms"], 3)]
+                                     for q in rep["points"]],
+                "seconds": round(time.perf_counter() - t_tune, 2)}
+    flags = tune.get("bin_cells", 0)
+
+    def new_plan(lon, lat, on_device):
+        p = H.hegrid_plan_create(N, lon, lat, on_device, g, wl["fwhm_deg"], 3.0, flags, sh)
+        if tune:
+            H.hegrid_plan_set_tuning(p, mode, tune["band"], tune["seg"])
+        return p
+
     ev = []
 
     def step(record):
@@ -227,7 +286,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, 0, sh)
+        plan = new_plan(lon_d, lat_d, 1)
         e1.record(stream)
         H.hegrid_grid(plan, vals_d, H.HEGRID_F32, C, C, map_d, C, w_d, mode, sh)
         e2.record(stream)
@@ -261,7 +320,7 @@ def main():
     value = job_value(N * C * args.steps, world, elapsed)
 
     # plan facts and accuracy on sampled cells (vs the FP64 oracle)
-    plan = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, 0, sh)
+    plan = new_plan(lon_d, lat_d, 1)
     info = H.hegrid_plan_info(plan)
     P = info["n_pairs"]
     forms = {}
@@ -305,13 +364,13 @@ def main():
         peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
         achieved = 2.0 * P * C / t_grid / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic("k_grid_f32"),
                 "note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived); "
                         "achieved = 2 P C / grid-kernel time"}
     else:
         achieved = alg_bytes / t_grid / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": measured_traffic("k_grid_tc"),
                 "note": f"algorithmic bytes N*C*4 + M*C*4 + M*4 per grid launch; peak {peak_kind}"}
 
     # ---- end to end through the C ABI with host buffers -------------------
@@ -328,7 +387,7 @@ def main():
             chunks[k].copy_(host_vals[:, k * cc:(k + 1) * cc])
 
         def e2e_step():
-            p = H.hegrid_plan_create(N, lon_h, lat_h, 0, g, wl["fwhm_deg"], 3.0, 0, sh)
+            p = new_plan(lon_h, lat_h, 0)
             H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, mode, host_map, C, host_w)
             H.hegrid_plan_destroy(p)
 
@@ -357,7 +416,7 @@ def main():
                 "config": {"workload": "FAST-like 19-beam drift scan, 5x5 deg at (30,41), "
                                        f"N={N}, C={C} FP32, 600x600 map at 0.5', FWHM 2.9', R=3 sigma",
                            "mode": mode_name, "N": N, "C": C, "M": M, "pairs": P,
-                           "l2": "inputs larger than L2 (values 8 GB)",
+                           "l2": "inputs larger than L2 (values 8 GB)", "tuning": tune,
                            "parallelism": f"replicas x{world}"},
                 "plan_ms": t_plan * 1e3, "grid_ms": t_grid * 1e3,
                 "forms": forms, "err_vs_oracle": err, "roofline": roof, "cpu_baseline": cpu,
