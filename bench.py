@@ -156,6 +156,11 @@ def cpu_oracle_sample(wl, frac_rows=20, nthreads=0):
                       f"({t_full:.1f}s)"}
 
 
+def workload_desc(N, C):
+    return (f"FAST-like 19-beam drift scan, 5x5 deg at (30,41), N={N}, C={C} FP32, 600x600 map "
+            "at 0.5', FWHM 2.9', R=3 sigma")
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -174,8 +179,8 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "N": N, "C": C, "M": wl["geom"]["nx"] ** 2,
-                       "seed": W.SEED_BASE + 2},
+            "config": {"workload": workload_desc(N, C), "N": N, "C": C,
+                       "M": wl["geom"]["nx"] * wl["geom"]["ny"], "seed": W.SEED_BASE + 2},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
                              "cores": os.cpu_count(), "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -412,9 +417,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if mode_name == "fp32" else "bf16", "data": "synthetic",
-                "config": {"workload": "FAST-like 19-beam drift scan, 5x5 deg at (30,41), "
-                                       f"N={N}, C={C} FP32, 600x600 map at 0.5', FWHM 2.9', R=3 sigma",
+                "dtype": "f32" if mode_name == "fp32" else "f16", "data": "synthetic",
+                "config": {"workload": workload_desc(N, C),
                            "mode": mode_name, "N": N, "C": C, "M": M, "pairs": P,
                            "l2": "inputs larger than L2 (values 8 GB)", "tuning": tune,
                            "parallelism": f"replicas x{world}"},

@@ -20,7 +20,8 @@
 // so a block's sum is built in segments of J.seg chunks: segment 0 accumulates
 // into a "total" TMEM region, later segments into a "segment" region that the
 // drain warps add into the total with FP32 round-to-nearest adds (tcgen05
-// ld/st).  Weights enter the A tiles scaled by 2^15 (exact), which keeps the
+// ld/st).  Consecutive items swap the two regions' roles, so an item's
+// epilogue overlaps the next item's first segment.  Weights enter the A tiles scaled by 2^15 (exact), which keeps the
 // low FP16 half of their split a normal number; W comes from the plan
 // (compensated sums of the weights) and is scaled to match.
 //
@@ -64,8 +65,7 @@ constexpr int kRawStages = 3;              // staged sample rows + weight entrie
 constexpr int kEntCap = 1792;              // weight entries staged per chunk (more: read from global)
 constexpr int kEntStage = kEntCap - 8;     // entries copied (leaves room for 16-byte alignment)
 constexpr int kRawPitch = kN * 4;          // bytes per staged row slot (4-byte elements)
-constexpr uint32_t kTmemCols = 512;        // segment sums in [0,256), running total in [256,512)
-constexpr uint32_t kTotCol = 256;
+constexpr uint32_t kTmemCols = 512;        // two 256-column accumulator regions
 constexpr int kDefaultSeg = 32;            // chunks per accumulation segment
 constexpr int kDefaultBand = 8;            // blocks per band of the work order
 constexpr int kHalves = kProducers / kN;   // producer threads per B row
@@ -91,7 +91,11 @@ struct __align__(512) TcSmem {
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t raw_full[kRawStages], raw_empty[kRawStages], ent_empty[kRawStages];
   uint64_t ab_full[kStages], ab_empty[kStages];
-  uint64_t segdone, segfree, totfree;
+  // MMA -> drains: a segment's MMAs are complete.  Two barriers used by
+  // alternate segments: with the regions swapping roles per item the MMA
+  // warp can complete up to two segments the drains have not taken yet.
+  uint64_t segdone[2];
+  uint64_t regfree[2];  // drains -> MMA: an accumulator region may be reused
   uint32_t tmem_base;
 };
 
@@ -381,9 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       S.red[i][0] = 0u;
       S.red[i][1] = 0x7f800000u;
     }
-    mbar_init(&S.segdone, 1);
-    mbar_init(&S.segfree, 4);
-    mbar_init(&S.totfree, 4);
+    mbar_init(&S.segdone[0], 1);
+    mbar_init(&S.segdone[1], 1);
+    mbar_init(&S.regfree[0], 4);
+    mbar_init(&S.regfree[1], 4);
     fence_mbar_init();
   }
   if (warp == kMmaWarp) {
@@ -399,7 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   uint32_t g = 0;     // chunks through the A/B ring so far
   uint32_t gr = 0;    // chunks through the raw ring so far
   uint32_t n_tm = 0;  // items that used TMEM so far
-  uint32_t n_sg = 0;  // accumulation segments so far (segdone / segfree phases)
+  uint32_t n_sg = 0;  // accumulation segments so far (segdone phases)
+  uint32_t uses[2] = {0u, 0u};  // MMA warp: segments accumulated into each region so far
   uint32_t rslot = 0; // producers: range-reduction slot of the next chunk
 
   for (int64_t item = blockIdx.x; item < jt.n_items && !bail; item += gridDim.x) {
@@ -483,24 +489,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       // ---------------- MMA issuer ----------------
       if (n_chunks == 0) continue;
       const uint32_t idS16 = idesc_f16(0u, kM, kN), idSbf = idesc_f16(1u, kM, kN);
-      uint32_t dcol = kTotCol;
+      // Item n_tm accumulates its total in region rT and later segments in
+      // rS; the next item swaps them, so its first segment can run while
+      // this item's epilogue still reads rT.
+      const uint32_t rT = n_tm & 1u, rS = rT ^ 1u;
+      uint32_t dcol = 0;
       for (int j = 0; j < n_chunks && !bail; ++j, ++g) {
         const int s = g % kStages;
         const int q = j / kSeg;
         const bool seg_start = j % kSeg == 0;
         const bool seg_end = j % kSeg == kSeg - 1 || j == n_chunks - 1;
         if (seg_start) {
-          // segment 0 writes the total (free once the previous epilogue read
-          // it); later segments write the segment region (free once drained)
-          // (the drains acknowledge every segment in order, so waiting for the
-          // previous one also means the segment region has been drained)
-          if (q == 0) {
-            dcol = kTotCol;
-            if (n_tm > 0 && !mbar_wait(&S.totfree, (n_tm - 1) & 1u, err)) bail = true;
-          } else {
-            dcol = 0;
-            if (!mbar_wait(&S.segfree, (n_sg - 1) & 1u, err)) bail = true;
-          }
+          // the region is free once the drains released its previous use
+          // (a drained segment, or an epilogue that read a total)
+          const uint32_t r = q == 0 ? rT : rS;
+          if (uses[r] > 0 && !mbar_wait(&S.regfree[r], (uses[r] - 1) & 1u, err)) bail = true;
+          ++uses[r];
+          dcol = r * 256u;
           tc_fence_after();
           if (bail) break;
         }
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
               tc_mma_f16(d, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(b_hi + o), idS, 1u);
           }
           tc_commit(&S.ab_empty[s]);
-          if (seg_end) tc_commit(&S.segdone);
+          if (seg_end) tc_commit(&S.segdone[n_sg & 1u]);
         }
         __syncwarp();
         if (seg_end) ++n_sg;
@@ -554,9 +559,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         continue;
       }
       const uint32_t lrow = (uint32_t)(quarter * 32) << 16;
-      const uint32_t tseg = tmem + lrow, ttot = tmem + lrow + kTotCol;
+      const uint32_t rT = n_tm & 1u, rS = rT ^ 1u;
+      const uint32_t tseg = tmem + lrow + rS * 256u, ttot = tmem + lrow + rT * 256u;
       for (int q = 0; q < n_seg; ++q) {
-        if (!mbar_wait(&S.segdone, n_sg & 1u, err)) {
+        if (!mbar_wait(&S.segdone[n_sg & 1u], (n_sg >> 1) & 1u, err)) {
           bail = true;
           break;
         }
@@ -576,11 +582,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
             tmem_st_32x32b_x32(ttot + cb * 32, t);
           }
           tmem_st_wait();
+          // the segment region is drained
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.regfree[rS]);
         }
-        // acknowledge the segment (segment 0 needs no work)
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.segfree);
       }
       if (bail) break;
       // epilogue: map = total / W, W from the plan's compensated sums: FP32
@@ -615,9 +621,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
       }
       if (active && c0 == 0 && J.weight_out) J.weight_out[m] = Wm;
+      // the total region has been read
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.totfree);
+      if (lane == 0) mbar_arrive(&S.regfree[rT]);
       ++n_tm;
       continue;
     }
