@@ -103,11 +103,15 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": None, "bytes": None, "capture": None},
+                  "sha256": "fa1922e998779380ecc6da028f528588dda7c37dc445f5eba48849a45074600b",
+                  "bytes": 4 * (8.642127e9 + 0.423278e9),
+                  "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": None, "bytes": None, "capture": None},
+                   "sha256": "5e020be29dd66b4ca59f8b72550e15d234bf8e72c71c65b7e01a5bca06d8372f",
+                   "bytes": 4 * (6.408942e9 + 0.363721e9),
+                   "capture": "profiles/k_grid_f32_fast_drift_c256.md (C=256 x 4)"},
 }
 
 
