@@ -400,6 +400,19 @@ def main():
             H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, mode, host_map, C, host_w)
             H.hegrid_plan_destroy(p)
 
+        # the host link: one pinned 1 GiB copy each way, timed on the device
+        link = {}
+        lh = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+        ld_ = torch.empty_like(lh, device=dev)
+        for name, dst, src in (("h2d", ld_, lh), ("d2h", lh, ld_)):
+            dst.copy_(src, non_blocking=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dst.copy_(src, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            link[name + "_gbs"] = (1 << 30) / (a.elapsed_time(b) * 1e-3) / 1e9
+        del lh, ld_
         e2e_step()
         torch.cuda.synchronize()
         ts = time.perf_counter()
@@ -410,6 +423,9 @@ def main():
         e2e = {"value": world * N * C / te, "unit": UNIT,
                "h2d_bytes_per_step": N * 16 + N * C * 4,
                "d2h_bytes_per_step": M * C * 4 + M * 4, "ms_per_step": te * 1e3,
+               "link": link,
+               "link_bound_ms": max((N * 16 + N * C * 4) / link["h2d_gbs"],
+                                    (M * C * 4 + M * 4) / link["d2h_gbs"]) / 1e6,
                "path": "hegrid_plan_create(host coords) + hegrid_grid_stream(4 pinned channel "
                        "chunks -> pinned host map)"}
 

@@ -569,17 +569,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         ++n_sg;
         tc_fence_after();
         if (q > 0) {
-          // total += segment, FP32 round-to-nearest
-          uint32_t a[32], t[32];
+          // total += segment, FP32 round-to-nearest (16-column slices keep
+          // the kernel within its register budget without spills)
+          uint32_t a[16], t[16];
 #pragma unroll 1
-          for (int cb = 0; cb < kN / 32; ++cb) {
-            tmem_ld_32x32b_x32(tseg + cb * 32, a);
-            tmem_ld_32x32b_x32(ttot + cb * 32, t);
+          for (int cb = 0; cb < kN / 16; ++cb) {
+            tmem_ld_32x32b_x16(tseg + cb * 16, a);
+            tmem_ld_32x32b_x16(ttot + cb * 16, t);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
+            for (int i = 0; i < 16; ++i)
               t[i] = __float_as_uint(__fadd_rn(__uint_as_float(t[i]), __uint_as_float(a[i])));
-            tmem_st_32x32b_x32(ttot + cb * 32, t);
+            tmem_st_32x32b_x16(ttot + cb * 16, t);
           }
           tmem_st_wait();
           // the segment region is drained
