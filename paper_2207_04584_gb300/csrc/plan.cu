@@ -412,8 +412,9 @@ __global__ void __launch_bounds__(kChunk)
                   float* __restrict__ ent_w, float* __restrict__ wsum,
                   unsigned long long* __restrict__ totals) {
   constexpr int kQ = kChunk / 32;
-  __shared__ float s_eh[3][kChunk];
-  __shared__ float s_el[3][kChunk];
+  // staged candidates' block-local coordinates as float-float (x, y, z, -)
+  __shared__ float4 s_eh[kChunk];
+  __shared__ float4 s_el[kChunk];
   __shared__ double s_u[3][kChunk];
   __shared__ int32_t s_n[kChunk];
   __shared__ uint32_t s_umask[kQ];
@@ -421,8 +422,8 @@ __global__ void __launch_bounds__(kChunk)
   // Cell coordinates, candidate-major cell masks (bit i of
   // s_cm[k][w]: cell 32 w + i has staged candidate k), entries before each
   // staged candidate, candidate index within its 32-candidate sub-chunk.
-  __shared__ float s_mh[3][kChunk];
-  __shared__ float s_ml[3][kChunk];
+  __shared__ float4 s_mh[kChunk];
+  __shared__ float4 s_ml[kChunk];
   __shared__ uint32_t s_cm[kChunk][kQ];
   __shared__ int32_t s_pre[kChunk + 1];
   __shared__ int32_t s_loc[kChunk];
@@ -452,18 +453,19 @@ __global__ void __launch_bounds__(kChunk)
     for (int i = 0; i < 3; ++i) {
       mh[i] = __double2float_rn(e[i]);
       ml[i] = __double2float_rn(e[i] - (double)mh[i]);
-      s_mh[i][t] = mh[i];
-      s_ml[i][t] = ml[i];
     }
   }
 
+  s_mh[t] = make_float4(mh[0], mh[1], mh[2], 0.0f);
+  s_ml[t] = make_float4(ml[0], ml[1], ml[2], 0.0f);
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
   int64_t erun = 0;    // entries of the block so far
   // W of the cell for each weight representation the grid kernels use
   // (FP32; FP16-rounded as the tensor-core single form rounds them), so
   // that every form normalises by the sum of exactly the weights it
   // multiplied.
-  CSum wsv[kWsumVariants];
+  CSum wsv;         // FP32 weights, compensated
+  float w16 = 0.0f;  // FP16-rounded weights x kTcWeightScale (plain sum: single form only)
   const int64_t cbase = cand_off[b], ebase = blk_pair_off[b], sbase = cbase / 32;
   const int4 wb = win[b];  // by0, by1, bx0, bx1
   for (int by = wb.x; by <= wb.y; ++by) {
@@ -475,13 +477,15 @@ __global__ void __launch_bounds__(kChunk)
       if (s < s_end) {
         double u[3] = {sx[s], sy[s], sz[s]};
         double e[3] = {u[0] - bx0, u[1] - by0, u[2] - bz0};
+        float hv[3], lv[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          float hv = __double2float_rn(e[i]);
-          s_eh[i][t] = hv;
-          s_el[i][t] = __double2float_rn(e[i] - (double)hv);
+          hv[i] = __double2float_rn(e[i]);
+          lv[i] = __double2float_rn(e[i] - (double)hv[i]);
           s_u[i][t] = u[i];
         }
+        s_eh[t] = make_float4(hv[0], hv[1], hv[2], 0.0f);
+        s_el[t] = make_float4(lv[0], lv[1], lv[2], 0.0f);
         s_n[t] = perm[s];
       }
       if (t < kQ) s_umask[t] = 0u;
@@ -495,7 +499,8 @@ __global__ void __launch_bounds__(kChunk)
         const int kend = active ? min(32, nk - 32 * q) : 0;
         for (int r = 0; r < kend; ++r) {
           const int k = 32 * q + r;
-          float dx = mh[0] - s_eh[0][k], dy = mh[1] - s_eh[1][k], dz = mh[2] - s_eh[2][k];
+          const float4 n4 = s_eh[k];
+          float dx = mh[0] - n4.x, dy = mh[1] - n4.y, dz = mh[2] - n4.z;
           float c2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
           bool in;
           if (c2 <= pp.lo_thr) {
@@ -608,10 +613,9 @@ __global__ void __launch_bounds__(kChunk)
           for (int e = t; e < gT; e += kChunk) {
             const int ent = s_ent[e];
             const int cell = ent >> 5, k = 32 * q + (ent & 31);
-            const float ch[3] = {s_mh[0][cell], s_mh[1][cell], s_mh[2][cell]};
-            const float cl[3] = {s_ml[0][cell], s_ml[1][cell], s_ml[2][cell]};
-            const float nh[3] = {s_eh[0][k], s_eh[1][k], s_eh[2][k]};
-            const float nl[3] = {s_el[0][k], s_el[1][k], s_el[2][k]};
+            const float4 ch4 = s_mh[cell], cl4 = s_ml[cell], nh4 = s_eh[k], nl4 = s_el[k];
+            const float ch[3] = {ch4.x, ch4.y, ch4.z}, cl[3] = {cl4.x, cl4.y, cl4.z};
+            const float nh[3] = {nh4.x, nh4.y, nh4.z}, nl[3] = {nl4.x, nl4.y, nl4.z};
             const float wgt = pair_weight(ch, cl, nh, nl, pp.k_hi, pp.k_lo);
             const int64_t pos = ebase + erun + g0 + e;
             ent_ck[pos] = (uint16_t)tile_off(cell, s_loc[k]);
@@ -622,9 +626,8 @@ __global__ void __launch_bounds__(kChunk)
           auto addw = [&](int e0, int n) {
             for (int e = e0; e < e0 + n; ++e) {
               const float wgt = s_w[e];
-              wsv[0].add(wgt);
-              wsv[1].add(__half2float(__float2half_rn(wgt * kTcWeightScale)) *
-                         (1.0f / kTcWeightScale));
+              wsv.add(wgt);
+              w16 += __half2float(__float2half_rn(wgt * kTcWeightScale));
             }
           };
           addw(a0, cA);
@@ -636,9 +639,10 @@ __global__ void __launch_bounds__(kChunk)
       __syncthreads();
     }
   }
-  if (active)
-#pragma unroll
-    for (int v = 0; v < kWsumVariants; ++v) wsum[(int64_t)v * pp.M + m] = wsv[v].value();
+  if (active) {
+    wsum[m] = wsv.value();
+    wsum[pp.M + m] = w16 * (1.0f / kTcWeightScale);
+  }
   // Pad the candidate list to a multiple of HG_KPAD with a valid sample index
   // (its weight is zero in every cell); empty sub-chunks and the end
   // sentinel point at the block's end.
