@@ -193,6 +193,153 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_config4(args, H, torch, dev, rank):
+    """64 uneven fields (scaled: samples 1e4-2e5, maps 64^2-512^2, 64-1024 channels, FP32 or
+    BF16, footprint <= 60 GB) gridded by one graph-captured batch per step (TC split)."""
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    t_gen = time.perf_counter()
+    fields, est = W.config4_fields(n_fields=64, max_bytes=60e9, n_range=(1e4, 2e5),
+                                   side_choices=(64, 128, 256, 512), c_range=(64, 1024))
+    wls = [W.field_samples(f) for f in fields]
+    t_gen = time.perf_counter() - t_gen
+    plans, args_b, keep = [], [], []
+    units = 0
+    t0 = time.perf_counter()
+    for wl in wls:
+        g = wl["geom"]
+        M = g["nx"] * g["ny"]
+        N, C = wl["values"].shape
+        plans.append(H.hegrid_plan_create(N, np.ascontiguousarray(wl["lon"]),
+                                          np.ascontiguousarray(wl["lat"]), 0, g, wl["fwhm_deg"],
+                                          3.0, 0, sh))
+        v = torch.from_numpy(wl["values"])
+        if wl["dtype"] == "bf16":
+            ld = (C + 7) // 8 * 8
+            dv = torch.zeros((N, ld), dtype=torch.bfloat16, device=dev)
+            dv[:, :C] = v.to(torch.bfloat16).to(dev)
+            dt = H.HEGRID_BF16
+        else:
+            ld = (C + 3) // 4 * 4
+            dv = torch.zeros((N, ld), dtype=torch.float32, device=dev)
+            dv[:, :C] = v.to(dev)
+            dt = H.HEGRID_F32
+        out = torch.empty((M, C), device=dev)
+        args_b.append({"values": dv, "dtype": dt, "n_channels": C, "ld_values": ld,
+                       "map_out": out, "ld_map": C, "weight_out": None,
+                       "mode": H.HEGRID_MODE_TC_SPLIT})
+        keep.append((dv, out))
+        units += N * C
+    torch.cuda.synchronize()
+    t_plans = time.perf_counter() - t0
+    captured0 = H.hegrid_launch_count()
+    batch = H.hegrid_batch_create(plans, args_b, sh)
+    graph_kernels = H.hegrid_launch_count() - captured0  # kernels captured in the graph
+    try:
+        for _ in range(max(3, args.warmup)):
+            H.hegrid_batch_launch(batch, sh)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            H.hegrid_batch_launch(batch, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3 / args.steps
+        for p in plans:
+            H.hegrid_status_poll(p)
+        finite = all(bool(torch.isfinite(o).any()) for _, o in keep)
+    finally:
+        H.hegrid_batch_destroy(batch)
+        for p in plans:
+            H.hegrid_plan_destroy(p)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC.replace("plan + grid per step", "batched grid per step"),
+            "value": units / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f16",
+            "data": "synthetic",
+            "config": {"workload": "64 uneven fields (drift, raster, uniform), samples 1e4-2e5, "
+                                   "maps 64^2-512^2 at 0.5'-1', 64-1024 channels FP32/BF16, "
+                                   "FWHM 2.9'-6', one CUDA-graph batch (TC split)",
+                       "fields": len(wls), "sample_channels": units,
+                       "samples": int(sum(len(w["lon"]) for w in wls)),
+                       "bf16_fields": int(sum(w["dtype"] == "bf16" for w in wls)),
+                       "footprint_estimate_gb": est / 1e9},
+            "plan_s_all_fields": t_plans, "maps_finite": finite,
+            "accuracy": "parity of the batched path: tests/test_gpu_runtime.py",
+            "gpu_launches": graph_kernels,
+            "gen_s": t_gen}), flush=True)
+
+
+def run_config5(args, H, torch, dev, rank):
+    """65,536 BF16 channels of 1M samples streamed from pinned host memory in 4,096-channel
+    chunks (4 distinct chunks cycled, as the 131 GB band does not fit host memory)."""
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    t_gen = time.perf_counter()
+    wl = W.config5()
+    N = len(wl["lon"])
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    CC, NCH, NDIST = 4096, 16, 4
+    chunks = []
+    f32 = np.empty((N, CC), np.float32)
+    for k in range(NDIST):
+        W.config5_chunk(wl, k, C_chunk=CC, out=f32)
+        chunks.append(torch.from_numpy(f32).to(torch.bfloat16).pin_memory())
+    del f32
+    t_gen = time.perf_counter() - t_gen
+    host_map = torch.empty((M, NCH * CC), dtype=torch.float32, pin_memory=True)
+    host_w = torch.empty(M, dtype=torch.float32, pin_memory=True)
+    order = [chunks[k % NDIST] for k in range(NCH)]
+    lon_h, lat_h = np.ascontiguousarray(wl["lon"]), np.ascontiguousarray(wl["lat"])
+    plan = H.hegrid_plan_create(N, lon_h, lat_h, 0, g, wl["fwhm_deg"], 3.0, 0, sh)
+    link = {}
+    try:
+        # the host link, as in the config-2 e2e
+        lh = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+        ld_ = torch.empty_like(lh, device=dev)
+        for name, dst, src in (("h2d", ld_, lh), ("d2h", lh, ld_)):
+            dst.copy_(src, non_blocking=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dst.copy_(src, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            link[name + "_gbs"] = (1 << 30) / (a.elapsed_time(b) * 1e-3) / 1e9
+        del lh, ld_
+        H.hegrid_grid_stream(plan, order, CC, H.HEGRID_BF16, H.HEGRID_MODE_TC_SPLIT, host_map,
+                             NCH * CC, host_w)
+        ts = time.perf_counter()
+        steps = max(1, args.steps // 5)
+        for _ in range(steps):
+            H.hegrid_grid_stream(plan, order, CC, H.HEGRID_BF16, H.HEGRID_MODE_TC_SPLIT,
+                                 host_map, NCH * CC, host_w)
+        t = (time.perf_counter() - ts) / steps
+        finite = bool(torch.isfinite(host_map[:, :8]).any())
+    finally:
+        H.hegrid_plan_destroy(plan)
+    h2d = N * NCH * CC * 2
+    d2h = M * NCH * CC * 4
+    bound = max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC.replace("plan + grid per step", "streamed from pinned host memory"),
+            "value": N * NCH * CC / t, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "dtype": "f16",
+            "data": "synthetic",
+            "config": {"workload": "1M-sample 19-beam drift scan, 3.3x3.3 deg at (30,41), "
+                                   f"{M} cells at 0.5', FWHM 2.9', 65,536 BF16 channels in 16 "
+                                   "chunks of 4,096 (4 distinct chunks cycled)",
+                       "N": N, "C": NCH * CC, "M": M},
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "link": link,
+            "link_bound_ms": bound * 1e3, "link_frac": bound / t,
+            "maps_finite": finite,
+            "accuracy": "parity of the streaming path: tests/test_gpu_runtime.py",
+            "gen_s": t_gen}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +352,10 @@ def main():
     ap.add_argument("--channels", type=int, default=1024)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch shapes, bin edge 2)")
+    ap.add_argument("--workload", default="config2", choices=["config2", "config4", "config5"],
+                    help="config2 (default): the bench line; config4: 64 uneven fields in one "
+                         "graph-captured batch; config5: 65,536 BF16 channels streamed from "
+                         "pinned host memory")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (no per-form timings, accuracy check, e2e or CPU "
                          "baseline): the command used for profiler captures")
@@ -227,6 +378,10 @@ def main():
     torch.cuda.set_device(dev)
     from paper_2207_04584_gb300 import hegrid as H
     H.lib()
+    if args.workload == "config4":
+        return run_config4(args, H, torch, dev, rank)
+    if args.workload == "config5":
+        return run_config5(args, H, torch, dev, rank)
 
     # ---- workload (config 2: FAST-like drift scan, FP32 values) ----------
     t_gen = time.perf_counter()
@@ -328,7 +483,10 @@ def main():
     t_grid = statistics.mean(b.elapsed_time(c) for a, b, c in ev) / 1e3
     value = job_value(N * C * args.steps, world, elapsed)
 
-    # plan facts and accuracy on sampled cells (vs the FP64 oracle)
+    # plan facts, per-form timings, and each form's map on 256 sampled cells
+    # (compared with the FP64 oracle in the CPU-baseline leg below)
+    sample_cells = np.sort(np.random.default_rng(7).choice(M, 256, replace=False))
+    sampled = {}
     plan = new_plan(lon_d, lat_d, 1)
     info = H.hegrid_plan_info(plan)
     P = info["n_pairs"]
@@ -351,18 +509,7 @@ def main():
         tg = es.elapsed_time(ee) / 1e3 / reps
         forms[nm] = {"grid_ms": tg * 1e3, "grid_contrib_per_s": N * C / tg,
                      "pair_channel_per_s": P * C / tg}
-        if rank == 0:
-            import oracle
-            rng = np.random.default_rng(7)
-            cells = np.sort(rng.choice(M, 256, replace=False))
-            ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
-            ref, Wref = ix.grid(wl["values"], cells=cells)
-            got = map_d[torch.from_numpy(cells).to(dev)].cpu().numpy().astype(np.float64)
-            mask = Wref >= 1e-3 * Wref.max()
-            rms = np.sqrt(np.mean(ref[mask] ** 2, axis=0))
-            e = np.max(np.abs(got[mask] - ref[mask]), axis=0) / rms
-            err[nm] = {"max": float(e.max()), "median": float(np.median(e)),
-                       "cells": int(mask.sum())}
+        sampled[nm] = map_d[torch.from_numpy(sample_cells).to(dev)].cpu().numpy().astype(np.float64)
     H.hegrid_plan_destroy(plan)
 
     # ---- roofline of the dominant kernel (the grid step) ------------------
@@ -429,9 +576,21 @@ def main():
                "path": "hegrid_plan_create(host coords) + hegrid_grid_stream(4 pinned channel "
                        "chunks -> pinned host map)"}
 
+    # ---- CPU baseline: the FP64 oracle timed on the host cores, and the
+    # same oracle's values on the sampled cells for each form's error -------
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and not args.lean:
         cpu = cpu_oracle_sample(wl, frac_rows=20)
+        if sampled:
+            import oracle
+            ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
+            ref, Wref = ix.grid(wl["values"], cells=sample_cells)
+            mask = Wref >= 1e-3 * Wref.max()
+            rms = np.sqrt(np.mean(ref[mask] ** 2, axis=0))
+            for nm, got in sampled.items():
+                e = np.max(np.abs(got[mask] - ref[mask]), axis=0) / rms
+                err[nm] = {"max": float(e.max()), "median": float(np.median(e)),
+                           "cells": int(mask.sum())}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
