@@ -103,8 +103,8 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "fa1922e998779380ecc6da028f528588dda7c37dc445f5eba48849a45074600b",
-                  "bytes": 4 * (8.642127e9 + 0.423278e9),
+                  "sha256": "379e18b2b8d15006662a1839d42dd5c37e8318c2a3e5f7e70fe7b9a7b53c6da9",
+                  "bytes": 4 * (8.631201e9 + 0.366430e9),
                   "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
