@@ -69,7 +69,8 @@ typedef struct {
 
 /* hegrid_grid modes */
 #define HEGRID_MODE_FP32 0u     /* CUDA-core FP32 gather/accumulate */
-#define HEGRID_MODE_TC 1u       /* tcgen05 tensor cores, one BF16 (or F16) pass */
+#define HEGRID_MODE_TC 1u       /* tcgen05 tensor cores, one 16-bit pass (FP16; BF16 for
+                                   chunks of values outside FP16's range) */
 #define HEGRID_MODE_TC_SPLIT 2u /* tcgen05 with hi/lo splits of values and weights */
 
 /* plan_create flags: bits 0-7 give the bin edge in map cells (0 = default 2). */
@@ -85,7 +86,8 @@ typedef struct {
  * geom, kern       map geometry and kernel (host structs, copied).
  * flags            HEGRID_PLAN_BIN_CELLS(b) or 0.
  * stream           stream for every launch; the call synchronises it once to
- *                  learn the number of (cell, sample) pairs.
+ *                  learn the sizes of the pair ranges it reserves (upper
+ *                  bounds from the binned samples); the rest is asynchronous.
  *
  * Errors: INVALID_ARG (N < 1, nx/ny < 1, cell size <= 0, FWHM <= 0, support
  * <= 0); UNSUPPORTED (a cell row within R of a pole, a padded map wider than
