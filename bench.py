@@ -515,14 +515,19 @@ def main():
     # ---- roofline of the dominant kernel (the grid step) ------------------
     hbm, tc_peak, peak_kind = _peaks()
     alg_bytes = N * C * 4 + M * C * 4 + M * 4
+    # FP32 FMA peak of this GPU, measured (the plain form's ALU roofline)
+    fp32_peak = H.hegrid_fp32_peak(sh)
+    if "fp32" in forms and "grid_ms" in forms["fp32"]:
+        f = 2.0 * P * C / (forms["fp32"]["grid_ms"] * 1e-3) / 1e12
+        forms["fp32"]["useful_tflops"] = f
+        forms["fp32"]["alu_frac"] = f / fp32_peak
     if mode == H.HEGRID_MODE_FP32:
-        clk_mhz = 2070.0
-        peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+        peak = fp32_peak
         achieved = 2.0 * P * C / t_grid / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic("k_grid_f32"),
-                "note": "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived); "
-                        "achieved = 2 P C / grid-kernel time"}
+                "note": "FP32 FMA peak measured by hegrid_fp32_peak (independent FMA chains "
+                        "on every SM); achieved = 2 P C / grid-kernel time"}
     else:
         achieved = alg_bytes / t_grid / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -602,7 +607,8 @@ def main():
                            "l2": "inputs larger than L2 (values 8 GB)", "tuning": tune,
                            "parallelism": f"replicas x{world}"},
                 "plan_ms": t_plan * 1e3, "grid_ms": t_grid * 1e3,
-                "forms": forms, "err_vs_oracle": err, "roofline": roof, "cpu_baseline": cpu,
+                "forms": forms, "fp32_peak_tflops": fp32_peak, "err_vs_oracle": err,
+                "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "gen_s": t_gen}
         print(json.dumps(line), flush=True)
     if dist:

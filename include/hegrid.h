@@ -238,6 +238,14 @@ hegrid_status hegrid_autotune_bins(int64_t n_samples, const double *lon_deg, con
                                    const hegrid_kernel *kern, void *stream,
                                    int32_t *best_bin_cells, float *ms);
 
+/*
+ * hegrid_fp32_peak -- measure the GPU's FP32 FMA throughput (TFLOP/s, 2 flop
+ * per FMA): every SM runs independent FMA chains for a few milliseconds.  The
+ * roofline of HEGRID_MODE_FP32, whose bound is the CUDA-core ALU.
+ * Synchronises `stream`.
+ */
+hegrid_status hegrid_fp32_peak(double *tflops, void *stream);
+
 /* Device-side error word of the plan (bounded waits that timed out). */
 hegrid_status hegrid_status_poll(const hegrid_plan *plan);
 

@@ -30,7 +30,8 @@ EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_
             "hegrid_batch_create", "hegrid_batch_launch", "hegrid_batch_destroy",
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
             "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc",
-            "hegrid_autotune", "hegrid_autotune_bins", "hegrid_plan_set_tuning"]
+            "hegrid_autotune", "hegrid_autotune_bins", "hegrid_plan_set_tuning",
+            "hegrid_fp32_peak"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -101,6 +102,7 @@ def lib():
                                        ctypes.POINTER(hegrid_kernel), P,
                                        ctypes.POINTER(ctypes.c_int32), P]
     L.hegrid_plan_set_tuning.argtypes = [P, u32, ctypes.c_int32, ctypes.c_int32]
+    L.hegrid_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), P]
     L.hegrid_last_error.restype = ctypes.c_char_p
     L.hegrid_launch_count.restype = ctypes.c_int64
     for name in EXPORTED:
@@ -265,3 +267,10 @@ def hegrid_autotune_bins(n_samples, lon_deg, lat_deg, coords_on_device, geom, fw
 def hegrid_plan_set_tuning(plan, mode, band, seg=0):
     return _check(lib().hegrid_plan_set_tuning(plan, int(mode), int(band), int(seg)),
                   "hegrid_plan_set_tuning")
+
+
+def hegrid_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the GPU in TFLOP/s."""
+    t = ctypes.c_double(0.0)
+    _check(lib().hegrid_fp32_peak(ctypes.byref(t), _ptr(stream)), "hegrid_fp32_peak")
+    return t.value

@@ -19,7 +19,7 @@ def lib():
 def declared_symbols():
     txt = open(os.path.join(ROOT, "include", "hegrid.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(hegrid_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(hegrid_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_declares_boundary():
