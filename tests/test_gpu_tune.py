@@ -123,3 +123,10 @@ def test_autotune_bins_plan_matches_oracle(H):
     ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
     err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
     assert err <= TOL_F32, err
+
+
+def test_fp32_peak_is_plausible(H):
+    """The measured FMA throughput is within reach of the part's FP32 units
+    (152 SMs x 128 lanes x 2 flop at 1-2.1 GHz: 39-81 TFLOP/s)."""
+    t = H.hegrid_fp32_peak(torch.cuda.current_stream().cuda_stream)
+    assert 25.0 < t < 90.0, t
