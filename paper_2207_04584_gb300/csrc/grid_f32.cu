@@ -5,11 +5,12 @@
 // in a fixed stride, in the job's work order (the channel tiles of a block
 // back to back, or channel tiles slowest with the blocks in bands of block
 // columns).  For each K chunk of 32 candidate samples of the block:
-//   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) into shared
-//     memory with bulk async copies (TMA engine, one row per lane) completing
-//     on an mbarrier, double-buffered;
-//   * each of 128 threads scatters its cell's pairs that fall in the chunk
-//     into a dense 32 x 128 weight tile and ORs a per-patch occupancy mask;
+//   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) and the
+//     chunk's weight entries into shared memory with bulk async copies (TMA
+//     engine, one row per lane, two entry windows) completing on an mbarrier,
+//     double-buffered, one chunk ahead;
+//   * the threads scatter the staged entries into a dense 32 x 128 weight
+//     tile and OR a per-patch occupancy mask;
 //   * each warp owns a 4x4-cell patch and 128 channels; a thread accumulates
 //     8 cells x 8 channels in registers, skipping samples that touch no cell
 //     of its patch.
@@ -27,11 +28,23 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kKC = 32;   // candidates per K chunk
 constexpr int kCT = 128;  // channels per tile
-constexpr int kPre = 6;   // weight entries prefetched per thread and chunk
+constexpr int kEntCap = 2048;           // weight entries staged per chunk (more: global)
+constexpr int kEntStage = kEntCap - 8;  // entries copied (room for 16-byte alignment)
+
+// Where a staged chunk's weight entries are: entry i < ns at byte ck_off + 2 i
+// of eck[] and w_off + 4 i of ew[]; entries ns..n-1 are read from global.
+struct EntWin {
+  int64_t e_lo;
+  int32_t n, ns;
+  uint32_t ck_off, w_off;
+};
 
 struct __align__(128) SmemF32 {
-  float V[2][kKC][kCT];   // staged sample rows
-  float Wt[2][kKC][kCT];  // dense weight tile [k][cell column]
+  float V[2][kKC][kCT];         // staged sample rows
+  float Wt[2][kKC][kCT];        // dense weight tile [k][cell column]
+  uint8_t eck[2][kEntCap * 2];  // staged entry tile offsets (16-byte aligned window)
+  uint8_t ew[2][kEntCap * 4];   // staged entry weights (16-byte aligned window)
+  EntWin win[2];
   uint32_t pmask[2][kKC];  // per sample k: bit p set if any cell of patch p has it
   uint64_t bar[2];
 };
@@ -100,15 +113,48 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = pv.cand_cnt[b] / kKC;
 
-    const int64_t sub0 = kb0 / kKC;  // first 32-candidate sub-chunk of the block
+    const int64_t* __restrict__ so = pv.sub_off + kb0 / kKC;  // the block's sub-chunks
 
-    // Stage the 32 sample rows of chunk j: warp 0, one row per lane.
+    // Stage chunk j (warp 0): its 32 sample rows (one bulk copy per lane) and
+    // its weight entries (two bulk copies of 16-byte aligned windows), all
+    // completing on bar[j & 1].  Candidate indices come one chunk ahead in
+    // registers, sub-chunk offsets 31 chunks at a time.
+    int32_t n_cur = 0, n_next = 0;
+    int64_t sob = 0;
+    if (warp == 0 && n_chunks > 0) {
+      n_cur = pv.cand_idx[kb0 + lane];
+      if (n_chunks > 1) n_next = pv.cand_idx[kb0 + kKC + lane];
+    }
     auto issue = [&](int j) {
       const int s = j & 1;
-      if (lane == 0) mbar_arrive_expect_tx(&S.bar[s], row_bytes * kKC);
+      const int jb = j % 31;
+      if (jb == 0) sob = j + lane <= n_chunks ? __ldg(so + j + lane) : 0;
+      const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb);
+      const int64_t e_hi = __shfl_sync(0xffffffffu, sob, jb + 1);
+      const int ne = (int)(e_hi - e_lo);
+      const int ns = ne < kEntStage ? ne : kEntStage;
+      const int64_t a0 = (e_lo * 2) & ~(int64_t)15, b0 = (e_lo * 4) & ~(int64_t)15;
+      const uint32_t ab = ns > 0 ? (uint32_t)((((e_lo + ns) * 2 + 15) & ~(int64_t)15) - a0) : 0u;
+      const uint32_t wb = ns > 0 ? (uint32_t)((((e_lo + ns) * 4 + 15) & ~(int64_t)15) - b0) : 0u;
+      if (lane == 0) {
+        EntWin w;
+        w.e_lo = e_lo;
+        w.n = ne;
+        w.ns = ns;
+        w.ck_off = (uint32_t)(e_lo * 2 - a0);
+        w.w_off = (uint32_t)(e_lo * 4 - b0);
+        S.win[s] = w;
+        mbar_arrive_expect_tx(&S.bar[s], row_bytes * kKC + ab + wb);
+      }
       __syncwarp();
-      const int32_t n = pv.cand_idx[kb0 + (int64_t)j * kKC + lane];
+      const int32_t n = n_cur;
+      n_cur = n_next;
+      if (j + 2 < n_chunks) n_next = pv.cand_idx[kb0 + (int64_t)(j + 2) * kKC + lane];
       bulk_g2s(&S.V[s][lane][0], vals + (int64_t)n * J.ld_values + c0, row_bytes, &S.bar[s]);
+      if (lane == 0 && ab)
+        bulk_g2s(S.eck[s], reinterpret_cast<const uint8_t*>(pv.ent_ck) + a0, ab, &S.bar[s]);
+      if (lane == 1 && wb)
+        bulk_g2s(S.ew[s], reinterpret_cast<const uint8_t*>(pv.ent_w) + b0, wb, &S.bar[s]);
     };
 
     float acc[8][8];
@@ -119,49 +165,16 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int patch = warp, cs = lane >> 4, cg = lane & 15;
     if (warp == 0 && n_chunks > 0) issue(0);
-    int64_t e_lo = 0, e_hi = 0;
-    if (n_chunks > 0) {
-      e_lo = pv.sub_off[sub0];
-      e_hi = pv.sub_off[sub0 + 1];
-    }
     for (int j = 0; j < n_chunks; ++j) {
       const int s = j & 1;
       if (warp == 0 && j + 1 < n_chunks) issue(j + 1);
-      // The chunk's weight entries, loaded before the tile is cleared so the
-      // loads' latency overlaps the clearing and the barrier.
-      uint32_t pck[kPre];
-      float pw[kPre];
-#pragma unroll
-      for (int i = 0; i < kPre; ++i) {
-        const int64_t e = e_lo + tid + (int64_t)i * kThreads;
-        pck[i] = e < e_hi ? (uint32_t)__ldg(pv.ent_ck + e) : 0xffffffffu;
-        pw[i] = e < e_hi ? __ldg(pv.ent_w + e) : 0.0f;
-      }
-      const int64_t e_next = j + 1 < n_chunks ? __ldg(pv.sub_off + sub0 + j + 2) : 0;
-      // weight tile for chunk j: zero, then scatter the chunk's entries
+      // weight tile for chunk j: zero, wait for the staged rows and entries,
+      // then scatter the entries
       {
         float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][0]);
         for (int i = tid; i < kKC * kCT / 4; i += kThreads) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tid < kKC) S.pmask[s][tid] = 0u;
       }
-      __syncthreads();
-      {
-        auto put = [&](uint32_t ck, float w) {
-          int col, k;
-          tile_rk(ck, col, k);
-          const int tc = cell_to_col(col % HG_BX, col / HG_BX);
-          S.Wt[s][k][tc] = w;
-          atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
-        };
-#pragma unroll
-        for (int i = 0; i < kPre; ++i)
-          if (pck[i] != 0xffffffffu) put(pck[i], pw[i]);
-        for (int64_t e = e_lo + tid + (int64_t)kPre * kThreads; e < e_hi; e += kThreads)
-          put(pv.ent_ck[e], pv.ent_w[e]);
-        e_lo = e_hi;
-        e_hi = e_next;
-      }
-      __syncthreads();
       const int timed_out = !mbar_wait(&S.bar[s], phase[s], pv.err_word);
       if (__syncthreads_or(timed_out)) {
         // give up: wait (bounded) for the other stage's copies, then leave
@@ -169,6 +182,29 @@ __global__ void __launch_bounds__(kThreads, 2)
         bail = true;
         break;
       }
+      {
+        const EntWin w = S.win[s];
+        const uint32_t eck = smem_u32(S.eck[s]) + w.ck_off, ew = smem_u32(S.ew[s]) + w.w_off;
+        for (int i = tid; i < w.n; i += kThreads) {
+          uint32_t ck;
+          float wt;
+          if (i < w.ns) {
+            uint16_t h;
+            asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(eck + 2 * i));
+            ck = h;
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(wt) : "r"(ew + 4 * i));
+          } else {
+            ck = pv.ent_ck[w.e_lo + i];
+            wt = pv.ent_w[w.e_lo + i];
+          }
+          int col, k;
+          tile_rk(ck, col, k);
+          const int tc = cell_to_col(col % HG_BX, col / HG_BX);
+          S.Wt[s][k][tc] = wt;
+          atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
+        }
+      }
+      __syncthreads();
       phase[s] ^= 1u;
       const uint32_t* pm = S.pmask[s];
       const float* wrow = &S.Wt[s][0][patch * 16 + cs * 8];
