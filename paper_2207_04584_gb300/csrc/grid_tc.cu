@@ -4,8 +4,9 @@
 // run as dense MMAs over the block's candidate samples k (sorted spatially by
 // the plan, 32 per chunk):  D[128 cells x 256 ch] (+)= A[128 x 16] * B[16 x 256]
 // with A = the block's weight tile (built in shared memory from the plan's
-// candidate-major entries) and B = the sample values of the chunk (K-major, so
-// each channel row holds the chunk's samples).  FP32 accumulation in TMEM.
+// weight entries, which carry their byte offset in the tile) and B = the
+// sample values of the chunk (K-major, so each channel row holds the chunk's
+// samples).  FP32 accumulation in TMEM.
 //
 // Precision: values and weights are split into a high and a low 16-bit part;
 // HEGRID_MODE_TC_SPLIT issues hi*hi + hi*lo + lo*hi (the lo*lo term is below
@@ -21,14 +22,15 @@
 // into a "total" TMEM region, later segments into a "segment" region that the
 // drain warps add into the total with FP32 round-to-nearest adds (tcgen05
 // ld/st).  Consecutive items swap the two regions' roles, so an item's
-// epilogue overlaps the next item's first segment.  Weights enter the A tiles scaled by 2^15 (exact), which keeps the
-// low FP16 half of their split a normal number; W comes from the plan
-// (compensated sums of the weights) and is scaled to match.
+// epilogue overlaps the next item's first segment.  Weights enter the A tiles
+// scaled by 2^15 (exact), which keeps the low FP16 half of their split a
+// normal number; W comes from the plan (compensated sums of the weights) and
+// is scaled to match.
 //
 // Warp roles (one CTA per SM, persistent over work items):
-//   warp 17     stages the chunk's 32 sample rows (raw, as stored) into a
-//               4-deep shared-memory ring with bulk async copies (TMA
-//               engine), one row per lane;
+//   warp 17     stages the chunk's 32 sample rows (raw, as stored; eight
+//               four-row TMA tensor gathers) and its weight entries (bulk
+//               copies) into a 3-deep shared-memory ring;
 //   warps 0-15  convert a staged chunk into the B tiles (row = channel, two
 //               threads per row) and store the chunk's weight entries into the
 //               A tiles at the tile offsets the plan precomputed (2-deep ring);
