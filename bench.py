@@ -103,14 +103,14 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "379e18b2b8d15006662a1839d42dd5c37e8318c2a3e5f7e70fe7b9a7b53c6da9",
-                  "bytes": 4 * (8.631201e9 + 0.366430e9),
+                  "sha256": "88f2e210d7b32c5fbc598c5e244526f85bf4a02708ed41e04d91e78235ac4e95",
+                  "bytes": 4 * (8.595589e9 + 0.366694e9),
                   "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": "5e020be29dd66b4ca59f8b72550e15d234bf8e72c71c65b7e01a5bca06d8372f",
-                   "bytes": 4 * (6.408942e9 + 0.363721e9),
+                   "sha256": "2c35cb9e609674acc6077367e87caf06eed27708fd449a37f45b2cde4f9e2e4a",
+                   "bytes": 4 * (6.387795e9 + 0.362828e9),
                    "capture": "profiles/k_grid_f32_fast_drift_c256.md (C=256 x 4)"},
 }
 
@@ -136,9 +136,10 @@ def job_value(units_per_rank, world, elapsed_max):
     return world * units_per_rank / elapsed_max
 
 
-def cpu_oracle_sample(wl, frac_rows=20, nthreads=0):
+def cpu_oracle_sample(wl, frac_rows=20, nthreads=0, keep=None):
     """Time the FP64 oracle on a bounded sample: every frac_rows-th map row,
-    all channels; extrapolate to the full map as t_index + t_cells * M / cells."""
+    all channels; extrapolate to the full map as t_index + t_cells * M / cells.
+    With ``keep`` (a dict), the oracle's index is left in keep["index"]."""
     import oracle
     g = wl["geom"]
     nx, ny = g["nx"], g["ny"]
@@ -146,6 +147,8 @@ def cpu_oracle_sample(wl, frac_rows=20, nthreads=0):
     cells = (rows[:, None] * nx + np.arange(nx)[None, :]).ravel()
     t0 = time.perf_counter()
     ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"], wl.get("support", 3.0))
+    if keep is not None:
+        keep["index"] = ix
     t1 = time.perf_counter()
     ix.grid(wl["values"], cells=cells, nthreads=nthreads)
     t2 = time.perf_counter()
@@ -191,6 +194,23 @@ def run_reference(args, rank):
                     "d2h_bytes_per_step": 0},
             "gen_s": t_gen}
     print(json.dumps(line), flush=True)
+
+
+def _link(torch, dev, stream):
+    """Pinned host <-> device copy rates (GB/s) of one 1 GiB copy each way, device-timed."""
+    out = {}
+    lh = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+    ld_ = torch.empty_like(lh, device=dev)
+    for name, dst, src in (("h2d", ld_, lh), ("d2h", lh, ld_)):
+        dst.copy_(src, non_blocking=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dst.copy_(src, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_gbs"] = (1 << 30) / (a.elapsed_time(b) * 1e-3) / 1e9
+    del lh, ld_
+    return out
 
 
 def run_config4(args, H, torch, dev, rank):
@@ -295,20 +315,8 @@ def run_config5(args, H, torch, dev, rank):
     order = [chunks[k % NDIST] for k in range(NCH)]
     lon_h, lat_h = np.ascontiguousarray(wl["lon"]), np.ascontiguousarray(wl["lat"])
     plan = H.hegrid_plan_create(N, lon_h, lat_h, 0, g, wl["fwhm_deg"], 3.0, 0, sh)
-    link = {}
     try:
-        # the host link, as in the config-2 e2e
-        lh = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
-        ld_ = torch.empty_like(lh, device=dev)
-        for name, dst, src in (("h2d", ld_, lh), ("d2h", lh, ld_)):
-            dst.copy_(src, non_blocking=True)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            dst.copy_(src, non_blocking=True)
-            b.record(stream)
-            torch.cuda.synchronize()
-            link[name + "_gbs"] = (1 << 30) / (a.elapsed_time(b) * 1e-3) / 1e9
-        del lh, ld_
+        link = _link(torch, dev, stream)
         H.hegrid_grid_stream(plan, order, CC, H.HEGRID_BF16, H.HEGRID_MODE_TC_SPLIT, host_map,
                              NCH * CC, host_w)
         ts = time.perf_counter()
@@ -340,6 +348,181 @@ def run_config5(args, H, torch, dev, rank):
             "gen_s": t_gen}), flush=True)
 
 
+# Table 3 (Sec. 5.2): HEGrid's end-to-end times in seconds on a V100 for the simulated
+# survey (50 channels) at each sample count; context only (another machine, and the paper's
+# times include reading the input files).
+SIM_SIZES = (15_000_000, 16_000_000, 17_000_000, 18_000_000, 19_000_000)
+PAPER_V100_S = {15_000_000: 30.21, 16_000_000: 32.77, 17_000_000: 35.27, 18_000_000: 38.20,
+                19_000_000: 40.94}
+
+
+def run_sim(args, H, torch, dev, rank):
+    """The paper's simulated survey (Table 2): 60 x 20 deg at (30, 41), 1 arcmin cells,
+    180 arcsec beam, 50 FP32 channels, 1.5e7 - 1.9e7 uniform samples.  Each step is the whole
+    pipeline (plan + grid); every sample count of Table 3 is timed with inputs resident on the
+    device and end to end from pinned host buffers to a pinned host map."""
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    C = 50
+    sizes = SIM_SIZES if not args.sim_n else (args.sim_n,)
+    paper = PAPER_V100_S if args.sim_span == 60.0 else {}
+    nmax = max(sizes)
+    t_gen = time.perf_counter()
+    host_vals = torch.empty((nmax, C), dtype=torch.float32, pin_memory=True)
+    wl = W.sim_survey(n=nmax, C=C, out=host_vals.numpy(), lon_span=args.sim_span)
+    t_gen = time.perf_counter() - t_gen
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    # coordinates in pinned host memory, like the values
+    lon_h = torch.from_numpy(np.ascontiguousarray(wl["lon"])).pin_memory().numpy()
+    lat_h = torch.from_numpy(np.ascontiguousarray(wl["lat"])).pin_memory().numpy()
+    ldv = (C + 3) // 4 * 4  # device rows padded to 16 bytes
+    vals_d = torch.zeros((nmax, ldv), dtype=torch.float32, device=dev)
+    vals_d[:, :C].copy_(host_vals.to(dev))
+    lon_d = torch.from_numpy(lon_h).to(dev)
+    lat_d = torch.from_numpy(lat_h).to(dev)
+    map_d = torch.empty((M, C), device=dev)
+    w_d = torch.empty(M, device=dev)
+    host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
+    host_w = torch.empty(M, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    modes = {"tc_split": H.HEGRID_MODE_TC_SPLIT, "fp32": H.HEGRID_MODE_FP32}
+    nmid = sizes[len(sizes) // 2]
+
+    # the form (FP32 or split tensor core, both within the parity bound) and its launch
+    # shape, chosen on the middle sample count outside the timed region
+    tune = {}
+    flags = 0
+    if not args.no_tune:
+        flags, bin_ms = H.hegrid_autotune_bins(nmid, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, sh)
+        tune["bin_cells"] = flags
+        tune["plan_ms_by_bin"] = [round(x, 3) for x in bin_ms]
+    p = H.hegrid_plan_create(nmid, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, flags, sh)
+    forms = {}
+    try:
+        for nm, md in modes.items():
+            if args.mode not in ("auto", nm):
+                continue
+            q = {}
+            if not args.no_tune:
+                rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, ldv, md, sh)
+                best = rep["points"][rep["best"]]
+                q = {"band": best["band"], "seg": best["seg"], "ms": best["ms"]}
+                H.hegrid_plan_set_tuning(p, md, best["band"], best["seg"])
+            H.hegrid_grid(p, vals_d, H.HEGRID_F32, C, ldv, map_d, C, w_d, md, sh)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                H.hegrid_grid(p, vals_d, H.HEGRID_F32, C, ldv, map_d, C, w_d, md, sh)
+            b.record(stream)
+            torch.cuda.synchronize()
+            q["grid_ms"] = a.elapsed_time(b) / 3
+            forms[nm] = q
+        info = H.hegrid_plan_info(p)
+    finally:
+        H.hegrid_plan_destroy(p)
+    mode_name = min(forms, key=lambda k: forms[k]["grid_ms"])
+    mode = modes[mode_name]
+    shape = forms[mode_name]
+
+    def new_plan(n, lon, lat, on_device):
+        pl = H.hegrid_plan_create(n, lon, lat, on_device, g, wl["fwhm_deg"], 3.0, flags, sh)
+        if "band" in shape:
+            H.hegrid_plan_set_tuning(pl, mode, shape["band"], shape["seg"])
+        return pl
+
+    link = _link(torch, dev, stream)
+    rows = []
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    launches = 0
+    sample_cells = np.sort(np.random.default_rng(7).choice(M, 256, replace=False))
+    sampled = None
+    for n in sizes:
+        ev = []
+        l0 = H.hegrid_launch_count()
+        for i in range(args.warmup + args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            pl = new_plan(n, lon_d, lat_d, 1)
+            e1.record(stream)
+            H.hegrid_grid(pl, vals_d, H.HEGRID_F32, C, ldv, map_d, C, w_d, mode, sh)
+            e2.record(stream)
+            H.hegrid_plan_destroy(pl)
+            if i >= args.warmup:
+                ev.append((e0, e1, e2))
+        torch.cuda.synchronize()
+        launches = (H.hegrid_launch_count() - l0) / (args.warmup + args.steps)
+        t_dev = statistics.mean(a.elapsed_time(c) for a, b, c in ev) / 1e3
+        t_plan = statistics.mean(a.elapsed_time(b) for a, b, c in ev) / 1e3
+        t_grid = statistics.mean(b.elapsed_time(c) for a, b, c in ev) / 1e3
+
+        def e2e_step():
+            pl = new_plan(n, lon_h[:n], lat_h[:n], 0)
+            H.hegrid_grid_stream(pl, [host_vals[:n]], C, H.HEGRID_F32, mode, host_map, C, host_w)
+            H.hegrid_plan_destroy(pl)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        te = []
+        for _ in range(max(1, args.e2e_steps)):
+            ts = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - ts)
+        t_e2e = statistics.mean(te)
+        if n == nmid:
+            sampled = host_map[torch.from_numpy(sample_cells)].numpy().astype(np.float64)
+        h2d = n * 16 + n * C * 4
+        d2h = M * C * 4 + M * 4
+        rows.append({"N": n, "device_ms": t_dev * 1e3, "plan_ms": t_plan * 1e3,
+                     "grid_ms": t_grid * 1e3, "e2e_ms": t_e2e * 1e3,
+                     "e2e_contrib_per_s": n * C / t_e2e, "device_contrib_per_s": n * C / t_dev,
+                     "h2d_bytes": h2d, "d2h_bytes": d2h,
+                     "link_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
+                     "paper_v100_s": paper.get(n),
+                     "paper_v100_contrib_per_s": n * C / paper[n] if n in paper else None})
+    clk = clocks.stop()
+    head = next(r for r in rows if r["N"] == nmid)
+    finite = bool(torch.isfinite(host_map[:: max(1, M // 4096)]).all())
+
+    # CPU baseline: the FP64 oracle on every 100th map row at the headline sample count,
+    # and its values on 256 sampled cells of the end-to-end map of that count
+    cpu, err = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        keep = {}
+        cpu = cpu_oracle_sample({"lon": lon_h[:nmid], "lat": lat_h[:nmid], "geom": g,
+                                 "fwhm_deg": wl["fwhm_deg"], "support": 3.0,
+                                 "values": host_vals.numpy()[:nmid]}, frac_rows=100, keep=keep)
+        ref, Wref = keep["index"].grid(host_vals.numpy()[:nmid], cells=sample_cells)
+        mask = Wref >= 1e-3 * Wref.max()
+        rms = np.sqrt(np.mean(ref[mask] ** 2, axis=0))
+        e = np.max(np.abs(sampled[mask] - ref[mask]), axis=0) / rms
+        err = {mode_name: {"max": float(e.max()), "median": float(np.median(e)),
+                           "cells": int(mask.sum()), "map": "end-to-end host map"}}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": head["device_contrib_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["device_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if mode_name == "fp32" else "f16", "data": "synthetic",
+            "config": {"workload": f"simulated survey (Table 2): {g['nx'] / 60:g}x20 deg at "
+                                   f"({g['lon0']:g},41), {g['nx']}x1200 map at 1', FWHM 180'', "
+                                   "R=3 sigma, 50 FP32 channels, uniform samples, "
+                                   f"headline N={nmid}",
+                       "N": nmid, "C": C, "M": M, "pairs": info["n_pairs"], "mode": mode_name,
+                       "l2": "inputs larger than L2 (values 3.4 GB)",
+                       "tuning": tune, "forms": forms},
+            "e2e": {"value": head["e2e_contrib_per_s"], "unit": UNIT,
+                    "h2d_bytes_per_step": head["h2d_bytes"],
+                    "d2h_bytes_per_step": head["d2h_bytes"], "ms_per_step": head["e2e_ms"],
+                    "path": "hegrid_plan_create(host coords) + hegrid_grid_stream(one pinned "
+                            "50-channel chunk -> pinned host map)"},
+            "table3": rows, "link": link, "maps_finite": finite,
+            "cpu_baseline": cpu, "err_vs_oracle": err,
+            "accuracy": "parity on this workload's shape: tests/test_gpu_sim.py",
+            "gpu_launches": launches, "clocks": clk, "gen_s": t_gen}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,10 +535,17 @@ def main():
     ap.add_argument("--channels", type=int, default=1024)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch shapes, bin edge 2)")
-    ap.add_argument("--workload", default="config2", choices=["config2", "config4", "config5"],
+    ap.add_argument("--workload", default="config2", choices=["config2", "config4", "config5", "sim"],
                     help="config2 (default): the bench line; config4: 64 uneven fields in one "
                          "graph-captured batch; config5: 65,536 BF16 channels streamed from "
-                         "pinned host memory")
+                         "pinned host memory; sim: the paper's 60x20 deg simulated survey "
+                         "at every sample count of Table 3, plan + grid, device and end to "
+                         "end")
+    ap.add_argument("--sim-n", type=int, default=0,
+                    help="sim workload: time this one sample count only")
+    ap.add_argument("--sim-span", type=float, default=60.0,
+                    help="sim workload: RA span of the field in degrees (60: the paper's; "
+                         "smaller: a cut of it, for profiler captures)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (no per-form timings, accuracy check, e2e or CPU "
                          "baseline): the command used for profiler captures")
@@ -382,6 +572,8 @@ def main():
         return run_config4(args, H, torch, dev, rank)
     if args.workload == "config5":
         return run_config5(args, H, torch, dev, rank)
+    if args.workload == "sim":
+        return run_sim(args, H, torch, dev, rank)
 
     # ---- workload (config 2: FAST-like drift scan, FP32 values) ----------
     t_gen = time.perf_counter()
@@ -539,7 +731,9 @@ def main():
     if args.e2e_steps > 0 and not args.lean:
         host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
         host_w = torch.empty(M, dtype=torch.float32, pin_memory=True)
-        lon_h, lat_h = np.ascontiguousarray(wl["lon"]), np.ascontiguousarray(wl["lat"])
+        # coordinates in pinned host memory, like the values
+        lon_h = torch.from_numpy(np.ascontiguousarray(wl["lon"])).pin_memory().numpy()
+        lat_h = torch.from_numpy(np.ascontiguousarray(wl["lat"])).pin_memory().numpy()
         n_chunks = 4
         cc = C // n_chunks
         chunks = [torch.empty((N, cc), dtype=torch.float32, pin_memory=True)
@@ -553,18 +747,7 @@ def main():
             H.hegrid_plan_destroy(p)
 
         # the host link: one pinned 1 GiB copy each way, timed on the device
-        link = {}
-        lh = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
-        ld_ = torch.empty_like(lh, device=dev)
-        for name, dst, src in (("h2d", ld_, lh), ("d2h", lh, ld_)):
-            dst.copy_(src, non_blocking=True)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            dst.copy_(src, non_blocking=True)
-            b.record(stream)
-            torch.cuda.synchronize()
-            link[name + "_gbs"] = (1 << 30) / (a.elapsed_time(b) * 1e-3) / 1e9
-        del lh, ld_
+        link = _link(torch, dev, stream)
         e2e_step()
         torch.cuda.synchronize()
         ts = time.perf_counter()

@@ -161,7 +161,11 @@ hegrid_status hegrid_batch_destroy(hegrid_batch *batch);
  * host [n_samples x chunk_channels] of `dtype` (pinned memory recommended).
  * host_map is host FP32 [M x ld_host_map] with ld_host_map >= n_chunks *
  * chunk_channels; host_weight is host FP32 [M] or NULL.  Uses internal
- * streams and a device ring of two chunk buffers; blocks until done.
+ * streams and a device ring of two chunk buffers (one for a single chunk);
+ * blocks until done.  Each chunk crosses the host link as one dense copy;
+ * rows that are not a multiple of 16 bytes are then spread on the device to
+ * the 16-byte row pitch the grid kernels read, through a staging buffer of
+ * one chunk per ring slot.
  */
 hegrid_status hegrid_grid_stream(hegrid_plan *plan, const void *const *host_chunks, int n_chunks,
                                  int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,

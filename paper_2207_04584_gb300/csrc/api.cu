@@ -15,6 +15,42 @@
 namespace hg {
 namespace {
 
+// Rows of `row_units` words, dense in `src`, copied to rows `pitch_units`
+// words apart in `dst` (the padding words are left as they are).  Host chunks
+// whose rows are not a multiple of 16 bytes arrive by one dense copy and are
+// spread to the grid kernels' 16-byte row pitch here, instead of by a 2-D
+// copy, whose per-row transfers run the host link at a few GB/s for rows of
+// a few hundred bytes.
+template <typename U>
+__global__ void __launch_bounds__(256) k_pad_rows(const U* __restrict__ src, U* __restrict__ dst,
+                                                  int64_t n_units, int64_t row_units,
+                                                  int64_t pitch_units) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_units; i += stride) {
+    const int64_t r = i / row_units;
+    dst[r * pitch_units + (i - r * row_units)] = src[i];
+  }
+}
+
+cudaError_t pad_rows(const void* src, void* dst, int64_t n_rows, int64_t row_bytes,
+                     int64_t pitch_bytes, int n_sm, cudaStream_t s) {
+  const int blocks = std::max(1, n_sm) * 8;
+  if (row_bytes % 8 == 0) {
+    k_pad_rows<uint2><<<blocks, 256, 0, s>>>((const uint2*)src, (uint2*)dst, n_rows * (row_bytes / 8),
+                                             row_bytes / 8, pitch_bytes / 8);
+  } else if (row_bytes % 4 == 0) {
+    k_pad_rows<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)src, (uint32_t*)dst,
+                                                n_rows * (row_bytes / 4), row_bytes / 4,
+                                                pitch_bytes / 4);
+  } else {
+    k_pad_rows<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t*)src, (uint16_t*)dst,
+                                                n_rows * (row_bytes / 2), row_bytes / 2,
+                                                pitch_bytes / 2);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 int elem_bytes(int dtype) {
   switch (dtype) {
     case HEGRID_F32: return 4;
@@ -245,9 +281,12 @@ hegrid_status hegrid_batch_destroy(hegrid_batch* batch) {
   return HEGRID_OK;
 }
 
-// Streaming: a ring of two device chunk buffers and two map buffers.  Chunk
-// k's H2D copy runs on the copy-in stream, its kernel on the compute stream,
-// its D2H copy on the copy-out stream; events order reuse of ring slots.
+// Streaming: a ring of (up to) two device chunk buffers and two map buffers.
+// Chunk k's H2D copy runs on the copy-in stream, its kernel on the compute
+// stream, its D2H copy on the copy-out stream; events order reuse of ring
+// slots.  Host rows that are not a multiple of 16 bytes are copied densely
+// into a staging slot and spread to the padded pitch by k_pad_rows on the
+// compute stream, ahead of the grid kernel.
 hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chunks, int n_chunks,
                                  int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,
                                  float* host_map, int64_t ld_host_map, float* host_weight) {
@@ -268,9 +307,19 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
   const int64_t N = plan->N, M = plan->M;
   // device rows padded to 16 bytes
   const int64_t ldv = ((chunk_channels * eb + 15) / 16 * 16) / eb;
+  const bool padded = ldv != chunk_channels;
+  const int n_slots = n_chunks < 2 ? 1 : 2;
+  const size_t hbytes = (size_t)N * chunk_channels * eb;  // one host chunk
   const size_t vbytes = (size_t)N * ldv * eb;
   const size_t mbytes = (size_t)M * chunk_channels * sizeof(float);
+  int n_sm = 0;
+  {
+    int dev = 0;
+    HG_CUDA_TRY(cudaGetDevice(&dev));
+    HG_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
   void* dv[2] = {nullptr, nullptr};
+  void* dstage[2] = {nullptr, nullptr};
   float* dm[2] = {nullptr, nullptr};
   float* dw = nullptr;
   cudaStream_t sin = nullptr, scomp = nullptr, sout = nullptr;
@@ -283,6 +332,7 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
     if (sout) cudaStreamSynchronize(sout);
     for (int i = 0; i < 2; ++i) {
       if (dv[i]) cudaFreeAsync(dv[i], scomp);
+      if (dstage[i]) cudaFreeAsync(dstage[i], scomp);
       if (dm[i]) cudaFreeAsync(dm[i], scomp);
       if (ev_in[i]) cudaEventDestroy(ev_in[i]);
       if (ev_k[i]) cudaEventDestroy(ev_k[i]);
@@ -306,8 +356,9 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
     }                                                                          \
   } while (0)
   HG_STREAM_TRY(cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking));
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < n_slots; ++i) {
     HG_STREAM_TRY(hg::pool_alloc(&dv[i], vbytes, scomp));
+    if (padded) HG_STREAM_TRY(hg::pool_alloc(&dstage[i], hbytes, scomp));
     HG_STREAM_TRY(hg::pool_alloc((void**)&dm[i], mbytes, scomp));
     HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming));
     HG_STREAM_TRY(cudaEventCreateWithFlags(&ev_k[i], cudaEventDisableTiming));
@@ -324,15 +375,17 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
   cudaEventDestroy(ev_alloc);
   HG_STREAM_TRY(cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking));
   for (int k = 0; k < n_chunks; ++k) {
-    const int r = k & 1;
-    // slot r's value buffer is free once chunk k-2's kernel finished
-    if (k >= 2) HG_STREAM_TRY(cudaStreamWaitEvent(sin, ev_k[r], 0));
-    HG_STREAM_TRY(cudaMemcpy2DAsync(dv[r], ldv * eb, host_chunks[k], chunk_channels * eb,
-                                    chunk_channels * eb, N, cudaMemcpyHostToDevice, sin));
+    const int r = k % n_slots;
+    // slot r's buffers are free once chunk k-n_slots's kernel finished
+    if (k >= n_slots) HG_STREAM_TRY(cudaStreamWaitEvent(sin, ev_k[r], 0));
+    HG_STREAM_TRY(cudaMemcpyAsync(padded ? dstage[r] : dv[r], host_chunks[k], hbytes,
+                                  cudaMemcpyHostToDevice, sin));
     HG_STREAM_TRY(cudaEventRecord(ev_in[r], sin));
     HG_STREAM_TRY(cudaStreamWaitEvent(scomp, ev_in[r], 0));
-    // slot r's map buffer is free once chunk k-2's D2H finished
-    if (k >= 2) HG_STREAM_TRY(cudaStreamWaitEvent(scomp, ev_out[r], 0));
+    if (padded)
+      HG_STREAM_TRY(hg::pad_rows(dstage[r], dv[r], N, chunk_channels * eb, ldv * eb, n_sm, scomp));
+    // slot r's map buffer is free once chunk k-n_slots's D2H finished
+    if (k >= n_slots) HG_STREAM_TRY(cudaStreamWaitEvent(scomp, ev_out[r], 0));
     st = hegrid_grid(plan, dv[r], dtype, chunk_channels, ldv, dm[r], chunk_channels,
                      k == 0 ? dw : nullptr, mode, scomp);
     if (st != HEGRID_OK) {

@@ -376,3 +376,41 @@ def config5_chunk(wl, k, C_chunk=4096, seed=SEED_BASE + 5, n_sources=300, out=No
     _fill_noise(values, int(crng.integers(2**62)), 0.02, offsets)
     add_sources(values, lon, lat, src_lon, src_lat, 2.9 * ARCMIN, spectra)
     return values
+
+
+def sim_survey(seed=SEED_BASE + 6, n=19_000_000, C=50, n_sources=1000, with_values=True,
+               out=None, lon_span=60.0):
+    """The simulated survey of Sec. 5 (Table 2): a 60 x 20 deg map centred on (30, 41),
+    ``n`` samples (1.5e7 - 1.9e7 in Tables 3 and 4) of ``C`` = 50 channels, 180 arcsec beam.
+
+    Sample positions are uniform in (lon, lat) over the map; the map has 1 arcmin cells
+    (3600 x 1200) and the gridding kernel's FWHM is the beam's.  Because the positions are
+    i.i.d., the first ``k`` samples of this set are the same workload with ``k`` samples.
+    Values: Gaussian point sources of the beam's width with power-law spectra, a 1/f-like
+    spectral baseline and white noise.  ``out`` (optional) is a preallocated float32
+    [n, C] (e.g. pinned host memory).  ``lon_span`` < 60 keeps the first ``lon_span``
+    degrees of RA (a smaller field at the same density when ``n`` is scaled with it).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centre = (0.5 * lon_span, 41.0)
+    lon, lat = uniform_positions(rng, n, (0.0, lon_span), (31.0, 51.0))
+    beam_deg = 180.0 * ARCSEC
+    wl = {"name": "sim-survey-60x20", "lon": lon, "lat": lat,
+          "geom": _geom(int(round(lon_span * 60)), 1200, centre[0], centre[1], ARCMIN),
+          "fwhm_deg": beam_deg, "support": 3.0}
+    if not with_values:
+        return wl
+    vrng = np.random.Generator(np.random.PCG64(seed + 1000))
+    src_lon = vrng.uniform(0.0, lon_span, n_sources)
+    src_lat = vrng.uniform(31.0, 51.0, n_sources)
+    amp = np.exp(vrng.uniform(math.log(0.1), math.log(10.0), n_sources))
+    beta = vrng.uniform(-2.0, 1.0, n_sources)
+    nu = np.linspace(1.0, 1.5, C) / 1.25
+    spectra = (amp[:, None] * nu[None, :] ** beta[:, None]).astype(np.float32)
+    baseline = one_over_f(vrng, C)
+    values = out if out is not None else np.empty((n, C), np.float32)
+    assert values.shape == (n, C) and values.dtype == np.float32
+    _fill_noise(values, int(vrng.integers(2**62)), 0.02, lambda a, b: baseline[None, :])
+    add_sources(values, lon, lat, src_lon, src_lat, beam_deg, spectra)
+    wl["values"] = values
+    return wl

@@ -154,3 +154,38 @@ def test_stream_matches_device_call(H):
     a, b = out.cpu().numpy(), hmap.numpy()
     assert np.array_equal(np.isnan(a), np.isnan(b))
     assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+
+
+@pytest.mark.parametrize("dtype,cc,n_chunks", [("f32", 50, 1), ("f32", 13, 3), ("bf16", 13, 2)])
+def test_stream_unaligned_rows(H, dtype, cc, n_chunks):
+    """Host chunks whose rows are not a multiple of 16 bytes (200, 52 and 26
+    bytes: each width of the row repack) stream to the map the device call
+    makes from the same values in padded rows, bit for bit."""
+    wl = W.config1(n=9000, C=cc * n_chunks, nx=40, ny=40)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    N = len(wl["lon"])
+    C = cc * n_chunks
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    hdt = H.HEGRID_F32 if dtype == "f32" else H.HEGRID_BF16
+    vals = torch.from_numpy(wl["values"]).to(tdt)
+    chunks = [vals[:, k * cc:(k + 1) * cc].contiguous().pin_memory() for k in range(n_chunks)]
+    eb = 4 if dtype == "f32" else 2
+    ld = (cc * eb + 15) // 16 * 16 // eb
+    plan = _plan(H, wl)
+    try:
+        s = torch.cuda.current_stream().cuda_stream
+        ref = torch.empty((M, C), device="cuda")
+        for k in range(n_chunks):
+            dv = torch.zeros((N, ld), dtype=tdt, device="cuda")
+            dv[:, :cc] = chunks[k].cuda()
+            H.hegrid_grid(plan, dv, hdt, cc, ld, ref[:, k * cc:], C, None,
+                          H.HEGRID_MODE_TC_SPLIT, s)
+        torch.cuda.synchronize()
+        hmap = torch.full((M, C), -7.0).pin_memory()
+        H.hegrid_grid_stream(plan, chunks, cc, hdt, H.HEGRID_MODE_TC_SPLIT, hmap, C)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    a, b = ref.cpu().numpy(), hmap.numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
