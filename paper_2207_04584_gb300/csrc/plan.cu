@@ -356,14 +356,16 @@ __device__ __forceinline__ float pair_weight(const float (&mh)[3], const float (
   return expf(-th) * (1.0f - tl);
 }
 
-// One CTA per 16x8 cell block; thread t owns block-local cell t (= ly*16 + lx).
-// The samples of the bins around the block are staged kChunk at a time and
-// tested against the block's cells.  The block writes, inside the slot and
-// entry ranges its upper bounds reserved: the candidate list (original sample
-// indices, union order, padded to HG_KPAD), its padded length, the weight
-// entries in 32-candidate sub-chunks (entry = tile_off(cell, candidate & 31),
-// FP32 weight; cell-major inside each sub-chunk), the offsets of every
-// sub-chunk plus an end sentinel, and W[m].
+// One CTA per 16x8 cell block; thread t owns block-local cell thread_cell(t)
+// (each warp an 8 x 4 tile).  The samples of the bins around the block are
+// staged kChunk at a time, one bin row at a time; each warp tests those in
+// its own tile's bin window against its cells.  The block writes, inside the
+// slot and entry ranges its upper bounds reserved: the candidate list
+// (original sample indices, union order, padded to HG_KPAD), its padded
+// length, the weight entries in 32-candidate sub-chunks (entry =
+// tile_off(cell, candidate & 31), FP32 weight; inside each sub-chunk the
+// entries of a cell are contiguous, cells in thread order), the offsets of
+// every sub-chunk plus an end sentinel, and W[m].
 // Neumaier-compensated running sum.
 struct CSum {
   float s = 0.0f, c = 0.0f;
@@ -402,8 +404,17 @@ __device__ __forceinline__ int select_bit(uint32_t x, int j) {
   return pos;
 }
 
+// Block-local cell of thread t: each warp owns an 8 x 4 tile of the 16 x 8
+// block (warp w: columns 8 (w & 1) .. +7, rows 4 (w >> 1) .. +3), so that a
+// warp's bin window is narrower than the block's in both directions.
+__host__ __device__ __forceinline__ int thread_cell(int t) {
+  const int w = t >> 5, lane = t & 31;
+  return ((w >> 1) * 4 + (lane >> 3)) * HG_BX + (w & 1) * 8 + (lane & 7);
+}
+
 __global__ void __launch_bounds__(kChunk)
-    k_block_pairs(PairParams pp, const int4* __restrict__ win, const int32_t* __restrict__ bin_off,
+    k_block_pairs(PairParams pp, const int4* __restrict__ win, const int4* __restrict__ wwin,
+                  const int32_t* __restrict__ bin_off,
                   const int32_t* __restrict__ perm, const double* __restrict__ sx,
                   const double* __restrict__ sy, const double* __restrict__ sz,
                   const int64_t* __restrict__ cand_off, const int64_t* __restrict__ blk_pair_off,
@@ -419,9 +430,10 @@ __global__ void __launch_bounds__(kChunk)
   __shared__ int32_t s_n[kChunk];
   __shared__ uint32_t s_umask[kQ];
   __shared__ int32_t s_red[kQ];
-  // Cell coordinates, candidate-major cell masks (bit i of
-  // s_cm[k][w]: cell 32 w + i has staged candidate k), entries before each
-  // staged candidate, candidate index within its 32-candidate sub-chunk.
+  // Cell coordinates (by block-local cell), candidate-major masks (bit i
+  // of s_cm[k][w]: the cell of thread 32 w + i has staged candidate k),
+  // entries before each staged candidate, candidate index within its
+  // 32-candidate sub-chunk.
   __shared__ float4 s_mh[kChunk];
   __shared__ float4 s_ml[kChunk];
   __shared__ uint32_t s_cm[kChunk][kQ];
@@ -434,9 +446,11 @@ __global__ void __launch_bounds__(kChunk)
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
   const int bbx = b % pp.nbx_b, bby = b / pp.nbx_b;
-  const int ix = bbx * HG_BX + (t % HG_BX), iy = bby * HG_BY + (t / HG_BX);
+  const int cell = thread_cell(t);
+  const int ix = bbx * HG_BX + (cell % HG_BX), iy = bby * HG_BY + (cell / HG_BX);
   const bool active = ix < pp.nx && iy < pp.ny;
   const int64_t m = (int64_t)iy * pp.nx + ix;
+  const int4 ww = wwin[4 * (int64_t)b + wid];  // this warp's bin window
 
   // Block-local frame: origin at the unit vector of the block's centre.
   double bx0, by0, bz0;
@@ -456,8 +470,8 @@ __global__ void __launch_bounds__(kChunk)
     }
   }
 
-  s_mh[t] = make_float4(mh[0], mh[1], mh[2], 0.0f);
-  s_ml[t] = make_float4(ml[0], ml[1], ml[2], 0.0f);
+  s_mh[cell] = make_float4(mh[0], mh[1], mh[2], 0.0f);
+  s_ml[cell] = make_float4(ml[0], ml[1], ml[2], 0.0f);
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
   int64_t erun = 0;    // entries of the block so far
   // W of the cell for each weight representation the grid kernels use
@@ -489,31 +503,42 @@ __global__ void __launch_bounds__(kChunk)
         s_n[t] = perm[s];
       }
       if (t < kQ) s_umask[t] = 0u;
+      // The staged candidates this warp tests: those of the bins of its own
+      // window in this bin row (a contiguous range of the row's samples).
+      int k0 = 0, k1 = 0;
+      if (by >= ww.x && by <= ww.y) {
+        k0 = max(bin_off[(int64_t)by * pp.nbx + ww.z] - base, 0);
+        k1 = min(bin_off[(int64_t)by * pp.nbx + ww.w + 1] - base, nk);
+      }
       __syncthreads();
 
       // Phase 1: membership of each staged candidate for this thread's cell.
+      // FP32 test first (bit set in `in32` when surely inside, in `maybe`
+      // when not surely outside); pairs inside the FP32 error band are
+      // decided in FP64 afterwards.
       uint32_t mask[kQ];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
-        uint32_t mm = 0u;
-        const int kend = active ? min(32, nk - 32 * q) : 0;
-        for (int r = 0; r < kend; ++r) {
-          const int k = 32 * q + r;
-          const float4 n4 = s_eh[k];
-          float dx = mh[0] - n4.x, dy = mh[1] - n4.y, dz = mh[2] - n4.z;
-          float c2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-          bool in;
-          if (c2 <= pp.lo_thr) {
-            in = true;
-          } else if (c2 > pp.hi_thr) {
-            in = false;
-          } else {  // inside the FP32 error band: decide in FP64
-            double ex = um[0] - s_u[0][k], ey = um[1] - s_u[1][k], ez = um[2] - s_u[2][k];
-            in = ex * ex + ey * ey + ez * ez <= pp.cR2;
-          }
-          mm |= (uint32_t)in << r;
+        const int r0 = max(k0 - 32 * q, 0), r1 = min(k1 - 32 * q, 32);
+        uint32_t in32 = 0u, maybe = 0u;
+#pragma unroll 4
+        for (int r = r0; r < r1; ++r) {
+          const float4 n4 = s_eh[32 * q + r];
+          const float dx = mh[0] - n4.x, dy = mh[1] - n4.y, dz = mh[2] - n4.z;
+          const float c2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const uint32_t bit = 1u << r;
+          if (c2 <= pp.lo_thr) in32 |= bit;
+          if (c2 <= pp.hi_thr) maybe |= bit;
         }
-        mask[q] = mm;
+        uint32_t band = active ? maybe & ~in32 : 0u;
+        while (band) {
+          const int r = __ffs(band) - 1;
+          band &= band - 1u;
+          const int k = 32 * q + r;
+          const double ex = um[0] - s_u[0][k], ey = um[1] - s_u[1][k], ez = um[2] - s_u[2][k];
+          if (ex * ex + ey * ey + ez * ez <= pp.cR2) in32 |= 1u << r;
+        }
+        mask[q] = active ? in32 : 0u;
       }
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
@@ -568,9 +593,10 @@ __global__ void __launch_bounds__(kChunk)
         // list the group's (cell, candidate) pairs in entry order, compute
         // the weights one entry per thread (coalesced writes), then add them
         // into W of each cell in candidate order.  Within a group, entries
-        // are cell-major on each side of the 32-candidate sub-chunk boundary
-        // that may fall inside it (candidate r_split starts a new
-        // sub-chunk), so every sub-chunk's entries stay contiguous.
+        // are grouped by cell (in thread order) on each side of the
+        // 32-candidate sub-chunk boundary that may fall inside it (candidate
+        // r_split starts a new sub-chunk), so every sub-chunk's entries stay
+        // contiguous.
         int ubefore = 0;  // union candidates of the staged chunk before group q
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
@@ -606,19 +632,19 @@ __global__ void __launch_bounds__(kChunk)
             while (mm) {
               const int r = __ffs(mm) - 1;
               mm &= mm - 1u;
-              s_ent[r < r_split ? pa++ : pb++] = (uint16_t)((t << 5) | r);
+              s_ent[r < r_split ? pa++ : pb++] = (uint16_t)((cell << 5) | r);
             }
           }
           __syncthreads();
           for (int e = t; e < gT; e += kChunk) {
             const int ent = s_ent[e];
-            const int cell = ent >> 5, k = 32 * q + (ent & 31);
-            const float4 ch4 = s_mh[cell], cl4 = s_ml[cell], nh4 = s_eh[k], nl4 = s_el[k];
+            const int ec = ent >> 5, k = 32 * q + (ent & 31);
+            const float4 ch4 = s_mh[ec], cl4 = s_ml[ec], nh4 = s_eh[k], nl4 = s_el[k];
             const float ch[3] = {ch4.x, ch4.y, ch4.z}, cl[3] = {cl4.x, cl4.y, cl4.z};
             const float nh[3] = {nh4.x, nh4.y, nh4.z}, nl[3] = {nl4.x, nl4.y, nl4.z};
             const float wgt = pair_weight(ch, cl, nh, nl, pp.k_hi, pp.k_lo);
             const int64_t pos = ebase + erun + g0 + e;
-            ent_ck[pos] = (uint16_t)tile_off(cell, s_loc[k]);
+            ent_ck[pos] = (uint16_t)tile_off(ec, s_loc[k]);
             ent_w[pos] = wgt;
             s_w[e] = wgt;
           }
@@ -881,14 +907,16 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
 
-  // --- block windows (host) ------------------------------------------------
-  std::vector<int4> hwin(p->n_blocks);
+  // --- bin windows (host): of each block, and of each warp's 8 x 4 cell
+  // tile within it (the bins that can hold a sample within R of a cell of
+  // the rectangle; the block's window is the union of its warps') ------------
+  std::vector<int4> hwin((size_t)p->n_blocks * 5);
   const double eps_px = 1e-6;
   const double sR = std::sin(p->R_rad);
-  for (int64_t b = 0; b < p->n_blocks; ++b) {
-    int bbx = (int)(b % p->nbx_b), bby = (int)(b / p->nbx_b);
-    int ix0 = bbx * HG_BX, ix1 = std::min(ix0 + HG_BX - 1, g.nx - 1);
-    int iy0 = bby * HG_BY, iy1 = std::min(iy0 + HG_BY - 1, g.ny - 1);
+  auto window = [&](int ix0, int ix1, int iy0, int iy1) -> int4 {
+    ix1 = std::min(ix1, g.nx - 1);
+    iy1 = std::min(iy1, g.ny - 1);
+    if (ix0 > ix1 || iy0 > iy1) return make_int4(1, 0, 1, 0);  // no cells: empty
     double la0 = g.lat0_deg + ((double)iy0 - 0.5 * (g.ny - 1)) * g.dlat_deg;
     double la1 = g.lat0_deg + ((double)iy1 - 0.5 * (g.ny - 1)) * g.dlat_deg;
     double lmax = std::max(std::fabs(la0), std::fabs(la1));
@@ -901,11 +929,20 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     int by1 = std::min(p->nby - 1, (int)std::floor(qy_hi) / B);
     int bx0 = std::max(0, (int)std::floor(qx_lo) / B);
     int bx1 = std::min(p->nbx - 1, (int)std::floor(qx_hi) / B);
-    hwin[b] = make_int4(by0, by1, bx0, bx1);
+    return make_int4(by0, by1, bx0, bx1);
+  };
+  for (int64_t b = 0; b < p->n_blocks; ++b) {
+    int bbx = (int)(b % p->nbx_b), bby = (int)(b / p->nbx_b);
+    int ix0 = bbx * HG_BX, iy0 = bby * HG_BY;
+    hwin[b] = window(ix0, ix0 + HG_BX - 1, iy0, iy0 + HG_BY - 1);
+    for (int w = 0; w < 4; ++w) {
+      int wx0 = ix0 + (w & 1) * 8, wy0 = iy0 + (w >> 1) * 4;
+      hwin[p->n_blocks + 4 * b + w] = window(wx0, wx0 + 7, wy0, wy0 + 3);
+    }
   }
   int4* dwin;
-  HG_CUDA_TRY(sc.get(&dwin, p->n_blocks));
-  HG_CUDA_TRY(cudaMemcpyAsync(dwin, hwin.data(), sizeof(int4) * p->n_blocks,
+  HG_CUDA_TRY(sc.get(&dwin, p->n_blocks * 5));
+  HG_CUDA_TRY(cudaMemcpyAsync(dwin, hwin.data(), sizeof(int4) * p->n_blocks * 5,
                               cudaMemcpyHostToDevice, st));
 
   // --- a4 parameters -------------------------------------------------------
@@ -1004,7 +1041,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(cudaMemsetAsync(p->totals, 0, 2 * sizeof(unsigned long long), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * kWsumVariants * p->M, st));
   k_block_pairs<<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-      pp, dwin, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
+      pp, dwin, dwin + p->n_blocks, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
       p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
