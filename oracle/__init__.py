@@ -73,6 +73,12 @@ def _load():
     lib.og_bin_layout.restype = i64
     lib.og_bin_keys.argtypes = [i64, P, P, G, K, i32, P, P, P]
     lib.og_bin_keys.restype = i64
+    lib.og_hpx_ang2pix.argtypes = [i64, i64, P, P, P, P, P]
+    lib.og_hpx_centres.argtypes = [i64, P, P]
+    lib.og_hpx_layout.argtypes = [G, K, i64, P, P, P]
+    lib.og_hpx_layout.restype = i64
+    lib.og_hpx_keys.argtypes = [i64, P, P, G, K, i64, P, P, P]
+    lib.og_hpx_keys.restype = i64
     _lib = lib
     return lib
 
@@ -230,5 +236,56 @@ def bin_keys(lon, lat, geom, fwhm_deg, support=3.0, bin_cells=2):
     off = np.zeros(n_bins + 1, np.int32)
     _load().og_bin_keys(len(lon), _ptr(lon), _ptr(lat), ctypes.byref(_geom(geom)),
                         ctypes.byref(_kern(fwhm_deg, support)), int(bin_cells), _ptr(key),
+                        _ptr(perm), _ptr(off))
+    return key, perm, off
+
+
+# ---------------------------------------------------------------------------
+# HEALPix ring scheme (the paper's pixelisation, Sec. 4.1.1)
+# ---------------------------------------------------------------------------
+def hpx_ang2pix(nside, z, phi_deg):
+    """(ring 1..4N-1, pixel in ring, RING-scheme pixel index) of points given by
+    z = sin(lat) and phi in degrees."""
+    z, phi = _f64(z), _f64(phi_deg)
+    n = len(z)
+    ring = np.zeros(n, np.int64)
+    pix = np.zeros(n, np.int64)
+    ipix = np.zeros(n, np.int64)
+    _load().og_hpx_ang2pix(int(nside), n, _ptr(z), _ptr(phi), _ptr(ring), _ptr(pix), _ptr(ipix))
+    return ring, pix, ipix
+
+
+def hpx_centres(nside):
+    """(z, phi in degrees) of the 12 nside^2 pixel centres in RING order."""
+    n = 12 * int(nside) ** 2
+    z = np.zeros(n)
+    phi = np.zeros(n)
+    _load().og_hpx_centres(int(nside), _ptr(z), _ptr(phi))
+    return z, phi
+
+
+def hpx_layout(geom, fwhm_deg, support=3.0, nside=4096):
+    """(n_bins, ring0, table int64[n_rings, 4] = n_i, J0, cnt, half) of the HEALPix
+    variant's bins over the padded map."""
+    r0 = ctypes.c_int64(0)
+    nr = ctypes.c_int64(0)
+    G, K = ctypes.byref(_geom(geom)), ctypes.byref(_kern(fwhm_deg, support))
+    n_bins = _load().og_hpx_layout(G, K, int(nside), ctypes.byref(r0), ctypes.byref(nr), None)
+    if n_bins < 0:
+        raise ValueError("geometry reaches a pole or wraps onto itself")
+    tab = np.zeros((nr.value, 4), np.int64)
+    _load().og_hpx_layout(G, K, int(nside), ctypes.byref(r0), ctypes.byref(nr), _ptr(tab))
+    return int(n_bins), int(r0.value), tab
+
+
+def hpx_keys(lon, lat, geom, fwhm_deg, support=3.0, nside=4096):
+    """(key uint32[N], perm int32[N], bin_off int32[n_bins+1]) of the HEALPix variant."""
+    lon, lat = _f64(lon), _f64(lat)
+    n_bins, _, _ = hpx_layout(geom, fwhm_deg, support, nside)
+    key = np.zeros(len(lon), np.uint32)
+    perm = np.zeros(len(lon), np.int32)
+    off = np.zeros(n_bins + 1, np.int32)
+    _load().og_hpx_keys(len(lon), _ptr(lon), _ptr(lat), ctypes.byref(_geom(geom)),
+                        ctypes.byref(_kern(fwhm_deg, support)), int(nside), _ptr(key),
                         _ptr(perm), _ptr(off))
     return key, perm, off

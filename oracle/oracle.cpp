@@ -11,8 +11,10 @@
 //   * Algorithm 1 (Sec. 4.1.2): a sample contributes to a cell iff d <= R
 //     (inclusive).
 //   * Sec. 4.1.1: samples are given a spatial key, sorted by it, and a table of
-//     key ranges is built.  The GPU path replaces HEALPix pixels by bins of the
-//     padded target map; bin_key() below writes that key from its definition.
+//     key ranges is built.  The GPU path's default key is a bin of the padded
+//     target map (og_bin_keys, written from its definition); its HEALPix
+//     variant uses the paper's own RING-scheme pixels (og_hpx_*, written from
+//     Gorski et al. 2005's definitions) with a per-ring table of pixel ranges.
 // Readings where the paper is silent (kernel shape, distance formula, grid
 // geometry, empty cells) are listed in the design doc; in short:
 //   * w = exp(-d^2 / (2 sigma^2)), sigma = FWHM / sqrt(8 ln 2), R = support*sigma;
@@ -24,7 +26,9 @@
 // Parity pins: every function here is pinned by tests/test_oracle_pins.py
 // (brute force vs indexed, closed forms along a meridian, isolated-sample
 // kernel recovery by the chord formula, constant sky, linearity, convexity,
-// wrap and permutation invariance, point-source FWHM).
+// wrap and permutation invariance, point-source FWHM); the HEALPix functions by
+// tests/test_oracle_hpx.py (centre round trip, equal area, ring sizes, named
+// pixels, a layout that keeps every neighbour).
 //
 // Build: g++ -O2 -std=c++17 -fopenmp -ffp-contract=off -shared -fPIC.
 // -ffp-contract=off keeps the bin key arithmetic to single IEEE operations.
@@ -470,6 +474,227 @@ int64_t og_bin_keys(int64_t n, const double* lon, const double* lat, const og_ge
   for (int64_t b = 0; b <= n_bins; ++b) {
     bin_off[b] = (int32_t)acc;
     if (b < n_bins) acc += cnt[b];
+  }
+  return n_bins;
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// HEALPix, RING scheme (Gorski et al. 2005, ApJ 622, 759; the paper's
+// pixelisation, Sec. 4.1.1), written from the scheme's definitions.  With
+// N = nside: 12 N^2 equal-area pixels on 4N - 1 rings of constant latitude,
+// numbered from the north pole (i = 1 .. 4N-1).  Polar caps (|z| > 2/3,
+// z = sin(lat)): ring i < N holds 4i pixels (mirrored in the south, ring
+// 4N - i); the equatorial belt (rings N .. 3N) holds 4N pixels per ring.
+// Pixel j of a ring has its centre at phi = (j + s/2) * 360 / n_i degrees with
+// s = 1 in the caps and s = (i - N + 1) mod 2 in the belt.  Ring centres:
+// z = 1 - i^2 / (3 N^2) in the north cap, z = (4N - 2i) / (3N) in the belt.
+//
+// ang2pix (point -> ring, pixel in ring), from the same definitions: in the
+// belt the pixel edges are the lines t - 3z/4 = const and t + 3z/4 = const in
+// (t = phi / 90 deg, z), spaced 1/N, so the two edge indices jp = floor(N (1/2
+// + t) - 3Nz/4) and jm = floor(N (1/2 + t) + 3Nz/4) give the ring (from their
+// difference) and the pixel (from their sum).  In a cap, within each 90-degree
+// face the edges are tp * N sqrt(3 (1 - |z|)) = const and (1 - tp) * N
+// sqrt(3 (1 - |z|)) = const (tp = t mod 1); their indices give the ring from
+// the pole, and the pixel is floor(t * ring) (cap pixels are exact
+// 360 / n_i slices of their ring).
+// All arithmetic is single IEEE operations (no contraction): nside is a power
+// of two, so the products by N are exact.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HpxRing {
+  int64_t n;     // pixels in the ring
+  int64_t half;  // 1 if the centres are offset by half a pixel
+};
+
+HpxRing hpx_ring(int64_t N, int64_t i) {
+  if (i < N) return {4 * i, 1};
+  if (i > 3 * N) return {4 * (4 * N - i), 1};
+  int64_t s = (i - N + 1) & 1;
+  if (g_mutation == 7) s ^= 1;  // belt shift on the wrong rings
+  return {4 * N, s};
+}
+
+// (ring, pixel in ring) of a point: z = sin(lat), t = phi / 90 deg in [0, 4).
+void hpx_ang2pix(int64_t N, double z, double t, int64_t* ring, int64_t* pix) {
+  const double Nd = (double)N;
+  const double az = std::fabs(z);
+  if (az <= 2.0 / 3.0) {
+    double t1 = Nd * (0.5 + t);
+    double t2 = (Nd * 0.75) * z;
+    int64_t jp = (int64_t)std::floor(t1 - t2);
+    int64_t jm = (int64_t)std::floor(t1 + t2);
+    int64_t ir = N + 1 + jp - jm;  // 1 .. 2N+1 from the ring at z = 2/3
+    int64_t kshift = 1 - (ir & 1);
+    if (g_mutation == 9) kshift = ir & 1;  // pixel shift on the wrong rings
+    int64_t ip = (jp + jm - N + kshift + 1) / 2;
+    ip = ((ip % (4 * N)) + 4 * N) % (4 * N);
+    *ring = N - 1 + ir;
+    *pix = ip;
+    return;
+  }
+  double tp = t - std::floor(t);
+  double tmp = Nd * std::sqrt(3.0 * (1.0 - az));
+  if (g_mutation == 8) tmp = Nd * std::sqrt(3.0 * (1.0 + az));  // wrong cap edge spacing
+  int64_t jp = (int64_t)std::floor(tp * tmp);
+  int64_t jm = (int64_t)std::floor((1.0 - tp) * tmp);
+  int64_t ir = jp + jm + 1;  // ring from the nearest pole, 1 .. N
+  if (ir > N) ir = N;
+  int64_t ip = (int64_t)std::floor(t * (double)ir);
+  if (ip >= 4 * ir) ip = 4 * ir - 1;
+  *ring = z > 0.0 ? ir : 4 * N - ir;
+  *pix = ip;
+}
+
+// Continuous ring coordinate of z (ring centres at integers), for ring
+// ranges; a pixel of ring i lies between the centres of rings i - 1 and
+// i + 1, so the pixels holding points with z in [z0, z1] are in rings
+// floor(rho(z1)) - 1 .. ceil(rho(z0)) + 1.
+double hpx_rho(int64_t N, double z) {
+  const double Nd = (double)N;
+  if (z > 2.0 / 3.0) return Nd * std::sqrt(3.0 * (1.0 - z));
+  if (z < -2.0 / 3.0) return 4.0 * Nd - Nd * std::sqrt(3.0 * (1.0 + z));
+  return 2.0 * Nd - (3.0 * Nd * z) / 2.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void og_hpx_ang2pix(int64_t nside, int64_t n, const double* z, const double* phi_deg,
+                    int64_t* ring, int64_t* pix, int64_t* ipix) {
+  const int64_t N = nside;
+  for (int64_t k = 0; k < n; ++k) {
+    double a = phi_deg[k] - 360.0 * std::floor(phi_deg[k] / 360.0);
+    int64_t i, j;
+    hpx_ang2pix(N, z[k], a / 90.0, &i, &j);
+    // pixels before ring i: 2 i (i - 1) in the north cap, then 4N per ring
+    int64_t before;
+    if (i <= N) {
+      before = 2 * i * (i - 1);
+    } else if (i <= 3 * N) {
+      before = 2 * N * (N - 1) + (i - N) * 4 * N;
+    } else {
+      int64_t ii = 4 * N - i;  // south cap, counted from the south pole
+      before = 12 * N * N - 2 * ii * (ii + 1);
+    }
+    ring[k] = i;
+    pix[k] = j;
+    ipix[k] = before + j;
+  }
+}
+
+// Centres of all 12 nside^2 pixels in ring order (z and phi in degrees).
+void og_hpx_centres(int64_t nside, double* z, double* phi_deg) {
+  const int64_t N = nside;
+  const double Nd = (double)N;
+  int64_t k = 0;
+  for (int64_t i = 1; i <= 4 * N - 1; ++i) {
+    HpxRing r = hpx_ring(N, i);
+    double zi;
+    if (i < N)
+      zi = 1.0 - (double)(i * i) / (3.0 * Nd * Nd);
+    else if (i > 3 * N)
+      zi = -(1.0 - (double)((4 * N - i) * (4 * N - i)) / (3.0 * Nd * Nd));
+    else
+      zi = (double)(4 * N - 2 * i) / (3.0 * Nd);
+    for (int64_t j = 0; j < r.n; ++j, ++k) {
+      z[k] = zi;
+      phi_deg[k] = ((double)j + 0.5 * (double)r.half) * 360.0 / (double)r.n;
+    }
+  }
+}
+
+// Bin layout of the HEALPix variant (the LUT of Sec. 4.1.1 restricted to the
+// padded map): the rings whose pixels can hold a sample within R of a cell,
+// and in each ring the pixels whose centres lie within 2 pixels of the
+// map's RA range widened by Hmax (a pixel's RA extent is its centre +- half
+// a pixel).  table[4 r + 0..3] = n_i, J0 (first pixel, unwrapped), cnt,
+// half for ring ring0 + r; bins are numbered ring by ring, pixel (j - J0) mod
+// n_i inside a ring.  Returns n_bins (-1: the map reaches a pole or wraps).
+int64_t og_hpx_layout(const og_geom* g, const og_kernel* k, int64_t nside, int64_t* ring0,
+                      int64_t* n_rings, int64_t* table) {
+  Derived d = derive(k);
+  const int64_t N = nside;
+  double half_rows = 0.5 * (double)(g->ny - 1) * g->dlat;
+  double half_cols = 0.5 * (double)(g->nx - 1) * g->dlon;
+  double lat_lo = g->lat0 - half_rows, lat_hi = g->lat0 + half_rows;
+  double lat_max = std::max(std::fabs(lat_lo), std::fabs(lat_hi));
+  if (lat_max + d.R_deg >= 90.0) return -1;
+  double Hmax = std::asin(std::sin(d.R_rad) / std::cos(lat_max * kDeg)) / kDeg;
+  double pa = (g->lon0 - half_cols) - Hmax, pb = (g->lon0 + half_cols) + Hmax;
+  if (pb - pa >= 360.0) return -1;
+  double z0 = std::sin((lat_lo - d.R_deg) * kDeg), z1 = std::sin((lat_hi + d.R_deg) * kDeg);
+  int64_t i0 = std::max<int64_t>(1, (int64_t)std::floor(hpx_rho(N, z1)) - 2);
+  int64_t i1 = std::min<int64_t>(4 * N - 1, (int64_t)std::ceil(hpx_rho(N, z0)) + 2);
+  int64_t total = 0;
+  for (int64_t i = i0; i <= i1; ++i) {
+    HpxRing r = hpx_ring(N, i);
+    double ua = (pa * (double)r.n) / 360.0 - 0.5 * (double)r.half;
+    double ub = (pb * (double)r.n) / 360.0 - 0.5 * (double)r.half;
+    int64_t J0 = (int64_t)std::ceil(ua - 2.0), J1 = (int64_t)std::floor(ub + 2.0);
+    int64_t cnt = J1 - J0 + 1;
+    if (cnt >= r.n) {
+      cnt = r.n;
+      J0 = 0;
+    }
+    if (table) {
+      int64_t* e = table + 4 * (i - i0);
+      e[0] = r.n;
+      e[1] = J0;
+      e[2] = cnt;
+      e[3] = r.half;
+    }
+    total += cnt;
+  }
+  if (ring0) *ring0 = i0;
+  if (n_rings) *n_rings = i1 - i0 + 1;
+  return total;
+}
+
+// HEALPix-variant bin keys: z = sin(lat), phi = lon wrapped into [0, 360);
+// key = (bins of the rings before) + (j - J0) mod n_i, or n_bins when the
+// ring or pixel is outside the layout.  perm / bin_off as og_bin_keys.
+int64_t og_hpx_keys(int64_t n, const double* lon, const double* lat, const og_geom* g,
+                    const og_kernel* k, int64_t nside, uint32_t* key, int32_t* perm,
+                    int32_t* bin_off) {
+  int64_t i0 = 0, nr = 0;
+  int64_t n_bins = og_hpx_layout(g, k, nside, &i0, &nr, nullptr);
+  if (n_bins < 0) return -1;
+  std::vector<int64_t> tab(4 * nr), base(nr);
+  og_hpx_layout(g, k, nside, &i0, &nr, tab.data());
+  int64_t acc = 0;
+  for (int64_t r = 0; r < nr; ++r) {
+    base[r] = acc;
+    acc += tab[4 * r + 2];
+  }
+  for (int64_t q = 0; q < n; ++q) {
+    double z = std::sin(lat[q] * kDeg);
+    double a = lon[q] - 360.0 * std::floor(lon[q] / 360.0);
+    int64_t i, j;
+    hpx_ang2pix(nside, z, a / 90.0, &i, &j);
+    uint32_t kk = (uint32_t)n_bins;
+    if (i >= i0 && i < i0 + nr) {
+      const int64_t* e = tab.data() + 4 * (i - i0);
+      int64_t jr = ((j - e[1]) % e[0] + e[0]) % e[0];
+      if (jr < e[2]) kk = (uint32_t)(base[i - i0] + jr);
+    }
+    key[q] = kk;
+  }
+  std::vector<int32_t> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  std::memcpy(perm, idx.data(), sizeof(int32_t) * n);
+  std::vector<int64_t> cnt(n_bins + 1, 0);
+  for (int64_t q = 0; q < n; ++q) cnt[key[q]]++;
+  int64_t run = 0;
+  for (int64_t b = 0; b <= n_bins; ++b) {
+    bin_off[b] = (int32_t)run;
+    if (b < n_bins) run += cnt[b];
   }
   return n_bins;
 }
