@@ -392,8 +392,8 @@ def run_sim(args, H, torch, dev, rank):
     # the form (FP32 or split tensor core, both within the parity bound) and its launch
     # shape, chosen on the middle sample count outside the timed region
     tune = {}
-    flags = 0
-    if not args.no_tune:
+    flags = H.HEGRID_PLAN_HEALPIX(args.healpix) if args.healpix else 0
+    if not args.no_tune and not args.healpix:
         flags, bin_ms = H.hegrid_autotune_bins(nmid, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, sh)
         tune["bin_cells"] = flags
         tune["plan_ms_by_bin"] = [round(x, 3) for x in bin_ms]
@@ -511,7 +511,9 @@ def run_sim(args, H, torch, dev, rank):
                                    f"headline N={nmid}",
                        "N": nmid, "C": C, "M": M, "pairs": info["n_pairs"], "mode": mode_name,
                        "l2": "inputs larger than L2 (values 3.4 GB)",
-                       "tuning": tune, "forms": forms},
+                       "tuning": tune, "forms": forms,
+                       "binning": (f"HEALPix RING nside {1 << args.healpix}" if args.healpix
+                                   else "map bins")},
             "e2e": {"value": head["e2e_contrib_per_s"], "unit": UNIT,
                     "h2d_bytes_per_step": head["h2d_bytes"],
                     "d2h_bytes_per_step": head["d2h_bytes"], "ms_per_step": head["e2e_ms"],
@@ -541,6 +543,9 @@ def main():
                          "pinned host memory; sim: the paper's 60x20 deg simulated survey "
                          "at every sample count of Table 3, plan + grid, device and end to "
                          "end")
+    ap.add_argument("--healpix", type=int, default=0,
+                    help="bin the samples by HEALPix RING-scheme pixels at nside 2^K (the "
+                         "paper's own index) instead of map bins; 0: map bins")
     ap.add_argument("--sim-n", type=int, default=0,
                     help="sim workload: time this one sample count only")
     ap.add_argument("--sim-span", type=float, default=60.0,
@@ -613,9 +618,14 @@ def main():
     # ---- autotuning, outside the timed region: the plan's bin edge and the
     # grid step's launch shape, applied to every plan the steps create -----
     tune = {}
+    hpx_flag = H.HEGRID_PLAN_HEALPIX(args.healpix) if args.healpix else 0
     if not args.no_tune:
         t_tune = time.perf_counter()
-        bin_cells, bin_ms = H.hegrid_autotune_bins(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, sh)
+        if args.healpix:
+            bin_cells, bin_ms = hpx_flag, []
+        else:
+            bin_cells, bin_ms = H.hegrid_autotune_bins(N, lon_d, lat_d, 1, g, wl["fwhm_deg"],
+                                                       3.0, sh)
         p = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, bin_cells, sh)
         try:
             rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, C, mode, sh)
@@ -627,7 +637,7 @@ def main():
                 "grid_ms_by_shape": [[q["band"], q["seg"], round(q["ms"], 3)]
                                      for q in rep["points"]],
                 "seconds": round(time.perf_counter() - t_tune, 2)}
-    flags = tune.get("bin_cells", 0)
+    flags = tune.get("bin_cells", hpx_flag)
 
     def new_plan(lon, lat, on_device):
         p = H.hegrid_plan_create(N, lon, lat, on_device, g, wl["fwhm_deg"], 3.0, flags, sh)
@@ -788,6 +798,8 @@ def main():
                 "config": {"workload": workload_desc(N, C),
                            "mode": mode_name, "N": N, "C": C, "M": M, "pairs": P,
                            "l2": "inputs larger than L2 (values 8 GB)", "tuning": tune,
+                           "binning": (f"HEALPix RING nside {1 << args.healpix}" if args.healpix
+                                       else "map bins"),
                            "parallelism": f"replicas x{world}"},
                 "plan_ms": t_plan * 1e3, "grid_ms": t_grid * 1e3,
                 "forms": forms, "fp32_peak_tflops": fp32_peak, "err_vs_oracle": err,

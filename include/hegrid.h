@@ -73,8 +73,16 @@ typedef struct {
                                    chunks of values outside FP16's range) */
 #define HEGRID_MODE_TC_SPLIT 2u /* tcgen05 with hi/lo splits of values and weights */
 
-/* plan_create flags: bits 0-7 give the bin edge in map cells (0 = default 2). */
+/* plan_create flags: bits 0-7 give the bin edge in map cells (0 = default 2).
+ * Bits 8-12, HEGRID_PLAN_HEALPIX(k) with 1 <= k <= 13, select the paper's own
+ * pixelisation instead (Sec. 4.1.1): samples are keyed by their HEALPix
+ * RING-scheme pixel at nside = 2^k (Gorski et al. 2005) and found through a
+ * table of rings x pixel ranges over the padded map; the bin edge is then
+ * unused.  The pairs, weights and maps are the same as with map bins (only the
+ * candidate search differs); bin_off of hegrid_plan_export then indexes the
+ * table's pixels, ring by ring from the north. */
 #define HEGRID_PLAN_BIN_CELLS(b) ((uint32_t)(b) & 0xffu)
+#define HEGRID_PLAN_HEALPIX(k) (((uint32_t)(k) & 0x1fu) << 8)
 
 /*
  * hegrid_plan_create -- bin the samples and build the shared weights.
@@ -84,7 +92,8 @@ typedef struct {
  * lon_deg, lat_deg N coordinates in degrees (FP64); host memory if
  *                  coords_on_device == 0, device memory otherwise.  Not kept.
  * geom, kern       map geometry and kernel (host structs, copied).
- * flags            HEGRID_PLAN_BIN_CELLS(b) or 0.
+ * flags            HEGRID_PLAN_BIN_CELLS(b), HEGRID_PLAN_HEALPIX(k) or 0;
+ *                  other bits, or k > 13: INVALID_ARG.
  * stream           stream for every launch; the call synchronises it once to
  *                  learn the sizes of the pair ranges it reserves (upper
  *                  bounds from the binned samples); the rest is asynchronous.
@@ -284,7 +293,8 @@ const char *hegrid_last_error(void);
  * call before any stream capture.
  *
  * lon_deg, lat_deg  device FP64 [n_samples] (caller-owned).
- * geom, kern, flags as for hegrid_plan_create.
+ * geom, kern, flags as for hegrid_plan_create (map bins only: a
+ * HEGRID_PLAN_HEALPIX flag is INVALID_ARG here).
  * perm_out          device int32 [n_samples].
  * bin_off_out       device int32 [bin_off_capacity], capacity >= n_bins + 1.
  * n_bins_out        host; set to the number of bins even when the capacity is

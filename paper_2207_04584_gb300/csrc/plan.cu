@@ -53,30 +53,132 @@ struct KeyParams {
   uint32_t n_bins;
 };
 
+// ---------------------------------------------------------------------------
+// HEALPix variant of a2: the paper's own pixelisation (Sec. 4.1.1), RING
+// scheme (Gorski et al. 2005).  N = nside: 4N - 1 rings from the north pole;
+// ring i holds 4i pixels in the north cap (i < N), 4N in the belt (N <= i <=
+// 3N), 4(4N - i) in the south cap; pixel j's centre is at RA (j + s/2) 360 /
+// n_i with s = 1 in the caps and (i - N + 1) mod 2 in the belt.  The key of a
+// sample is its pixel's position in a table of the rings that reach the
+// padded map and, in each, the pixels whose centres lie within two pixels of
+// the map's RA range widened by the kernel (the ring -> pixel-range LUT of
+// Sec. 4.1.1).
+// ---------------------------------------------------------------------------
+struct HpxRing {
+  int32_t n;     // pixels in the ring
+  int32_t J0;    // first pixel of the ring's range (unwrapped; 0 for a whole ring)
+  int32_t cnt;   // pixels in the range
+  int32_t half;  // 1: pixel centres offset by half a pixel
+  int64_t base;  // first bin of the ring
+};
+
+struct HpxParams {
+  int32_t nside, ring0, n_rings;
+  uint32_t n_bins;
+  const HpxRing* rings;
+};
+
+// Ring (1 .. 4N-1) and pixel in ring of the point z = sin(lat), t = RA / 90
+// deg in [0, 4).  In the belt the pixel edges are the lines t -+ 3z/4 =
+// const spaced 1/N: the two edge indices give the ring (difference) and the
+// pixel (sum).  In a cap, within each 90-degree face, the edge indices along
+// tp = t mod 1 and 1 - tp scaled by N sqrt(3 (1 - |z|)) give the ring from the
+// pole, and cap pixels are exact 360 / n_i slices of their ring.  Single IEEE
+// operations (no contraction): the bin key is reproducible bit for bit.
+__device__ __forceinline__ void hpx_ang2pix(int32_t N, double z, double t, int32_t& ring,
+                                            int32_t& pix) {
+  const double Nd = (double)N;
+  const double az = fabs(z);
+  if (az <= 2.0 / 3.0) {
+    const double t1 = __dmul_rn(Nd, __dadd_rn(0.5, t));
+    const double t2 = __dmul_rn(__dmul_rn(Nd, 0.75), z);
+    const int64_t jp = (int64_t)floor(__dsub_rn(t1, t2));
+    const int64_t jm = (int64_t)floor(__dadd_rn(t1, t2));
+    const int64_t ir = N + 1 + jp - jm;  // 1 .. 2N+1 from the ring at z = 2/3
+    const int64_t kshift = 1 - (ir & 1);
+    int64_t ip = (jp + jm - N + kshift + 1) / 2;
+    ip = ((ip % (4 * (int64_t)N)) + 4 * (int64_t)N) % (4 * (int64_t)N);
+    ring = (int32_t)(N - 1 + ir);
+    pix = (int32_t)ip;
+    return;
+  }
+  const double tp = __dsub_rn(t, floor(t));
+  const double tmp = __dmul_rn(Nd, __dsqrt_rn(__dmul_rn(3.0, __dsub_rn(1.0, az))));
+  const int64_t jp = (int64_t)floor(__dmul_rn(tp, tmp));
+  const int64_t jm = (int64_t)floor(__dmul_rn(__dsub_rn(1.0, tp), tmp));
+  int64_t ir = jp + jm + 1;  // ring from the nearest pole, 1 .. N
+  if (ir > N) ir = N;
+  int64_t ip = (int64_t)floor(__dmul_rn(t, (double)ir));
+  if (ip >= 4 * ir) ip = 4 * ir - 1;
+  ring = (int32_t)(z > 0.0 ? ir : 4 * (int64_t)N - ir);
+  pix = (int32_t)ip;
+}
+
+// Continuous ring coordinate of z (ring centres at integers).  A pixel of
+// ring i lies between the centres of rings i - 1 and i + 1.
+__host__ __device__ __forceinline__ float hpx_rho_f(int32_t N, float z) {
+  const float Nf = (float)N;
+  if (z > 2.0f / 3.0f) return Nf * sqrtf(fmaxf(3.0f * (1.0f - z), 0.0f));
+  if (z < -2.0f / 3.0f) return 4.0f * Nf - Nf * sqrtf(fmaxf(3.0f * (1.0f + z), 0.0f));
+  return Nf * (2.0f - 1.5f * z);
+}
+
+// Bins [x, y] of ring e whose pixels can hold a point with RA in [pa, pb]
+// (degrees, unwrapped): pixels whose centres lie within two pixels of the
+// range (a pixel's RA extent is its centre +- half a pixel); x > y if none.
+__device__ __forceinline__ int2 hpx_span(const HpxRing& e, float pa, float pb) {
+  const float s = (float)e.n * (1.0f / 360.0f);
+  const float h = e.half ? 0.5f : 0.0f;
+  const int ja = (int)ceilf(pa * s - h - 2.0f), jb = (int)floorf(pb * s - h + 2.0f);
+  if (e.cnt == e.n) {  // the whole ring is in the table (J0 = 0)
+    if (jb - ja + 1 >= e.n) return make_int2(0, e.n - 1);
+    const int a = ((ja % e.n) + e.n) % e.n, b = a + (jb - ja);
+    return b >= e.n ? make_int2(0, e.n - 1) : make_int2(a, b);
+  }
+  return make_int2(max(ja - e.J0, 0), min(jb - e.J0, e.cnt - 1));
+}
+
+template <bool kHpx>
 __global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* __restrict__ lat,
-                       KeyParams kp, uint32_t* __restrict__ key, int32_t* __restrict__ idx,
-                       double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ uz) {
+                       KeyParams kp, HpxParams hp, uint32_t* __restrict__ key,
+                       int32_t* __restrict__ idx, double* __restrict__ ux,
+                       double* __restrict__ uy, double* __restrict__ uz) {
   int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   double lo = lon[n], la = lat[n];
-  // Bin key: single IEEE operations only (no contraction), so the key is
-  // reproducible bit for bit by any IEEE-754 implementation.
-  double a = __dsub_rn(lo, kp.lon0);
-  double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
-  a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
-  double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
-  double qy = __dadd_rn(__ddiv_rn(__dsub_rn(la, kp.lat0), kp.dlat), kp.cy);
-  double fx = floor(qx), fy = floor(qy);
-  uint32_t k = kp.n_bins;
-  if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
-    int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
-    k = (uint32_t)(by * kp.nbx + bx);
-  }
-  key[n] = k;
-  idx[n] = n;
   double sa, ca, sd, cd;
   sincos(lo * kDeg, &sa, &ca);
   sincos(la * kDeg, &sd, &cd);
+  uint32_t k;
+  if constexpr (kHpx) {
+    // RA wrapped into [0, 360), then the ring-scheme pixel of (sin(lat), RA)
+    const double a = __dsub_rn(lo, __dmul_rn(360.0, floor(__ddiv_rn(lo, 360.0))));
+    int32_t ring, pix;
+    hpx_ang2pix(hp.nside, sd, __ddiv_rn(a, 90.0), ring, pix);
+    k = hp.n_bins;
+    const int32_t r = ring - hp.ring0;
+    if (r >= 0 && r < hp.n_rings) {
+      const HpxRing e = hp.rings[r];
+      const int32_t jr = ((pix - e.J0) % e.n + e.n) % e.n;
+      if (jr < e.cnt) k = (uint32_t)(e.base + jr);
+    }
+  } else {
+    // Bin key: single IEEE operations only (no contraction), so the key is
+    // reproducible bit for bit by any IEEE-754 implementation.
+    double a = __dsub_rn(lo, kp.lon0);
+    double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
+    a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
+    double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
+    double qy = __dadd_rn(__ddiv_rn(__dsub_rn(la, kp.lat0), kp.dlat), kp.cy);
+    double fx = floor(qx), fy = floor(qy);
+    k = kp.n_bins;
+    if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
+      int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
+      k = (uint32_t)(by * kp.nbx + bx);
+    }
+  }
+  key[n] = k;
+  idx[n] = n;
   ux[n] = cd * ca;
   uy[n] = cd * sa;
   uz[n] = sd;
@@ -282,6 +384,44 @@ __global__ void k_gather_u(const int32_t* __restrict__ perm, int32_t N,
 // ---------------------------------------------------------------------------
 // a4 + a5: block-local neighbour search and weights.
 // ---------------------------------------------------------------------------
+// Candidate windows of a cell block and of each warp's 8 x 4 tile of it.
+// Padded-map bins: rows by0..by1, columns bx0..bx1 (int4 x, y, z, w).
+// HEALPix: rings r0..r1 and, in each, the bins of the pixels that can hold a
+// point with RA in [pa, pb] (hpx_span).
+struct HWin {
+  int32_t r0, r1;
+  float pa, pb;
+};
+
+struct WinArgs {
+  const int4* win;    // [n_blocks] padded-map bins
+  const int4* wwin;   // [4 n_blocks]
+  const HWin* hwin;   // [n_blocks] HEALPix
+  const HWin* hwwin;  // [4 n_blocks]
+  HpxParams hp;
+};
+
+// Sample range [lo, hi) of window row `row` (a bin row, or a ring).
+template <bool kHpx>
+__device__ __forceinline__ void window_row(const WinArgs& wa, const int32_t* __restrict__ bin_off,
+                                           int32_t nbx, int row, int4 w, HWin h, int32_t& lo,
+                                           int32_t& hi) {
+  if constexpr (kHpx) {
+    lo = hi = 0;
+    if (row < h.r0 || row > h.r1) return;
+    const HpxRing e = wa.hp.rings[row - wa.hp.ring0];
+    const int2 sp = hpx_span(e, h.pa, h.pb);
+    if (sp.x > sp.y) return;
+    lo = bin_off[e.base + sp.x];
+    hi = bin_off[e.base + sp.y + 1];
+  } else {
+    lo = hi = 0;
+    if (row < w.x || row > w.y) return;
+    lo = bin_off[(int64_t)row * nbx + w.z];
+    hi = bin_off[(int64_t)row * nbx + w.w + 1];
+  }
+}
+
 struct PairParams {
   int32_t nx, ny, nbx_b, nbx;  // map, cell blocks along RA, bins along RA
   int64_t M;
@@ -412,9 +552,9 @@ __host__ __device__ __forceinline__ int thread_cell(int t) {
   return ((w >> 1) * 4 + (lane >> 3)) * HG_BX + (w & 1) * 8 + (lane & 7);
 }
 
+template <bool kHpx>
 __global__ void __launch_bounds__(kChunk)
-    k_block_pairs(PairParams pp, const int4* __restrict__ win, const int4* __restrict__ wwin,
-                  const int32_t* __restrict__ bin_off,
+    k_block_pairs(PairParams pp, WinArgs wa, const int32_t* __restrict__ bin_off,
                   const int32_t* __restrict__ perm, const double* __restrict__ sx,
                   const double* __restrict__ sy, const double* __restrict__ sz,
                   const int64_t* __restrict__ cand_off, const int64_t* __restrict__ blk_pair_off,
@@ -450,7 +590,17 @@ __global__ void __launch_bounds__(kChunk)
   const int ix = bbx * HG_BX + (cell % HG_BX), iy = bby * HG_BY + (cell / HG_BX);
   const bool active = ix < pp.nx && iy < pp.ny;
   const int64_t m = (int64_t)iy * pp.nx + ix;
-  const int4 ww = wwin[4 * (int64_t)b + wid];  // this warp's bin window
+  // this block's and this warp's candidate windows
+  int4 wb = make_int4(1, 0, 0, 0), ww = make_int4(1, 0, 0, 0);
+  HWin hb = {1, 0, 0.0f, 0.0f}, hw = {1, 0, 0.0f, 0.0f};
+  if constexpr (kHpx) {
+    hb = wa.hwin[b];
+    hw = wa.hwwin[4 * (int64_t)b + wid];
+  } else {
+    wb = wa.win[b];
+    ww = wa.wwin[4 * (int64_t)b + wid];
+  }
+  const int row0 = kHpx ? hb.r0 : wb.x, row1 = kHpx ? hb.r1 : wb.y;
 
   // Block-local frame: origin at the unit vector of the block's centre.
   double bx0, by0, bz0;
@@ -481,10 +631,12 @@ __global__ void __launch_bounds__(kChunk)
   CSum wsv;         // FP32 weights, compensated
   float w16 = 0.0f;  // FP16-rounded weights x kTcWeightScale (plain sum: single form only)
   const int64_t cbase = cand_off[b], ebase = blk_pair_off[b], sbase = cbase / 32;
-  const int4 wb = win[b];  // by0, by1, bx0, bx1
-  for (int by = wb.x; by <= wb.y; ++by) {
-    const int32_t s_beg = bin_off[(int64_t)by * pp.nbx + wb.z];
-    const int32_t s_end = bin_off[(int64_t)by * pp.nbx + wb.w + 1];
+  for (int row = row0; row <= row1; ++row) {
+    // the row's samples (staged), and the part this warp tests: the bins of
+    // its own window, a contiguous sub-range
+    int32_t s_beg, s_end, w_lo, w_hi;
+    window_row<kHpx>(wa, bin_off, pp.nbx, row, wb, hb, s_beg, s_end);
+    window_row<kHpx>(wa, bin_off, pp.nbx, row, ww, hw, w_lo, w_hi);
     for (int32_t base = s_beg; base < s_end; base += kChunk) {
       const int32_t s = base + t;
       const int nk = min(kChunk, s_end - base);
@@ -503,13 +655,8 @@ __global__ void __launch_bounds__(kChunk)
         s_n[t] = perm[s];
       }
       if (t < kQ) s_umask[t] = 0u;
-      // The staged candidates this warp tests: those of the bins of its own
-      // window in this bin row (a contiguous range of the row's samples).
-      int k0 = 0, k1 = 0;
-      if (by >= ww.x && by <= ww.y) {
-        k0 = max(bin_off[(int64_t)by * pp.nbx + ww.z] - base, 0);
-        k1 = min(bin_off[(int64_t)by * pp.nbx + ww.w + 1] - base, nk);
-      }
+      // The staged candidates this warp tests (those of its own window).
+      const int k0 = max(w_lo - base, 0), k1 = min(w_hi - base, nk);
       __syncthreads();
 
       // Phase 1: membership of each staged candidate for this thread's cell.
@@ -691,13 +838,13 @@ __global__ void __launch_bounds__(kChunk)
 // within R of the cell, the same construction as the block window).
 struct BoundParams {
   int32_t nx, ny, nbx_b, nbx, nby, bin_cells, padx, pady;
-  double lat0, dlat, dlon, R_deg, sinR, eps_px;
+  double lon0, lat0, dlat, dlon, R_deg, sinR, eps_px;
 };
 
+template <bool kHpx>
 __global__ void __launch_bounds__(kChunk)
-    k_block_bounds(BoundParams bp, const int4* __restrict__ win,
-                   const int32_t* __restrict__ bin_off, int64_t* __restrict__ slots_ub,
-                   int64_t* __restrict__ pairs_ub) {
+    k_block_bounds(BoundParams bp, WinArgs wa, const int32_t* __restrict__ bin_off,
+                   int64_t* __restrict__ slots_ub, int64_t* __restrict__ pairs_ub) {
   __shared__ long long s_sum[kChunk / 32];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
@@ -707,15 +854,33 @@ __global__ void __launch_bounds__(kChunk)
   if (ix < bp.nx && iy < bp.ny) {
     const double lat = bp.lat0 + ((double)iy - 0.5 * (bp.ny - 1)) * bp.dlat;
     const double H = asin(bp.sinR / cos(fabs(lat) * kDeg)) / kDeg;
-    const double qy_lo = iy + bp.pady + 0.5 - bp.R_deg / bp.dlat - bp.eps_px;
-    const double qy_hi = iy + bp.pady + 0.5 + bp.R_deg / bp.dlat + bp.eps_px;
-    const double qx_lo = ix + bp.padx + 0.5 - H / bp.dlon - bp.eps_px;
-    const double qx_hi = ix + bp.padx + 0.5 + H / bp.dlon + bp.eps_px;
-    const int B = bp.bin_cells;
-    const int by0 = max(0, (int)floor(qy_lo) / B), by1 = min(bp.nby - 1, (int)floor(qy_hi) / B);
-    const int bx0 = max(0, (int)floor(qx_lo) / B), bx1 = min(bp.nbx - 1, (int)floor(qx_hi) / B);
-    for (int by = by0; by <= by1; ++by)
-      cnt += bin_off[(int64_t)by * bp.nbx + bx1 + 1] - bin_off[(int64_t)by * bp.nbx + bx0];
+    if constexpr (kHpx) {
+      // the cell's own window: rings that can hold a point within R of the
+      // cell, RA within H of it (FP32; the two-pixel and two-ring margins of
+      // the window cover its rounding)
+      const HpxParams& hp = wa.hp;
+      const double lon = bp.lon0 + ((double)ix - 0.5 * (bp.nx - 1)) * bp.dlon;
+      const float z_lo = sinf((float)((lat - bp.R_deg) * kDeg));
+      const float z_hi = sinf((float)((lat + bp.R_deg) * kDeg));
+      const int r0 = max(hp.ring0, (int)floorf(hpx_rho_f(hp.nside, z_hi)) - 2);
+      const int r1 = min(hp.ring0 + hp.n_rings - 1, (int)ceilf(hpx_rho_f(hp.nside, z_lo)) + 2);
+      const HWin h = {r0, r1, (float)(lon - H) - 1e-4f, (float)(lon + H) + 1e-4f};
+      for (int r = r0; r <= r1; ++r) {
+        int32_t lo, hi;
+        window_row<true>(wa, bin_off, bp.nbx, r, make_int4(0, 0, 0, 0), h, lo, hi);
+        cnt += hi - lo;
+      }
+    } else {
+      const double qy_lo = iy + bp.pady + 0.5 - bp.R_deg / bp.dlat - bp.eps_px;
+      const double qy_hi = iy + bp.pady + 0.5 + bp.R_deg / bp.dlat + bp.eps_px;
+      const double qx_lo = ix + bp.padx + 0.5 - H / bp.dlon - bp.eps_px;
+      const double qx_hi = ix + bp.padx + 0.5 + H / bp.dlon + bp.eps_px;
+      const int B = bp.bin_cells;
+      const int by0 = max(0, (int)floor(qy_lo) / B), by1 = min(bp.nby - 1, (int)floor(qy_hi) / B);
+      const int bx0 = max(0, (int)floor(qx_lo) / B), bx1 = min(bp.nbx - 1, (int)floor(qx_hi) / B);
+      for (int by = by0; by <= by1; ++by)
+        cnt += bin_off[(int64_t)by * bp.nbx + bx1 + 1] - bin_off[(int64_t)by * bp.nbx + bx0];
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -725,10 +890,18 @@ __global__ void __launch_bounds__(kChunk)
     long long tot = 0;
     for (int w = 0; w < kChunk / 32; ++w) tot += s_sum[w];
     pairs_ub[b] = tot;
-    const int4 wb = win[b];
     long long ws = 0;
-    for (int by = wb.x; by <= wb.y; ++by)
-      ws += bin_off[(int64_t)by * bp.nbx + wb.w + 1] - bin_off[(int64_t)by * bp.nbx + wb.z];
+    int4 wb = make_int4(1, 0, 0, 0);
+    HWin hb = {1, 0, 0.0f, 0.0f};
+    if constexpr (kHpx)
+      hb = wa.hwin[b];
+    else
+      wb = wa.win[b];
+    for (int row = kHpx ? hb.r0 : wb.x; row <= (kHpx ? hb.r1 : wb.y); ++row) {
+      int32_t lo, hi;
+      window_row<kHpx>(wa, bin_off, bp.nbx, row, wb, hb, lo, hi);
+      ws += hi - lo;
+    }
     slots_ub[b] = (ws + HG_KPAD - 1) / HG_KPAD * HG_KPAD + HG_KPAD;
   }
 }
@@ -799,8 +972,65 @@ struct Scratch {
   }
 };
 
+// HEALPix-variant layout (host, FP64): the rings that can hold a sample
+// within R of a cell (two rings of margin beyond the continuous ring
+// coordinate of the padded latitude band) and, in each, the pixels whose
+// centres lie within two pixels of the map's RA range widened by Hmax.
+// Single IEEE operations apart from products by powers of two, so that any
+// contraction leaves the table unchanged.
+double hpx_rho(int32_t N, double z) {
+  const double Nd = (double)N;
+  if (z > 2.0 / 3.0) return Nd * std::sqrt(3.0 * (1.0 - z));
+  if (z < -2.0 / 3.0) return 4.0 * Nd - Nd * std::sqrt(3.0 * (1.0 + z));
+  return 2.0 * Nd - (3.0 * Nd * z) / 2.0;
+}
+
+int64_t hpx_layout(const hegrid_map_geom& g, double R_deg, double R_rad, int32_t N,
+                   int32_t* ring0, std::vector<HpxRing>* rings) {
+  const double half_rows = 0.5 * (double)(g.ny - 1) * g.dlat_deg;
+  const double half_cols = 0.5 * (double)(g.nx - 1) * g.dlon_deg;
+  const double lat_lo = g.lat0_deg - half_rows, lat_hi = g.lat0_deg + half_rows;
+  const double lat_max = std::max(std::fabs(lat_lo), std::fabs(lat_hi));
+  const double Hmax = std::asin(std::sin(R_rad) / std::cos(lat_max * kDeg)) / kDeg;
+  const double pa = (g.lon0_deg - half_cols) - Hmax, pb = (g.lon0_deg + half_cols) + Hmax;
+  if (pb - pa >= 360.0) return -1;
+  const double z0 = std::sin((lat_lo - R_deg) * kDeg), z1 = std::sin((lat_hi + R_deg) * kDeg);
+  const int64_t i0 = std::max<int64_t>(1, (int64_t)std::floor(hpx_rho(N, z1)) - 2);
+  const int64_t i1 = std::min<int64_t>(4 * (int64_t)N - 1, (int64_t)std::ceil(hpx_rho(N, z0)) + 2);
+  int64_t total = 0;
+  rings->clear();
+  for (int64_t i = i0; i <= i1; ++i) {
+    HpxRing e;
+    if (i < N) {
+      e.n = (int32_t)(4 * i);
+      e.half = 1;
+    } else if (i > 3 * (int64_t)N) {
+      e.n = (int32_t)(4 * (4 * (int64_t)N - i));
+      e.half = 1;
+    } else {
+      e.n = 4 * N;
+      e.half = (int32_t)((i - N + 1) & 1);
+    }
+    const double ua = (pa * (double)e.n) / 360.0 - 0.5 * (double)e.half;
+    const double ub = (pb * (double)e.n) / 360.0 - 0.5 * (double)e.half;
+    int64_t J0 = (int64_t)std::ceil(ua - 2.0), J1 = (int64_t)std::floor(ub + 2.0);
+    int64_t cnt = J1 - J0 + 1;
+    if (cnt >= e.n) {
+      cnt = e.n;
+      J0 = 0;
+    }
+    e.J0 = (int32_t)J0;
+    e.cnt = (int32_t)cnt;
+    e.base = total;
+    total += cnt;
+    rings->push_back(e);
+  }
+  *ring0 = (int32_t)i0;
+  return total;
+}
+
 hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
-                                int coords_on_device, cudaStream_t st) {
+                         int coords_on_device, cudaStream_t st, int hpx_log2) {
   const int32_t N = (int32_t)p->N;
   const hegrid_map_geom& g = p->geom;
   Scratch sc(st);
@@ -823,6 +1053,18 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   p->nbx = (g.nx + 2 * p->padx + B - 1) / B;
   p->nby = (g.ny + 2 * p->pady + B - 1) / B;
   p->n_bins = (int64_t)p->nbx * p->nby;
+  // HEALPix variant: the bins are the table's ring pixels instead
+  const bool hpx = hpx_log2 > 0;
+  const int32_t nside = hpx ? (int32_t)1 << hpx_log2 : 0;
+  int32_t ring0 = 0;
+  std::vector<HpxRing> hrings;
+  if (hpx) {
+    p->n_bins = hpx_layout(g, p->R_deg, p->R_rad, nside, &ring0, &hrings);
+    if (p->n_bins < 0) {
+      set_error("padded map is wider than 360 degrees of RA");
+      return HEGRID_ERR_UNSUPPORTED;
+    }
+  }
   if (p->n_bins >= (int64_t)0x7fffffff) {
     set_error("too many bins");
     return HEGRID_ERR_UNSUPPORTED;
@@ -870,7 +1112,22 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   kp.bin_cells = B;
   kp.nbx = p->nbx;
   kp.n_bins = (uint32_t)p->n_bins;
-  k_prep<<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, key0, val0, ux, uy, uz);
+  HpxParams hp;
+  hp.nside = nside;
+  hp.ring0 = ring0;
+  hp.n_rings = (int32_t)hrings.size();
+  hp.n_bins = (uint32_t)p->n_bins;
+  hp.rings = nullptr;
+  if (hpx) {
+    HpxRing* dr;
+    HG_CUDA_TRY(sc.get(&dr, (int64_t)hrings.size()));
+    HG_CUDA_TRY(cudaMemcpyAsync(dr, hrings.data(), sizeof(HpxRing) * hrings.size(),
+                                cudaMemcpyHostToDevice, st));
+    hp.rings = dr;
+    k_prep<true><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0, ux, uy, uz);
+  } else {
+    k_prep<false><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0, ux, uy, uz);
+  }
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
 
@@ -944,6 +1201,54 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(sc.get(&dwin, p->n_blocks * 5));
   HG_CUDA_TRY(cudaMemcpyAsync(dwin, hwin.data(), sizeof(int4) * p->n_blocks * 5,
                               cudaMemcpyHostToDevice, st));
+  WinArgs wa;
+  wa.win = dwin;
+  wa.wwin = dwin + p->n_blocks;
+  wa.hwin = nullptr;
+  wa.hwwin = nullptr;
+  wa.hp = hp;
+  // HEALPix windows: the same rectangles as rings (two rings of margin beyond
+  // the continuous ring coordinate of their latitude band +- R) and an RA
+  // range (the cells' RA +- Hb, rounded outwards to FP32)
+  double hpx_pad_deg = 0.0;  // widest pixel of the table, for the FP32 error band
+  if (hpx) {
+    for (const HpxRing& e : hrings) hpx_pad_deg = std::max(hpx_pad_deg, 360.0 / e.n);
+    std::vector<HWin> hh((size_t)p->n_blocks * 5);
+    const int32_t r_last = ring0 + (int32_t)hrings.size() - 1;
+    auto hwindow = [&](int ix0, int ix1, int iy0, int iy1) -> HWin {
+      ix1 = std::min(ix1, g.nx - 1);
+      iy1 = std::min(iy1, g.ny - 1);
+      if (ix0 > ix1 || iy0 > iy1) return HWin{1, 0, 0.0f, 0.0f};  // no cells: empty
+      const double la0 = g.lat0_deg + ((double)iy0 - 0.5 * (g.ny - 1)) * g.dlat_deg;
+      const double la1 = g.lat0_deg + ((double)iy1 - 0.5 * (g.ny - 1)) * g.dlat_deg;
+      const double lmax = std::max(std::fabs(la0), std::fabs(la1));
+      const double Hb = std::asin(sR / std::cos(lmax * kDeg)) / kDeg;
+      const double pa = g.lon0_deg + ((double)ix0 - 0.5 * (g.nx - 1)) * g.dlon_deg - Hb;
+      const double pb = g.lon0_deg + ((double)ix1 - 0.5 * (g.nx - 1)) * g.dlon_deg + Hb;
+      const double zl = std::sin((la0 - p->R_deg) * kDeg), zh = std::sin((la1 + p->R_deg) * kDeg);
+      HWin h;
+      h.r0 = std::max(ring0, (int32_t)std::floor(hpx_rho(nside, zh)) - 2);
+      h.r1 = std::min(r_last, (int32_t)std::ceil(hpx_rho(nside, zl)) + 2);
+      h.pa = std::nextafter((float)pa, -INFINITY);
+      h.pb = std::nextafter((float)pb, INFINITY);
+      return h;
+    };
+    for (int64_t b = 0; b < p->n_blocks; ++b) {
+      int bbx = (int)(b % p->nbx_b), bby = (int)(b / p->nbx_b);
+      int ix0 = bbx * HG_BX, iy0 = bby * HG_BY;
+      hh[b] = hwindow(ix0, ix0 + HG_BX - 1, iy0, iy0 + HG_BY - 1);
+      for (int w = 0; w < 4; ++w) {
+        int wx0 = ix0 + (w & 1) * 8, wy0 = iy0 + (w >> 1) * 4;
+        hh[p->n_blocks + 4 * b + w] = hwindow(wx0, wx0 + 7, wy0, wy0 + 3);
+      }
+    }
+    HWin* dh;
+    HG_CUDA_TRY(sc.get(&dh, p->n_blocks * 5));
+    HG_CUDA_TRY(cudaMemcpyAsync(dh, hh.data(), sizeof(HWin) * p->n_blocks * 5,
+                                cudaMemcpyHostToDevice, st));
+    wa.hwin = dh;
+    wa.hwwin = dh + p->n_blocks;
+  }
 
   // --- a4 parameters -------------------------------------------------------
   PairParams pp;
@@ -966,6 +1271,10 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     double cR = 2.0 * s;
     double wx_cells = HG_BX + 2.0 * (Hmax / g.dlon_deg + 2.0 * B + 1.0);
     double wy_cells = HG_BY + 2.0 * (p->R_deg / g.dlat_deg + 2.0 * B + 1.0);
+    if (hpx) {  // windows widened by up to two pixels and three rings each side
+      wx_cells = HG_BX + 2.0 * ((Hmax + 4.0 * hpx_pad_deg) / g.dlon_deg + 1.0);
+      wy_cells = HG_BY + 2.0 * ((p->R_deg + 4.0 * hpx_pad_deg) / g.dlat_deg + 1.0);
+    }
     double E = 0.5 * std::sqrt(wx_cells * wx_cells * g.dlon_deg * g.dlon_deg +
                                wy_cells * wy_cells * g.dlat_deg * g.dlat_deg) * kDeg;
     double band = std::ldexp(8.0 + 8.0 * E / cR, -20);
@@ -991,14 +1300,19 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     bp.bin_cells = B;
     bp.padx = p->padx;
     bp.pady = p->pady;
+    bp.lon0 = g.lon0_deg;
     bp.lat0 = g.lat0_deg;
     bp.dlat = g.dlat_deg;
     bp.dlon = g.dlon_deg;
     bp.R_deg = p->R_deg;
     bp.sinR = sR;
     bp.eps_px = eps_px;
-    k_block_bounds<<<(unsigned)p->n_blocks, kChunk, 0, st>>>(bp, dwin, p->bin_off, slots_ub,
-                                                             pairs_ub);
+    if (hpx)
+      k_block_bounds<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(bp, wa, p->bin_off,
+                                                                     slots_ub, pairs_ub);
+    else
+      k_block_bounds<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(bp, wa, p->bin_off,
+                                                                      slots_ub, pairs_ub);
     count_launch();
   }
   int64_t* stmp64;
@@ -1040,9 +1354,14 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->totals, 0, 2 * sizeof(unsigned long long), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * kWsumVariants * p->M, st));
-  k_block_pairs<<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-      pp, dwin, dwin + p->n_blocks, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
-      p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
+  if (hpx)
+    k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
+        pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
+        p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
+  else
+    k_block_pairs<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
+        pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
+        p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   p->P = -1;  // exact totals: read on first use (plan_totals)
@@ -1080,6 +1399,9 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
                "map centre must be finite");
   HG_ARG_CHECK(kern->fwhm_deg > 0 && kern->support_sigmas > 0, "FWHM and support must be > 0");
   uint32_t bc = flags & 0xffu;
+  const int hpx_log2 = (int)((flags >> 8) & 0x1fu);
+  HG_ARG_CHECK((flags >> 13) == 0, "unknown plan_create flag bits");
+  HG_ARG_CHECK(hpx_log2 <= 13, "HEALPix nside above 2^13");
   hegrid_plan* p = new hegrid_plan();
   std::memset(p, 0, sizeof(*p));
   p->geom = *geom;
@@ -1097,7 +1419,8 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
     hg::set_error("kernel radius above 11 degrees is not supported");
     return HEGRID_ERR_UNSUPPORTED;
   }
-  hegrid_status s = hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream);
+  hegrid_status s =
+      hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream, hpx_log2);
   if (s != HEGRID_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     hg::free_plan_arrays(p, (cudaStream_t)stream);
@@ -1322,6 +1645,7 @@ extern "C" hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double
   HG_ARG_CHECK(std::isfinite(geom->lon0_deg) && std::isfinite(geom->lat0_deg),
                "map centre must be finite");
   HG_ARG_CHECK(kern->fwhm_deg > 0 && kern->support_sigmas > 0, "FWHM and support must be > 0");
+  HG_ARG_CHECK((flags >> 8) == 0, "only map bins (HEGRID_PLAN_BIN_CELLS) are sorted here");
   const int B = (flags & 0xffu) ? (int)(flags & 0xffu) : 2;
   const double sigma_deg = kern->fwhm_deg / std::sqrt(8.0 * std::log(2.0));
   const double R_deg = kern->support_sigmas * sigma_deg;

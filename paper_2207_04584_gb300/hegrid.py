@@ -26,6 +26,15 @@ STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT"
 HEGRID_F32, HEGRID_BF16, HEGRID_F16, HEGRID_BF16X2 = 0, 1, 2, 3
 HEGRID_MODE_FP32, HEGRID_MODE_TC, HEGRID_MODE_TC_SPLIT = 0, 1, 2
 
+
+def HEGRID_PLAN_BIN_CELLS(b):
+    return int(b) & 0xFF
+
+
+def HEGRID_PLAN_HEALPIX(k):
+    """plan_create flag: bin by HEALPix RING-scheme pixels at nside = 2**k."""
+    return (int(k) & 0x1F) << 8
+
 EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_grid_batched",
             "hegrid_batch_create", "hegrid_batch_launch", "hegrid_batch_destroy",
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
