@@ -435,8 +435,7 @@ def run_sim(args, H, torch, dev, rank):
     rows = []
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     launches = 0
-    sample_cells = np.sort(np.random.default_rng(7).choice(M, 256, replace=False))
-    sampled = None
+    # device-timed steps at every sample count (clocks sampled meanwhile)
     for n in sizes:
         ev = []
         l0 = H.hegrid_launch_count()
@@ -451,10 +450,21 @@ def run_sim(args, H, torch, dev, rank):
             if i >= args.warmup:
                 ev.append((e0, e1, e2))
         torch.cuda.synchronize()
-        launches = (H.hegrid_launch_count() - l0) / (args.warmup + args.steps)
+        if n == nmid:
+            launches = (H.hegrid_launch_count() - l0) / (args.warmup + args.steps)
         t_dev = statistics.mean(a.elapsed_time(c) for a, b, c in ev) / 1e3
         t_plan = statistics.mean(a.elapsed_time(b) for a, b, c in ev) / 1e3
         t_grid = statistics.mean(b.elapsed_time(c) for a, b, c in ev) / 1e3
+        rows.append({"N": n, "device_ms": t_dev * 1e3, "plan_ms": t_plan * 1e3,
+                     "grid_ms": t_grid * 1e3, "device_contrib_per_s": n * C / t_dev})
+    clk = clocks.stop()
+
+    # end to end at every sample count, after the sampler has stopped (its
+    # nvidia-smi queries contend with the host-side CUDA calls of these steps)
+    sample_cells = np.sort(np.random.default_rng(7).choice(M, 256, replace=False))
+    sampled = None
+    for r in rows:
+        n = r["N"]
 
         def e2e_step():
             pl = new_plan(n, lon_h[:n], lat_h[:n], 0)
@@ -474,14 +484,11 @@ def run_sim(args, H, torch, dev, rank):
             sampled = host_map[torch.from_numpy(sample_cells)].numpy().astype(np.float64)
         h2d = n * 16 + n * C * 4
         d2h = M * C * 4 + M * 4
-        rows.append({"N": n, "device_ms": t_dev * 1e3, "plan_ms": t_plan * 1e3,
-                     "grid_ms": t_grid * 1e3, "e2e_ms": t_e2e * 1e3,
-                     "e2e_contrib_per_s": n * C / t_e2e, "device_contrib_per_s": n * C / t_dev,
-                     "h2d_bytes": h2d, "d2h_bytes": d2h,
-                     "link_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
-                     "paper_v100_s": paper.get(n),
-                     "paper_v100_contrib_per_s": n * C / paper[n] if n in paper else None})
-    clk = clocks.stop()
+        r.update({"e2e_ms": t_e2e * 1e3, "e2e_contrib_per_s": n * C / t_e2e,
+                  "h2d_bytes": h2d, "d2h_bytes": d2h,
+                  "link_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
+                  "paper_v100_s": paper.get(n),
+                  "paper_v100_contrib_per_s": n * C / paper[n] if n in paper else None})
     head = next(r for r in rows if r["N"] == nmid)
     finite = bool(torch.isfinite(host_map[:: max(1, M // 4096)]).all())
 

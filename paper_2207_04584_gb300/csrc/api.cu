@@ -146,8 +146,10 @@ hegrid_status encode_rows_map(GridJob& j, int tile) {
   return HEGRID_OK;
 }
 
-// Launch all jobs of one kernel family, kMaxJobs per launch.
-hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStream_t s) {
+// Launch all jobs of one kernel family (one tensor-core channel tile),
+// kMaxJobs per launch.
+hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStream_t s,
+                            int tile = 0) {
   for (size_t base = 0; base < jobs.size(); base += kMaxJobs) {
     JobTable jt;
     std::memset(&jt, 0, sizeof(jt));
@@ -159,7 +161,7 @@ hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStrea
       items += jt.job[i].pv.n_blocks * jt.job[i].n_ctiles;
     }
     jt.n_items = items;
-    hegrid_status st = tc ? launch_grid_tc(jt, s) : launch_grid_f32(jt, s);
+    hegrid_status st = tc ? launch_grid_tc(jt, s, tile) : launch_grid_f32(jt, s);
     if (st != HEGRID_OK) return st;
   }
   return HEGRID_OK;
@@ -171,18 +173,22 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
                         cudaStream_t s, bool wait_ready = true) {
   HG_ARG_CHECK(n >= 0, "n must be >= 0");
   HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
-  std::vector<GridJob> f32, tc;
+  // tensor-core jobs grouped by channel tile (64, 128, 256): one launch each
+  std::vector<GridJob> f32, tc[3];
+  const int tiles[3] = {64, 128, 256};
   for (int i = 0; i < n; ++i) {
     hegrid_status st = check_args(plans[i], args[i]);
     if (st != HEGRID_OK) return st;
   }
   for (int i = 0; i < n; ++i) {
     if (wait_ready) HG_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ready, 0));
-    if (args[i].mode == HEGRID_MODE_FP32)
+    if (args[i].mode == HEGRID_MODE_FP32) {
       f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
-    else {
-      tc.push_back(make_job(plans[i], args[i], tc_channel_tile()));
-      hegrid_status st = encode_rows_map(tc.back(), tc_channel_tile());
+    } else {
+      const int tile = tc_channel_tile(args[i].n_channels);
+      std::vector<GridJob>& fam = tc[tile == 64 ? 0 : tile == 128 ? 1 : 2];
+      fam.push_back(make_job(plans[i], args[i], tile));
+      hegrid_status st = encode_rows_map(fam.back(), tile);
       if (st != HEGRID_OK) return st;
     }
   }
@@ -190,8 +196,9 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
     hegrid_status st = launch_family(f32, false, s);
     if (st != HEGRID_OK) return st;
   }
-  if (!tc.empty()) {
-    hegrid_status st = launch_family(tc, true, s);
+  for (int t = 0; t < 3; ++t) {
+    if (tc[t].empty()) continue;
+    hegrid_status st = launch_family(tc[t], true, s, tiles[t]);
     if (st != HEGRID_OK) return st;
   }
   return HEGRID_OK;
@@ -394,11 +401,15 @@ hegrid_status hegrid_grid_stream(hegrid_plan* plan, const void* const* host_chun
     }
     HG_STREAM_TRY(cudaEventRecord(ev_k[r], scomp));
     HG_STREAM_TRY(cudaStreamWaitEvent(sout, ev_k[r], 0));
-    HG_STREAM_TRY(cudaMemcpy2DAsync(host_map + (int64_t)k * chunk_channels,
-                                    ld_host_map * sizeof(float), dm[r],
-                                    chunk_channels * sizeof(float),
-                                    chunk_channels * sizeof(float), M, cudaMemcpyDeviceToHost,
-                                    sout));
+    if (ld_host_map == chunk_channels)  // the chunk's map rows are contiguous on the host
+      HG_STREAM_TRY(cudaMemcpyAsync(host_map + (int64_t)k * chunk_channels, dm[r], mbytes,
+                                    cudaMemcpyDeviceToHost, sout));
+    else
+      HG_STREAM_TRY(cudaMemcpy2DAsync(host_map + (int64_t)k * chunk_channels,
+                                      ld_host_map * sizeof(float), dm[r],
+                                      chunk_channels * sizeof(float),
+                                      chunk_channels * sizeof(float), M, cudaMemcpyDeviceToHost,
+                                      sout));
     if (k == 0 && host_weight)
       HG_STREAM_TRY(
           cudaMemcpyAsync(host_weight, dw, sizeof(float) * M, cudaMemcpyDeviceToHost, sout));

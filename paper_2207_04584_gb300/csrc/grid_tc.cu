@@ -60,18 +60,26 @@ constexpr int kTmaWarp = kProducerWarps + 1;
 constexpr int kDrainWarp0 = kProducerWarps + 2;  // 4 warps: drains and epilogue
 constexpr int kThreads = (kProducerWarps + 6) * 32;
 constexpr int kK = 32;                     // candidates per chunk (64-byte rows of 16-bit values)
-constexpr int kN = 256;                    // channels per tile
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kRawStages = 3;              // staged sample rows + weight entries ring
 constexpr int kEntCap = 1792;              // weight entries staged per chunk (more: read from global)
 constexpr int kEntStage = kEntCap - 8;     // entries copied (leaves room for 16-byte alignment)
-constexpr int kRawPitch = kN * 4;          // bytes per staged row slot (4-byte elements)
-constexpr uint32_t kTmemCols = 512;        // two 256-column accumulator regions
 constexpr int kDefaultSeg = 32;            // chunks per accumulation segment
 constexpr int kDefaultBand = 8;            // blocks per band of the work order
-constexpr int kHalves = kProducers / kN;   // producer threads per B row
-constexpr int kKT = kK / kHalves;          // samples of a row converted per thread
+// The channel tile kN (64, 128 or 256: the MMA's N) is a template parameter:
+// the launcher takes the narrowest tile that holds C (256 above it), so few
+// channels do not pay for 256-column tiles.  Per tile width: staged row slot
+// bytes (4-byte elements), TMEM columns (two accumulator regions), 16-byte
+// B-tile pieces per converting producer thread and converting threads.
+template <int kN>
+struct TcShape {
+  static constexpr int kRawPitch = kN * 4;
+  static constexpr uint32_t kTmemCols = 2 * kN;
+  static constexpr int kCPT = (kN * (kK / 8) + kProducers - 1) / kProducers;
+  static constexpr int kBThreads = kN * (kK / 8) / kCPT;
+  static constexpr int kKT = 8 * kCPT;  // samples of a B row converted per thread
+};
 
 // Where a staged chunk's weight entries are: e_lo is the global index of its
 // first entry, n the number of entries, ns how many were staged; entry i < ns
@@ -82,10 +90,11 @@ struct EntInfo {
   uint32_t ck_off, w_off;
 };
 
+template <int kN>
 struct __align__(512) TcSmem {
   uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
-  uint8_t raw[kRawStages][kK * kRawPitch];  // staged sample rows as stored
+  uint8_t raw[kRawStages][kK * TcShape<kN>::kRawPitch];  // staged sample rows as stored
   uint8_t eck[kRawStages][kEntCap * 2];     // staged entry tile offsets (16-byte aligned window)
   uint8_t ew[kRawStages][kEntCap * 4];      // staged entry weights (16-byte aligned window)
   EntInfo einfo[kRawStages];
@@ -180,16 +189,21 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uin
 // A tiles.  DT is the stored value type; SPLIT selects the hi/lo form.  rslot
 // rotates over the three range-reduction slots (see below).
 // Returns false if a bounded wait gave up.
-template <int DT, bool SPLIT>
-__device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_chunks,
+template <int DT, bool SPLIT, int kN>
+__device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, int n_chunks,
                                              int64_t c0, uint32_t& g, uint32_t& gr,
                                              uint32_t& rslot, int32_t* err) {
+  using Sh = TcShape<kN>;
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
   constexpr uint32_t kLoTile = kM * 64;  // A[s][1] follows A[s][0]
-  constexpr int kPitch = kWide ? kRawPitch : kRawPitch / 2;  // staged rows are packed
+  constexpr int kPitch = kWide ? Sh::kRawPitch : Sh::kRawPitch / 2;  // staged rows are packed
+  constexpr int kKT = Sh::kKT;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int row = tid % kN, kh = tid / kN;  // B row (channel c0 + row), half of the chunk
+  // B row (channel c0 + row) and first 16-byte piece (8 samples) this thread
+  // converts; threads from kBThreads on convert none (narrow tiles)
+  const int row = tid % kN, q0 = (tid / kN) * Sh::kCPT;
+  const bool has_b = Sh::kBThreads >= kProducers || tid < Sh::kBThreads;
   const PlanView& pv = J.pv;
   constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
   constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
@@ -203,8 +217,8 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
     // Channel column `row` of this thread's half of the staged rows (the
     // gathers fill channels past C with zeros).
     uint32_t x[kKT];
-    {
-      const uint32_t rb = smem_u32(S.raw[rs]) + kh * kKT * kPitch;
+    if (has_b) {
+      const uint32_t rb = smem_u32(S.raw[rs]) + q0 * 8 * kPitch;
 #pragma unroll
       for (int k = 0; k < kKT; ++k) {
         if (kWide)
@@ -212,6 +226,9 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
         else
           x[k] = ld_shared_u16(rb + k * kPitch + row * 2);
       }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kKT; ++k) x[k] = 0u;
     }
     // A tiles: zero (the scatter follows the barrier).  Independent of the
     // loads above and below, so their latencies overlap.
@@ -290,12 +307,12 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
     auto tiles = [&](auto fmt) {
       constexpr bool H16 = decltype(fmt)::value;
       // B tiles: row `row` holds the chunk's samples of channel c0 + row; this
-      // thread writes its half (16-byte chunks kh*kKT/8 ...).
-      {
+      // thread writes 16-byte pieces q0 .. q0 + kCPT - 1.
+      if (has_b) {
         const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
         for (int qq = 0; qq < kKT / 8; ++qq) {
-          const int q = kh * (kKT / 8) + qq;
+          const int q = q0 + qq;
           uint32_t h2[4], l2[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -364,12 +381,14 @@ __device__ __forceinline__ bool produce_item(TcSmem& S, const GridJob& J, int n_
   return true;
 }
 
+template <int kN>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
+  using Sh = TcShape<kN>;
   extern __shared__ unsigned char smem_raw[];
   // 64B-swizzled tiles need 512-byte alignment (the swizzle atom); offsetting
   // smem_raw (not an integer round trip) keeps the shared address space.
   const uint32_t pad = (512u - (smem_u32(smem_raw) & 511u)) & 511u;
-  TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw + pad);
+  TcSmem<kN>& S = *reinterpret_cast<TcSmem<kN>*>(smem_raw + pad);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* err = jt.job[0].pv.err_word;
 
@@ -394,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     fence_mbar_init();
   }
   if (warp == kMmaWarp) {
-    tmem_alloc(&S.tmem_base, kTmemCols);
+    tmem_alloc(&S.tmem_base, Sh::kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -507,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           const uint32_t r = q == 0 ? rT : rS;
           if (uses[r] > 0 && !mbar_wait(&S.regfree[r], (uses[r] - 1) & 1u, err)) bail = true;
           ++uses[r];
-          dcol = r * 256u;
+          dcol = r * (uint32_t)kN;
           tc_fence_after();
           if (bail) break;
         }
@@ -562,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       }
       const uint32_t lrow = (uint32_t)(quarter * 32) << 16;
       const uint32_t rT = n_tm & 1u, rS = rT ^ 1u;
-      const uint32_t tseg = tmem + lrow + rS * 256u, ttot = tmem + lrow + rT * 256u;
+      const uint32_t tseg = tmem + lrow + rS * (uint32_t)kN, ttot = tmem + lrow + rT * (uint32_t)kN;
       for (int q = 0; q < n_seg; ++q) {
         if (!mbar_wait(&S.segdone[n_sg & 1u], (n_sg >> 1) & 1u, err)) {
           bail = true;
@@ -638,17 +657,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       bool ok = true;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
         }
       }
       bail = !ok;
@@ -659,31 +678,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
+  if (warp == kMmaWarp) tmem_dealloc(tmem, Sh::kTmemCols);
+}
+
+template <int kN>
+hegrid_status launch_tile(const JobTable& jt, cudaStream_t s) {
+  static int sms = 0;
+  const size_t smem = sizeof(TcSmem<kN>) + 512;
+  if (!sms) {
+    int dev;
+    cudaGetDevice(&dev);
+    HG_CUDA_TRY(cudaFuncSetAttribute(k_grid_tc<kN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int64_t grid = std::min<int64_t>(jt.n_items, (int64_t)sms);
+  if (grid < 1) return HEGRID_OK;
+  k_grid_tc<kN><<<(unsigned)grid, kThreads, smem, s>>>(jt);
+  count_launch();
+  HG_CUDA_TRY(cudaGetLastError());
+  return HEGRID_OK;
 }
 
 }  // namespace
 
-int tc_channel_tile() { return kN; }
+int tc_channel_tile(int64_t C) { return C <= 64 ? 64 : C <= 128 ? 128 : 256; }
 int tc_default_band() { return kDefaultBand; }
 int tc_default_seg() { return kDefaultSeg; }
 
-hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s) {
-  static int sms = 0;
-  const size_t smem = sizeof(TcSmem) + 512;
-  if (!sms) {
-    int dev;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    HG_CUDA_TRY(cudaFuncSetAttribute(k_grid_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile) {
+  switch (tile) {
+    case 64: return launch_tile<64>(jt, s);
+    case 128: return launch_tile<128>(jt, s);
+    case 256: return launch_tile<256>(jt, s);
+    default:
+      set_error("unsupported tensor-core channel tile");
+      return HEGRID_ERR_UNSUPPORTED;
   }
-  int64_t grid = std::min<int64_t>(jt.n_items, (int64_t)sms);
-  if (grid < 1) return HEGRID_OK;
-  k_grid_tc<<<(unsigned)grid, kThreads, smem, s>>>(jt);
-  count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
-  return HEGRID_OK;
 }
 
 }  // namespace hg

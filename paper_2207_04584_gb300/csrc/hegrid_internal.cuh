@@ -174,9 +174,12 @@ struct JobTable {
 };
 
 hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s);
-hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s);
+// `tile`: the channel tile of every job in the table (tc_channel_tile(C)).
+hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile);
 int f32_channel_tile();
-int tc_channel_tile();
+// Tensor-core channel tile for C channels: the narrowest of 64, 128, 256
+// that holds C, else 256.
+int tc_channel_tile(int64_t C);
 int tc_default_band();
 int tc_default_seg();
 
