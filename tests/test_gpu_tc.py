@@ -85,8 +85,9 @@ def test_tc_f32_config1(H, mode, tol):
     assert np.max(np.abs(gw[has] / Wref[has] - 1.0)) <= wtol
 
 
-@pytest.mark.parametrize("C", [1, 5, 256, 300])
+@pytest.mark.parametrize("C", [1, 5, 64, 65, 100, 128, 129, 256, 257, 300])
 def test_tc_split_ragged_channels(H, C):
+    """Every channel-tile width (64, 128, 256) and its edges, ragged and full."""
     wl = _case(51, C=C)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
@@ -255,3 +256,43 @@ def test_tc_split_mixed_chunk_formats(H):
     h = hot_cell & (Wref >= 1e-3 * Wref.max())
     rel = np.abs(got[h] - ref[h]) / np.abs(ref[h]).max(axis=0)
     assert rel.max() <= 4 * 2.0 ** -17, rel.max()
+
+
+@pytest.mark.parametrize("C", [40, 120])
+def test_tc_narrow_tiles_bf16_and_batch(H, C):
+    """The 64- and 128-channel tiles on BF16 values, and a batch mixing all
+    three tile widths in one call (one launch per width)."""
+    wl = _case(61, C=C)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    vb = torch.from_numpy(wl["values"]).to(torch.bfloat16)
+    ld = (C + 7) // 8 * 8
+    vdev = torch.zeros((len(wl["lon"]), ld), dtype=torch.bfloat16, device="cuda")
+    vdev[:, :C] = vb.cuda()
+    up = vb.float().numpy()
+    plan = _plan(H, wl)
+    try:
+        got, _ = _run(H, plan, vdev, H.HEGRID_BF16, C, ld, M, H.HEGRID_MODE_TC_SPLIT)
+        # the same plan three times in one batch, at 40/120/300 channels
+        outs, args = [], []
+        for c in (40, 120, 300):
+            v = torch.from_numpy(_padded(np.tile(wl["values"], (1, 3))[:, :c], 4)[0]).cuda()
+            o = torch.full((M, c), -7.0, device="cuda")
+            outs.append((v, o, c))
+            args.append({"values": v, "dtype": H.HEGRID_F32, "n_channels": c,
+                         "ld_values": v.shape[1], "map_out": o, "ld_map": c, "weight_out": None,
+                         "mode": H.HEGRID_MODE_TC_SPLIT})
+        H.hegrid_grid_batched([plan] * 3, args, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
+    ref, Wref = ix.grid(np.ascontiguousarray(up))
+    err, _, _ = map_error(got, ref, Wref)
+    assert err <= TOL_SPLIT, err
+    tiled = np.ascontiguousarray(np.tile(wl["values"], (1, 3)))
+    ref3, W3 = ix.grid(tiled[:, :300])
+    for v, o, c in outs:
+        err, _, _ = map_error(o.cpu().numpy(), ref3[:, :c], W3)
+        assert err <= TOL_SPLIT, (c, err)
