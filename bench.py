@@ -103,14 +103,14 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "88f2e210d7b32c5fbc598c5e244526f85bf4a02708ed41e04d91e78235ac4e95",
-                  "bytes": 4 * (8.595589e9 + 0.366694e9),
+                  "sha256": "35bfd8ea01b88fddccafe8f0526cf69df2108333e3e782c86abb9099bf98abe0",
+                  "bytes": 4 * (8.637584e9 + 0.366337e9),
                   "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": "2c35cb9e609674acc6077367e87caf06eed27708fd449a37f45b2cde4f9e2e4a",
-                   "bytes": 4 * (6.387795e9 + 0.362828e9),
+                   "sha256": "653a0bac79a9102ef94587588b65e68adb334df48b3f130f135599a10a9d6176",
+                   "bytes": 4 * (6.276867e9 + 0.361791e9),
                    "capture": "profiles/k_grid_f32_fast_drift_c256.md (C=256 x 4)"},
 }
 

@@ -274,9 +274,10 @@ def test_tc_narrow_tiles_bf16_and_batch(H, C):
     try:
         got, _ = _run(H, plan, vdev, H.HEGRID_BF16, C, ld, M, H.HEGRID_MODE_TC_SPLIT)
         # the same plan three times in one batch, at 40/120/300 channels
+        wide = np.ascontiguousarray(np.tile(wl["values"], (1, -(-300 // C)))[:, :300])
         outs, args = [], []
         for c in (40, 120, 300):
-            v = torch.from_numpy(_padded(np.tile(wl["values"], (1, 3))[:, :c], 4)[0]).cuda()
+            v = torch.from_numpy(_padded(wide[:, :c], 4)[0]).cuda()
             o = torch.full((M, c), -7.0, device="cuda")
             outs.append((v, o, c))
             args.append({"values": v, "dtype": H.HEGRID_F32, "n_channels": c,
@@ -291,8 +292,7 @@ def test_tc_narrow_tiles_bf16_and_batch(H, C):
     ref, Wref = ix.grid(np.ascontiguousarray(up))
     err, _, _ = map_error(got, ref, Wref)
     assert err <= TOL_SPLIT, err
-    tiled = np.ascontiguousarray(np.tile(wl["values"], (1, 3)))
-    ref3, W3 = ix.grid(tiled[:, :300])
+    ref3, W3 = ix.grid(wide)
     for v, o, c in outs:
         err, _, _ = map_error(o.cpu().numpy(), ref3[:, :c], W3)
         assert err <= TOL_SPLIT, (c, err)
