@@ -532,6 +532,90 @@ def run_sim(args, H, torch, dev, rank):
             "gpu_launches": launches, "clocks": clk, "gen_s": t_gen}), flush=True)
 
 
+def run_sweep(args, H, torch, dev, rank):
+    """The paper's concurrency and reuse studies (Sec. 5.3: thread-block size with L1/L2 hit
+    rates, stream count, thread-level reuse), as reports of this design's knobs on the
+    FAST-like drift scan: the plan's bin edge and HEALPix nside (the index resolution), the
+    grid step's launch shapes (band width: which cell blocks run together and share sample
+    rows in L2; segment length), the streaming path's chunk count (copy/compute overlap),
+    and the reuse a 16x8 cell block gets from one staged candidate list."""
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    pos = W.config2(with_values=False, C=args.channels)
+    N = len(pos["lon"])
+    C = args.channels
+    host_vals = torch.empty((N, C), dtype=torch.float32, pin_memory=True)
+    wl = W.config2(C=C, out=host_vals.numpy())
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    fw = wl["fwhm_deg"]
+    lon_d = torch.from_numpy(wl["lon"]).to(dev)
+    lat_d = torch.from_numpy(wl["lat"]).to(dev)
+    vals_d = host_vals.to(dev)
+    torch.cuda.synchronize()
+
+    def plan_ms(flags, reps=3):
+        p = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, fw, 3.0, flags, sh)
+        H.hegrid_plan_destroy(p)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            p = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, fw, 3.0, flags, sh)
+            H.hegrid_plan_destroy(p)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # index resolution: map-bin edge 1..4 cells, HEALPix nside 2^10..2^13
+    index = [{"binning": f"map bins {B}", "plan_ms": plan_ms(B)} for B in (1, 2, 3, 4)]
+    index += [{"binning": f"HEALPix nside {1 << k}", "plan_ms": plan_ms(H.HEGRID_PLAN_HEALPIX(k))}
+              for k in (10, 11, 12, 13)]
+
+    # launch shapes of the grid step (both tensor-core forms and the FP32 form)
+    p = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, fw, 3.0, 0, sh)
+    info = H.hegrid_plan_info(p)
+    shapes = {}
+    try:
+        for nm, md in (("tc_split", H.HEGRID_MODE_TC_SPLIT), ("fp32", H.HEGRID_MODE_FP32)):
+            rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, C, md, sh)
+            shapes[nm] = [{"band": q["band"], "seg": q["seg"], "grid_ms": q["ms"]}
+                          for q in rep["points"]]
+        # streaming: the same plan, C channels from pinned host memory in k chunks
+        host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
+        streams = []
+        for k in (1, 2, 4, 8, 16):
+            if C % k:
+                continue
+            cc = C // k
+            chunks = [host_vals[:, i * cc:(i + 1) * cc].contiguous().pin_memory() for i in range(k)]
+            H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT, host_map, C,
+                                 None)
+            ts = time.perf_counter()
+            for _ in range(3):
+                H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT,
+                                     host_map, C, None)
+            streams.append({"chunks": k, "chunk_channels": cc,
+                            "ms": (time.perf_counter() - ts) / 3 * 1e3})
+            del chunks
+    finally:
+        H.hegrid_plan_destroy(p)
+    for r in streams:
+        r["speedup_vs_one_chunk"] = streams[0]["ms"] / r["ms"]
+    # reuse (the paper's gamma: cells sharing one contribution region): each candidate row
+    # staged for a 16x8 cell block serves all 128 of its cells
+    P, K = info["n_pairs"], info["n_cand"]
+    reuse = {"pairs": P, "candidate_slots": K, "blocks": info["n_blocks"],
+             "samples_needed_per_cell": P / M, "rows_staged_per_cell": K / M,
+             "reuse_factor": P / K, "dense_macs_per_useful": K * 128 / P}
+    if rank == 0:
+        print(json.dumps({
+            "report": "concurrency and reuse sweeps (Sec. 5.3 analogues)",
+            "config": {"workload": workload_desc(N, C), "N": N, "C": C, "M": M},
+            "index_resolution": index, "launch_shapes": shapes, "streaming": streams,
+            "reuse": reuse}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -544,7 +628,7 @@ def main():
     ap.add_argument("--channels", type=int, default=1024)
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch shapes, bin edge 2)")
-    ap.add_argument("--workload", default="config2", choices=["config2", "config4", "config5", "sim"],
+    ap.add_argument("--workload", default="config2", choices=["config2", "config4", "config5", "sim", "sweep"],
                     help="config2 (default): the bench line; config4: 64 uneven fields in one "
                          "graph-captured batch; config5: 65,536 BF16 channels streamed from "
                          "pinned host memory; sim: the paper's 60x20 deg simulated survey "
@@ -586,6 +670,8 @@ def main():
         return run_config5(args, H, torch, dev, rank)
     if args.workload == "sim":
         return run_sim(args, H, torch, dev, rank)
+    if args.workload == "sweep":
+        return run_sweep(args, H, torch, dev, rank)
 
     # ---- workload (config 2: FAST-like drift scan, FP32 values) ----------
     t_gen = time.perf_counter()
