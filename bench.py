@@ -581,6 +581,25 @@ def run_sweep(args, H, torch, dev, rank):
             rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, C, md, sh)
             shapes[nm] = [{"band": q["band"], "seg": q["seg"], "grid_ms": q["ms"]}
                           for q in rep["points"]]
+        # per-channel masking: two passes of the plan (values with non-finite entries
+        # zeroed, then the 0/1 mask) against one plain pass, 1% of the values NaN
+        vm = vals_d.clone()
+        vm.view(-1)[::97] = float("nan")
+        out = torch.empty((M, C), device=dev)
+        masked = {}
+        for nm, fn in (("grid_ms", lambda: H.hegrid_grid(p, vm, H.HEGRID_F32, C, C, out, C, None,
+                                                         H.HEGRID_MODE_TC_SPLIT, sh)),
+                       ("masked_grid_ms", lambda: H.hegrid_grid_masked(
+                           p, vm, H.HEGRID_F32, C, C, out, C, None, H.HEGRID_MODE_TC_SPLIT, sh))):
+            fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            masked[nm] = a.elapsed_time(b) / 3
+        del vm, out
         # streaming: the same plan, C channels from pinned host memory in k chunks
         host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
         streams = []
@@ -613,6 +632,7 @@ def run_sweep(args, H, torch, dev, rank):
             "report": "concurrency and reuse sweeps (Sec. 5.3 analogues)",
             "config": {"workload": workload_desc(N, C), "N": N, "C": C, "M": M},
             "index_resolution": index, "launch_shapes": shapes, "streaming": streams,
+            "masking": masked,
             "reuse": reuse}), flush=True)
 
 

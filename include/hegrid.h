@@ -180,6 +180,25 @@ hegrid_status hegrid_grid_stream(hegrid_plan *plan, const void *const *host_chun
                                  int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,
                                  float *host_map, int64_t ld_host_map, float *host_weight);
 
+/*
+ * hegrid_grid_masked -- Eq. 1 with per-channel masking: in channel c a sample
+ * whose value is not finite (NaN, +-Inf) contributes to neither sum, so the
+ * channel has its own weight sum W_c[m] = sum of w(m; s_n) over the samples
+ * with a finite value there, and map[m, c] = sum_n w v / W_c[m] (NaN where
+ * W_c[m] = 0).  The paper leaves invalid data implicit; this is the reading
+ * that keeps the shared weights: two grid passes of the same plan and form,
+ * one over the values with non-finite entries replaced by 0 and one over
+ * their 0/1 finiteness mask, each normalised by the plan's W, so that their
+ * ratio is S_c / W_c.  Arguments as for hegrid_grid; wc_out is device FP32
+ * [M x ld_map] receiving W_c, or NULL.  Scratch from the library's pool
+ * (freed before return, stream-ordered): the cleaned values (the input's
+ * size), the mask (N x C FP32 for HEGRID_MODE_FP32, BF16 otherwise) and an
+ * M x C FP32 map.  Asynchronous on `stream`.  Errors as for hegrid_grid.
+ */
+hegrid_status hegrid_grid_masked(hegrid_plan *plan, const void *values, hegrid_dtype dtype,
+                                 int64_t n_channels, int64_t ld_values, float *map_out,
+                                 int64_t ld_map, float *wc_out, uint32_t mode, void *stream);
+
 /* Plan sizes: pairs P, bins, cell blocks, candidate slots in use (padded to 64
  * per block), device bytes held.  Waits until the plan has been built. */
 hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_t *n_bins,

@@ -69,6 +69,7 @@ def _load():
     lib.og_index_count.restype = i64
     lib.og_index_fill.argtypes = [P, i64, P, P, P, P, P, ctypes.c_int]
     lib.og_index_grid.argtypes = [P, i64, P, i64, P, i64, P, P, ctypes.c_int]
+    lib.og_index_grid_masked.argtypes = [P, i64, P, i64, P, i64, P, P, ctypes.c_int]
     lib.og_bin_layout.argtypes = [G, K, i32, P]
     lib.og_bin_layout.restype = i64
     lib.og_bin_keys.argtypes = [i64, P, P, G, K, i32, P, P, P]
@@ -205,6 +206,19 @@ class Index:
         self._lib.og_index_fill(self._h, nc, _ptr(c), _ptr(off), _ptr(idx), _ptr(w), _ptr(h),
                                 nthreads)
         return (off, idx, w, h) if with_h else (off, idx, w)
+
+    def grid_masked(self, values, cells=None, nthreads=0):
+        """Eq. 1 with per-channel masking of non-finite values: (map [ncells, C], W_c
+        [ncells, C]) FP64."""
+        values = _values(values)
+        c, nc = self._cells(cells)
+        C = values.shape[1]
+        out = np.zeros((nc, C))
+        Wc = np.zeros((nc, C))
+        self._lib.og_index_grid_masked(self._h, nc, _ptr(c), C,
+                                       values.ctypes.data_as(ctypes.c_void_p),
+                                       values.strides[0] // 4, _ptr(out), _ptr(Wc), nthreads)
+        return out, Wc
 
     def grid(self, values, cells=None, nthreads=0):
         """Eq. 1 for ``cells``: (map [ncells, C] FP64, W [ncells] FP64)."""

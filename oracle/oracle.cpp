@@ -375,6 +375,15 @@ void og_index_fill(void* h, int64_t ncells, const int64_t* cells, const int64_t*
   }
 }
 
+// Eq. 1 with per-channel masking (NEXT-4's reading of the paper's "invalid
+// data" handling, which it leaves implicit): in channel c a sample whose value
+// is not finite contributes to neither sum, so each channel has its own
+// W_c[m] = sum of the weights of the cell's samples with a finite value;
+// map = S_c / W_c, NaN where W_c = 0.  map and Wc are [ncells x C] FP64.
+void og_index_grid_masked(void* h, int64_t ncells, const int64_t* cells, int64_t C,
+                          const float* values, int64_t ld, double* map, double* Wc,
+                          int nthreads);
+
 // Eq. 1 for ncells cells straight from the index (no stored CSR): map is
 // [ncells x C] FP64, W is [ncells].
 void og_index_grid(void* h, int64_t ncells, const int64_t* cells, int64_t C, const float* values,
@@ -400,6 +409,36 @@ void og_index_grid(void* h, int64_t ncells, const int64_t* cells, int64_t C, con
         double r = wsum > 0.0 ? s[c] / wsum : std::numeric_limits<double>::quiet_NaN();
         if (g_mutation == 6 && wsum > 0.0) r = s[c] / (double)nb.size();
         map[i * C + c] = r;
+      }
+    }
+  }
+}
+
+void og_index_grid_masked(void* h, int64_t ncells, const int64_t* cells, int64_t C,
+                          const float* values, int64_t ld, double* map, double* Wc,
+                          int nthreads) {
+  Index* ix = static_cast<Index*>(h);
+#pragma omp parallel num_threads(threads_or_default(nthreads))
+  {
+    std::vector<std::pair<int64_t, double>> nb;
+    std::vector<double> s(C), wc(C);
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t i = 0; i < ncells; ++i) {
+      neighbours_of(ix, cell_at(i, cells), &nb);
+      std::fill(s.begin(), s.end(), 0.0);
+      std::fill(wc.begin(), wc.end(), 0.0);
+      for (auto& e : nb) {
+        double w = weight_of(e.second, ix->d);
+        const float* v = values + e.first * ld;
+        for (int64_t c = 0; c < C; ++c) {
+          if (!std::isfinite(v[c]) && g_mutation != 10) continue;  // 10: mask ignored
+          wc[c] += w;
+          s[c] += w * (double)v[c];
+        }
+      }
+      for (int64_t c = 0; c < C; ++c) {
+        Wc[i * C + c] = wc[c];
+        map[i * C + c] = wc[c] > 0.0 ? s[c] / wc[c] : std::numeric_limits<double>::quiet_NaN();
       }
     }
   }

@@ -51,6 +51,63 @@ cudaError_t pad_rows(const void* src, void* dst, int64_t n_rows, int64_t row_byt
   return cudaGetLastError();
 }
 
+// Per-channel masking, step 1: values with every non-finite entry replaced by
+// 0 (same type and layout as the input) and the 0/1 finiteness mask (FP32 or
+// BF16, rows ld_mask apart).  A BF16 hi/lo pair is finite if both halves are.
+__device__ __forceinline__ bool bits_finite(uint32_t v, int dtype) {
+  switch (dtype) {
+    case HEGRID_F32: return (v & 0x7f800000u) != 0x7f800000u;
+    case HEGRID_BF16: return (v & 0x7f80u) != 0x7f80u;
+    case HEGRID_F16: return (v & 0x7c00u) != 0x7c00u;
+    default: return (v & 0x7f80u) != 0x7f80u && (v & 0x7f800000u) != 0x7f800000u;  // BF16X2
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mask_split(const void* __restrict__ values, int dtype,
+                                                    int64_t n_rows, int64_t C, int64_t ld,
+                                                    void* __restrict__ clean,
+                                                    void* __restrict__ mask, int mask_f32,
+                                                    int64_t ld_mask) {
+  const int64_t total = n_rows * C, stride = (int64_t)gridDim.x * blockDim.x;
+  const bool wide = dtype == HEGRID_F32 || dtype == HEGRID_BF16X2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t n = i / C, c = i - n * C;
+    const int64_t at = n * ld + c;
+    bool ok;
+    if (wide) {
+      const uint32_t v = static_cast<const uint32_t*>(values)[at];
+      ok = bits_finite(v, dtype);
+      static_cast<uint32_t*>(clean)[at] = ok ? v : 0u;
+    } else {
+      const uint16_t v = static_cast<const uint16_t*>(values)[at];
+      ok = bits_finite(v, dtype);
+      static_cast<uint16_t*>(clean)[at] = ok ? v : (uint16_t)0;
+    }
+    if (mask_f32)
+      static_cast<float*>(mask)[n * ld_mask + c] = ok ? 1.0f : 0.0f;
+    else
+      static_cast<uint16_t*>(mask)[n * ld_mask + c] = ok ? (uint16_t)0x3f80u : (uint16_t)0;
+  }
+}
+
+// Step 3: map = (S_c / W) / (W_c / W) = S_c / W_c, NaN where W_c = 0; the
+// per-channel weight sums W_c = (W_c / W) * W from the plan's W.
+__global__ void __launch_bounds__(256) k_mask_divide(float* __restrict__ map, int64_t ld_map,
+                                                     const float* __restrict__ q, int64_t M,
+                                                     int64_t C, const float* __restrict__ W,
+                                                     float* __restrict__ wc_out) {
+  const int64_t total = M * C, stride = (int64_t)gridDim.x * blockDim.x;
+  const float qnan = __int_as_float(0x7fc00000);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t m = i / C, c = i - m * C;
+    const float r = q[i];
+    const bool has = r > 0.0f;  // false for 0 and NaN (W = 0)
+    float* o = map + m * ld_map + c;
+    *o = has ? __fdiv_rn(*o, r) : qnan;
+    if (wc_out) wc_out[m * ld_map + c] = has ? __fmul_rn(r, W[m]) : 0.0f;
+  }
+}
+
 int elem_bytes(int dtype) {
   switch (dtype) {
     case HEGRID_F32: return 4;
@@ -228,6 +285,70 @@ hegrid_status hegrid_grid(hegrid_plan* plan, const void* values, hegrid_dtype dt
   a.mode = mode;
   hegrid_plan* p[1] = {plan};
   return hg::grid_many(1, p, &a, (cudaStream_t)stream);
+}
+
+hegrid_status hegrid_grid_masked(hegrid_plan* plan, const void* values, hegrid_dtype dtype,
+                                 int64_t n_channels, int64_t ld_values, float* map_out,
+                                 int64_t ld_map, float* wc_out, uint32_t mode, void* stream) {
+  hg::set_error("");
+  hegrid_grid_args a;
+  a.values = values;
+  a.dtype = dtype;
+  a.n_channels = n_channels;
+  a.ld_values = ld_values;
+  a.map_out = map_out;
+  a.ld_map = ld_map;
+  a.weight_out = nullptr;
+  a.mode = mode;
+  hegrid_status st = hg::check_args(plan, a);
+  if (st != HEGRID_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = plan->N, M = plan->M, C = n_channels;
+  const int eb = hg::elem_bytes((int)dtype);
+  const bool mask_f32 = mode == HEGRID_MODE_FP32;  // the FP32 form takes FP32 values only
+  const int64_t ldm = mask_f32 ? (C + 3) / 4 * 4 : (C + 7) / 8 * 8;
+  int dev = 0, n_sm = 0;
+  HG_CUDA_TRY(cudaGetDevice(&dev));
+  HG_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  void *clean = nullptr, *mask = nullptr;
+  float* q = nullptr;
+  auto release = [&]() {
+    if (clean) cudaFreeAsync(clean, s);
+    if (mask) cudaFreeAsync(mask, s);
+    if (q) cudaFreeAsync(q, s);
+  };
+  auto fail = [&](cudaError_t e, const char* what) {
+    hg::set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    release();
+    return e == cudaErrorMemoryAllocation ? HEGRID_ERR_OOM : HEGRID_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = hg::pool_alloc(&clean, (size_t)N * ld_values * eb, s)) != cudaSuccess)
+    return fail(e, "scratch values");
+  if ((e = hg::pool_alloc(&mask, (size_t)N * ldm * (mask_f32 ? 4 : 2), s)) != cudaSuccess)
+    return fail(e, "scratch mask");
+  if ((e = hg::pool_alloc((void**)&q, sizeof(float) * (size_t)M * C, s)) != cudaSuccess)
+    return fail(e, "scratch weight fractions");
+  const int blocks = std::max(1, n_sm) * 8;
+  hg::k_mask_split<<<blocks, 256, 0, s>>>(values, (int)dtype, N, C, ld_values, clean, mask,
+                                          mask_f32 ? 1 : 0, ldm);
+  hg::count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_mask_split");
+  // S_c / W and W_c / W: two passes of the same plan and form
+  st = hegrid_grid(plan, clean, dtype, C, ld_values, map_out, ld_map, nullptr, mode, stream);
+  if (st == HEGRID_OK)
+    st = hegrid_grid(plan, mask, mask_f32 ? HEGRID_F32 : HEGRID_BF16, C, ldm, q, C, nullptr,
+                     mode, stream);
+  if (st != HEGRID_OK) {
+    release();
+    return st;
+  }
+  const float* W = plan->wsum + (mode == HEGRID_MODE_TC ? plan->M : 0);
+  hg::k_mask_divide<<<blocks, 256, 0, s>>>(map_out, ld_map, q, M, C, W, wc_out);
+  hg::count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_mask_divide");
+  release();
+  return HEGRID_OK;
 }
 
 hegrid_status hegrid_grid_batched(int n, hegrid_plan* const* plans, const hegrid_grid_args* args,

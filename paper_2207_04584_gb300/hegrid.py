@@ -40,7 +40,7 @@ EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
             "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc",
             "hegrid_autotune", "hegrid_autotune_bins", "hegrid_plan_set_tuning",
-            "hegrid_fp32_peak"]
+            "hegrid_fp32_peak", "hegrid_grid_masked"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -95,6 +95,7 @@ def lib():
     L.hegrid_plan_create.argtypes = [PP, i64, P, P, c_int, ctypes.POINTER(hegrid_map_geom),
                                      ctypes.POINTER(hegrid_kernel), u32, P]
     L.hegrid_grid.argtypes = [P, P, c_int, i64, i64, P, i64, P, u32, P]
+    L.hegrid_grid_masked.argtypes = [P, P, c_int, i64, i64, P, i64, P, u32, P]
     L.hegrid_plan_destroy.argtypes = [P]
     L.hegrid_grid_batched.argtypes = [c_int, PP, ctypes.POINTER(hegrid_grid_args), P]
     L.hegrid_batch_create.argtypes = [PP, c_int, PP, ctypes.POINTER(hegrid_grid_args), P]
@@ -167,6 +168,15 @@ def hegrid_grid(plan, values, dtype, n_channels, ld_values, map_out, ld_map, wei
     return _check(lib().hegrid_grid(plan, _ptr(values), int(dtype), int(n_channels),
                                     int(ld_values), _ptr(map_out), int(ld_map), _ptr(weight_out),
                                     int(mode), _ptr(stream)), "hegrid_grid")
+
+
+def hegrid_grid_masked(plan, values, dtype, n_channels, ld_values, map_out, ld_map, wc_out,
+                       mode, stream=None):
+    """Eq. 1 with per-channel masking of non-finite values (see the header)."""
+    return _check(lib().hegrid_grid_masked(plan, _ptr(values), int(dtype), int(n_channels),
+                                           int(ld_values), _ptr(map_out), int(ld_map),
+                                           _ptr(wc_out), int(mode), _ptr(stream)),
+                  "hegrid_grid_masked")
 
 
 def hegrid_plan_destroy(plan):
