@@ -25,7 +25,8 @@ _lib = None
 class Geom(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
                 ("lon0", ctypes.c_double), ("lat0", ctypes.c_double),
-                ("dlon", ctypes.c_double), ("dlat", ctypes.c_double)]
+                ("dlon", ctypes.c_double), ("dlat", ctypes.c_double),
+                ("proj", ctypes.c_int32)]
 
 
 class Kernel(ctypes.Structure):
@@ -106,8 +107,9 @@ def _values(values):
 
 
 def _geom(g) -> Geom:
+    proj = {"": 0, "car": 0, "sfl": 1}[str(g.get("proj", "")).lower()]
     return Geom(int(g["nx"]), int(g["ny"]), float(g["lon0"]), float(g["lat0"]),
-                float(g["dlon"]), float(g["dlat"]))
+                float(g["dlon"]), float(g["dlat"]), proj)
 
 
 def _kern(fwhm_deg, support) -> Kernel:

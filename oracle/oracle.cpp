@@ -52,6 +52,7 @@ struct og_geom {
   int32_t nx, ny;
   double lon0, lat0;  // map centre, degrees
   double dlon, dlat;  // cell size, degrees
+  int32_t proj;       // 0: plain lon/lat grid; 1: Sanson-Flamsteed (x = (lon - lon0) cos lat)
 };
 
 struct og_kernel {
@@ -87,11 +88,36 @@ Derived derive(const og_kernel* k) {
   return d;
 }
 
+// Cell centres.  Plain grid: (lon0 + x, lat0 + y).  Sanson-Flamsteed (the
+// sinusoidal projection about lon0, a cos(lat)-scaled grid): the cell's
+// projected coordinates x = (lon - lon0) cos(lat), y = lat - lat0 lie on the
+// regular grid, so lon = lon0 + x / cos(lat).
+// x = (ix - (nx-1)/2) dlon, y = (iy - (ny-1)/2) dlat.
 void cell_centre(const og_geom* g, int64_t m, double* lon_deg, double* lat_deg) {
   int64_t ix = m % g->nx, iy = m / g->nx;
   if (g_mutation == 4) std::swap(ix, iy);  // transposed cell index
-  *lon_deg = g->lon0 + ((double)ix - 0.5 * (double)(g->nx - 1)) * g->dlon;
+  const double x = ((double)ix - 0.5 * (double)(g->nx - 1)) * g->dlon;
   *lat_deg = g->lat0 + ((double)iy - 0.5 * (double)(g->ny - 1)) * g->dlat;
+  double c = std::cos(*lat_deg * kDeg);
+  if (g_mutation == 11) c = 1.0;  // projection's cos(lat) dropped
+  *lon_deg = g->proj == 1 ? g->lon0 + x / c : g->lon0 + x;
+}
+
+// Sanson-Flamsteed: x-range (degrees of projected x) that holds every point
+// within R of the cell at RA offset a_c = lon_c - lon0 and latitude lat_c:
+// such points have |lon - lon_c| <= H = asin(sin R / cos lat_c) and lat in
+// [lat_c - R, lat_c + R], where cos(lat) lies between the cosines of the
+// ends (and 1 if the range holds lat = 0); x = (lon - lon0) cos(lat) is
+// extreme at those bounds.
+void sfl_xrange(double a_c, double lat_c, double R_deg, double sinR, double* x_lo,
+                double* x_hi) {
+  const double H = std::asin(sinR / std::cos(lat_c * kDeg)) / kDeg;
+  const double c1 = std::cos((lat_c - R_deg) * kDeg), c2 = std::cos((lat_c + R_deg) * kDeg);
+  const double cmin = std::min(c1, c2);
+  const double cmax = (lat_c - R_deg <= 0.0 && lat_c + R_deg >= 0.0) ? 1.0 : std::max(c1, c2);
+  const double a = a_c - H, b = a_c + H;
+  *x_lo = a >= 0.0 ? a * cmin : a * cmax;
+  *x_hi = b >= 0.0 ? b * cmax : b * cmin;
 }
 
 // Haversine of the great-circle separation (radians in, dimensionless out).
@@ -466,6 +492,22 @@ int64_t og_bin_layout(const og_geom* g, const og_kernel* k, int32_t bin_cells, i
   double Hmax = std::asin(std::sin(d.R_rad) / std::cos(lat_max * kDeg)) / kDeg;
   int32_t pad_y = (int32_t)std::ceil(d.R_deg / g->dlat) + 1;
   int32_t pad_x = (int32_t)std::ceil(Hmax / g->dlon) + 1;
+  if (g->proj == 1) {
+    // the widest x-excess of a first or last column cell's R-disc, over all rows
+    const double sinR = std::sin(d.R_rad), xe = 0.5 * (double)(g->nx - 1) * g->dlon;
+    double ex = 0.0;
+    for (int32_t iy = 0; iy < g->ny; ++iy) {
+      const double la = g->lat0 + ((double)iy - 0.5 * (double)(g->ny - 1)) * g->dlat;
+      const double ce = std::cos(la * kDeg);
+      double lo, hi;
+      sfl_xrange(-xe / ce, la, d.R_deg, sinR, &lo, &hi);
+      ex = std::max(ex, -xe - lo);
+      sfl_xrange(xe / ce, la, d.R_deg, sinR, &lo, &hi);
+      ex = std::max(ex, hi - xe);
+    }
+    pad_x = (int32_t)std::ceil(ex / g->dlon) + 1;
+    if ((double)(g->nx + 2 * pad_x) * g->dlon / std::cos(lat_max * kDeg) >= 360.0) return -1;
+  }
   if ((double)(g->nx + 2 * pad_x) * g->dlon >= 360.0) return -1;
   int32_t nbx = (g->nx + 2 * pad_x + bin_cells - 1) / bin_cells;
   int32_t nby = (g->ny + 2 * pad_y + bin_cells - 1) / bin_cells;
@@ -492,6 +534,7 @@ int64_t og_bin_keys(int64_t n, const double* lon, const double* lat, const og_ge
   for (int64_t j = 0; j < n; ++j) {
     double a = lon[j] - g->lon0;
     a = a - 360.0 * std::floor((a + 180.0) / 360.0);
+    if (g->proj == 1) a = a * std::cos(lat[j] * kDeg);  // projected x
     double qx = a / g->dlon + cx;
     double qy = (lat[j] - g->lat0) / g->dlat + cy;
     double fx = std::floor(qx), fy = std::floor(qy);
