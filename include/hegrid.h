@@ -83,6 +83,12 @@ typedef struct {
  * table's pixels, ring by ring from the north. */
 #define HEGRID_PLAN_BIN_CELLS(b) ((uint32_t)(b) & 0xffu)
 #define HEGRID_PLAN_HEALPIX(k) (((uint32_t)(k) & 0x1fu) << 8)
+/* Bit 13: the map is a Sanson-Flamsteed (sinusoidal, about lon0) grid instead
+ * of the plain lon/lat grid: cell (ix, iy) has lat = lat0 + (iy - (ny-1)/2)
+ * dlat and lon = lon0 + x / cos(lat), x = (ix - (nx-1)/2) dlon, so dlon is a
+ * length along the parallel and cells are equal in area.  Map bins only (not
+ * with HEGRID_PLAN_HEALPIX). */
+#define HEGRID_PLAN_SFL (1u << 13)
 
 /*
  * hegrid_plan_create -- bin the samples and build the shared weights.
@@ -92,8 +98,9 @@ typedef struct {
  * lon_deg, lat_deg N coordinates in degrees (FP64); host memory if
  *                  coords_on_device == 0, device memory otherwise.  Not kept.
  * geom, kern       map geometry and kernel (host structs, copied).
- * flags            HEGRID_PLAN_BIN_CELLS(b), HEGRID_PLAN_HEALPIX(k) or 0;
- *                  other bits, or k > 13: INVALID_ARG.
+ * flags            HEGRID_PLAN_BIN_CELLS(b) or HEGRID_PLAN_HEALPIX(k), optionally
+ *                  | HEGRID_PLAN_SFL (not with HEALPix), or 0; other bits,
+ *                  k > 13, or HEALPix with SFL: INVALID_ARG.
  * stream           stream for every launch; the call synchronises it once to
  *                  learn the sizes of the pair ranges it reserves (upper
  *                  bounds from the binned samples); the rest is asynchronous.

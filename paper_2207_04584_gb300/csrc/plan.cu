@@ -51,7 +51,27 @@ struct KeyParams {
   double lon0, lat0, dlon, dlat, cx, cy, wx, wy;
   int32_t bin_cells, nbx;
   uint32_t n_bins;
+  int32_t sfl;  // 1: Sanson-Flamsteed map, bins of projected x = (lon - lon0) cos(lat)
 };
+
+// Sanson-Flamsteed map (the sinusoidal projection about lon0): cells lie on
+// the regular grid of x = (lon - lon0) cos(lat), y = lat - lat0, so the cell
+// (ix, iy) has lon = lon0 + x / cos(lat).  The x-range that holds every point
+// within R of a cell at RA offset a_c and latitude lat_c: such points have
+// |lon - lon_c| <= H = asin(sin R / cos lat_c) and latitudes within R, where
+// cos(lat) lies between the cosines of the ends (1 if the range holds the
+// equator); x is extreme at those bounds.  (Same arithmetic on host and
+// device; the host's sizes the padding identically to the oracle.)
+__host__ __device__ __forceinline__ void sfl_xrange(double a_c, double lat_c, double R_deg,
+                                                    double sinR, double& x_lo, double& x_hi) {
+  const double H = asin(sinR / cos(lat_c * kDeg)) / kDeg;
+  const double c1 = cos((lat_c - R_deg) * kDeg), c2 = cos((lat_c + R_deg) * kDeg);
+  const double cmin = fmin(c1, c2);
+  const double cmax = (lat_c - R_deg <= 0.0 && lat_c + R_deg >= 0.0) ? 1.0 : fmax(c1, c2);
+  const double a = a_c - H, b = a_c + H;
+  x_lo = a >= 0.0 ? a * cmin : a * cmax;
+  x_hi = b >= 0.0 ? b * cmax : b * cmin;
+}
 
 // ---------------------------------------------------------------------------
 // HEALPix variant of a2: the paper's own pixelisation (Sec. 4.1.1), RING
@@ -168,6 +188,7 @@ __global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* 
     double a = __dsub_rn(lo, kp.lon0);
     double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
     a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
+    if (kp.sfl) a = __dmul_rn(a, cd);  // projected x
     double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
     double qy = __dadd_rn(__ddiv_rn(__dsub_rn(la, kp.lat0), kp.dlat), kp.cy);
     double fx = floor(qx), fy = floor(qy);
@@ -424,6 +445,7 @@ __device__ __forceinline__ void window_row(const WinArgs& wa, const int32_t* __r
 
 struct PairParams {
   int32_t nx, ny, nbx_b, nbx;  // map, cell blocks along RA, bins along RA
+  int32_t sfl;                 // 1: Sanson-Flamsteed cell centres
   int64_t M;
   double lon0, lat0, dlon, dlat;
   double cR2;       // chord^2 at R: 4 sin^2(R/2), FP64
@@ -604,12 +626,21 @@ __global__ void __launch_bounds__(kChunk)
 
   // Block-local frame: origin at the unit vector of the block's centre.
   double bx0, by0, bz0;
-  unit_vec(pp.lon0 + ((double)bbx * HG_BX + 0.5 * (HG_BX - 1) - 0.5 * (pp.nx - 1)) * pp.dlon,
-           pp.lat0 + ((double)bby * HG_BY + 0.5 * (HG_BY - 1) - 0.5 * (pp.ny - 1)) * pp.dlat,
-           bx0, by0, bz0);
+  // (x, lat) -> lon of a cell centre: x itself on the plain grid, x / cos(lat)
+  // on the Sanson-Flamsteed map
+  auto lon_of = [&](double x, double lat) {
+    return pp.sfl ? pp.lon0 + x / cos(lat * kDeg) : pp.lon0 + x;
+  };
+  {
+    const double xb = ((double)bbx * HG_BX + 0.5 * (HG_BX - 1) - 0.5 * (pp.nx - 1)) * pp.dlon;
+    const double lb = pp.lat0 + ((double)bby * HG_BY + 0.5 * (HG_BY - 1) - 0.5 * (pp.ny - 1)) * pp.dlat;
+    unit_vec(lon_of(xb, lb), lb, bx0, by0, bz0);
+  }
   double um[3];
-  unit_vec(pp.lon0 + ((double)ix - 0.5 * (pp.nx - 1)) * pp.dlon,
-           pp.lat0 + ((double)iy - 0.5 * (pp.ny - 1)) * pp.dlat, um[0], um[1], um[2]);
+  {
+    const double lc = pp.lat0 + ((double)iy - 0.5 * (pp.ny - 1)) * pp.dlat;
+    unit_vec(lon_of(((double)ix - 0.5 * (pp.nx - 1)) * pp.dlon, lc), lc, um[0], um[1], um[2]);
+  }
   float mh[3], ml[3];
   {
     double e[3] = {um[0] - bx0, um[1] - by0, um[2] - bz0};
@@ -838,6 +869,7 @@ __global__ void __launch_bounds__(kChunk)
 // within R of the cell, the same construction as the block window).
 struct BoundParams {
   int32_t nx, ny, nbx_b, nbx, nby, bin_cells, padx, pady;
+  int32_t sfl;  // 1: Sanson-Flamsteed map (x-ranges of sfl_xrange)
   double lon0, lat0, dlat, dlon, R_deg, sinR, eps_px;
 };
 
@@ -873,8 +905,15 @@ __global__ void __launch_bounds__(kChunk)
     } else {
       const double qy_lo = iy + bp.pady + 0.5 - bp.R_deg / bp.dlat - bp.eps_px;
       const double qy_hi = iy + bp.pady + 0.5 + bp.R_deg / bp.dlat + bp.eps_px;
-      const double qx_lo = ix + bp.padx + 0.5 - H / bp.dlon - bp.eps_px;
-      const double qx_hi = ix + bp.padx + 0.5 + H / bp.dlon + bp.eps_px;
+      double qx_lo = ix + bp.padx + 0.5 - H / bp.dlon - bp.eps_px;
+      double qx_hi = ix + bp.padx + 0.5 + H / bp.dlon + bp.eps_px;
+      if (bp.sfl) {
+        const double xc = ((double)ix - 0.5 * (bp.nx - 1)) * bp.dlon;
+        double xl, xh;
+        sfl_xrange(xc / cos(lat * kDeg), lat, bp.R_deg, bp.sinR, xl, xh);
+        qx_lo = xl / bp.dlon + 0.5 * bp.nx + bp.padx - bp.eps_px;
+        qx_hi = xh / bp.dlon + 0.5 * bp.nx + bp.padx + bp.eps_px;
+      }
       const int B = bp.bin_cells;
       const int by0 = max(0, (int)floor(qy_lo) / B), by1 = min(bp.nby - 1, (int)floor(qy_hi) / B);
       const int bx0 = max(0, (int)floor(qx_lo) / B), bx1 = min(bp.nbx - 1, (int)floor(qx_hi) / B);
@@ -1030,7 +1069,7 @@ int64_t hpx_layout(const hegrid_map_geom& g, double R_deg, double R_rad, int32_t
 }
 
 hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
-                         int coords_on_device, cudaStream_t st, int hpx_log2) {
+                         int coords_on_device, cudaStream_t st, int hpx_log2, bool sfl) {
   const int32_t N = (int32_t)p->N;
   const hegrid_map_geom& g = p->geom;
   Scratch sc(st);
@@ -1045,6 +1084,30 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   const double Hmax = std::asin(std::sin(p->R_rad) / std::cos(lat_max * kDeg)) / kDeg;
   p->pady = (int32_t)std::ceil(p->R_deg / g.dlat_deg) + 1;
   p->padx = (int32_t)std::ceil(Hmax / g.dlon_deg) + 1;
+  // Sanson-Flamsteed: per row, the x-ranges of the first and last cells'
+  // R-discs (sfl_xrange) set the padding (the oracle's arithmetic)
+  std::vector<double> row_ce;  // cos(lat) of each cell row (SFL)
+  const double sinR = std::sin(p->R_rad);
+  if (sfl) {
+    const double xe = 0.5 * (double)(g.nx - 1) * g.dlon_deg;
+    double ex = 0.0;
+    row_ce.resize(g.ny);
+    for (int32_t iy = 0; iy < g.ny; ++iy) {
+      const double la = g.lat0_deg + ((double)iy - 0.5 * (double)(g.ny - 1)) * g.dlat_deg;
+      const double ce = std::cos(la * kDeg);
+      row_ce[iy] = ce;
+      double lo, hi;
+      sfl_xrange(-xe / ce, la, p->R_deg, sinR, lo, hi);
+      ex = std::max(ex, -xe - lo);
+      sfl_xrange(xe / ce, la, p->R_deg, sinR, lo, hi);
+      ex = std::max(ex, hi - xe);
+    }
+    p->padx = (int32_t)std::ceil(ex / g.dlon_deg) + 1;
+    if ((double)(g.nx + 2 * p->padx) * g.dlon_deg / std::cos(lat_max * kDeg) >= 360.0) {
+      set_error("padded map is wider than 360 degrees of RA");
+      return HEGRID_ERR_UNSUPPORTED;
+    }
+  }
   if ((double)(g.nx + 2 * p->padx) * g.dlon_deg >= 360.0) {
     set_error("padded map is wider than 360 degrees of RA");
     return HEGRID_ERR_UNSUPPORTED;
@@ -1112,6 +1175,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   kp.bin_cells = B;
   kp.nbx = p->nbx;
   kp.n_bins = (uint32_t)p->n_bins;
+  kp.sfl = sfl ? 1 : 0;
   HpxParams hp;
   hp.nside = nside;
   hp.ring0 = ring0;
@@ -1170,6 +1234,23 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   std::vector<int4> hwin((size_t)p->n_blocks * 5);
   const double eps_px = 1e-6;
   const double sR = std::sin(p->R_rad);
+  // Sanson-Flamsteed: per cell row, the first and last columns' x-ranges
+  // (x_lo grows with the column, so a rectangle's extremes are at its ends)
+  std::vector<double> row_lat, row_H, row_cmin, row_cmax;
+  if (sfl) {
+    row_lat.resize(g.ny);
+    row_H.resize(g.ny);
+    row_cmin.resize(g.ny);
+    row_cmax.resize(g.ny);
+    for (int32_t iy = 0; iy < g.ny; ++iy) {
+      const double la = g.lat0_deg + ((double)iy - 0.5 * (double)(g.ny - 1)) * g.dlat_deg;
+      const double c1 = std::cos((la - p->R_deg) * kDeg), c2 = std::cos((la + p->R_deg) * kDeg);
+      row_lat[iy] = la;
+      row_H[iy] = std::asin(sR / row_ce[iy]) / kDeg;
+      row_cmin[iy] = std::min(c1, c2);
+      row_cmax[iy] = (la - p->R_deg <= 0.0 && la + p->R_deg >= 0.0) ? 1.0 : std::max(c1, c2);
+    }
+  }
   auto window = [&](int ix0, int ix1, int iy0, int iy1) -> int4 {
     ix1 = std::min(ix1, g.nx - 1);
     iy1 = std::min(iy1, g.ny - 1);
@@ -1182,6 +1263,18 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     double qy_hi = iy1 + p->pady + 0.5 + p->R_deg / g.dlat_deg + eps_px;
     double qx_lo = ix0 + p->padx + 0.5 - Hb / g.dlon_deg - eps_px;
     double qx_hi = ix1 + p->padx + 0.5 + Hb / g.dlon_deg + eps_px;
+    if (sfl) {
+      const double x0 = ((double)ix0 - 0.5 * (g.nx - 1)) * g.dlon_deg;
+      const double x1 = ((double)ix1 - 0.5 * (g.nx - 1)) * g.dlon_deg;
+      double xl = INFINITY, xh = -INFINITY;
+      for (int iy = iy0; iy <= iy1; ++iy) {
+        const double a = x0 / row_ce[iy] - row_H[iy], b = x1 / row_ce[iy] + row_H[iy];
+        xl = std::min(xl, a >= 0.0 ? a * row_cmin[iy] : a * row_cmax[iy]);
+        xh = std::max(xh, b >= 0.0 ? b * row_cmax[iy] : b * row_cmin[iy]);
+      }
+      qx_lo = xl / g.dlon_deg + 0.5 * g.nx + p->padx - eps_px;
+      qx_hi = xh / g.dlon_deg + 0.5 * g.nx + p->padx + eps_px;
+    }
     int by0 = std::max(0, (int)std::floor(qy_lo) / B);
     int by1 = std::min(p->nby - 1, (int)std::floor(qy_hi) / B);
     int bx0 = std::max(0, (int)std::floor(qx_lo) / B);
@@ -1257,6 +1350,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   pp.M = p->M;
   pp.nbx_b = p->nbx_b;
   pp.nbx = p->nbx;
+  pp.sfl = sfl ? 1 : 0;
   pp.lon0 = g.lon0_deg;
   pp.lat0 = g.lat0_deg;
   pp.dlon = g.dlon_deg;
@@ -1271,6 +1365,8 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     double cR = 2.0 * s;
     double wx_cells = HG_BX + 2.0 * (Hmax / g.dlon_deg + 2.0 * B + 1.0);
     double wy_cells = HG_BY + 2.0 * (p->R_deg / g.dlat_deg + 2.0 * B + 1.0);
+    if (sfl)  // the padding bounds the sheared discs' x-excess
+      wx_cells = HG_BX + 2.0 * (p->padx + 2.0 * B + 1.0);
     if (hpx) {  // windows widened by up to two pixels and three rings each side
       wx_cells = HG_BX + 2.0 * ((Hmax + 4.0 * hpx_pad_deg) / g.dlon_deg + 1.0);
       wy_cells = HG_BY + 2.0 * ((p->R_deg + 4.0 * hpx_pad_deg) / g.dlat_deg + 1.0);
@@ -1300,6 +1396,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     bp.bin_cells = B;
     bp.padx = p->padx;
     bp.pady = p->pady;
+    bp.sfl = sfl ? 1 : 0;
     bp.lon0 = g.lon0_deg;
     bp.lat0 = g.lat0_deg;
     bp.dlat = g.dlat_deg;
@@ -1400,8 +1497,10 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
   HG_ARG_CHECK(kern->fwhm_deg > 0 && kern->support_sigmas > 0, "FWHM and support must be > 0");
   uint32_t bc = flags & 0xffu;
   const int hpx_log2 = (int)((flags >> 8) & 0x1fu);
-  HG_ARG_CHECK((flags >> 13) == 0, "unknown plan_create flag bits");
+  const bool sfl = (flags & HEGRID_PLAN_SFL) != 0;
+  HG_ARG_CHECK((flags >> 14) == 0, "unknown plan_create flag bits");
   HG_ARG_CHECK(hpx_log2 <= 13, "HEALPix nside above 2^13");
+  HG_ARG_CHECK(!(sfl && hpx_log2 > 0), "HEALPix binning works on the plain grid only");
   hegrid_plan* p = new hegrid_plan();
   std::memset(p, 0, sizeof(*p));
   p->geom = *geom;
@@ -1420,7 +1519,7 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
     return HEGRID_ERR_UNSUPPORTED;
   }
   hegrid_status s =
-      hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream, hpx_log2);
+      hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream, hpx_log2, sfl);
   if (s != HEGRID_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     hg::free_plan_arrays(p, (cudaStream_t)stream);

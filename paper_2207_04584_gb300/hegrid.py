@@ -31,6 +31,9 @@ def HEGRID_PLAN_BIN_CELLS(b):
     return int(b) & 0xFF
 
 
+HEGRID_PLAN_SFL = 1 << 13  # plan_create flag: Sanson-Flamsteed map geometry
+
+
 def HEGRID_PLAN_HEALPIX(k):
     """plan_create flag: bin by HEALPix RING-scheme pixels at nside = 2**k."""
     return (int(k) & 0x1F) << 8

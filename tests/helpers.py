@@ -29,11 +29,15 @@ def haversine_h(lon_m, lat_m, lon_n, lat_n):
 
 
 def centres(geom, cells=None):
+    """Cell centres (used only to classify tie pairs): the plain grid, or the
+    Sanson-Flamsteed grid (lon = lon0 + x / cos(lat)) for geom["proj"] == "sfl"."""
     m = np.arange(geom["nx"] * geom["ny"]) if cells is None else np.asarray(cells)
     ix, iy = m % geom["nx"], m // geom["nx"]
-    lon = geom["lon0"] + (ix - 0.5 * (geom["nx"] - 1)) * geom["dlon"]
+    x = (ix - 0.5 * (geom["nx"] - 1)) * geom["dlon"]
     lat = geom["lat0"] + (iy - 0.5 * (geom["ny"] - 1)) * geom["dlat"]
-    return lon, lat
+    if str(geom.get("proj", "")).lower() == "sfl":
+        return geom["lon0"] + x / np.cos(np.radians(lat)), lat
+    return geom["lon0"] + x, lat
 
 
 def csr_diff_in_tie_band(off_a, idx_a, off_b, idx_b, lon, lat, geom, hR, cells=None, tau=1e-9):
