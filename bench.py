@@ -571,6 +571,9 @@ def run_sweep(args, H, torch, dev, rank):
     index = [{"binning": f"map bins {B}", "plan_ms": plan_ms(B)} for B in (1, 2, 3, 4)]
     index += [{"binning": f"HEALPix nside {1 << k}", "plan_ms": plan_ms(H.HEGRID_PLAN_HEALPIX(k))}
               for k in (10, 11, 12, 13)]
+    # the same map as a Sanson-Flamsteed grid (cells dlon apart along each parallel)
+    index.append({"binning": "map bins 2, Sanson-Flamsteed map",
+                  "plan_ms": plan_ms(H.HEGRID_PLAN_SFL)})
 
     # launch shapes of the grid step (both tensor-core forms and the FP32 form)
     p = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, fw, 3.0, 0, sh)
@@ -581,6 +584,23 @@ def run_sweep(args, H, torch, dev, rank):
             rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, C, md, sh)
             shapes[nm] = [{"band": q["band"], "seg": q["seg"], "grid_ms": q["ms"]}
                           for q in rep["points"]]
+        # streaming: the same plan, C channels from pinned host memory in k chunks
+        host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
+        streams = []
+        for k in (1, 2, 4, 8, 16):
+            if C % k:
+                continue
+            cc = C // k
+            chunks = [host_vals[:, i * cc:(i + 1) * cc].contiguous().pin_memory() for i in range(k)]
+            H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT, host_map, C,
+                                 None)
+            ts = time.perf_counter()
+            for _ in range(3):
+                H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT,
+                                     host_map, C, None)
+            streams.append({"chunks": k, "chunk_channels": cc,
+                            "ms": (time.perf_counter() - ts) / 3 * 1e3})
+            del chunks
         # per-channel masking: two passes of the plan (values with non-finite entries
         # zeroed, then the 0/1 mask) against one plain pass, 1% of the values NaN
         vm = vals_d.clone()
@@ -600,23 +620,6 @@ def run_sweep(args, H, torch, dev, rank):
             torch.cuda.synchronize()
             masked[nm] = a.elapsed_time(b) / 3
         del vm, out
-        # streaming: the same plan, C channels from pinned host memory in k chunks
-        host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
-        streams = []
-        for k in (1, 2, 4, 8, 16):
-            if C % k:
-                continue
-            cc = C // k
-            chunks = [host_vals[:, i * cc:(i + 1) * cc].contiguous().pin_memory() for i in range(k)]
-            H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT, host_map, C,
-                                 None)
-            ts = time.perf_counter()
-            for _ in range(3):
-                H.hegrid_grid_stream(p, chunks, cc, H.HEGRID_F32, H.HEGRID_MODE_TC_SPLIT,
-                                     host_map, C, None)
-            streams.append({"chunks": k, "chunk_channels": cc,
-                            "ms": (time.perf_counter() - ts) / 3 * 1e3})
-            del chunks
     finally:
         H.hegrid_plan_destroy(p)
     for r in streams:
