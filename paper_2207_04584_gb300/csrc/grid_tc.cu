@@ -1,8 +1,9 @@
 // Tensor-core form of the cell update (Eq. 1 accumulate + normalise) on
-// tcgen05: per 16x8 cell block b and 256-channel tile, the sums
+// tcgen05: per 16x8 cell block b and channel tile of N channels (N = 64, 128
+// or 256, a template parameter: the narrowest that holds C), the sums
 //     S[cell, c] = sum_k T[cell, k] V[k, c]
 // run as dense MMAs over the block's candidate samples k (sorted spatially by
-// the plan, 32 per chunk):  D[128 cells x 256 ch] (+)= A[128 x 16] * B[16 x 256]
+// the plan, 32 per chunk):  D[128 cells x N ch] (+)= A[128 x 16] * B[16 x N]
 // with A = the block's weight tile (built in shared memory from the plan's
 // weight entries, which carry their byte offset in the tile) and B = the
 // sample values of the chunk (K-major, so each channel row holds the chunk's
@@ -31,8 +32,9 @@
 //   warp 17     stages the chunk's 32 sample rows (raw, as stored; eight
 //               four-row TMA tensor gathers) and its weight entries (bulk
 //               copies) into a 3-deep shared-memory ring;
-//   warps 0-15  convert a staged chunk into the B tiles (row = channel, two
-//               threads per row) and store the chunk's weight entries into the
+//   warps 0-15  convert a staged chunk into the B tiles (row = channel; 16-byte
+//               pieces of 8 samples per thread, all 512 threads at N >= 128,
+//               256 at N = 64) and store the chunk's weight entries into the
 //               A tiles at the tile offsets the plan precomputed (2-deep ring);
 //   warp 16     allocates TMEM and issues the MMAs (one lane);
 //   warps 18-21 drain finished segments into the running total and run the

@@ -1581,7 +1581,7 @@ hegrid_status hegrid_plan_export(const hegrid_plan* plan, int32_t* perm, int32_t
   if (weight)
     HG_CUDA_TRY(cudaMemcpy(weight, plan->wsum, sizeof(float) * plan->M, cudaMemcpyDeviceToHost));
   if (nb_off || nb_idx || nb_w) {
-    // Rebuild the cell-major CSR from the blocks' sub-chunk entries.
+    // Rebuild the CSR by cell (rows = cells) from the blocks' sub-chunk entries.
     int64_t P = 0, nc_used = 0;
     hegrid_status st = plan_totals(plan, &P, &nc_used);
     if (st != HEGRID_OK) return st;
