@@ -103,8 +103,8 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "35bfd8ea01b88fddccafe8f0526cf69df2108333e3e782c86abb9099bf98abe0",
-                  "bytes": 4 * (8.637584e9 + 0.366337e9),
+                  "sha256": "0a960a4e5532f0048e540ea496bb87150eecd342cf4a0d5d5d70e269380614b5",
+                  "bytes": 4 * (8.614382e9 + 0.366298e9),
                   "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
