@@ -384,8 +384,9 @@ def sim_survey(seed=SEED_BASE + 6, n=19_000_000, C=50, n_sources=1000, with_valu
     ``n`` samples (1.5e7 - 1.9e7 in Tables 3 and 4) of ``C`` = 50 channels, 180 arcsec beam.
 
     Sample positions are uniform in (lon, lat) over the map; the map has 1 arcmin cells
-    (3600 x 1200) and the gridding kernel's FWHM is the beam's.  Because the positions are
-    i.i.d., the first ``k`` samples of this set are the same workload with ``k`` samples.
+    (3600 x 1200) and the gridding kernel's FWHM is the beam's.  The positions are i.i.d.,
+    so the first ``k`` samples of this set are a ``k``-sample draw of the same workload
+    (the benchmark times prefixes of one 1.9e7-sample set).
     Values: Gaussian point sources of the beam's width with power-law spectra, a 1/f-like
     spectral baseline and white noise.  ``out`` (optional) is a preallocated float32
     [n, C] (e.g. pinned host memory).  ``lon_span`` < 60 keeps the first ``lon_span``

@@ -1,0 +1,77 @@
+"""Host-side logic that needs no GPU: plan-flag encodings match the header,
+flag and argument checks that run before any CUDA call, seeded workload
+generators, and the bench's traffic table guard."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2207_04584_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2207_04584_gb300 import build
+    build.build()
+    from paper_2207_04584_gb300 import hegrid
+    hegrid.lib()
+    return hegrid
+
+
+def test_flag_encodings_match_header(H):
+    txt = open(os.path.join(ROOT, "include", "hegrid.h")).read()
+    assert "#define HEGRID_PLAN_SFL (1u << 13)" in txt
+    assert re.search(r"#define HEGRID_PLAN_HEALPIX\(k\) \(\(\(uint32_t\)\(k\) & 0x1fu\) << 8\)", txt)
+    assert H.HEGRID_PLAN_SFL == 1 << 13
+    assert H.HEGRID_PLAN_HEALPIX(12) == 12 << 8 and H.HEGRID_PLAN_HEALPIX(33) == 1 << 8
+    assert H.HEGRID_PLAN_BIN_CELLS(3) == 3
+
+
+@pytest.mark.parametrize("flags", [1 << 14, (14 << 8), (1 << 13) | (12 << 8)])
+def test_bad_plan_flags_rejected_before_cuda(H, flags):
+    lib = H.lib()
+    out = ctypes.c_void_p()
+    lon = np.array([10.0, 10.01])
+    lat = np.array([20.0, 20.01])
+    g = H.hegrid_map_geom(10, 10, 10.0, 20.0, 0.01, 0.01)
+    k = H.hegrid_kernel(0.05, 3.0)
+    st = lib.hegrid_plan_create(ctypes.byref(out), 2, lon.ctypes.data, lat.ctypes.data, 0,
+                                ctypes.byref(g), ctypes.byref(k), flags, None)
+    assert st == H.HEGRID_ERR_INVALID_ARG and out.value is None
+
+
+def test_masked_and_stream_argument_checks(H):
+    lib = H.lib()
+    assert lib.hegrid_grid_masked(None, None, 0, 1, 1, None, 1, None, 0, None) == \
+        H.HEGRID_ERR_INVALID_ARG
+    assert "plan" in H.hegrid_last_error()
+
+
+def test_generators_are_seeded():
+    a = W.sim_survey(n=3000, C=4)
+    b = W.sim_survey(n=3000, C=4)
+    assert np.array_equal(a["lon"], b["lon"]) and np.array_equal(a["values"], b["values"])
+    g = a["geom"]
+    assert (g["nx"], g["ny"], g["lon0"], g["lat0"]) == (3600, 1200, 30.0, 41.0)
+    assert np.all((a["lon"] >= 0) & (a["lon"] < 60) & (a["lat"] >= 31) & (a["lat"] < 51))
+    c = W.sim_survey(n=3000, C=4, lon_span=10.0)
+    assert c["geom"]["nx"] == 600 and c["geom"]["lon0"] == 5.0 and c["lon"].max() < 10.0
+    d1 = W.config1(with_values=False)
+    d2 = W.config1(with_values=False)
+    assert np.array_equal(d1["lat"], d2["lat"])
+
+
+def test_traffic_guard(monkeypatch):
+    import bench
+    t = bench.TRAFFIC["k_grid_tc"]
+    assert bench.measured_traffic("k_grid_tc") in (None, t["bytes"])
+    monkeypatch.setitem(bench.TRAFFIC, "k_grid_tc", dict(t, sha256="0" * 64))
+    assert bench.measured_traffic("k_grid_tc") is None
+    monkeypatch.setitem(bench.TRAFFIC, "k_grid_tc",
+                        dict(t, sha256=bench.sources_sha256(t["sources"])))
+    assert bench.measured_traffic("k_grid_tc") == t["bytes"]
+    assert bench.job_value(100, 2, 0.5) == 400
