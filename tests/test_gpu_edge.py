@@ -88,3 +88,34 @@ def test_field_across_ra_zero(H, mode):
     lat = 10.0 + rng.uniform(-0.6, 0.6, n) * 32 * cell
     values = rng.normal(2.0, 1.0, (n, 8)).astype(np.float32)
     _run(H, lon, lat, values, geom, 2.5 * ARCMIN, mode)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tc_split"])
+def test_no_sample_reaches_the_map(H, mode):
+    """Every sample lies far from the map: no pairs at all, every block empty;
+    the map is NaN everywhere and W is 0 (plain and masked calls)."""
+    rng = np.random.default_rng(905)
+    geom = {"nx": 40, "ny": 20, "lon0": 100.0, "lat0": 10.0, "dlon": ARCMIN, "dlat": ARCMIN}
+    n = 500
+    lon = 150.0 + rng.uniform(-1, 1, n)
+    lat = -30.0 + rng.uniform(-1, 1, n)
+    values = rng.normal(size=(n, 8)).astype(np.float32)
+    M = geom["nx"] * geom["ny"]
+    s = torch.cuda.current_stream().cuda_stream
+    md = H.HEGRID_MODE_FP32 if mode == "fp32" else H.HEGRID_MODE_TC_SPLIT
+    plan = H.hegrid_plan_create(n, lon, lat, 0, geom, 3 * ARCMIN, 3.0, 0, s)
+    try:
+        assert H.hegrid_plan_info(plan)["n_pairs"] == 0
+        v = torch.from_numpy(values).cuda()
+        out = torch.zeros((M, 8), device="cuda")
+        wout = torch.full((M,), -7.0, device="cuda")
+        H.hegrid_grid(plan, v, H.HEGRID_F32, 8, 8, out, 8, wout, md, s)
+        out2 = torch.zeros((M, 8), device="cuda")
+        wc = torch.full((M, 8), -7.0, device="cuda")
+        H.hegrid_grid_masked(plan, v, H.HEGRID_F32, 8, 8, out2, 8, wc, md, s)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    assert torch.isnan(out).all() and (wout == 0).all()
+    assert torch.isnan(out2).all() and (wc == 0).all()
