@@ -827,7 +827,9 @@ def main():
         tg = es.elapsed_time(ee) / 1e3 / reps
         forms[nm] = {"grid_ms": tg * 1e3, "grid_contrib_per_s": N * C / tg,
                      "pair_channel_per_s": P * C / tg}
-        sampled[nm] = map_d[torch.from_numpy(sample_cells).to(dev)].cpu().numpy().astype(np.float64)
+        sc = torch.from_numpy(sample_cells).to(dev)
+        sampled[nm] = (map_d[sc].cpu().numpy().astype(np.float64),
+                       w_d[sc].cpu().numpy().astype(np.float64))
     H.hegrid_plan_destroy(plan)
 
     # ---- roofline of the dominant kernel (the grid step) ------------------
@@ -896,16 +898,20 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and not args.lean:
         cpu = cpu_oracle_sample(wl, frac_rows=20)
+        # the same oracle on one host core (every 100th map row)
+        one = cpu_oracle_sample(wl, frac_rows=100, nthreads=1)
+        cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
         if sampled:
             import oracle
             ix = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"])
             ref, Wref = ix.grid(wl["values"], cells=sample_cells)
             mask = Wref >= 1e-3 * Wref.max()
             rms = np.sqrt(np.mean(ref[mask] ** 2, axis=0))
-            for nm, got in sampled.items():
+            for nm, (got, gw) in sampled.items():
                 e = np.max(np.abs(got[mask] - ref[mask]), axis=0) / rms
                 err[nm] = {"max": float(e.max()), "median": float(np.median(e)),
-                           "cells": int(mask.sum())}
+                           "cells": int(mask.sum()),
+                           "weight_map": float(np.max(np.abs(gw - Wref)) / Wref.max())}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
