@@ -8,7 +8,8 @@
 //   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) and the
 //     chunk's weight entries into shared memory with bulk async copies (TMA
 //     engine, one row per lane, two entry windows) completing on an mbarrier,
-//     double-buffered, one chunk ahead;
+//     double-buffered: chunk j + 1 is staged while chunk j is computed, one
+//     CTA barrier per chunk;
 //   * the threads scatter the staged entries into a dense 32 x 128 weight
 //     tile and OR a per-patch occupancy mask;
 //   * each warp owns a 4x4-cell patch and 128 channels; a thread accumulates
@@ -167,9 +168,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 0 && n_chunks > 0) issue(0);
     for (int j = 0; j < n_chunks; ++j) {
       const int s = j & 1;
-      if (warp == 0 && j + 1 < n_chunks) issue(j + 1);
       // weight tile for chunk j: zero, wait for the staged rows and entries,
-      // then scatter the entries
+      // then scatter the entries (buffer s was last read by chunk j-2, which
+      // every warp finished before the previous barrier)
       {
         float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][0]);
         for (int i = tid; i < kKC * kCT / 4; i += kThreads) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -177,8 +178,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       const int timed_out = !mbar_wait(&S.bar[s], phase[s], pv.err_word);
       if (__syncthreads_or(timed_out)) {
-        // give up: wait (bounded) for the other stage's copies, then leave
-        if (tid == 0 && j + 1 < n_chunks) mbar_wait(&S.bar[s ^ 1], phase[s ^ 1], nullptr);
+        // give up (chunk j + 1 is not staged yet: no other copies in flight)
         bail = true;
         break;
       }
@@ -206,6 +206,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       __syncthreads();
       phase[s] ^= 1u;
+      // every warp is past chunk j - 1, so its staged rows and entry windows
+      // (buffer s ^ 1) are free: stage chunk j + 1 while chunk j is computed
+      if (warp == 0 && j + 1 < n_chunks) issue(j + 1);
       const uint32_t* pm = S.pmask[s];
       const float* wrow = &S.Wt[s][0][patch * 16 + cs * 8];
       const float* vrow = &S.V[s][0][cg * 8];
@@ -222,8 +225,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
           for (int e = 0; e < 8; ++e) acc[i][e] = __fmaf_rn(w[i], v[e], acc[i][e]);
       }
-      __syncthreads();
     }
+    // every warp is done with this item's staged rows before the next item
+    // stages its first chunk
+    __syncthreads();
 
     if (bail) break;
     // epilogue: normalise and store
