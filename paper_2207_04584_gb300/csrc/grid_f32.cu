@@ -8,8 +8,9 @@
 //   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) and the
 //     chunk's weight entries into shared memory with bulk async copies (TMA
 //     engine, one row per lane, two entry windows) completing on an mbarrier,
-//     double-buffered: chunk j + 1 is staged while chunk j is computed, one
-//     CTA barrier per chunk;
+//     double-buffered: chunk j + 1 is staged while chunk j is computed;
+//     one CTA barrier per chunk (after the scatter; each warp clears its own
+//     columns of the weight tile after computing);
 //   * the threads scatter the staged entries into a dense 32 x 128 weight
 //     tile and OR a per-patch occupancy mask;
 //   * each warp owns a 4x4-cell patch and 128 channels; a thread accumulates
@@ -83,6 +84,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     mbar_init(&S.bar[0], 1);
     mbar_init(&S.bar[1], 1);
     fence_mbar_init();
+  }
+  {  // both weight tiles and patch masks start zero (and are left zero by every chunk)
+    float4* wz = reinterpret_cast<float4*>(&S.Wt[0][0][0]);
+    for (int i = tid; i < 2 * kKC * kCT / 4; i += kThreads) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < 2 * kKC) (&S.pmask[0][0])[tid] = 0u;
   }
   __syncthreads();
   uint32_t phase[2] = {0u, 0u};
@@ -168,21 +174,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 0 && n_chunks > 0) issue(0);
     for (int j = 0; j < n_chunks; ++j) {
       const int s = j & 1;
-      // weight tile for chunk j: zero, wait for the staged rows and entries,
-      // then scatter the entries (buffer s was last read by chunk j-2, which
-      // every warp finished before the previous barrier)
-      {
-        float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][0]);
-        for (int i = tid; i < kKC * kCT / 4; i += kThreads) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tid < kKC) S.pmask[s][tid] = 0u;
-      }
-      const int timed_out = !mbar_wait(&S.bar[s], phase[s], pv.err_word);
-      if (__syncthreads_or(timed_out)) {
-        // give up (chunk j + 1 is not staged yet: no other copies in flight)
-        bail = true;
-        break;
-      }
-      {
+      // weight tile for chunk j: wait for the staged rows and entries, then
+      // scatter the entries into tile s (all zero: each warp cleared its own
+      // columns after computing chunk j - 2, before the previous barrier)
+      const bool staged = mbar_wait(&S.bar[s], phase[s], pv.err_word);
+      if (staged) {
         const EntWin w = S.win[s];
         const uint32_t eck = smem_u32(S.eck[s]) + w.ck_off, ew = smem_u32(S.ew[s]) + w.w_off;
         for (int i = tid; i < w.n; i += kThreads) {
@@ -204,7 +200,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
         }
       }
-      __syncthreads();
+      if (__syncthreads_or(!staged)) {
+        // give up (chunk j + 1 is not staged yet: no other copies in flight)
+        bail = true;
+        break;
+      }
       phase[s] ^= 1u;
       // every warp is past chunk j - 1, so its staged rows and entry windows
       // (buffer s ^ 1) are free: stage chunk j + 1 while chunk j is computed
@@ -224,6 +224,17 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int i = 0; i < 8; ++i)
 #pragma unroll
           for (int e = 0; e < 8; ++e) acc[i][e] = __fmaf_rn(w[i], v[e], acc[i][e]);
+      }
+      // clear this warp's columns of tile s and its bit of the patch masks
+      // (no other warp reads or writes them before the next barrier; the
+      // warp's own lanes have all finished reading them)
+      __syncwarp();
+      {
+        float4* wz = reinterpret_cast<float4*>(&S.Wt[s][0][patch * 16]);
+#pragma unroll
+        for (int i = lane; i < kKC * 4; i += 32)  // 32 rows x 4 float4 of 16 columns
+          wz[(i >> 2) * (kCT / 4) + (i & 3)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        atomicAnd(&S.pmask[s][lane], ~(1u << patch));
       }
     }
     // every warp is done with this item's staged rows before the next item
