@@ -109,8 +109,8 @@ TRAFFIC = {
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": "653a0bac79a9102ef94587588b65e68adb334df48b3f130f135599a10a9d6176",
-                   "bytes": 4 * (6.276867e9 + 0.361791e9),
+                   "sha256": "94341235311b9b30b72b4f47e6eb70ff3f50530850303a335f2d4d68f7969c92",
+                   "bytes": 4 * (6.582210e9 + 0.363151e9),
                    "capture": "profiles/k_grid_f32_fast_drift_c256.md (C=256 x 4)"},
 }
 
