@@ -599,9 +599,9 @@ __global__ void __launch_bounds__(kChunk)
   __shared__ float4 s_mh[kChunk];
   __shared__ float4 s_ml[kChunk];
   __shared__ uint32_t s_cm[kChunk][kQ];
-  __shared__ int32_t s_pre[kChunk + 1];
   __shared__ int32_t s_loc[kChunk];
-  __shared__ int32_t s_gred[kQ];                     // per-warp partial sums of a group
+  __shared__ int32_t s_gred[kQ][kQ];       // per group, per warp: summed (cA | cB << 16)
+  __shared__ int32_t s_ginc[kQ][kChunk];   // per group, per thread: inclusive warp prefix
   __shared__ uint16_t s_ent[32 * kChunk];  // (cell << 5 | candidate) of a group
   __shared__ float s_w[32 * kChunk];       // weights of a group's entries
 
@@ -745,6 +745,31 @@ __global__ void __launch_bounds__(kChunk)
           if (lane >= o) incl += y;
         }
         if (lane == 31) s_red[wid] = incl;
+        // Per group of 32 staged candidates: this cell's entry counts on each
+        // side of the sub-chunk boundary that may fall inside the group
+        // (candidate r_split starts a new sub-chunk), packed in 16-bit halves,
+        // and their inclusive prefix over the warp; published with s_red by
+        // the one barrier below.
+        {
+          int ub = 0;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const uint32_t uq = um4[q];
+            const int jb = (int)((32 - ((kcount + ub) & 31)) & 31);
+            ub += __popc(uq);
+            const int r_split = jb < __popc(uq) ? select_bit(uq, jb) : 32;
+            const uint32_t amask = r_split >= 32 ? 0xffffffffu : ((1u << r_split) - 1u);
+            const int v = __popc(mask[q] & amask) | (__popc(mask[q] & ~amask) << 16);
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, inc, o);
+              if (lane >= o) inc += y;
+            }
+            s_ginc[q][t] = inc;
+            if (lane == 31) s_gred[q][wid] = inc;
+          }
+        }
         __syncthreads();
         int wpre = 0, total = 0;
 #pragma unroll
@@ -753,8 +778,6 @@ __global__ void __launch_bounds__(kChunk)
           total += s_red[w];
         }
         const int pre_t = wpre + incl - cc;
-        s_pre[t] = pre_t;
-        if (t == 0) s_pre[kChunk] = total;
         // candidate list and sub-chunk offsets (by the candidate's own thread)
         if (cc > 0) {
           int before = 0;
@@ -766,7 +789,6 @@ __global__ void __launch_bounds__(kChunk)
           if ((loc & 31) == 0) sub_off[sbase + loc / 32] = ebase + erun + pre_t;
           s_loc[t] = (int)(loc & 31);
         }
-        __syncthreads();
         // The staged candidates in groups of 32 (at most 32 x 128 entries):
         // list the group's (cell, candidate) pairs in entry order, compute
         // the weights one entry per thread (coalesced writes), then add them
@@ -776,33 +798,27 @@ __global__ void __launch_bounds__(kChunk)
         // r_split starts a new sub-chunk), so every sub-chunk's entries stay
         // contiguous.
         int ubefore = 0;  // union candidates of the staged chunk before group q
+        int g0 = 0;       // entries of the staged chunk before group q
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-          const int g0 = s_pre[32 * q], gT = s_pre[32 * q + 32] - g0;
+          const int gT = s_red[q];  // the group's candidates are warp q's staged ones
           const uint32_t uq = um4[q];
           const int jb = (int)((32 - ((kcount + ubefore) & 31)) & 31);
           ubefore += __popc(uq);
+          g0 += q > 0 ? s_red[q - 1] : 0;
           if (gT == 0) continue;
           const int r_split = jb < __popc(uq) ? select_bit(uq, jb) : 32;
           const uint32_t amask = r_split >= 32 ? 0xffffffffu : ((1u << r_split) - 1u);
           const int cA = __popc(mask[q] & amask), cB = __popc(mask[q] & ~amask);
           // exclusive prefix of (cA, cB) over the cells, packed in 16-bit halves
           const int v = cA | (cB << 16);
-          int inc = v;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-          }
-          if (lane == 31) s_gred[wid] = inc;
-          __syncthreads();
           int wp = 0, tot = 0;
 #pragma unroll
           for (int w = 0; w < kQ; ++w) {
-            if (w < wid) wp += s_gred[w];
-            tot += s_gred[w];
+            if (w < wid) wp += s_gred[q][w];
+            tot += s_gred[q][w];
           }
-          const int ex = wp + inc - v;
+          const int ex = wp + s_ginc[q][t] - v;
           const int a0 = ex & 0xffff, b0 = (tot & 0xffff) + (ex >> 16);
           {
             int pa = a0, pb = b0;
