@@ -128,7 +128,10 @@ hegrid_status hegrid_plan_create(hegrid_plan **out, int64_t n_samples, const dou
  *             W = 0 get NaN.
  * weight_out  device FP32 [M] or NULL: W[m] as used for the normalisation.
  * mode        HEGRID_MODE_FP32 (dtype F32 only), HEGRID_MODE_TC or
- *             HEGRID_MODE_TC_SPLIT (any dtype).
+ *             HEGRID_MODE_TC_SPLIT (any dtype).  The tensor-core modes work in
+ *             channel tiles of 64, 128 or 256 channels (the narrowest that
+ *             holds C, 256 above it); the FP32 mode in tiles of 128.
+ * Non-finite values are outside this call's contract (see hegrid_grid_masked).
  *
  * Errors: INVALID_ARG (NULL plan/values/map, bad C/ld/alignment/dtype/mode);
  * UNSUPPORTED (mode not available for dtype); CUDA (launch failure).
