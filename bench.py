@@ -479,12 +479,15 @@ def run_sim(args, H, torch, dev, rank):
             e2e_step()
             torch.cuda.synchronize()
             te.append(time.perf_counter() - ts)
-        t_e2e = statistics.mean(te)
+        # median of the steps: a host-side hiccup in one step (seen as single
+        # steps of 2-3x the others) does not move it; the mean is reported too
+        t_e2e = statistics.median(te)
         if n == nmid:
             sampled = host_map[torch.from_numpy(sample_cells)].numpy().astype(np.float64)
         h2d = n * 16 + n * C * 4
         d2h = M * C * 4 + M * 4
-        r.update({"e2e_ms": t_e2e * 1e3, "e2e_contrib_per_s": n * C / t_e2e,
+        r.update({"e2e_ms": t_e2e * 1e3, "e2e_mean_ms": statistics.mean(te) * 1e3,
+                  "e2e_contrib_per_s": n * C / t_e2e,
                   "h2d_bytes": h2d, "d2h_bytes": d2h,
                   "link_bound_ms": max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"]) / 1e6,
                   "paper_v100_s": paper.get(n),
