@@ -3,7 +3,8 @@
 // or 256, a template parameter: the narrowest that holds C), the sums
 //     S[cell, c] = sum_k T[cell, k] V[k, c]
 // run as dense MMAs over the block's candidate samples k (sorted spatially by
-// the plan, 32 per chunk):  D[128 cells x N ch] (+)= A[128 x 16] * B[16 x N]
+// the plan; 32 per sub-chunk, one sub-chunk per chunk at N >= 128 and two at
+// N = 64):  D[128 cells x N ch] (+)= A[128 x 16] * B[16 x N]
 // with A = the block's weight tile (built in shared memory from the plan's
 // weight entries, which carry their byte offset in the tile) and B = the
 // sample values of the chunk (K-major, so each channel row holds the chunk's
@@ -19,7 +20,8 @@
 // each MMA carries its own instruction descriptor and all accumulate in FP32.
 // The tensor core's FP32 accumulate loses about 2^-22 of the running sum per
 // MMA (measured; it grows with the number of MMAs added into one accumulator),
-// so a block's sum is built in segments of J.seg chunks: segment 0 accumulates
+// so a block's sum is built in segments of J.seg sub-chunks (rounded down to
+// whole chunks, at least one): segment 0 accumulates
 // into a "total" TMEM region, later segments into a "segment" region that the
 // drain warps add into the total with FP32 round-to-nearest adds (tcgen05
 // ld/st).  Consecutive items swap the two regions' roles, so an item's
@@ -29,13 +31,13 @@
 // is scaled to match.
 //
 // Warp roles (one CTA per SM, persistent over work items):
-//   warp 17     stages the chunk's 32 sample rows (raw, as stored; eight
-//               four-row TMA tensor gathers) and its weight entries (bulk
-//               copies) into a 3-deep shared-memory ring;
+//   warp 17     stages the chunk's sample rows (raw, as stored; eight
+//               four-row TMA tensor gathers per sub-chunk) and its weight
+//               entries (bulk copies) into a 3-deep shared-memory ring;
 //   warps 0-15  convert a staged chunk into the B tiles (row = channel; 16-byte
-//               pieces of 8 samples per thread, all 512 threads at N >= 128,
-//               256 at N = 64) and store the chunk's weight entries into the
-//               A tiles at the tile offsets the plan precomputed (2-deep ring);
+//               pieces of 8 samples per thread, all 512 threads) and store
+//               the chunk's weight entries into the A tiles at the tile
+//               offsets the plan precomputed (2-deep ring);
 //   warp 16     allocates TMEM and issues the MMAs (one lane);
 //   warps 18-21 drain finished segments into the running total and run the
 //               epilogue (TMEM -> registers -> S / W -> global).
@@ -61,44 +63,52 @@ constexpr int kMmaWarp = kProducerWarps;
 constexpr int kTmaWarp = kProducerWarps + 1;
 constexpr int kDrainWarp0 = kProducerWarps + 2;  // 4 warps: drains and epilogue
 constexpr int kThreads = (kProducerWarps + 6) * 32;
-constexpr int kK = 32;                     // candidates per chunk (64-byte rows of 16-bit values)
+constexpr int kK = 32;                     // candidates per sub-chunk (64-byte rows of 16-bit values)
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kRawStages = 3;              // staged sample rows + weight entries ring
-constexpr int kEntCap = 1792;              // weight entries staged per chunk (more: read from global)
-constexpr int kEntStage = kEntCap - 8;     // entries copied (leaves room for 16-byte alignment)
-constexpr int kDefaultSeg = 32;            // chunks per accumulation segment
+constexpr int kEntCap1 = 1792;             // weight entries staged per sub-chunk (more: from global)
+constexpr int kDefaultSeg = 32;            // sub-chunks per accumulation segment
 constexpr int kDefaultBand = 8;            // blocks per band of the work order
 // The channel tile kN (64, 128 or 256: the MMA's N) is a template parameter:
 // the launcher takes the narrowest tile that holds C (256 above it), so few
-// channels do not pay for 256-column tiles.  Per tile width: staged row slot
-// bytes (4-byte elements), TMEM columns (two accumulator regions), 16-byte
-// B-tile pieces per converting producer thread and converting threads.
-template <int kN>
+// channels do not pay for 256-column tiles.  So is kS, the 32-candidate
+// sub-chunks per chunk (the unit that passes through the rings with one set
+// of barrier hand-offs): 2 for the 64-channel tile, whose per-chunk hand-offs
+// would otherwise outweigh its small B tiles, else 1.  Per shape: candidates
+// per chunk, staged row slot bytes (4-byte elements), TMEM columns (two
+// accumulator regions), staged entries, 16-byte B-tile pieces per converting
+// producer thread and converting threads.
+template <int kN, int kS>
 struct TcShape {
+  static constexpr int kCK = kK * kS;
   static constexpr int kRawPitch = kN * 4;
   static constexpr uint32_t kTmemCols = 2 * kN;
-  static constexpr int kCPT = (kN * (kK / 8) + kProducers - 1) / kProducers;
-  static constexpr int kBThreads = kN * (kK / 8) / kCPT;
+  static constexpr int kEntCap = kEntCap1 * kS;
+  static constexpr int kEntStage = kEntCap - 8;  // leaves room for 16-byte alignment
+  static constexpr int kCPT = (kN * (kCK / 8) + kProducers - 1) / kProducers;
+  static constexpr int kBThreads = kN * (kCK / 8) / kCPT;
   static constexpr int kKT = 8 * kCPT;  // samples of a B row converted per thread
 };
 
 // Where a staged chunk's weight entries are: e_lo is the global index of its
-// first entry, n the number of entries, ns how many were staged; entry i < ns
-// sits at byte ck_off + 2 i of eck[] and w_off + 4 i of ew[].
+// first entry, n the number of entries (the first n0 belong to its first
+// sub-chunk), ns how many were staged; entry i < ns sits at byte ck_off + 2 i
+// of eck[] and w_off + 4 i of ew[].
 struct EntInfo {
   int64_t e_lo;
-  int32_t n, ns;
+  int32_t n, ns, n0;
   uint32_t ck_off, w_off;
 };
 
-template <int kN>
+template <int kN, int kS>
 struct __align__(512) TcSmem {
-  uint8_t A[kStages][2][kM * 64];      // [stage][hi, lo]: weights, K-major, 64B swizzle
-  uint8_t B[kStages][2][kN * 64];      // [stage][hi, lo]: values, K-major, 64B swizzle
-  uint8_t raw[kRawStages][kK * TcShape<kN>::kRawPitch];  // staged sample rows as stored
-  uint8_t eck[kRawStages][kEntCap * 2];     // staged entry tile offsets (16-byte aligned window)
-  uint8_t ew[kRawStages][kEntCap * 4];      // staged entry weights (16-byte aligned window)
+  using Sh = TcShape<kN, kS>;
+  uint8_t A[kStages][2][kS][kM * 64];  // [stage][hi, lo][sub-chunk]: weights, K-major, 64B swizzle
+  uint8_t B[kStages][2][kS][kN * 64];  // [stage][hi, lo][sub-chunk]: values, K-major, 64B swizzle
+  uint8_t raw[kRawStages][Sh::kCK * Sh::kRawPitch];  // staged sample rows as stored
+  uint8_t eck[kRawStages][Sh::kEntCap * 2];  // staged entry tile offsets (16-byte aligned window)
+  uint8_t ew[kRawStages][Sh::kEntCap * 4];   // staged entry weights (16-byte aligned window)
   EntInfo einfo[kRawStages];
   uint32_t red[3][2];                        // range slots: max|v|, min|v|>0 (float bits)
   uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
@@ -189,21 +199,24 @@ __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uin
 // Producer side of one work item (warps 0-15): for every chunk, convert the
 // staged rows into the B tiles and store the staged weight entries into the
 // A tiles.  DT is the stored value type; SPLIT selects the hi/lo form.  rslot
-// rotates over the three range-reduction slots (see below).
-// Returns false if a bounded wait gave up.
-template <int DT, bool SPLIT, int kN>
-__device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, int n_chunks,
-                                             int64_t c0, uint32_t& g, uint32_t& gr,
+// rotates over the three range-reduction slots (see below).  n_sub is the
+// item's count of 32-candidate sub-chunks (the last chunk may hold fewer
+// than kS).  Returns false if a bounded wait gave up.
+template <int DT, bool SPLIT, int kN, int kS>
+__device__ __forceinline__ bool produce_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
+                                             int n_sub, int64_t c0, uint32_t& g, uint32_t& gr,
                                              uint32_t& rslot, int32_t* err) {
-  using Sh = TcShape<kN>;
+  using Sh = TcShape<kN, kS>;
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
-  constexpr uint32_t kLoTile = kM * 64;  // A[s][1] follows A[s][0]
+  constexpr uint32_t kSubTile = kM * 64;       // A[s][h][1] follows A[s][h][0]
+  constexpr uint32_t kLoTile = kS * kSubTile;  // A[s][1] follows A[s][0]
   constexpr int kPitch = kWide ? Sh::kRawPitch : Sh::kRawPitch / 2;  // staged rows are packed
   constexpr int kKT = Sh::kKT;
   const int tid = threadIdx.x, lane = tid & 31;
   // B row (channel c0 + row) and first 16-byte piece (8 samples) this thread
-  // converts; threads from kBThreads on convert none (narrow tiles)
+  // converts; threads from kBThreads on convert none (narrow tiles).  Pieces
+  // 4 t .. 4 t + 3 belong to sub-chunk t.
   const int row = tid % kN, q0 = (tid / kN) * Sh::kCPT;
   const bool has_b = Sh::kBThreads >= kProducers || tid < Sh::kBThreads;
   const PlanView& pv = J.pv;
@@ -216,10 +229,11 @@ __device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, in
     const int rs = gr % kRawStages;
     if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
-    // Channel column `row` of this thread's half of the staged rows (the
-    // gathers fill channels past C with zeros).
+    // Channel column `row` of this thread's part of the staged rows (the
+    // gathers fill channels past C with zeros; the rows of a sub-chunk the
+    // last chunk lacks are not staged and read as zeros).
     uint32_t x[kKT];
-    if (has_b) {
+    if (has_b && (kS == 1 || q0 * 8 < (n_sub - j * kS) * kK)) {
       const uint32_t rb = smem_u32(S.raw[rs]) + q0 * 8 * kPitch;
 #pragma unroll
       for (int k = 0; k < kKT; ++k) {
@@ -237,7 +251,7 @@ __device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, in
     {
       const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
 #pragma unroll
-      for (int i = tid; i < kM * 64 / 16; i += kProducers) {
+      for (int i = tid; i < kS * kM * 64 / 16; i += kProducers) {
         st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
         if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
       }
@@ -314,7 +328,8 @@ __device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, in
         const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
         for (int qq = 0; qq < kKT / 8; ++qq) {
-          const int q = q0 + qq;
+          const int q = (q0 + qq) & 3;
+          const uint32_t sub = kS == 1 ? 0u : (uint32_t)((q0 + qq) >> 2) * (uint32_t)(kN * 64);
           uint32_t h2[4], l2[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -339,18 +354,22 @@ __device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, in
               l2[e] = 0u;
             }
           }
-          st_shared_v4(bh + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
-          if (kVsplit) st_shared_v4(bl + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
+          st_shared_v4(bh + sub + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
+          if (kVsplit) st_shared_v4(bl + sub + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
         }
       }
       // A tiles: the chunk's weight entries, scaled by kTcWeightScale, split
       // into the chunk's 16-bit format and stored at their precomputed tile
-      // offsets; two entries per step.
+      // offsets (in the second sub-tile from entry n0 on); two entries per step.
       {
         const uint32_t ah = smem_u32(S.A[s][0]);
         auto put2 = [&](int i0, uint32_t p0, float v0, uint32_t p1, float v1) {
           uint32_t h2, l2;
           split2<H16>(v0 * kTcWeightScale, v1 * kTcWeightScale, h2, l2);
+          if (kS > 1) {
+            p0 += i0 >= ei.n0 ? kSubTile : 0u;
+            p1 += i0 + kProducers >= ei.n0 ? kSubTile : 0u;
+          }
           if (i0 < ei.n) {
             st_shared_u16(ah + p0, (uint16_t)(h2 & 0xffffu));
             if (SPLIT) st_shared_u16(ah + kLoTile + p0, (uint16_t)(l2 & 0xffffu));
@@ -383,14 +402,14 @@ __device__ __forceinline__ bool produce_item(TcSmem<kN>& S, const GridJob& J, in
   return true;
 }
 
-template <int kN>
+template <int kN, int kS>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
-  using Sh = TcShape<kN>;
+  using Sh = TcShape<kN, kS>;
   extern __shared__ unsigned char smem_raw[];
   // 64B-swizzled tiles need 512-byte alignment (the swizzle atom); offsetting
   // smem_raw (not an integer round trip) keeps the shared address space.
   const uint32_t pad = (512u - (smem_u32(smem_raw) & 511u)) & 511u;
-  TcSmem<kN>& S = *reinterpret_cast<TcSmem<kN>*>(smem_raw + pad);
+  TcSmem<kN, kS>& S = *reinterpret_cast<TcSmem<kN, kS>*>(smem_raw + pad);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* err = jt.job[0].pv.err_word;
 
@@ -439,8 +458,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const int64_t c0 = ct * kN;
     const int64_t C = J.C;
     const int64_t kb0 = pv.cand_off[b];
-    const int n_chunks = pv.cand_cnt[b] / kK;
-    const int kSeg = J.seg;
+    const int n_sub = pv.cand_cnt[b] / kK;  // 32-candidate sub-chunks
+    const int n_chunks = (n_sub + kS - 1) / kS;
+    // J.seg counts sub-chunks: segments keep (about) that many candidates
+    const int kSeg = kS == 1 ? J.seg : max(1, J.seg / kS);
     const int n_seg = (n_chunks + kSeg - 1) / kSeg;
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
@@ -448,34 +469,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
 
     if (warp == kTmaWarp) {
       // ---------------- row and entry stager ----------------
-      // Per chunk: the 32 sample rows (eight four-row tensor gathers of the
+      // Per chunk: the 32 kS sample rows (8 kS four-row tensor gathers of the
       // channel tile; channels past C arrive as zeros) and the chunk's
       // weight entries (two bulk copies of 16-byte aligned windows), all
       // completing on raw_full.  Candidate indices are loaded two chunks
-      // ahead, sub-chunk offsets 31 chunks at a time.
+      // ahead, sub-chunk offsets 31 / kS chunks at a time.
+      constexpr int kBatch = 31 / kS;
       const uint32_t row_bytes = (uint32_t)(kN * eb);
       const void* tmap = &J.rows;
       const int64_t* __restrict__ so = pv.sub_off + kb0 / kK;
-      int32_t nA = n_chunks > 0 ? __ldg(pv.cand_idx + kb0 + lane) : 0;
-      int32_t nB = n_chunks > 1 ? __ldg(pv.cand_idx + kb0 + kK + lane) : 0;
+      // this lane's candidate of each sub-chunk of chunk j (nA) and j + 1 (nB)
+      int32_t nA[kS], nB[kS];
+#pragma unroll
+      for (int t = 0; t < kS; ++t) {
+        nA[t] = t < n_sub ? __ldg(pv.cand_idx + kb0 + t * kK + lane) : 0;
+        nB[t] = kS + t < n_sub ? __ldg(pv.cand_idx + kb0 + (kS + t) * kK + lane) : 0;
+      }
       int64_t sob = 0;
       for (int j = 0; j < n_chunks; ++j, ++gr) {
         const int r = gr % kRawStages;
         const uint32_t u = gr / kRawStages;
-        const int jb = j % 31;
-        if (jb == 0) sob = j + lane <= n_chunks ? __ldg(so + j + lane) : 0;
-        const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb);
-        const int64_t e_hi = __shfl_sync(0xffffffffu, sob, jb + 1);
-        const int32_t n = nA;  // this lane's row
-        nA = nB;
-        if (j + 2 < n_chunks) nB = __ldg(pv.cand_idx + kb0 + (int64_t)(j + 2) * kK + lane);
+        const int jb = j % kBatch;
+        if (jb == 0) sob = j * kS + lane <= n_sub ? __ldg(so + j * kS + lane) : 0;
+        const int nsj = min(kS, n_sub - j * kS);  // sub-chunks in this chunk
+        const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb * kS);
+        const int64_t e_mid = kS == 1 ? e_lo : __shfl_sync(0xffffffffu, sob, jb * kS + 1);
+        const int64_t e_end = __shfl_sync(0xffffffffu, sob, jb * kS + kS);
+        const int64_t e_hi = nsj == kS ? e_end : e_mid;
+        int32_t n[kS];  // this lane's rows
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+          n[t] = nA[t];
+          nA[t] = nB[t];
+          const int64_t q = (int64_t)(j + 2) * kS + t;
+          if (q < n_sub) nB[t] = __ldg(pv.cand_idx + kb0 + q * kK + lane);
+        }
         if (u >= 1 && !(mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err) &&
                         mbar_wait(&S.ent_empty[r], (u - 1) & 1u, err))) {
           bail = true;
           break;
         }
         const int ne = (int)(e_hi - e_lo);
-        const int ns = ne < kEntStage ? ne : kEntStage;
+        const int ns = ne < Sh::kEntStage ? ne : Sh::kEntStage;
         const int64_t a0 = (e_lo * 2) & ~(int64_t)15, b0 = (e_lo * 4) & ~(int64_t)15;
         const uint32_t abytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 2 + 15) & ~(int64_t)15) - a0) : 0u;
         const uint32_t wbytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 4 + 15) & ~(int64_t)15) - b0) : 0u;
@@ -484,19 +519,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           ei.e_lo = e_lo;
           ei.n = ne;
           ei.ns = ns;
+          ei.n0 = kS == 1 ? ne : (int32_t)(e_mid - e_lo);
           ei.ck_off = (uint32_t)(e_lo * 2 - a0);
           ei.w_off = (uint32_t)(e_lo * 4 - b0);
           S.einfo[r] = ei;
-          mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * kK + abytes + wbytes);
+          mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * (uint32_t)(kK * nsj) + abytes + wbytes);
         }
         __syncwarp();
-        {
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
           const int q4 = (lane & 7) * 4;
-          const int32_t r0 = __shfl_sync(0xffffffffu, n, q4), r1 = __shfl_sync(0xffffffffu, n, q4 + 1);
-          const int32_t r2 = __shfl_sync(0xffffffffu, n, q4 + 2), r3 = __shfl_sync(0xffffffffu, n, q4 + 3);
-          if (lane < 8)
-            tma_gather4(&S.raw[r][lane * 4 * row_bytes], tmap, (int32_t)c0, r0, r1, r2, r3,
-                        &S.raw_full[r]);
+          const int32_t r0 = __shfl_sync(0xffffffffu, n[t], q4);
+          const int32_t r1 = __shfl_sync(0xffffffffu, n[t], q4 + 1);
+          const int32_t r2 = __shfl_sync(0xffffffffu, n[t], q4 + 2);
+          const int32_t r3 = __shfl_sync(0xffffffffu, n[t], q4 + 3);
+          if (lane < 8 && t < nsj)
+            tma_gather4(&S.raw[r][(t * kK + lane * 4) * row_bytes], tmap, (int32_t)c0, r0, r1, r2,
+                        r3, &S.raw_full[r]);
         }
         if (lane == 0 && abytes)
           bulk_g2s(S.eck[r], reinterpret_cast<const uint8_t*>(pv.ent_ck) + a0, abytes,
@@ -540,18 +579,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         if (lane == 0) {
           const bool h = S.fmt16[s] != 0u;
           const uint32_t idS = h ? idS16 : idSbf;
-          const uint32_t a_hi = smem_u32(S.A[s][0]), a_lo = smem_u32(S.A[s][1]);
-          const uint32_t b_hi = smem_u32(S.B[s][0]), b_lo = smem_u32(S.B[s][1]);
           const uint32_t d = tmem + dcol;
+          const int nsj = min(kS, n_sub - j * kS);
 #pragma unroll
-          for (int kk = 0; kk < kK / 16; ++kk) {
-            const uint32_t o = kk * 32;
-            const uint32_t acc = (!seg_start || kk > 0) ? 1u : 0u;
-            tc_mma_f16(d, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_hi + o), idS, acc);
-            if (vsplit)
-              tc_mma_f16(d, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_lo + o), idS, 1u);
-            if (split)
-              tc_mma_f16(d, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(b_hi + o), idS, 1u);
+          for (int t = 0; t < kS; ++t) {
+            if (t >= nsj) break;
+            const uint32_t a_hi = smem_u32(S.A[s][0][t]), a_lo = smem_u32(S.A[s][1][t]);
+            const uint32_t b_hi = smem_u32(S.B[s][0][t]), b_lo = smem_u32(S.B[s][1][t]);
+#pragma unroll
+            for (int kk = 0; kk < kK / 16; ++kk) {
+              const uint32_t o = kk * 32;
+              const uint32_t acc = (!seg_start || t > 0 || kk > 0) ? 1u : 0u;
+              tc_mma_f16(d, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_hi + o), idS, acc);
+              if (vsplit)
+                tc_mma_f16(d, smem_desc_k_sw64(a_hi + o), smem_desc_k_sw64(b_lo + o), idS, 1u);
+              if (split)
+                tc_mma_f16(d, smem_desc_k_sw64(a_lo + o), smem_desc_k_sw64(b_hi + o), idS, 1u);
+            }
           }
           tc_commit(&S.ab_empty[s]);
           if (seg_end) tc_commit(&S.segdone[n_sg & 1u]);
@@ -659,17 +703,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       bool ok = true;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false, kN>(S, J, n_chunks, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = produce_item<HEGRID_F32, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          case HEGRID_F16: ok = produce_item<HEGRID_F16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          default: ok = produce_item<HEGRID_BF16X2, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
         }
       }
       bail = !ok;
@@ -683,20 +727,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   if (warp == kMmaWarp) tmem_dealloc(tmem, Sh::kTmemCols);
 }
 
-template <int kN>
+template <int kN, int kS>
 hegrid_status launch_tile(const JobTable& jt, cudaStream_t s) {
   static int sms = 0;
-  const size_t smem = sizeof(TcSmem<kN>) + 512;
+  const size_t smem = sizeof(TcSmem<kN, kS>) + 512;
   if (!sms) {
     int dev;
     cudaGetDevice(&dev);
-    HG_CUDA_TRY(cudaFuncSetAttribute(k_grid_tc<kN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HG_CUDA_TRY(cudaFuncSetAttribute(k_grid_tc<kN, kS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   int64_t grid = std::min<int64_t>(jt.n_items, (int64_t)sms);
   if (grid < 1) return HEGRID_OK;
-  k_grid_tc<kN><<<(unsigned)grid, kThreads, smem, s>>>(jt);
+  k_grid_tc<kN, kS><<<(unsigned)grid, kThreads, smem, s>>>(jt);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
   return HEGRID_OK;
@@ -710,9 +754,9 @@ int tc_default_seg() { return kDefaultSeg; }
 
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile) {
   switch (tile) {
-    case 64: return launch_tile<64>(jt, s);
-    case 128: return launch_tile<128>(jt, s);
-    case 256: return launch_tile<256>(jt, s);
+    case 64: return launch_tile<64, 2>(jt, s);
+    case 128: return launch_tile<128, 1>(jt, s);
+    case 256: return launch_tile<256, 1>(jt, s);
     default:
       set_error("unsupported tensor-core channel tile");
       return HEGRID_ERR_UNSUPPORTED;
