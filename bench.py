@@ -103,8 +103,8 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "0a960a4e5532f0048e540ea496bb87150eecd342cf4a0d5d5d70e269380614b5",
-                  "bytes": 4 * (8.614382e9 + 0.366298e9),
+                  "sha256": "fbae6c5a8a120b7d82747e087b69a581c3743b25a06265ab74afe59b1fe2347b",
+                  "bytes": 4 * (8.595043e9 + 0.366710e9),
                   "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
