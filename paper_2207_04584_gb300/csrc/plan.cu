@@ -603,7 +603,8 @@ __global__ void __launch_bounds__(kChunk)
   __shared__ int32_t s_gred[kQ][kQ];       // per group, per warp: summed (cA | cB << 16)
   __shared__ int32_t s_ginc[kQ][kChunk];   // per group, per thread: inclusive warp prefix
   __shared__ uint16_t s_ent[32 * kChunk];  // (cell << 5 | candidate) of a group
-  __shared__ float s_w[32 * kChunk];       // weights of a group's entries
+  __shared__ float s_w[32 * kChunk];       // weights of a span of groups, by cell
+  __shared__ uint32_t s_pab[kQ][kChunk];   // per group, per cell: entry -> s_w slot shifts
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
@@ -791,12 +792,71 @@ __global__ void __launch_bounds__(kChunk)
         }
         // The staged candidates in groups of 32 (at most 32 x 128 entries):
         // list the group's (cell, candidate) pairs in entry order, compute
-        // the weights one entry per thread (coalesced writes), then add them
+        // the weights one entry per thread (coalesced writes), and add them
         // into W of each cell in candidate order.  Within a group, entries
         // are grouped by cell (in thread order) on each side of the
         // 32-candidate sub-chunk boundary that may fall inside it (candidate
         // r_split starts a new sub-chunk), so every sub-chunk's entries stay
-        // contiguous.
+        // contiguous.  Consecutive groups whose entries fit s_w together form
+        // a span; s_w holds a span's weights by cell (each cell's weights of
+        // the span contiguous, in the order they are added: group by group,
+        // each group's two sides in turn, candidates in order), so that W
+        // takes one pass per span whose length is the cell's own entry count
+        // over the span (a pass per group would cost every warp its busiest
+        // cell's count in each group).
+        uint32_t span_start = 0u;  // bit q: group q starts a span
+        {
+          int acc = 0;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const int gT = s_red[q];
+            if (gT == 0) continue;
+            if (acc == 0 || acc + gT > 32 * kChunk) {
+              span_start |= 1u << q;
+              acc = 0;
+            }
+            acc += gT;
+          }
+        }
+        // this cell's slot in s_w for each group (span start + the cell's
+        // entries in the span's earlier groups): the span start is the
+        // cell's exclusive prefix over the cells of its entries in the span
+        int slot[kQ];
+        {
+          int exT[kQ];
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            int wp = 0;
+#pragma unroll
+            for (int w = 0; w < kQ; ++w)
+              if (w < wid) wp += s_gred[q][w];
+            const int in2 = wp + s_ginc[q][t];
+            exT[q] = (in2 & 0xffff) + (in2 >> 16) - __popc(mask[q]);
+          }
+          int sum = 0;
+#pragma unroll
+          for (int q = kQ - 1; q >= 0; --q) {
+            if (s_red[q] > 0) sum += exT[q];
+            slot[q] = sum;  // at a span's first group: the span's start
+            if ((span_start >> q) & 1u) sum = 0;
+          }
+          int base = 0;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            if (s_red[q] == 0) continue;
+            if ((span_start >> q) & 1u) base = slot[q];
+            slot[q] = base;
+            base += __popc(mask[q]);
+          }
+        }
+        int sp0 = 0, sp1 = 0;  // this cell's s_w slots of the pending span
+        auto add_span = [&]() {
+          for (int e = sp0; e < sp1; ++e) {
+            const float wgt = s_w[e];
+            wsv.add(wgt);
+            w16 += __half2float(__float2half_rn(wgt * kTcWeightScale));
+          }
+        };
         int ubefore = 0;  // union candidates of the staged chunk before group q
         int g0 = 0;       // entries of the staged chunk before group q
 #pragma unroll
@@ -807,6 +867,13 @@ __global__ void __launch_bounds__(kChunk)
           ubefore += __popc(uq);
           g0 += q > 0 ? s_red[q - 1] : 0;
           if (gT == 0) continue;
+          if ((span_start >> q) & 1u) {
+            // the previous span's weights (published by the barrier after
+            // its last weight pass; s_w is next written after this group's
+            // listing barrier)
+            add_span();
+            sp0 = sp1 = slot[q];
+          }
           const int r_split = jb < __popc(uq) ? select_bit(uq, jb) : 32;
           const uint32_t amask = r_split >= 32 ? 0xffffffffu : ((1u << r_split) - 1u);
           const int cA = __popc(mask[q] & amask), cB = __popc(mask[q] & ~amask);
@@ -820,6 +887,12 @@ __global__ void __launch_bounds__(kChunk)
           }
           const int ex = wp + s_ginc[q][t] - v;
           const int a0 = ex & 0xffff, b0 = (tot & 0xffff) + (ex >> 16);
+          const int totA = tot & 0xffff;
+          // entry e of this cell sits at s_w slot e + shift (A side: entries
+          // a0.. go to slot[q]..; B side: entries b0.. follow them)
+          s_pab[q][cell] = (uint32_t)(slot[q] - a0) & 0xffffu |
+                           (uint32_t)(slot[q] + cA - b0) << 16;
+          sp1 += cA + cB;
           {
             int pa = a0, pb = b0;
             uint32_t mm = mask[q];
@@ -840,19 +913,12 @@ __global__ void __launch_bounds__(kChunk)
             const int64_t pos = ebase + erun + g0 + e;
             ent_ck[pos] = (uint16_t)tile_off(ec, s_loc[k]);
             ent_w[pos] = wgt;
-            s_w[e] = wgt;
+            const uint32_t pab = s_pab[q][ec];
+            s_w[e + (int)(int16_t)(e < totA ? pab & 0xffffu : pab >> 16)] = wgt;
           }
           __syncthreads();
-          auto addw = [&](int e0, int n) {
-            for (int e = e0; e < e0 + n; ++e) {
-              const float wgt = s_w[e];
-              wsv.add(wgt);
-              w16 += __half2float(__float2half_rn(wgt * kTcWeightScale));
-            }
-          };
-          addw(a0, cA);
-          addw(b0, cB);
         }
+        add_span();
         erun += total;
       }
       kcount += ucount;
