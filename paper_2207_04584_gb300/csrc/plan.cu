@@ -49,6 +49,7 @@ constexpr double kDeg = kPi / 180.0;
 // ---------------------------------------------------------------------------
 struct KeyParams {
   double lon0, lat0, dlon, dlat, cx, cy, wx, wy;
+  double rdlon, rdlat;  // RN(1 / dlon), RN(1 / dlat)
   int32_t bin_cells, nbx;
   uint32_t n_bins;
   int32_t sfl;  // 1: Sanson-Flamsteed map, bins of projected x = (lon - lon0) cos(lat)
@@ -158,6 +159,30 @@ __device__ __forceinline__ int2 hpx_span(const HpxRing& e, float pa, float pb) {
   return make_int2(max(ja - e.J0, 0), min(jb - e.J0, e.cnt - 1));
 }
 
+// floor(RN(RN(x / d) + c)), the key's FP64 expression, exactly, without the
+// division where that is safe: y0 = x * rcp + c (rcp = RN(1 / d)) lies within
+// a few units of 2^-53 (|x / d| + |c|) of RN(RN(x / d) + c), so when no integer
+// lies within 1e-12 (|x / d| + |c| + 1) of y0 both have the same floor;
+// otherwise (and for non-finite or huge values) the correctly rounded
+// expression decides.
+__device__ __forceinline__ double floor_div_add(double x, double d, double rcp, double c) {
+  const double q0 = x * rcp;
+  const double y0 = q0 + c;
+  const double f = floor(y0);
+  const double eps = 1e-12 * (fabs(q0) + fabs(c) + 1.0);
+  if (y0 - f > eps && (f + 1.0) - y0 > eps) return f;
+  return floor(__dadd_rn(__ddiv_rn(x, d), c));
+}
+
+// a - 360 floor(RN(RN(a + 180) / 360)) exactly: for RN(a + 180) in [0, 360)
+// the quotient rounds into [0, 1) (the largest double below 360, over 360,
+// rounds to 1 - 2^-53), so the floor is 0 without dividing.
+__device__ __forceinline__ double wrap_ra(double a) {
+  const double x = __dadd_rn(a, 180.0);
+  if (x >= 0.0 && x < 360.0) return a;
+  return __dsub_rn(a, __dmul_rn(360.0, floor(__ddiv_rn(x, 360.0))));
+}
+
 template <bool kHpx>
 __global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* __restrict__ lat,
                        KeyParams kp, HpxParams hp, uint32_t* __restrict__ key,
@@ -183,15 +208,13 @@ __global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* 
       if (jr < e.cnt) k = (uint32_t)(e.base + jr);
     }
   } else {
-    // Bin key: single IEEE operations only (no contraction), so the key is
-    // reproducible bit for bit by any IEEE-754 implementation.
-    double a = __dsub_rn(lo, kp.lon0);
-    double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
-    a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
+    // Bin key: the floor of an expression of single IEEE operations (no
+    // contraction), so the key is reproducible bit for bit by any IEEE-754
+    // implementation; the floors are taken exactly (floor_div_add, wrap_ra).
+    double a = wrap_ra(__dsub_rn(lo, kp.lon0));
     if (kp.sfl) a = __dmul_rn(a, cd);  // projected x
-    double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
-    double qy = __dadd_rn(__ddiv_rn(__dsub_rn(la, kp.lat0), kp.dlat), kp.cy);
-    double fx = floor(qx), fy = floor(qy);
+    double fx = floor_div_add(a, kp.dlon, kp.rdlon, kp.cx);
+    double fy = floor_div_add(__dsub_rn(la, kp.lat0), kp.dlat, kp.rdlat, kp.cy);
     k = kp.n_bins;
     if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
       int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
@@ -1250,6 +1273,8 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   kp.lat0 = g.lat0_deg;
   kp.dlon = g.dlon_deg;
   kp.dlat = g.dlat_deg;
+  kp.rdlon = 1.0 / g.dlon_deg;
+  kp.rdlat = 1.0 / g.dlat_deg;
   kp.cx = 0.5 * (double)g.nx + (double)p->padx;
   kp.cy = 0.5 * (double)g.ny + (double)p->pady;
   kp.wx = (double)(g.nx + 2 * p->padx);
@@ -1770,12 +1795,9 @@ __global__ void k_keys_only(int32_t N, const double* __restrict__ lon,
                             uint32_t* __restrict__ key, int32_t* __restrict__ idx) {
   int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  double a = __dsub_rn(lon[n], kp.lon0);
-  double t = __ddiv_rn(__dadd_rn(a, 180.0), 360.0);
-  a = __dsub_rn(a, __dmul_rn(360.0, floor(t)));
-  double qx = __dadd_rn(__ddiv_rn(a, kp.dlon), kp.cx);
-  double qy = __dadd_rn(__ddiv_rn(__dsub_rn(lat[n], kp.lat0), kp.dlat), kp.cy);
-  double fx = floor(qx), fy = floor(qy);
+  double a = wrap_ra(__dsub_rn(lon[n], kp.lon0));
+  double fx = floor_div_add(a, kp.dlon, kp.rdlon, kp.cx);
+  double fy = floor_div_add(__dsub_rn(lat[n], kp.lat0), kp.dlat, kp.rdlat, kp.cy);
   uint32_t k = kp.n_bins;
   if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
     int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
@@ -1878,6 +1900,8 @@ extern "C" hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double
   kp.lat0 = g.lat0_deg;
   kp.dlon = g.dlon_deg;
   kp.dlat = g.dlat_deg;
+  kp.rdlon = 1.0 / g.dlon_deg;
+  kp.rdlat = 1.0 / g.dlat_deg;
   kp.cx = 0.5 * (double)g.nx + (double)padx;
   kp.cy = 0.5 * (double)g.ny + (double)pady;
   kp.wx = (double)(g.nx + 2 * padx);
