@@ -628,6 +628,8 @@ __global__ void __launch_bounds__(kChunk)
   __shared__ uint16_t s_ent[32 * kChunk];  // (cell << 5 | candidate) of a group
   __shared__ float s_w[32 * kChunk];       // weights of a span of groups, by cell
   __shared__ uint32_t s_pab[kQ][kChunk];   // per group, per cell: entry -> s_w slot shifts
+  __shared__ double s_sc[HG_BX + HG_BY][2];  // (sin, cos) of the column RAs, then row latitudes
+  __shared__ double s_b0[3];                 // unit vector of the block centre
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
@@ -655,13 +657,34 @@ __global__ void __launch_bounds__(kChunk)
   auto lon_of = [&](double x, double lat) {
     return pp.sfl ? pp.lon0 + x / cos(lat * kDeg) : pp.lon0 + x;
   };
-  {
+  // FP64 sines and cosines once per block (the FP64 pipe is slow): the
+  // block centre's unit vector, and on the plain grid (RA by column, latitude
+  // by row) those of the block's 16 column RAs and 8 row latitudes, which a
+  // cell's unit vector combines; the Sanson-Flamsteed map takes its own per cell.
+  if (t == HG_BX + HG_BY) {
     const double xb = ((double)bbx * HG_BX + 0.5 * (HG_BX - 1) - 0.5 * (pp.nx - 1)) * pp.dlon;
     const double lb = pp.lat0 + ((double)bby * HG_BY + 0.5 * (HG_BY - 1) - 0.5 * (pp.ny - 1)) * pp.dlat;
-    unit_vec(lon_of(xb, lb), lb, bx0, by0, bz0);
+    unit_vec(lon_of(xb, lb), lb, s_b0[0], s_b0[1], s_b0[2]);
+  } else if (!pp.sfl && t < HG_BX) {
+    sincos((pp.lon0 + ((double)(bbx * HG_BX + t) - 0.5 * (pp.nx - 1)) * pp.dlon) * kDeg,
+           &s_sc[t][0], &s_sc[t][1]);
+  } else if (!pp.sfl && t < HG_BX + HG_BY) {
+    const int r = t - HG_BX;
+    sincos((pp.lat0 + ((double)(bby * HG_BY + r) - 0.5 * (pp.ny - 1)) * pp.dlat) * kDeg,
+           &s_sc[t][0], &s_sc[t][1]);
   }
+  __syncthreads();
+  bx0 = s_b0[0];
+  by0 = s_b0[1];
+  bz0 = s_b0[2];
   double um[3];
-  {
+  if (!pp.sfl) {
+    const double sa = s_sc[cell % HG_BX][0], ca = s_sc[cell % HG_BX][1];
+    const double sd = s_sc[HG_BX + cell / HG_BX][0], cd = s_sc[HG_BX + cell / HG_BX][1];
+    um[0] = cd * ca;
+    um[1] = cd * sa;
+    um[2] = sd;
+  } else {
     const double lc = pp.lat0 + ((double)iy - 0.5 * (pp.ny - 1)) * pp.dlat;
     unit_vec(lon_of(((double)ix - 0.5 * (pp.nx - 1)) * pp.dlon, lc), lc, um[0], um[1], um[2]);
   }
@@ -983,14 +1006,20 @@ __global__ void __launch_bounds__(kChunk)
     k_block_bounds(BoundParams bp, WinArgs wa, const int32_t* __restrict__ bin_off,
                    int64_t* __restrict__ slots_ub, int64_t* __restrict__ pairs_ub) {
   __shared__ long long s_sum[kChunk / 32];
+  __shared__ double s_H[HG_BY];  // RA half-width H of the block's rows (FP64, once per row)
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int b = blockIdx.x;
   const int bbx = b % bp.nbx_b, bby = b / bp.nbx_b;
   const int ix = bbx * HG_BX + (t % HG_BX), iy = bby * HG_BY + (t / HG_BX);
+  if (t < HG_BY) {
+    const double lat = bp.lat0 + ((double)(bby * HG_BY + t) - 0.5 * (bp.ny - 1)) * bp.dlat;
+    s_H[t] = asin(bp.sinR / cos(fabs(lat) * kDeg)) / kDeg;
+  }
+  __syncthreads();
   long long cnt = 0;
   if (ix < bp.nx && iy < bp.ny) {
     const double lat = bp.lat0 + ((double)iy - 0.5 * (bp.ny - 1)) * bp.dlat;
-    const double H = asin(bp.sinR / cos(fabs(lat) * kDeg)) / kDeg;
+    const double H = s_H[t / HG_BX];
     if constexpr (kHpx) {
       // the cell's own window: rings that can hold a point within R of the
       // cell, RA within H of it (FP32; the two-pixel and two-ring margins of
