@@ -186,14 +186,14 @@ __device__ __forceinline__ double wrap_ra(double a) {
 template <bool kHpx>
 __global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* __restrict__ lat,
                        KeyParams kp, HpxParams hp, uint32_t* __restrict__ key,
-                       int32_t* __restrict__ idx, double* __restrict__ ux,
-                       double* __restrict__ uy, double* __restrict__ uz) {
+                       int32_t* __restrict__ idx) {
   int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   double lo = lon[n], la = lat[n];
-  double sa, ca, sd, cd;
-  sincos(lo * kDeg, &sa, &ca);
-  sincos(la * kDeg, &sd, &cd);
+  // sin and cos of the latitude only where the key needs them (the HEALPix
+  // ring index, the projected x); the unit vectors follow the sort
+  double sd = 0.0, cd = 1.0;
+  if (kHpx || kp.sfl) sincos(la * kDeg, &sd, &cd);
   uint32_t k;
   if constexpr (kHpx) {
     // RA wrapped into [0, 360), then the ring-scheme pixel of (sin(lat), RA)
@@ -223,9 +223,6 @@ __global__ void k_prep(int32_t N, const double* __restrict__ lon, const double* 
   }
   key[n] = k;
   idx[n] = n;
-  ux[n] = cd * ca;
-  uy[n] = cd * sa;
-  uz[n] = sd;
 }
 
 // ---------------------------------------------------------------------------
@@ -413,16 +410,21 @@ __global__ void k_bin_offsets(const uint32_t* __restrict__ skey, int32_t N, uint
     for (int64_t k = cur + 1; k <= (int64_t)n_bins; ++k) bin_off[k] = N;
 }
 
-__global__ void k_gather_u(const int32_t* __restrict__ perm, int32_t N,
-                           const double* __restrict__ ux, const double* __restrict__ uy,
-                           const double* __restrict__ uz, double* __restrict__ sx,
-                           double* __restrict__ sy, double* __restrict__ sz) {
+// Unit vectors (FP64) of the samples in sorted order: the FP64 sines and
+// cosines bound this kernel, so the gathered coordinate reads cost little.
+__global__ void k_unit_sorted(const int32_t* __restrict__ perm, int32_t N,
+                              const double* __restrict__ lon, const double* __restrict__ lat,
+                              double* __restrict__ sx, double* __restrict__ sy,
+                              double* __restrict__ sz) {
   int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= N) return;
-  int32_t n = perm[s];
-  sx[s] = ux[n];
-  sy[s] = uy[n];
-  sz[s] = uz[n];
+  const int32_t n = perm[s];
+  double sa, ca, sd, cd;
+  sincos(lon[n] * kDeg, &sa, &ca);
+  sincos(lat[n] * kDeg, &sd, &cd);
+  sx[s] = cd * ca;
+  sy[s] = cd * sa;
+  sz[s] = sd;
 }
 
 // ---------------------------------------------------------------------------
@@ -1286,14 +1288,11 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   // --- a1 + a2 ------------------------------------------------------------
   uint32_t *key0, *key1;
   int32_t *val0, *val1;
-  double *ux, *uy, *uz, *sx, *sy, *sz;
+  double *sx, *sy, *sz;
   HG_CUDA_TRY(sc.get(&key0, N));
   HG_CUDA_TRY(sc.get(&key1, N));
   HG_CUDA_TRY(sc.get(&val0, N));
   HG_CUDA_TRY(sc.get(&val1, N));
-  HG_CUDA_TRY(sc.get(&ux, N));
-  HG_CUDA_TRY(sc.get(&uy, N));
-  HG_CUDA_TRY(sc.get(&uz, N));
   HG_CUDA_TRY(sc.get(&sx, N));
   HG_CUDA_TRY(sc.get(&sy, N));
   HG_CUDA_TRY(sc.get(&sz, N));
@@ -1324,9 +1323,9 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     HG_CUDA_TRY(cudaMemcpyAsync(dr, hrings.data(), sizeof(HpxRing) * hrings.size(),
                                 cudaMemcpyHostToDevice, st));
     hp.rings = dr;
-    k_prep<true><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0, ux, uy, uz);
+    k_prep<true><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0);
   } else {
-    k_prep<false><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0, ux, uy, uz);
+    k_prep<false><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0);
   }
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
@@ -1360,7 +1359,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(cudaMemcpyAsync(p->perm, vin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
   k_bin_offsets<<<(N + 255) / 256, 256, 0, st>>>(kin, N, (uint32_t)p->n_bins, p->bin_off);
   count_launch();
-  k_gather_u<<<(N + 255) / 256, 256, 0, st>>>(p->perm, N, ux, uy, uz, sx, sy, sz);
+  k_unit_sorted<<<(N + 255) / 256, 256, 0, st>>>(p->perm, N, dlon, dlat, sx, sy, sz);
   count_launch();
   HG_CUDA_TRY(cudaGetLastError());
 
