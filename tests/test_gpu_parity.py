@@ -120,9 +120,52 @@ def check_plan(H, wl, bin_cells=2):
     (5, {"n": 1, "nx": 5, "ny": 5}),                  # a single sample
     (6, {"n": 2000, "spread": 4.0}),                  # most samples off the map
     (7, {"cell": 0.5 * ARCMIN, "fwhm": 2.9 * ARCMIN}),
+    # dense: a staged chunk's entries overflow the pair kernel's weight buffer,
+    # so W is summed over several spans of candidate groups
+    (8, {"n": 20000, "nx": 48, "ny": 24, "cell": 0.5 * ARCMIN, "fwhm": 2.9 * ARCMIN,
+         "spread": 1.1}),
 ])
 def test_plan_matches_oracle(H, seed, kw):
     check_plan(H, _case(seed, **kw))
+
+
+def test_plan_keys_on_bin_edges(H):
+    """Samples on the exact FP64 bin edges of the key expression and a few ulp
+    either side (where floor(RN(RN(x / d) + c)) must come from the correctly
+    rounded quotient), and on the RA wrap at lon0 +- 180 deg."""
+    wl = _case(21, n=0, nx=37, ny=21)
+    g = wl["geom"]
+    rng = np.random.default_rng(22)
+    lons, lats = [], []
+    for k in range(-8, g["nx"] + 8):  # RA edges near and across the map
+        e = g["lon0"] + (k - 0.5 * g["nx"]) * g["dlon"]
+        for u in range(-3, 4):
+            x = e
+            for _ in range(abs(u)):
+                x = np.nextafter(x, np.inf if u > 0 else -np.inf)
+            lons.append(x)
+            lats.append(g["lat0"] + rng.uniform(-0.4, 0.4) * g["ny"] * g["dlat"])
+    for k in range(-8, g["ny"] + 8):  # Dec edges
+        e = g["lat0"] + (k - 0.5 * g["ny"]) * g["dlat"]
+        for u in range(-3, 4):
+            y = e
+            for _ in range(abs(u)):
+                y = np.nextafter(y, np.inf if u > 0 else -np.inf)
+            lats.append(y)
+            lons.append(g["lon0"] + rng.uniform(-0.4, 0.4) * g["nx"] * g["dlon"])
+    for d in (180.0, -180.0):  # the RA wrap of the key (off the map)
+        e = g["lon0"] + d
+        for u in range(-3, 4):
+            x = e
+            for _ in range(abs(u)):
+                x = np.nextafter(x, np.inf if u > 0 else -np.inf)
+            lons.append(x)
+            lats.append(g["lat0"])
+    wl["lon"] = np.asarray(lons, np.float64)
+    wl["lat"] = np.asarray(lats, np.float64)
+    wl["values"] = np.ones((len(lons), 1), np.float32)
+    for bin_cells in (1, 2, 3):
+        check_plan(H, wl, bin_cells=bin_cells)
 
 
 @pytest.mark.parametrize("bin_cells", [1, 4, 7])
