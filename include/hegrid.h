@@ -238,7 +238,8 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * this plan use it.  Shapes: the work order's band width in cell-block
  * columns (which blocks run concurrently and so share sample rows in L2),
  * and for the tensor-core modes the accumulation segment length (16 or 32
- * chunks; both keep the split form inside its error bound).  values,
+ * sub-chunks of 32 candidates; both keep the split form inside its error
+ * bound).  values,
  * dtype, n_channels, ld_values as for hegrid_grid; the maps computed while
  * timing go to a scratch buffer (stream-ordered pool) and are discarded.
  * Synchronises `stream`.  report (may be NULL) receives every shape timed
@@ -248,7 +249,7 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
 #define HEGRID_TUNE_MAX 16
 typedef struct {
   int32_t band; /* blocks per band (0: the channel tiles of a block back to back) */
-  int32_t seg;  /* chunks per accumulation segment (tensor-core modes) */
+  int32_t seg;  /* 32-candidate sub-chunks per accumulation segment (tensor-core modes) */
   float ms;     /* time per grid call */
 } hegrid_tune_point;
 typedef struct {
@@ -263,8 +264,10 @@ hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtyp
  * hegrid_plan_set_tuning -- set the launch shape hegrid_autotune would keep
  * (for instance one found in an earlier run).  band: blocks per band, >= 1
  * (0: default; FP32 mode also -1: the channel tiles of a block back to back);
- * seg: chunks per accumulation segment for the tensor-core modes, 1..32
- * (0: default; longer segments would exceed the split form's error bound).
+ * seg: 32-candidate sub-chunks per accumulation segment for the tensor-core
+ * modes, 1..32 (0: default; longer segments would exceed the split form's
+ * error bound).  The 64-channel tile moves two sub-chunks per step and rounds
+ * seg down to an even count (at least 2).
  * INVALID_ARG otherwise.
  */
 hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t band, int32_t seg);
