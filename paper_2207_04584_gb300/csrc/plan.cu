@@ -845,26 +845,25 @@ __global__ void __launch_bounds__(kChunk)
         // are grouped by cell (in thread order) on each side of the
         // 32-candidate sub-chunk boundary that may fall inside it (candidate
         // r_split starts a new sub-chunk), so every sub-chunk's entries stay
-        // contiguous.  Consecutive groups whose entries fit s_w together form
-        // a span; s_w holds a span's weights by cell (each cell's weights of
-        // the span contiguous, in the order they are added: group by group,
-        // each group's two sides in turn, candidates in order), so that W
-        // takes one pass per span whose length is the cell's own entry count
-        // over the span (a pass per group would cost every warp its busiest
-        // cell's count in each group).
-        uint32_t span_start = 0u;  // bit q: group q starts a span
+        // contiguous.  The groups form spans: the whole staged chunk when all
+        // its weights fit s_w, else each group alone (a span of part of the
+        // chunk saves less than its by-cell writes cost in bank conflicts).
+        // s_w holds a span's weights by cell (each cell's weights of the span
+        // contiguous, in the order they are added: group by group, each
+        // group's two sides in turn, candidates in order), so that W takes
+        // one pass per span whose length is the cell's own entry count over
+        // the span (a pass per group would cost every warp its busiest cell's
+        // count in each group).
+        uint32_t span_start;  // bit q: group q starts a span
         {
           int acc = 0;
+          uint32_t nonempty = 0u;
 #pragma unroll
           for (int q = 0; q < kQ; ++q) {
-            const int gT = s_red[q];
-            if (gT == 0) continue;
-            if (acc == 0 || acc + gT > 32 * kChunk) {
-              span_start |= 1u << q;
-              acc = 0;
-            }
-            acc += gT;
+            acc += s_red[q];
+            if (s_red[q] > 0) nonempty |= 1u << q;
           }
+          span_start = acc <= 32 * kChunk ? (nonempty & (0u - nonempty)) : nonempty;
         }
         // this cell's slot in s_w for each group (span start + the cell's
         // entries in the span's earlier groups): the span start is the
