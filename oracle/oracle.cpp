@@ -16,7 +16,7 @@
 //     variant uses the paper's own RING-scheme pixels (og_hpx_*, written from
 //     Gorski et al. 2005's definitions) with a per-ring table of pixel ranges.
 // Readings where the paper is silent (kernel shape, distance formula, grid
-// geometry, empty cells) are listed in the design doc; in short:
+// geometry, empty cells), in short:
 //   * w = exp(-d^2 / (2 sigma^2)), sigma = FWHM / sqrt(8 ln 2), R = support*sigma;
 //   * d is the great-circle separation; membership is tested on the haversine
 //     h = sin^2(dlat/2) + cos(lat_m) cos(lat_n) sin^2(dlon/2) <= sin^2(R/2);
