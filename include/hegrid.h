@@ -140,7 +140,8 @@ hegrid_status hegrid_grid(hegrid_plan *plan, const void *values, hegrid_dtype dt
                           int64_t n_channels, int64_t ld_values, float *map_out, int64_t ld_map,
                           float *weight_out, uint32_t mode, void *stream);
 
-/* Free the plan and all of its device memory (synchronises the device). */
+/* Free the plan and all of its device memory (synchronises the device).
+ * NULL is a no-op.  Returns OK. */
 hegrid_status hegrid_plan_destroy(hegrid_plan *plan);
 
 /* One entry of a batched launch (the arguments of hegrid_grid). */
@@ -157,7 +158,11 @@ typedef struct {
 /*
  * hegrid_grid_batched -- grid n independent fields in one persistent launch
  * per kernel kind (the multi-pipeline FIFO of Sec. 4.2, as one device work
- * queue).  plans[i] and args[i] describe field i (host arrays).  Asynchronous.
+ * queue).  plans[i] and args[i] describe field i (host arrays, read during
+ * the call; the device buffers they name stay the caller's).  Asynchronous.
+ * Errors: INVALID_ARG (n < 0; plans or args NULL with n > 0; any entry that
+ * hegrid_grid would reject -- every entry is checked before the first
+ * launch); UNSUPPORTED and CUDA as for hegrid_grid.  n = 0 does nothing.
  */
 hegrid_status hegrid_grid_batched(int n, hegrid_plan *const *plans, const hegrid_grid_args *args,
                                   void *stream);
@@ -166,7 +171,11 @@ hegrid_status hegrid_grid_batched(int n, hegrid_plan *const *plans, const hegrid
  * hegrid_batch_create / _launch / _destroy -- the same batch with its work
  * queue uploaded once and its launches captured in a CUDA graph; launch
  * replays the graph on `stream`.  The plans and buffers named in args must
- * outlive the batch.
+ * outlive the batch.  create waits (on the host) for the plans to be built
+ * and sets *out (NULL on error).
+ * Errors: create: INVALID_ARG (out NULL, and as for hegrid_grid_batched),
+ * CUDA (capture or instantiation failed); launch: INVALID_ARG (batch NULL),
+ * CUDA; destroy: NULL is a no-op, returns OK.
  */
 hegrid_status hegrid_batch_create(hegrid_batch **out, int n, hegrid_plan *const *plans,
                                   const hegrid_grid_args *args, void *stream);
@@ -185,6 +194,9 @@ hegrid_status hegrid_batch_destroy(hegrid_batch *batch);
  * rows that are not a multiple of 16 bytes are then spread on the device to
  * the 16-byte row pitch the grid kernels read, through a staging buffer of
  * one chunk per ring slot.
+ * Errors: INVALID_ARG (NULL plan, host_map or chunk pointer; n_chunks < 1;
+ * chunk_channels < 1; ld_host_map < n_chunks * chunk_channels; unknown dtype;
+ * and the checks of hegrid_grid); OOM (the device ring); CUDA.
  */
 hegrid_status hegrid_grid_stream(hegrid_plan *plan, const void *const *host_chunks, int n_chunks,
                                  int64_t chunk_channels, hegrid_dtype dtype, uint32_t mode,
@@ -209,8 +221,9 @@ hegrid_status hegrid_grid_masked(hegrid_plan *plan, const void *values, hegrid_d
                                  int64_t n_channels, int64_t ld_values, float *map_out,
                                  int64_t ld_map, float *wc_out, uint32_t mode, void *stream);
 
-/* Plan sizes: pairs P, bins, cell blocks, candidate slots in use (padded to 64
- * per block), device bytes held.  Waits until the plan has been built. */
+/* Plan sizes (any output may be NULL): pairs P, bins, cell blocks, candidate
+ * slots in use (padded to 64 per block), device bytes held.  Waits until the
+ * plan has been built.  Errors: INVALID_ARG (plan NULL); CUDA. */
 hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_t *n_bins,
                                int64_t *n_blocks, int64_t *n_cand, int64_t *bytes);
 
@@ -222,7 +235,8 @@ hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_
  *   nb_idx[P]        sample index of each pair, ascending per cell (canonical)
  *   nb_w[P]          FP32 weight of each pair, in the same order as nb_idx
  *   weight[M]        W[m] = sum of the FP32 weights of cell m
- * Synchronises the plan's device work.
+ * Synchronises the plan's device work.  Errors: INVALID_ARG (plan NULL); CUDA
+ * (a failed copy, or an entry count that disagrees with the pair total).
  */
 hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t *bin_off,
                                  int64_t *nb_off, int32_t *nb_idx, float *nb_w, float *weight);
@@ -244,7 +258,8 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * timing go to a scratch buffer (stream-ordered pool) and are discarded.
  * Synchronises `stream`.  report (may be NULL) receives every shape timed
  * (milliseconds per grid call, mean of 2 after 1 warm-up) and the index of
- * the one kept.
+ * the one kept.  Errors: INVALID_ARG (plan NULL, and the checks of
+ * hegrid_grid); UNSUPPORTED, OOM (the scratch map) and CUDA as for hegrid_grid.
  */
 #define HEGRID_TUNE_MAX 16
 typedef struct {
@@ -277,6 +292,8 @@ hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t b
  * of 1..4 map cells (the plan_create flags) on the given samples and return
  * the fastest in *best_bin_cells; ms[4] (may be NULL) receives the times.
  * Arguments as for hegrid_plan_create.  Synchronises the device.
+ * Errors: INVALID_ARG (best_bin_cells NULL, and as for hegrid_plan_create);
+ * UNSUPPORTED, OOM and CUDA as for hegrid_plan_create.
  */
 hegrid_status hegrid_autotune_bins(int64_t n_samples, const double *lon_deg, const double *lat_deg,
                                    int coords_on_device, const hegrid_map_geom *geom,
@@ -287,11 +304,14 @@ hegrid_status hegrid_autotune_bins(int64_t n_samples, const double *lon_deg, con
  * hegrid_fp32_peak -- measure the GPU's FP32 FMA throughput (TFLOP/s, 2 flop
  * per FMA): every SM runs independent FMA chains for a few milliseconds.  The
  * roofline of HEGRID_MODE_FP32, whose bound is the CUDA-core ALU.
- * Synchronises `stream`.
+ * Synchronises `stream`.  Errors: INVALID_ARG (tflops NULL); OOM; CUDA.
  */
 hegrid_status hegrid_fp32_peak(double *tflops, void *stream);
 
-/* Device-side error word of the plan (bounded waits that timed out). */
+/* Device-side error word of the plan: OK, or TIMEOUT if a bounded wait of a
+ * kernel that used the plan gave up (the kernel then returned early and its
+ * outputs are incomplete).  Waits for the plan's creation.  Errors:
+ * INVALID_ARG (plan NULL); CUDA. */
 hegrid_status hegrid_status_poll(const hegrid_plan *plan);
 
 /* Number of CUDA kernels this library has launched in this process (for
