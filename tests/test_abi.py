@@ -52,3 +52,23 @@ def test_argument_errors_without_gpu(lib):
     assert st == H.HEGRID_ERR_INVALID_ARG and out.value is None
     assert "nx" in H.hegrid_last_error()
     assert lib.hegrid_grid(None, None, 0, 1, 1, None, 1, None, 0, None) == H.HEGRID_ERR_INVALID_ARG
+
+
+def test_every_status_entry_point_documents_its_errors():
+    """Each declaration returning hegrid_status is preceded (after the previous
+    declaration) by a comment that states its error behaviour."""
+    txt = open(os.path.join(ROOT, "include", "hegrid.h")).read()
+    decl = re.compile(r"^hegrid_status\s+(hegrid_\w+)\s*\(", re.M)
+    prev_end = 0
+    pending = []
+    missing = []
+    for m in decl.finditer(txt):
+        seg = txt[prev_end:m.start()]
+        comments = " ".join(re.findall(r"/\*.*?\*/", seg, flags=re.S))
+        if comments.strip():
+            pending = [comments]
+        doc = " ".join(pending)
+        if not re.search(r"Errors?\b|INVALID_ARG|Returns OK|no-op", doc):
+            missing.append(m.group(1))
+        prev_end = txt.index(";", m.end()) + 1
+    assert not missing, missing
