@@ -141,7 +141,7 @@ hegrid_status hegrid_grid(hegrid_plan *plan, const void *values, hegrid_dtype dt
                           float *weight_out, uint32_t mode, void *stream);
 
 /* Free the plan and all of its device memory (synchronises the device).
- * NULL is a no-op.  Returns OK. */
+ * NULL is a no-op.  Returns OK.  (Library service; no step of the paper.) */
 hegrid_status hegrid_plan_destroy(hegrid_plan *plan);
 
 /* One entry of a batched launch (the arguments of hegrid_grid). */
@@ -168,8 +168,9 @@ hegrid_status hegrid_grid_batched(int n, hegrid_plan *const *plans, const hegrid
                                   void *stream);
 
 /*
- * hegrid_batch_create / _launch / _destroy -- the same batch with its work
- * queue uploaded once and its launches captured in a CUDA graph; launch
+ * hegrid_batch_create / _launch / _destroy -- the same batch (Sec. 4.2's
+ * pipelines) with its work queue uploaded once and its launches captured in a
+ * CUDA graph; launch
  * replays the graph on `stream`.  The plans and buffers named in args must
  * outlive the batch.  create waits (on the host) for the plans to be built
  * and sets *out (NULL on error).
@@ -221,7 +222,8 @@ hegrid_status hegrid_grid_masked(hegrid_plan *plan, const void *values, hegrid_d
                                  int64_t n_channels, int64_t ld_values, float *map_out,
                                  int64_t ld_map, float *wc_out, uint32_t mode, void *stream);
 
-/* Plan sizes (any output may be NULL): pairs P, bins, cell blocks, candidate
+/* Plan sizes of the neighbour search of Algorithm 1 (any output may be
+ * NULL): pairs P, bins, cell blocks, candidate
  * slots in use (padded to 64 per block), device bytes held.  Waits until the
  * plan has been built.  Errors: INVALID_ARG (plan NULL); CUDA. */
 hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_t *n_bins,
@@ -229,6 +231,8 @@ hegrid_status hegrid_plan_info(const hegrid_plan *plan, int64_t *n_pairs, int64_
 
 /*
  * hegrid_plan_export -- copy plan structures to host buffers (any may be NULL):
+ * the binning (Sec. 4.1.1's index, here map bins or HEALPix rings), the
+ * neighbour lists of Algorithm 1 and the kernel weights of Eq. 1:
  *   perm[N]          sample indices sorted by (bin key, index); discarded last
  *   bin_off[n_bins+1] start of each bin in perm (bin_off[n_bins] = kept count)
  *   nb_off[M+1]      CSR row offsets of the (cell -> sample) pairs
@@ -277,7 +281,7 @@ hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtyp
 
 /*
  * hegrid_plan_set_tuning -- set the launch shape hegrid_autotune would keep
- * (for instance one found in an earlier run).  band: blocks per band, >= 1
+ * (for instance one found in an earlier run; the tuning of Sec. 5.3).  band: blocks per band, >= 1
  * (0: default; FP32 mode also -1: the channel tiles of a block back to back);
  * seg: 32-candidate sub-chunks per accumulation segment for the tensor-core
  * modes, 1..32 (0: default; longer segments would exceed the split form's
@@ -289,7 +293,8 @@ hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t b
 
 /*
  * hegrid_autotune_bins -- time hegrid_plan_create (plus destroy) for bin edges
- * of 1..4 map cells (the plan_create flags) on the given samples and return
+ * of 1..4 map cells (the plan_create flags; the index-resolution study of
+ * Sec. 5.3) on the given samples and return
  * the fastest in *best_bin_cells; ms[4] (may be NULL) receives the times.
  * Arguments as for hegrid_plan_create.  Synchronises the device.
  * Errors: INVALID_ARG (best_bin_cells NULL, and as for hegrid_plan_create);
@@ -305,13 +310,14 @@ hegrid_status hegrid_autotune_bins(int64_t n_samples, const double *lon_deg, con
  * per FMA): every SM runs independent FMA chains for a few milliseconds.  The
  * roofline of HEGRID_MODE_FP32, whose bound is the CUDA-core ALU.
  * Synchronises `stream`.  Errors: INVALID_ARG (tflops NULL); OOM; CUDA.
+ * (Measurement service; no step of the paper.)
  */
 hegrid_status hegrid_fp32_peak(double *tflops, void *stream);
 
 /* Device-side error word of the plan: OK, or TIMEOUT if a bounded wait of a
  * kernel that used the plan gave up (the kernel then returned early and its
  * outputs are incomplete).  Waits for the plan's creation.  Errors:
- * INVALID_ARG (plan NULL); CUDA. */
+ * INVALID_ARG (plan NULL); CUDA.  (Library service; no step of the paper.) */
 hegrid_status hegrid_status_poll(const hegrid_plan *plan);
 
 /* Number of CUDA kernels this library has launched in this process (for
