@@ -75,3 +75,32 @@ def test_traffic_guard(monkeypatch):
                         dict(t, sha256=bench.sources_sha256(t["sources"])))
     assert bench.measured_traffic("k_grid_tc") == t["bytes"]
     assert bench.job_value(100, 2, 0.5) == 400
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built CUDA library every call path raises."""
+    from paper_2207_04584_gb300 import hegrid
+    monkeypatch.setattr(hegrid, "LIB_PATH", str(tmp_path / "libhegrid.so"))
+    monkeypatch.setattr(hegrid, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        hegrid.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        hegrid.hegrid_launch_count()
+
+
+def test_product_code_never_uses_the_oracle():
+    """The package (Python binding, workloads, CUDA sources) neither imports,
+    includes nor loads anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_2207_04584_gb300")
+    checked = 0
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if not f.endswith((".py", ".cu", ".cuh", ".h", ".cpp", ".c")):
+                continue
+            src = open(os.path.join(dirpath, f)).read()
+            checked += 1
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+            assert not re.search(r"#\s*include\s*[<\"][^>\"]*oracle", src), f
+            code = re.sub(r"//[^\n]*|#[^\n]*", "", src)
+            assert "liboracle" not in src and not re.search(r"\bog_\w+\s*\(", code), f
+    assert checked >= 6
