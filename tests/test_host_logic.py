@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: plan-flag encodings match the header,
 flag and argument checks that run before any CUDA call, seeded workload
-generators, and the bench's traffic table guard."""
+generators, the bench's traffic table guard, and that the product path has
+no fallback and never touches the oracle."""
 import ctypes
 import os
 import re
