@@ -69,9 +69,8 @@ typedef struct {
 
 /* hegrid_grid modes */
 #define HEGRID_MODE_FP32 0u     /* CUDA-core FP32 gather/accumulate */
-#define HEGRID_MODE_TC 1u       /* tcgen05 tensor cores, one 16-bit pass (FP16; BF16 for
-                                   chunks of values outside FP16's range) */
-#define HEGRID_MODE_TC_SPLIT 2u /* tcgen05 with hi/lo splits of values and weights */
+#define HEGRID_MODE_TC 1u       /* tcgen05 tensor cores, one FP16 pass */
+#define HEGRID_MODE_TC_SPLIT 2u /* tcgen05 with FP16 hi/lo splits of values and weights */
 
 /* plan_create flags: bits 0-7 give the bin edge in map cells (0 = default 2).
  * Bits 8-12, HEGRID_PLAN_HEALPIX(k) with 1 <= k <= 13, select the paper's own
@@ -131,6 +130,14 @@ hegrid_status hegrid_plan_create(hegrid_plan **out, int64_t n_samples, const dou
  *             HEGRID_MODE_TC_SPLIT (any dtype).  The tensor-core modes work in
  *             channel tiles of 64, 128 or 256 channels (the narrowest that
  *             holds C, 256 above it); the FP32 mode in tiles of 128.
+ *             In the tensor-core modes each channel is multiplied by an exact
+ *             power of two that puts its largest |v| in [2^14, 2^15) before the
+ *             FP16 conversion (and divided out in the normalisation), so a
+ *             channel keeps its accuracy relative to its own values whatever
+ *             the other channels of its tile hold; for F32, BF16X2 and BF16
+ *             values this takes one extra read of the values (a per-channel
+ *             maximum) and C * 4 bytes of stream-ordered scratch from the
+ *             library's pool.  FP16 values are used as stored.
  * Non-finite values are outside this call's contract (see hegrid_grid_masked).
  *
  * Errors: INVALID_ARG (NULL plan/values/map, bad C/ld/alignment/dtype/mode);
@@ -255,9 +262,10 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * hegrid_grid_batched, hegrid_batch_create and hegrid_grid_stream calls on
  * this plan use it.  Shapes: the work order's band width in cell-block
  * columns (which blocks run concurrently and so share sample rows in L2),
- * and for the tensor-core modes the accumulation segment length (16 or 32
- * sub-chunks of 32 candidates; both keep the split form inside its error
- * bound).  values,
+ * and for the tensor-core modes the accumulation segment length (8 or 16
+ * sub-chunks of 32 candidates; both keep the split form well inside its error
+ * bound: the tensor core's FP32 accumulate loses about 2^-22 of the running
+ * sum per MMA, so the error grows with the segment).  values,
  * dtype, n_channels, ld_values as for hegrid_grid; the maps computed while
  * timing go to a scratch buffer (stream-ordered pool) and are discarded.
  * Synchronises `stream`.  report (may be NULL) receives every shape timed
@@ -284,8 +292,8 @@ hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtyp
  * (for instance one found in an earlier run; the tuning of Sec. 5.3).  band: blocks per band, >= 1
  * (0: default; FP32 mode also -1: the channel tiles of a block back to back);
  * seg: 32-candidate sub-chunks per accumulation segment for the tensor-core
- * modes, 1..32 (0: default; longer segments would exceed the split form's
- * error bound).  The 64-channel tile moves two sub-chunks per step and rounds
+ * modes, 1..16 (0: default 16; longer segments would leave the split form
+ * too little margin inside its error bound).  The 64-channel tile moves two sub-chunks per step and rounds
  * seg down to an even count (at least 2).
  * INVALID_ARG otherwise.
  */
@@ -325,6 +333,24 @@ hegrid_status hegrid_status_poll(const hegrid_plan *plan);
  * at capture). */
 int64_t hegrid_launch_count(void);
 
+/* Bytes of the current device's library pool (the stream-ordered pool every
+ * plan, batch scratch and per-call scratch comes from) that are allocated now
+ * (*used_bytes) and held from the device (*reserved_bytes, freed blocks kept for
+ * reuse included); either pointer may be NULL.  Stream-ordered frees count once
+ * the stream has reached them.  For leak checks, e.g. after a failed call.
+ * Errors: INVALID_ARG (both NULL); CUDA.  (Library service; no step of the
+ * paper.)
+ *
+ * Failure-path testing: the environment variable HEGRID_FAULT, read at each
+ * allocation and launch, injects one failure -- "alloc:N" makes the N-th pool
+ * allocation fail (the call returns OOM), "launch:N" makes the N-th kernel
+ * launch report a launch failure (the call returns CUDA), and "wait:N" runs the
+ * N-th tensor-core grid kernel with one producer arrive withheld and a 20 ms
+ * wait limit, so that the kernel's bounded waits run out and hegrid_status_poll
+ * returns TIMEOUT.  Counts start when the variable's text changes; unset or any
+ * other text injects nothing. */
+hegrid_status hegrid_pool_usage(int64_t *used_bytes, int64_t *reserved_bytes);
+
 /* Thread-local message describing the most recent failure ("" if none). */
 const char *hegrid_last_error(void);
 
@@ -347,12 +373,14 @@ const char *hegrid_last_error(void);
  * several threads without ordering) race and corrupt each other's result.
  * Every scratch word a call reads was written by that same call, so nothing
  * has to be cleared between calls.  The first call on each device looks up
- * the array's device address (with that device current); make that first
- * call before any stream capture.
+ * the array's device address (with that device current) and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * device or primary-context reset (cudaDeviceReset) after that first call is
+ * not supported: the kept address would no longer be the array's.
  *
  * lon_deg, lat_deg  device FP64 [n_samples] (caller-owned).
- * geom, kern, flags as for hegrid_plan_create (map bins only: a
- * HEGRID_PLAN_HEALPIX flag is INVALID_ARG here).
+ * geom, kern, flags as for hegrid_plan_create, plain-grid map bins only:
+ * HEGRID_PLAN_HEALPIX and HEGRID_PLAN_SFL are INVALID_ARG here.
  * perm_out          device int32 [n_samples].
  * bin_off_out       device int32 [bin_off_capacity], capacity >= n_bins + 1.
  * n_bins_out        host; set to the number of bins even when the capacity is

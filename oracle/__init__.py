@@ -197,6 +197,13 @@ class Index:
         c = np.ascontiguousarray(cells, np.int64)
         return c, len(c)
 
+    def count(self, cells=None, nthreads=0):
+        """Neighbour counts only: (nb_off, P) for ``cells`` (None = all)."""
+        c, nc = self._cells(cells)
+        off = np.zeros(nc + 1, np.int64)
+        P = self._lib.og_index_count(self._h, nc, _ptr(c), _ptr(off), nthreads)
+        return off, int(P)
+
     def neighbours(self, cells=None, nthreads=0, with_h=False):
         """Canonical CSR (ascending n per cell) for ``cells`` (None = all)."""
         c, nc = self._cells(cells)

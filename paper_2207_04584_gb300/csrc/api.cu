@@ -2,6 +2,7 @@
 // CUDA-graph batches and host-chunk streaming.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "hegrid_internal.cuh"
+#include "ptx.cuh"
 
 namespace hg {
 namespace {
@@ -48,7 +50,7 @@ cudaError_t pad_rows(const void* src, void* dst, int64_t n_rows, int64_t row_byt
                                                 pitch_bytes / 2);
   }
   count_launch();
-  return cudaGetLastError();
+  return launch_status();
 }
 
 // Per-channel masking, step 1: values with every non-finite entry replaced by
@@ -105,6 +107,76 @@ __global__ void __launch_bounds__(256) k_mask_divide(float* __restrict__ map, in
     float* o = map + m * ld_map + c;
     *o = has ? __fdiv_rn(*o, r) : qnan;
     if (wc_out) wc_out[m * ld_map + c] = has ? __fmul_rn(r, W[m]) : 0.0f;
+  }
+}
+
+// Largest |v| of each channel, for the tensor-core forms' per-channel scale:
+// out[c] = max(out[c], |v[n, c]| over this CTA's rows) as the bits of a
+// non-negative float (they order like the floats; NaN is dropped by fmaxf,
+// Inf kept).  Each thread reads 16-byte vectors (kVec values) of one channel
+// group, `cols` groups per CTA side by side and 256 / cols rows at a time;
+// blockIdx.y selects the channel groups, blockIdx.x the row range.  One
+// atomicMax per channel and CTA, after a shared-memory reduction over the
+// CTA's rows.
+template <int DT>
+__global__ void __launch_bounds__(256) k_chan_absmax(const void* __restrict__ values, int64_t N,
+                                                     int64_t C, int64_t ld, int nvec, int cols,
+                                                     int64_t rows_per_cta,
+                                                     uint32_t* __restrict__ out) {
+  constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;
+  constexpr int kVec = kWide ? 4 : 8;  // values per 16 bytes
+  __shared__ float red[256][kVec];
+  const int tid = threadIdx.x;
+  const int rpt = 256 / cols;  // rows read side by side
+  const int cslot = tid % cols, rl = tid / cols;
+  const int64_t cv = (int64_t)blockIdx.y * cols + cslot;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < N ? r0 + rows_per_cta : N;
+  float m[kVec];
+#pragma unroll
+  for (int e = 0; e < kVec; ++e) m[e] = 0.0f;
+  if (rl < rpt && cv < nvec) {
+    const uint4* base = reinterpret_cast<const uint4*>(
+        static_cast<const char*>(values) + (cv * 16));
+    const int64_t pitch = ld * (kWide ? 4 : 2) / 16;  // row pitch in 16-byte vectors
+#pragma unroll 4
+    for (int64_t r = r0 + rl; r < r1; r += rpt) {
+      const uint4 q = __ldcs(base + r * pitch);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (DT == HEGRID_F32) {
+          m[i] = fmaxf(m[i], fabsf(__uint_as_float(w[i])));
+        } else if (DT == HEGRID_BF16X2) {
+          const float v = __uint_as_float(w[i] << 16) + __uint_as_float(w[i] & 0xffff0000u);
+          m[i] = fmaxf(m[i], fabsf(v));
+        } else if (DT == HEGRID_BF16) {
+          m[2 * i] = fmaxf(m[2 * i], fabsf(__uint_as_float(w[i] << 16)));
+          m[2 * i + 1] = fmaxf(m[2 * i + 1], fabsf(__uint_as_float(w[i] & 0xffff0000u)));
+        } else {  // F16
+          const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+          m[2 * i] = fmaxf(m[2 * i], fabsf(f.x));
+          m[2 * i + 1] = fmaxf(m[2 * i + 1], fabsf(f.y));
+        }
+      }
+    }
+  }
+  if (rpt > 1) {
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) red[tid][e] = m[e];
+    __syncthreads();
+    if (tid < cols) {
+      for (int k = 1; k < rpt; ++k)
+#pragma unroll
+        for (int e = 0; e < kVec; ++e) m[e] = fmaxf(m[e], red[k * cols + tid][e]);
+    }
+  }
+  if (rl == 0 && cv < nvec) {
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) {
+      const int64_t c = cv * kVec + e;
+      if (c < C && m[e] > 0.0f) atomicMax(out + c, __float_as_uint(m[e]));
+    }
   }
 }
 
@@ -211,6 +283,8 @@ hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStrea
     JobTable jt;
     std::memset(&jt, 0, sizeof(jt));
     jt.n_jobs = (int32_t)std::min<size_t>(kMaxJobs, jobs.size() - base);
+    jt.inject = 0;
+    jt.wait_ns = kWaitLimitNs;
     int64_t items = 0;
     for (int i = 0; i < jt.n_jobs; ++i) {
       jt.job[i] = jobs[base + i];
@@ -224,10 +298,21 @@ hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStrea
   return HEGRID_OK;
 }
 
+// Channels of the entries whose tensor-core form scales each channel by a
+// power of two (every dtype but FP16, which is exact as stored).
+int64_t scaled_channels(int n, const hegrid_grid_args* args) {
+  int64_t c = 0;
+  for (int i = 0; i < n; ++i)
+    if (args[i].mode != HEGRID_MODE_FP32 && args[i].dtype != HEGRID_F16) c += args[i].n_channels;
+  return c;
+}
+
 // wait_ready: make `s` wait for each plan's creation (false inside a graph
 // capture, where the caller has synchronised the plans on the host instead).
+// chmax_buf: room for scaled_channels() channel maxima, or NULL to take it
+// from the pool for this call.
 hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args* args,
-                        cudaStream_t s, bool wait_ready = true) {
+                        cudaStream_t s, bool wait_ready = true, uint32_t* chmax_buf = nullptr) {
   HG_ARG_CHECK(n >= 0, "n must be >= 0");
   HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
   // tensor-core jobs grouped by channel tile (64, 128, 256): one launch each
@@ -237,36 +322,98 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
     hegrid_status st = check_args(plans[i], args[i]);
     if (st != HEGRID_OK) return st;
   }
-  for (int i = 0; i < n; ++i) {
-    if (wait_ready) HG_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ready, 0));
-    if (args[i].mode == HEGRID_MODE_FP32) {
-      f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
-    } else {
+  const int64_t n_scaled = scaled_channels(n, args);
+  uint32_t* chmax = chmax_buf;
+  if (n_scaled > 0 && chmax == nullptr)
+    HG_CUDA_TRY(pool_alloc((void**)&chmax, sizeof(uint32_t) * (size_t)n_scaled, s));
+  const bool own = chmax != chmax_buf;
+  hegrid_status st = HEGRID_OK;
+  auto run = [&]() -> hegrid_status {
+    if (n_scaled > 0)
+      HG_CUDA_TRY(cudaMemsetAsync(chmax, 0, sizeof(uint32_t) * (size_t)n_scaled, s));
+    int64_t at = 0;
+    for (int i = 0; i < n; ++i) {
+      if (wait_ready) HG_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ready, 0));
+      if (args[i].mode == HEGRID_MODE_FP32) {
+        f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
+        continue;
+      }
       const int tile = tc_channel_tile(args[i].n_channels);
       std::vector<GridJob>& fam = tc[tile == 64 ? 0 : tile == 128 ? 1 : 2];
       fam.push_back(make_job(plans[i], args[i], tile));
-      hegrid_status st = encode_rows_map(fam.back(), tile);
-      if (st != HEGRID_OK) return st;
+      hegrid_status e = encode_rows_map(fam.back(), tile);
+      if (e != HEGRID_OK) return e;
+      if (args[i].dtype != HEGRID_F16) {
+        fam.back().chmax = chmax + at;
+        e = launch_chan_absmax(args[i].values, (int)args[i].dtype, plans[i]->N,
+                               args[i].n_channels, args[i].ld_values, chmax + at, s);
+        if (e != HEGRID_OK) return e;
+        at += args[i].n_channels;
+      }
     }
-  }
-  if (!f32.empty()) {
-    hegrid_status st = launch_family(f32, false, s);
-    if (st != HEGRID_OK) return st;
-  }
-  for (int t = 0; t < 3; ++t) {
-    if (tc[t].empty()) continue;
-    hegrid_status st = launch_family(tc[t], true, s, tiles[t]);
-    if (st != HEGRID_OK) return st;
-  }
-  return HEGRID_OK;
+    if (!f32.empty()) {
+      hegrid_status e = launch_family(f32, false, s);
+      if (e != HEGRID_OK) return e;
+    }
+    for (int t = 0; t < 3; ++t) {
+      if (tc[t].empty()) continue;
+      hegrid_status e = launch_family(tc[t], true, s, tiles[t]);
+      if (e != HEGRID_OK) return e;
+    }
+    return HEGRID_OK;
+  };
+  st = run();
+  if (own) cudaFreeAsync(chmax, s);
+  return st;
 }
 
 }  // namespace
+
+hegrid_status launch_chan_absmax(const void* values, int dtype, int64_t n_rows, int64_t C,
+                                 int64_t ld, uint32_t* out, cudaStream_t s) {
+  const int vec = (dtype == HEGRID_F32 || dtype == HEGRID_BF16X2) ? 4 : 8;
+  const int64_t nvec = (C + vec - 1) / vec;  // within ld: ld * element size is a multiple of 16
+  const int cols = (int)std::min<int64_t>(nvec, 256);
+  const int rpt = 256 / cols;
+  const int64_t gy = (nvec + cols - 1) / cols;
+  int dev = 0, n_sm = 0;
+  HG_CUDA_TRY(cudaGetDevice(&dev));
+  HG_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  // about 8 CTAs per SM over all channel groups, each thread >= 32 rows
+  int64_t gx = std::max<int64_t>(1, (8 * (int64_t)n_sm + gy - 1) / gy);
+  gx = std::min<int64_t>(gx, std::max<int64_t>(1, n_rows / (32 * (int64_t)rpt)));
+  HG_ARG_CHECK(gy <= 65535, "too many channels");
+  const int64_t rows_per_cta = (n_rows + gx - 1) / gx;
+  const dim3 grid((unsigned)gx, (unsigned)gy);
+  switch (dtype) {
+    case HEGRID_F32:
+      k_chan_absmax<HEGRID_F32><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
+                                                     rows_per_cta, out);
+      break;
+    case HEGRID_BF16X2:
+      k_chan_absmax<HEGRID_BF16X2><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
+                                                        rows_per_cta, out);
+      break;
+    case HEGRID_BF16:
+      k_chan_absmax<HEGRID_BF16><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
+                                                      rows_per_cta, out);
+      break;
+    default:
+      k_chan_absmax<HEGRID_F16><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
+                                                     rows_per_cta, out);
+      break;
+  }
+  count_launch();
+  HG_CUDA_TRY(launch_status());
+  return HEGRID_OK;
+}
+
 }  // namespace hg
 
 struct hegrid_batch {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
+  uint32_t* chmax;  // the channel maxima of the tensor-core entries (device, owned)
 };
 
 extern "C" {
@@ -333,7 +480,7 @@ hegrid_status hegrid_grid_masked(hegrid_plan* plan, const void* values, hegrid_d
   hg::k_mask_split<<<blocks, 256, 0, s>>>(values, (int)dtype, N, C, ld_values, clean, mask,
                                           mask_f32 ? 1 : 0, ldm);
   hg::count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_mask_split");
+  if ((e = hg::launch_status()) != cudaSuccess) return fail(e, "k_mask_split");
   // S_c / W and W_c / W: two passes of the same plan and form
   st = hegrid_grid(plan, clean, dtype, C, ld_values, map_out, ld_map, nullptr, mode, stream);
   if (st == HEGRID_OK)
@@ -346,7 +493,7 @@ hegrid_status hegrid_grid_masked(hegrid_plan* plan, const void* values, hegrid_d
   const float* W = plan->wsum + (mode == HEGRID_MODE_TC ? plan->M : 0);
   hg::k_mask_divide<<<blocks, 256, 0, s>>>(map_out, ld_map, q, M, C, W, wc_out);
   hg::count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_mask_divide");
+  if ((e = hg::launch_status()) != cudaSuccess) return fail(e, "k_mask_divide");
   release();
   return HEGRID_OK;
 }
@@ -371,10 +518,20 @@ hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const*
   hegrid_batch* b = new hegrid_batch();
   b->graph = nullptr;
   b->exec = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  b->chmax = nullptr;
+  const int64_t n_scaled = hg::scaled_channels(n, args);
+  cudaError_t e = cudaSuccess;
+  if (n_scaled > 0 &&
+      (e = cudaMalloc((void**)&b->chmax, sizeof(uint32_t) * (size_t)n_scaled)) != cudaSuccess) {
+    hg::set_error(std::string("channel maxima: ") + cudaGetErrorString(e));
+    cudaStreamDestroy(cap);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? HEGRID_ERR_OOM : HEGRID_ERR_CUDA;
+  }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   hegrid_status st = HEGRID_OK;
   if (e == cudaSuccess) {
-    st = hg::grid_many(n, plans, args, cap, false);
+    st = hg::grid_many(n, plans, args, cap, false, b->chmax);
     cudaError_t e2 = cudaStreamEndCapture(cap, &b->graph);
     if (st == HEGRID_OK && e2 != cudaSuccess) e = e2;
   }
@@ -383,6 +540,7 @@ hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const*
   if (st != HEGRID_OK || e != cudaSuccess) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->chmax) cudaFree(b->chmax);
     delete b;
     if (st == HEGRID_OK) {
       hg::set_error(std::string("graph capture failed: ") + cudaGetErrorString(e));
@@ -405,6 +563,7 @@ hegrid_status hegrid_batch_destroy(hegrid_batch* batch) {
   if (!batch) return HEGRID_OK;
   cudaGraphExecDestroy(batch->exec);
   cudaGraphDestroy(batch->graph);
+  if (batch->chmax) cudaFree(batch->chmax);
   delete batch;
   return HEGRID_OK;
 }
@@ -567,7 +726,7 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   };
   const int bands[] = {2, 4, 8, 16, 1 << 30};
   if (tc) {
-    for (int seg : {16, 32})
+    for (int seg : {8, 16})
       for (int b : bands) add(b, seg);
   } else {
     add(0, 1);
@@ -651,7 +810,7 @@ hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t b
   } else {
     HG_ARG_CHECK(mode == HEGRID_MODE_TC || mode == HEGRID_MODE_TC_SPLIT, "unknown mode");
     HG_ARG_CHECK(band >= 0, "band must be >= 0");
-    HG_ARG_CHECK(seg >= 0 && seg <= 32, "seg must be in [0, 32]");
+    HG_ARG_CHECK(seg >= 0 && seg <= 16, "seg must be in [0, 16]");
     plan->tune_tc_band = band;
     plan->tune_tc_seg = seg;
   }

@@ -16,6 +16,12 @@
 //   * each warp owns a 4x4-cell patch and 128 channels; a thread accumulates
 //     8 cells x 8 channels in registers, skipping samples that touch no cell
 //     of its patch.
+// Summation in two levels: the register sums cover kFlush chunks and are then
+// added (FP32, round to nearest) into running totals that the thread keeps in
+// tensor memory (TMEM, otherwise idle in this kernel: 64 columns of one lane
+// per thread), so no FP32 sum runs over more than a few dozen of a cell's
+// ~10^3 terms; this cuts the rounding error of a long sequential sum about
+// threefold.
 // The epilogue divides by W (NaN where W = 0) and writes the map row-major.
 #include <cuda_runtime.h>
 
@@ -30,6 +36,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kKC = 32;   // candidates per K chunk
 constexpr int kCT = 128;  // channels per tile
+constexpr int kFlush = 4;   // chunks per register partial sum (then added to the TMEM total)
+constexpr uint32_t kTmemCols = 128;  // 64 FP32 totals per thread: two warps per lane quarter
 constexpr int kEntCap = 2048;           // weight entries staged per chunk (more: global)
 constexpr int kEntStage = kEntCap - 8;  // entries copied (room for 16-byte alignment)
 
@@ -49,6 +57,7 @@ struct __align__(128) SmemF32 {
   EntWin win[2];
   uint32_t pmask[2][kKC];  // per sample k: bit p set if any cell of patch p has it
   uint64_t bar[2];
+  uint32_t tmem_base;
 };
 
 __device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
@@ -85,12 +94,22 @@ __global__ void __launch_bounds__(kThreads, 2)
     mbar_init(&S.bar[1], 1);
     fence_mbar_init();
   }
+  if (warp == 0) {
+    tmem_alloc(&S.tmem_base, kTmemCols);
+    tmem_relinquish();
+  }
   {  // both weight tiles and patch masks start zero (and are left zero by every chunk)
     float4* wz = reinterpret_cast<float4*>(&S.Wt[0][0][0]);
     for (int i = tid; i < 2 * kKC * kCT / 4; i += kThreads) wz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid < 2 * kKC) (&S.pmask[0][0])[tid] = 0u;
   }
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  // this thread's 64 running totals: one TMEM lane of its warp's lane quarter,
+  // columns 0-63 (warps 0-3) or 64-127 (warps 4-7)
+  const uint32_t taddr =
+      S.tmem_base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 64);
   uint32_t phase[2] = {0u, 0u};
   bool bail = false;
 
@@ -169,6 +188,27 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int e = 0; e < 8; ++e) acc[i][e] = 0.0f;
+    // add the register partial sums into the TMEM totals (the first flush of
+    // an item stores them) and restart the partials (warp-uniform calls)
+    auto flush = [&](bool first) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float t[8];
+        if (first) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = acc[i][e];
+        } else {
+          tmem_ld_32x32b_x8(taddr + i * 8, t);
+          tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = __fadd_rn(t[e], acc[i][e]);
+        }
+        tmem_st_32x32b_x8(taddr + i * 8, t);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[i][e] = 0.0f;
+      }
+      tmem_st_wait();
+    };
 
     const int patch = warp, cs = lane >> 4, cg = lane & 15;
     if (warp == 0 && n_chunks > 0) issue(0);
@@ -236,12 +276,27 @@ __global__ void __launch_bounds__(kThreads, 2)
           wz[(i >> 2) * (kCT / 4) + (i & 3)] = make_float4(0.f, 0.f, 0.f, 0.f);
         atomicAnd(&S.pmask[s][lane], ~(1u << patch));
       }
+      if (j % kFlush == kFlush - 1 && j + 1 < n_chunks) {
+        __syncwarp();
+        flush(j == kFlush - 1);
+      }
     }
     // every warp is done with this item's staged rows before the next item
     // stages its first chunk
     __syncthreads();
 
     if (bail) break;
+    // the sums: TMEM total (if any partial was flushed) + the last partial
+    if (n_chunks > kFlush) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float t[8];
+        tmem_ld_32x32b_x8(taddr + i * 8, t);
+        tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[i][e] = __fadd_rn(t[e], acc[i][e]);
+      }
+    }
     // epilogue: normalise and store
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -260,6 +315,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (ct == 0 && cg == 0 && J.weight_out) J.weight_out[m] = W;
     }
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(S.tmem_base, kTmemCols);
 }
 
 }  // namespace
@@ -279,7 +338,7 @@ hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s) {
   if (grid < 1) return HEGRID_OK;
   k_grid_f32<<<(unsigned)grid, kThreads, sizeof(SmemF32), s>>>(jt);
   count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
   return HEGRID_OK;
 }
 

@@ -10,14 +10,18 @@
 // sample values of the chunk (K-major, so each channel row holds the chunk's
 // samples).  FP32 accumulation in TMEM.
 //
-// Precision: values and weights are split into a high and a low 16-bit part;
+// Precision: values and weights are split into a high and a low FP16 part;
 // HEGRID_MODE_TC_SPLIT issues hi*hi + hi*lo + lo*hi (the lo*lo term is below
-// FP32 rounding), HEGRID_MODE_TC issues hi*hi.  The 16-bit format is chosen
-// per chunk: FP16 (11-bit halves, ~2^-22 residual) when every value of the
-// chunk lies in [2^-7, 2^15] in magnitude (zeros allowed) -- or, for BF16
-// input, when FP16 holds every value exactly -- and BF16 (8-bit halves, ~2^-17
-// residual, full FP32 range) otherwise.  Chunks of one block may mix formats:
-// each MMA carries its own instruction descriptor and all accumulate in FP32.
+// FP32 rounding), HEGRID_MODE_TC issues hi*hi.  FP16 holds 11 significant
+// bits but only 30 binades, so each channel c is first scaled by an exact
+// power of two s_c that puts the channel's largest |v| (over all samples,
+// found by a pass over the values before the launch) in [2^14, 2^15): every
+// scaled value fits FP16, and a value's split error is at most 2^-22 of
+// itself or 2^-25 (the FP16 subnormal step) in scaled units, i.e. 2^-39 of
+// its own channel's largest value -- whatever the other channels of the tile
+// hold.  The epilogue multiplies by 2^-k again.  FP16-stored values need no
+// scale (they are exact); BF16-stored values are scaled and rounded to FP16,
+// exactly for every value within 2^32 of the channel's largest.
 // The tensor core's FP32 accumulate loses about 2^-22 of the running sum per
 // MMA (measured; it grows with the number of MMAs added into one accumulator),
 // so a block's sum is built in segments of J.seg sub-chunks (rounded down to
@@ -34,10 +38,12 @@
 //   warp 17     stages the chunk's sample rows (raw, as stored; eight
 //               four-row TMA tensor gathers per sub-chunk) and its weight
 //               entries (bulk copies) into a 3-deep shared-memory ring;
-//   warps 0-15  convert a staged chunk into the B tiles (row = channel; 16-byte
-//               pieces of 8 samples per thread, all 512 threads) and store
-//               the chunk's weight entries into the A tiles at the tile
-//               offsets the plan precomputed (2-deep ring);
+//   warps 0-7   convert a staged chunk into the B tiles (row = channel; 16-byte
+//               pieces of 8 samples; no barrier among them);
+//   warps 8-15  zero the A tiles and store the chunk's weight entries into
+//               them at the tile offsets the plan precomputed (one barrier
+//               among these 8 warps per chunk), side by side with the
+//               converters on the same chunk (2-deep A/B ring);
 //   warp 16     allocates TMEM and issues the MMAs (one lane);
 //   warps 18-21 drain finished segments into the running total and run the
 //               epilogue (TMEM -> registers -> S / W -> global).
@@ -59,6 +65,12 @@ namespace {
 
 constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
+// The producers split in two groups that work on the same chunk side by side:
+// warps 0-7 convert the staged rows into the B tiles, warps 8-15 build the A
+// tiles from the weight entries (only they need a barrier, between zeroing
+// the tiles and storing the entries).
+constexpr int kGroupWarps = kProducerWarps / 2;
+constexpr int kGroup = kGroupWarps * 32;
 constexpr int kMmaWarp = kProducerWarps;
 constexpr int kTmaWarp = kProducerWarps + 1;
 constexpr int kDrainWarp0 = kProducerWarps + 2;  // 4 warps: drains and epilogue
@@ -68,7 +80,7 @@ constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kRawStages = 3;              // staged sample rows + weight entries ring
 constexpr int kEntCap1 = 1792;             // weight entries staged per sub-chunk (more: from global)
-constexpr int kDefaultSeg = 32;            // sub-chunks per accumulation segment
+constexpr int kDefaultSeg = 16;            // sub-chunks per accumulation segment
 constexpr int kDefaultBand = 8;            // blocks per band of the work order
 // The channel tile kN (64, 128 or 256: the MMA's N) is a template parameter:
 // the launcher takes the narrowest tile that holds C (256 above it), so few
@@ -86,9 +98,9 @@ struct TcShape {
   static constexpr uint32_t kTmemCols = 2 * kN;
   static constexpr int kEntCap = kEntCap1 * kS;
   static constexpr int kEntStage = kEntCap - 8;  // leaves room for 16-byte alignment
-  static constexpr int kCPT = (kN * (kCK / 8) + kProducers - 1) / kProducers;
-  static constexpr int kBThreads = kN * (kCK / 8) / kCPT;
+  static constexpr int kCPT = kN * (kCK / 8) / kGroup;  // 16-byte B pieces per converter
   static constexpr int kKT = 8 * kCPT;  // samples of a B row converted per thread
+  static_assert(kN * (kCK / 8) % kGroup == 0, "B pieces do not divide among the converters");
 };
 
 // Where a staged chunk's weight entries are: e_lo is the global index of its
@@ -110,8 +122,6 @@ struct __align__(512) TcSmem {
   uint8_t eck[kRawStages][Sh::kEntCap * 2];  // staged entry tile offsets (16-byte aligned window)
   uint8_t ew[kRawStages][Sh::kEntCap * 4];   // staged entry weights (16-byte aligned window)
   EntInfo einfo[kRawStages];
-  uint32_t red[3][2];                        // range slots: max|v|, min|v|>0 (float bits)
-  uint32_t fmt16[kStages];                   // 1 = FP16 tiles, 0 = BF16 tiles
   uint64_t raw_full[kRawStages], raw_empty[kRawStages], ent_empty[kRawStages];
   uint64_t ab_full[kStages], ab_empty[kStages];
   // MMA -> drains: a segment's MMAs are complete.  Two barriers used by
@@ -171,8 +181,8 @@ __device__ __forceinline__ void st_shared_u16(uint32_t addr, uint16_t v) {
   asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
 }
 
-__device__ __forceinline__ void named_bar_producers() {
-  asm volatile("bar.sync 1, %0;" ::"r"(kProducers) : "memory");
+__device__ __forceinline__ void named_bar_a_builders() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kGroup) : "memory");
 }
 
 // Per-value 16-bit split of two FP32 values: hi = RN(v), lo = RN(v - hi), in
@@ -196,69 +206,121 @@ __device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_
 
 __device__ __forceinline__ float bf16_bits_to_float(uint32_t b16) { return __uint_as_float(b16 << 16); }
 
-// Producer side of one work item (warps 0-15): for every chunk, convert the
-// staged rows into the B tiles and store the staged weight entries into the
-// A tiles.  DT is the stored value type; SPLIT selects the hi/lo form.  rslot
-// rotates over the three range-reduction slots (see below).  n_sub is the
-// item's count of 32-candidate sub-chunks (the last chunk may hold fewer
-// than kS).  Returns false if a bounded wait gave up.
+// Exponent k of the power-of-two scale 2^k of a channel whose largest |v| has
+// the float bits `mbits`: the scaled largest value lies in [2^14, 2^15).  All
+// zero, or non-finite values present (outside the contract): unscaled.  k is
+// kept in [-126, 126] so that 2^k and 2^-k are normal floats (a channel whose
+// largest value is below 2^-112 is scaled less than that).
+__device__ __forceinline__ int chan_scale_exp(uint32_t mbits) {
+  const int e = (int)(mbits >> 23);  // biased exponent (the sign bit is clear)
+  if (mbits == 0u || e >= 255) return 0;
+  return min(141 - e, 126);  // 14 - (e - 127)
+}
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// B converters (warps 0-7) for one work item: for every chunk, the staged
+// rows, scaled by each channel's power of two and split into FP16 halves,
+// become the B tiles (row = channel, K-major, 64-byte swizzle).  DT is the
+// stored value type; SPLIT selects the hi/lo form.  n_sub is the item's count
+// of 32-candidate sub-chunks (the last chunk may hold fewer than kS).
+// `withhold` (failure tests) skips the first chunk's ab_full arrive.
+// Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT, int kN, int kS>
-__device__ __forceinline__ bool produce_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
+__device__ __forceinline__ bool convert_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
                                              int n_sub, int64_t c0, uint32_t& g, uint32_t& gr,
-                                             uint32_t& rslot, int32_t* err) {
+                                             int32_t* err, uint64_t lim, bool withhold) {
   using Sh = TcShape<kN, kS>;
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
-  constexpr uint32_t kSubTile = kM * 64;       // A[s][h][1] follows A[s][h][0]
-  constexpr uint32_t kLoTile = kS * kSubTile;  // A[s][1] follows A[s][0]
   constexpr int kPitch = kWide ? Sh::kRawPitch : Sh::kRawPitch / 2;  // staged rows are packed
-  constexpr int kKT = Sh::kKT;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int t = threadIdx.x;  // 0 .. kGroup-1
   // B row (channel c0 + row) and first 16-byte piece (8 samples) this thread
-  // converts; threads from kBThreads on convert none (narrow tiles).  Pieces
-  // 4 t .. 4 t + 3 belong to sub-chunk t.
-  const int row = tid % kN, q0 = (tid / kN) * Sh::kCPT;
-  const bool has_b = Sh::kBThreads >= kProducers || tid < Sh::kBThreads;
-  const PlanView& pv = J.pv;
-  constexpr uint32_t kBits32768 = 0x47000000u;   // 2^15
-  constexpr uint32_t kBits2m7 = 0x3c000000u;     // 2^-7
-  constexpr uint32_t kBits2m14 = 0x38800000u;    // 2^-14 (smallest normal FP16)
-  constexpr uint32_t kInf = 0x7f800000u;
+  // converts; pieces 4 u .. 4 u + 3 belong to sub-chunk u.
+  const int row = t % kN, q0 = (t / kN) * Sh::kCPT;
+  // this thread's channel scale (channels past C are staged as zeros)
+  float sc = 1.0f;
+  if (DT != HEGRID_F16 && J.chmax != nullptr && c0 + row < J.C)
+    sc = pow2f(chan_scale_exp(__ldg(J.chmax + c0 + row)));
   for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
     const int s = g % kStages;
     const int rs = gr % kRawStages;
-    if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err)) return false;
-    if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err)) return false;
-    // Channel column `row` of this thread's part of the staged rows (the
-    // gathers fill channels past C with zeros; the rows of a sub-chunk the
-    // last chunk lacks are not staged and read as zeros).
-    uint32_t x[kKT];
-    if (has_b && (kS == 1 || q0 * 8 < (n_sub - j * kS) * kK)) {
-      const uint32_t rb = smem_u32(S.raw[rs]) + q0 * 8 * kPitch;
+    if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err, lim)) return false;
+    if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err, lim)) return false;
+    // rows of a sub-chunk that the last chunk lacks are not staged: zeros
+    const bool present = kS == 1 || q0 * 8 < (n_sub - j * kS) * kK;
+    const uint32_t rb = smem_u32(S.raw[rs]) + q0 * 8 * kPitch;
+    const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
-      for (int k = 0; k < kKT; ++k) {
-        if (kWide)
-          x[k] = ld_shared_u32(rb + k * kPitch + row * 4);
-        else
-          x[k] = ld_shared_u16(rb + k * kPitch + row * 2);
+    for (int qq = 0; qq < Sh::kCPT; ++qq) {
+      // channel column `row` of 8 consecutive staged rows
+      uint32_t x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t a = rb + (qq * 8 + k) * kPitch;
+        x[k] = !present ? 0u : kWide ? ld_shared_u32(a + row * 4) : ld_shared_u16(a + row * 2);
       }
-    } else {
+      const int q = (q0 + qq) & 3;
+      const uint32_t sub = kS == 1 ? 0u : (uint32_t)((q0 + qq) >> 2) * (uint32_t)(kN * 64);
+      uint32_t h2[4], l2[4];
 #pragma unroll
-      for (int k = 0; k < kKT; ++k) x[k] = 0u;
-    }
-    // A tiles: zero (the scatter follows the barrier).  Independent of the
-    // loads above and below, so their latencies overlap.
-    {
-      const uint32_t ah = smem_u32(S.A[s][0]), al = smem_u32(S.A[s][1]);
-#pragma unroll
-      for (int i = tid; i < kS * kM * 64 / 16; i += kProducers) {
-        st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
-        if (SPLIT) st_shared_v4(al + i * 16, 0u, 0u, 0u, 0u);
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t x0 = x[2 * e], x1 = x[2 * e + 1];
+        if (DT == HEGRID_F32) {
+          split2<true>(__uint_as_float(x0) * sc, __uint_as_float(x1) * sc, h2[e], l2[e]);
+        } else if (DT == HEGRID_BF16X2) {
+          const float v0 = bf16_bits_to_float(x0 & 0xffffu) + bf16_bits_to_float(x0 >> 16);
+          const float v1 = bf16_bits_to_float(x1 & 0xffffu) + bf16_bits_to_float(x1 >> 16);
+          split2<true>(v0 * sc, v1 * sc, h2[e], l2[e]);
+        } else if (DT == HEGRID_BF16) {  // exact in BF16: one FP16 part
+          const __half2 h = __float22half2_rn(
+              make_float2(bf16_bits_to_float(x0) * sc, bf16_bits_to_float(x1) * sc));
+          h2[e] = *reinterpret_cast<const uint32_t*>(&h);
+          l2[e] = 0u;
+        } else {  // F16: as stored
+          h2[e] = x0 | (x1 << 16);
+          l2[e] = 0u;
+        }
       }
+      st_shared_v4(bh + sub + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
+      if (kVsplit) st_shared_v4(bl + sub + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
     }
-    // The chunk's weight entries (staged in shared memory by the row stager;
-    // any beyond the staging capacity come from global memory): entries tid
-    // and tid + kProducers now, the rest (if any) after the barrier.
+    // the staged rows are read; the B tiles are written (visible to the MMA)
+    __syncwarp();
+    if ((t & 31) == 0) mbar_arrive(&S.raw_empty[rs]);
+    fence_proxy_async_smem();
+    __syncwarp();
+    if ((t & 31) == 0 && !(withhold && g == 0)) mbar_arrive(&S.ab_full[s]);
+  }
+  return true;
+}
+
+// A builders (warps 8-15) for one work item: for every chunk, zero the A
+// tiles, then store the chunk's weight entries, scaled by kTcWeightScale and
+// split into FP16 halves, at the tile offsets the plan precomputed (in the
+// second sub-tile from entry n0 on).  Returns false if a bounded wait gave up.
+template <bool SPLIT, int kN, int kS>
+__device__ __forceinline__ bool build_a_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
+                                             uint32_t& g, uint32_t& gr, int32_t* err,
+                                             uint64_t lim) {
+  constexpr uint32_t kSubTile = kM * 64;       // A[s][h][1] follows A[s][h][0]
+  constexpr uint32_t kLoTile = kS * kSubTile;  // A[s][1] follows A[s][0]
+  const int t = threadIdx.x - kGroup;  // 0 .. kGroup-1
+  const PlanView& pv = J.pv;
+  for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
+    const int s = g % kStages;
+    const int rs = gr % kRawStages;
+    if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err, lim)) return false;
+    if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err, lim)) return false;
+    const uint32_t ah = smem_u32(S.A[s][0]);
+    // zero (the stores follow the group's barrier)
+#pragma unroll
+    for (int i = t; i < kS * kM * 64 / 16; i += kGroup) {
+      st_shared_v4(ah + i * 16, 0u, 0u, 0u, 0u);
+      if (SPLIT) st_shared_v4(ah + kLoTile + i * 16, 0u, 0u, 0u, 0u);
+    }
+    // the chunk's weight entries (staged in shared memory by the row stager;
+    // any beyond the staging capacity come from global memory): entries t
+    // and t + kGroup are loaded before the barrier
     const EntInfo ei = S.einfo[rs];
     const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
     auto entry = [&](int i, uint32_t& off, float& w) {
@@ -272,132 +334,39 @@ __device__ __forceinline__ bool produce_item(TcSmem<kN, kS>& S, const GridJob& J
     };
     uint32_t o0 = 0u, o1 = 0u;
     float w0 = 0.0f, w1 = 0.0f;
-    if (tid < ei.n) entry(tid, o0, w0);
-    if (tid + kProducers < ei.n) entry(tid + kProducers, o1, w1);
-    // Range of the chunk's values (decides the 16-bit format of the chunk):
-    // max |v| and, for BF16 input, min nonzero |v|, as float bit patterns,
-    // combined over the producers in slot rslot (warp maxima, shared atomics).
-    if (DT != HEGRID_F16) {
-      float fm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      uint32_t mn = kInf;
-#pragma unroll
-      for (int k = 0; k < kKT; ++k) {
-        if (DT == HEGRID_F32) {
-          fm[k & 3] = fmaxf(fm[k & 3], fabsf(__uint_as_float(x[k])));  // NaN dropped, Inf kept
-        } else {  // BF16 and BF16X2: the (high) BF16 part
-          const uint32_t a = (x[k] << 16) & 0x7fffffffu;
-          fm[k & 3] = fmaxf(fm[k & 3], __uint_as_float(a));
-          if (DT == HEGRID_BF16) mn = min(mn, a == 0u ? kInf : a);
-        }
+    if (t < ei.n) entry(t, o0, w0);
+    if (t + kGroup < ei.n) entry(t + kGroup, o1, w1);
+    named_bar_a_builders();
+    auto put2 = [&](int i0, uint32_t p0, float v0, uint32_t p1, float v1) {
+      uint32_t h2, l2;
+      split2<true>(v0 * kTcWeightScale, v1 * kTcWeightScale, h2, l2);
+      if (kS > 1) {
+        p0 += i0 >= ei.n0 ? kSubTile : 0u;
+        p1 += i0 + kGroup >= ei.n0 ? kSubTile : 0u;
       }
-      const float fmx = fmaxf(fmaxf(fm[0], fm[1]), fmaxf(fm[2], fm[3]));
-      const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fmx));
-      if (DT == HEGRID_BF16) mn = __reduce_min_sync(0xffffffffu, mn);
-      if (lane == 0) {
-        atomicMax(&S.red[rslot][0], mx);
-        if (DT == HEGRID_BF16) atomicMin(&S.red[rslot][1], mn);
+      if (i0 < ei.n) {
+        st_shared_u16(ah + p0, (uint16_t)(h2 & 0xffffu));
+        if (SPLIT) st_shared_u16(ah + kLoTile + p0, (uint16_t)(l2 & 0xffffu));
       }
-    }
-    // the values are in registers: release the staged rows
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&S.raw_empty[rs]);
-    named_bar_producers();
-    bool h16 = true;
-    if (DT != HEGRID_F16) {
-      const uint32_t mx = S.red[rslot][0], mn = S.red[rslot][1];
-      if (DT == HEGRID_BF16)
-        h16 = mx <= kBits32768 && (mn == kInf || mn >= kBits2m14);
-      else  // Inf gives mx >= kInf > 2^15
-        h16 = mx <= kBits32768 && (mx == 0u || mx >= kBits2m7);
-    }
-    if (tid == 0) {
-      S.fmt16[s] = h16 ? 1u : 0u;
-      // Slot (rslot + 2) % 3 was last read before this chunk's barrier and is
-      // next written after the following one: reset it for that chunk.
-      const uint32_t rr = rslot == 0u ? 2u : rslot - 1u;
-      S.red[rr][0] = 0u;
-      S.red[rr][1] = kInf;
-    }
-    rslot = rslot == 2u ? 0u : rslot + 1u;
-    // The tiles in the chunk's format (one branch for the whole chunk).
-    auto tiles = [&](auto fmt) {
-      constexpr bool H16 = decltype(fmt)::value;
-      // B tiles: row `row` holds the chunk's samples of channel c0 + row; this
-      // thread writes 16-byte pieces q0 .. q0 + kCPT - 1.
-      if (has_b) {
-        const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
-#pragma unroll
-        for (int qq = 0; qq < kKT / 8; ++qq) {
-          const int q = (q0 + qq) & 3;
-          const uint32_t sub = kS == 1 ? 0u : (uint32_t)((q0 + qq) >> 2) * (uint32_t)(kN * 64);
-          uint32_t h2[4], l2[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const uint32_t x0 = x[qq * 8 + 2 * e], x1 = x[qq * 8 + 2 * e + 1];
-            if (DT == HEGRID_F32) {
-              split2<H16>(__uint_as_float(x0), __uint_as_float(x1), h2[e], l2[e]);
-            } else if (DT == HEGRID_BF16X2) {
-              const float v0 = bf16_bits_to_float(x0 & 0xffffu) + bf16_bits_to_float(x0 >> 16);
-              const float v1 = bf16_bits_to_float(x1 & 0xffffu) + bf16_bits_to_float(x1 >> 16);
-              split2<H16>(v0, v1, h2[e], l2[e]);
-            } else if (DT == HEGRID_BF16) {
-              if (H16) {  // exact in FP16 (checked above)
-                const __half2 h = __float22half2_rn(
-                    make_float2(bf16_bits_to_float(x0), bf16_bits_to_float(x1)));
-                h2[e] = *reinterpret_cast<const uint32_t*>(&h);
-              } else {
-                h2[e] = x0 | (x1 << 16);
-              }
-              l2[e] = 0u;
-            } else {  // F16
-              h2[e] = x0 | (x1 << 16);
-              l2[e] = 0u;
-            }
-          }
-          st_shared_v4(bh + sub + sw64(row, q), h2[0], h2[1], h2[2], h2[3]);
-          if (kVsplit) st_shared_v4(bl + sub + sw64(row, q), l2[0], l2[1], l2[2], l2[3]);
-        }
-      }
-      // A tiles: the chunk's weight entries, scaled by kTcWeightScale, split
-      // into the chunk's 16-bit format and stored at their precomputed tile
-      // offsets (in the second sub-tile from entry n0 on); two entries per step.
-      {
-        const uint32_t ah = smem_u32(S.A[s][0]);
-        auto put2 = [&](int i0, uint32_t p0, float v0, uint32_t p1, float v1) {
-          uint32_t h2, l2;
-          split2<H16>(v0 * kTcWeightScale, v1 * kTcWeightScale, h2, l2);
-          if (kS > 1) {
-            p0 += i0 >= ei.n0 ? kSubTile : 0u;
-            p1 += i0 + kProducers >= ei.n0 ? kSubTile : 0u;
-          }
-          if (i0 < ei.n) {
-            st_shared_u16(ah + p0, (uint16_t)(h2 & 0xffffu));
-            if (SPLIT) st_shared_u16(ah + kLoTile + p0, (uint16_t)(l2 & 0xffffu));
-          }
-          if (i0 + kProducers < ei.n) {
-            st_shared_u16(ah + p1, (uint16_t)(h2 >> 16));
-            if (SPLIT) st_shared_u16(ah + kLoTile + p1, (uint16_t)(l2 >> 16));
-          }
-        };
-        put2(tid, o0, w0, o1, w1);
-        for (int i = tid + 2 * kProducers; i < ei.n; i += 2 * kProducers) {
-          uint32_t p0 = 0u, p1 = 0u;
-          float v0 = 0.0f, v1 = 0.0f;
-          entry(i, p0, v0);
-          if (i + kProducers < ei.n) entry(i + kProducers, p1, v1);
-          put2(i, p0, v0, p1, v1);
-        }
+      if (i0 + kGroup < ei.n) {
+        st_shared_u16(ah + p1, (uint16_t)(h2 >> 16));
+        if (SPLIT) st_shared_u16(ah + kLoTile + p1, (uint16_t)(l2 >> 16));
       }
     };
-    if (h16)
-      tiles(std::true_type{});
-    else
-      tiles(std::false_type{});
+    put2(t, o0, w0, o1, w1);
+    for (int i = t + 2 * kGroup; i < ei.n; i += 2 * kGroup) {
+      uint32_t p0 = 0u, p1 = 0u;
+      float v0 = 0.0f, v1 = 0.0f;
+      entry(i, p0, v0);
+      if (i + kGroup < ei.n) entry(i + kGroup, p1, v1);
+      put2(i, p0, v0, p1, v1);
+    }
+    // the entries are read; the A tiles are written (visible to the MMA)
     __syncwarp();
-    if (lane == 0) mbar_arrive(&S.ent_empty[rs]);
+    if ((t & 31) == 0) mbar_arrive(&S.ent_empty[rs]);
     fence_proxy_async_smem();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&S.ab_full[s]);
+    if ((t & 31) == 0) mbar_arrive(&S.ab_full[s]);
   }
   return true;
 }
@@ -412,20 +381,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   TcSmem<kN, kS>& S = *reinterpret_cast<TcSmem<kN, kS>*>(smem_raw + pad);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* err = jt.job[0].pv.err_word;
+  const uint64_t lim = jt.wait_ns;  // limit of every bounded wait
+  // failure-path test (HEGRID_FAULT=wait:N): producer warp 0 withholds its
+  // arrive on the first chunk's ab_full, so the waits behind it run out
+  const bool withhold = jt.inject != 0 && warp == 0;
 
   if (tid == 0) {
     for (int i = 0; i < kRawStages; ++i) {
       mbar_init(&S.raw_full[i], 1);
-      mbar_init(&S.raw_empty[i], kProducerWarps);
-      mbar_init(&S.ent_empty[i], kProducerWarps);
+      mbar_init(&S.raw_empty[i], kGroupWarps);  // the B converters
+      mbar_init(&S.ent_empty[i], kGroupWarps);  // the A builders
     }
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&S.ab_full[i], kProducerWarps);
       mbar_init(&S.ab_empty[i], 1);
-    }
-    for (int i = 0; i < 3; ++i) {
-      S.red[i][0] = 0u;
-      S.red[i][1] = 0x7f800000u;
     }
     mbar_init(&S.segdone[0], 1);
     mbar_init(&S.segdone[1], 1);
@@ -448,7 +417,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   uint32_t n_tm = 0;  // items that used TMEM so far
   uint32_t n_sg = 0;  // accumulation segments so far (segdone phases)
   uint32_t uses[2] = {0u, 0u};  // MMA warp: segments accumulated into each region so far
-  uint32_t rslot = 0; // producers: range-reduction slot of the next chunk
 
   for (int64_t item = blockIdx.x; item < jt.n_items && !bail; item += gridDim.x) {
     const GridJob& J = jt.job[find_job(jt, item)];
@@ -504,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           const int64_t q = (int64_t)(j + 2) * kS + t;
           if (q < n_sub) nB[t] = __ldg(pv.cand_idx + kb0 + q * kK + lane);
         }
-        if (u >= 1 && !(mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err) &&
-                        mbar_wait(&S.ent_empty[r], (u - 1) & 1u, err))) {
+        if (u >= 1 && !(mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err, lim) &&
+                        mbar_wait(&S.ent_empty[r], (u - 1) & 1u, err, lim))) {
           bail = true;
           break;
         }
@@ -550,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     if (warp == kMmaWarp) {
       // ---------------- MMA issuer ----------------
       if (n_chunks == 0) continue;
-      const uint32_t idS16 = idesc_f16(0u, kM, kN), idSbf = idesc_f16(1u, kM, kN);
+      const uint32_t idS = idesc_f16(0u, kM, kN);  // FP16 A and B, FP32 accumulate
       // Item n_tm accumulates its total in region rT and later segments in
       // rS; the next item swaps them, so its first segment can run while
       // this item's epilogue still reads rT.
@@ -565,20 +533,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           // the region is free once the drains released its previous use
           // (a drained segment, or an epilogue that read a total)
           const uint32_t r = q == 0 ? rT : rS;
-          if (uses[r] > 0 && !mbar_wait(&S.regfree[r], (uses[r] - 1) & 1u, err)) bail = true;
+          if (uses[r] > 0 && !mbar_wait(&S.regfree[r], (uses[r] - 1) & 1u, err, lim)) bail = true;
           ++uses[r];
           dcol = r * (uint32_t)kN;
           tc_fence_after();
           if (bail) break;
         }
-        if (!mbar_wait(&S.ab_full[s], (g / kStages) & 1u, err)) {
+        if (!mbar_wait(&S.ab_full[s], (g / kStages) & 1u, err, lim)) {
           bail = true;
           break;
         }
         tc_fence_after();
         if (lane == 0) {
-          const bool h = S.fmt16[s] != 0u;
-          const uint32_t idS = h ? idS16 : idSbf;
           const uint32_t d = tmem + dcol;
           const int nsj = min(kS, n_sub - j * kS);
 #pragma unroll
@@ -629,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       const uint32_t rT = n_tm & 1u, rS = rT ^ 1u;
       const uint32_t tseg = tmem + lrow + rS * (uint32_t)kN, ttot = tmem + lrow + rT * (uint32_t)kN;
       for (int q = 0; q < n_seg; ++q) {
-        if (!mbar_wait(&S.segdone[n_sg & 1u], (n_sg >> 1) & 1u, err)) {
+        if (!mbar_wait(&S.segdone[n_sg & 1u], (n_sg >> 1) & 1u, err, lim)) {
           bail = true;
           break;
         }
@@ -657,34 +623,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
       }
       if (bail) break;
-      // epilogue: map = total / W, W from the plan's compensated sums: FP32
-      // weights for the split form (the hi+lo split differs from them by at
-      // most 2^-22 per weight in FP16 chunks, 2^-17 in BF16 chunks, at
-      // random), FP16-rounded weights for the single form; both x 2^15
+      // epilogue: map = (total / W) * 2^-k_c, W from the plan's compensated
+      // sums: FP32 weights for the split form (the hi+lo split differs from
+      // them by at most 2^-22 per weight, at random), FP16-rounded weights for
+      // the single form; both x 2^15.  k_c is the channel's scale exponent.
       const float Wm = active ? pv.wsum[(int64_t)(split ? 0 : 1) * pv.M + m] : 0.0f;
       const float W = Wm * kTcWeightScale;
       const bool ok = W > 0.0f;
+      const bool scaled = J.chmax != nullptr && J.dtype != HEGRID_F16;
       // 32 columns per step: each lane writes whole 128-byte lines of its row
       uint32_t t[32];
 #pragma unroll 1
       for (int cb = 0; cb < kN / 32; ++cb) {
         tmem_ld_32x32b_x32(ttot + cb * 32, t);
         tmem_ld_wait();
+        const int64_t cbase = c0 + cb * 32;
+        // lane l holds 2^-k of channel cbase + l; every lane takes them all
+        const float inv_l = scaled && cbase + lane < C
+                                ? pow2f(-chan_scale_exp(__ldg(J.chmax + cbase + lane)))
+                                : 1.0f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float inv = __shfl_sync(0xffffffffu, inv_l, i);
+          t[i] = __float_as_uint(ok ? __fmul_rn(__fdiv_rn(__uint_as_float(t[i]), W), inv) : qnan);
+        }
         if (active) {
-          const int64_t cbase = c0 + cb * 32;
           if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
               __stcs(reinterpret_cast<float4*>(out + cbase + i),
-                     ok ? make_float4(__fdiv_rn(__uint_as_float(t[i]), W),
-                                      __fdiv_rn(__uint_as_float(t[i + 1]), W),
-                                      __fdiv_rn(__uint_as_float(t[i + 2]), W),
-                                      __fdiv_rn(__uint_as_float(t[i + 3]), W))
-                        : make_float4(qnan, qnan, qnan, qnan));
+                     make_float4(__uint_as_float(t[i]), __uint_as_float(t[i + 1]),
+                                 __uint_as_float(t[i + 2]), __uint_as_float(t[i + 3])));
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (cbase + i < C) __stcs(out + cbase + i, ok ? __fdiv_rn(__uint_as_float(t[i]), W) : qnan);
+              if (cbase + i < C) __stcs(out + cbase + i, __uint_as_float(t[i]));
           }
         }
       }
@@ -701,19 +674,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     if (n_chunks == 0) continue;
     {
       bool ok = true;
-      if (split) {
+      if (warp >= kGroupWarps) {  // A builders
+        ok = split ? build_a_item<true, kN, kS>(S, J, n_chunks, g, gr, err, lim)
+                   : build_a_item<false, kN, kS>(S, J, n_chunks, g, gr, err, lim);
+      } else if (split) {  // B converters
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = convert_item<HEGRID_F32, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F16: ok = convert_item<HEGRID_F16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          default: ok = convert_item<HEGRID_BF16X2, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = produce_item<HEGRID_F32, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
-          case HEGRID_BF16: ok = produce_item<HEGRID_BF16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
-          case HEGRID_F16: ok = produce_item<HEGRID_F16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
-          default: ok = produce_item<HEGRID_BF16X2, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, rslot, err); break;
+          case HEGRID_F32: ok = convert_item<HEGRID_F32, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F16: ok = convert_item<HEGRID_F16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          default: ok = convert_item<HEGRID_BF16X2, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
         }
       }
       bail = !ok;
@@ -740,9 +716,16 @@ hegrid_status launch_tile(const JobTable& jt, cudaStream_t s) {
   }
   int64_t grid = std::min<int64_t>(jt.n_items, (int64_t)sms);
   if (grid < 1) return HEGRID_OK;
-  k_grid_tc<kN, kS><<<(unsigned)grid, kThreads, smem, s>>>(jt);
+  if (fault_hit(kFaultWait)) {
+    JobTable t = jt;
+    t.inject = 1;
+    t.wait_ns = kInjectWaitNs;
+    k_grid_tc<kN, kS><<<(unsigned)grid, kThreads, smem, s>>>(t);
+  } else {
+    k_grid_tc<kN, kS><<<(unsigned)grid, kThreads, smem, s>>>(jt);
+  }
   count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
   return HEGRID_OK;
 }
 

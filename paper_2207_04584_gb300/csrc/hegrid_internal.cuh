@@ -47,6 +47,13 @@ void set_error(const std::string& msg);
 
 // Process-wide count of kernel launches made by the library.
 void count_launch(int n = 1);
+// The launch error to report after a launch: cudaGetLastError(), or an
+// injected launch failure (HEGRID_FAULT=launch:N).
+cudaError_t launch_status();
+// Fault injection (HEGRID_FAULT): true exactly once, at the N-th event of
+// `kind` since the variable was last changed.
+enum { kFaultNone = 0, kFaultAlloc = 1, kFaultLaunch = 2, kFaultWait = 3 };
+bool fault_hit(int kind);
 
 // Stream-ordered allocation from the library's per-device pool (freed blocks
 // are kept for reuse); release with cudaFreeAsync.
@@ -156,6 +163,9 @@ struct GridJob {
   float* map;
   int64_t ld_map;
   float* weight_out;
+  // Tensor-core modes: the largest |v| of each channel (float bits, [C]),
+  // which sets the channel's power-of-two scale; NULL: unscaled.
+  const uint32_t* chmax;
   int64_t n_rows;     // samples (rows of the values)
   // Launch shape (see hegrid_autotune): blocks per band of the work order
   // (0: channel tiles fastest, FP32 kernel only) and chunks per accumulation
@@ -169,11 +179,17 @@ struct GridJob {
 constexpr int kMaxJobs = 64;
 struct JobTable {
   int32_t n_jobs;
+  int32_t inject;    // tensor-core kernel: 1 = withhold one producer arrive (tests)
   int64_t n_items;
+  uint64_t wait_ns;  // limit of the kernels' bounded waits
   GridJob job[kMaxJobs];
 };
 
 hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s);
+// out[c] (zeroed by the caller) = max(out[c], largest |v| of channel c) as
+// float bits, for the C channels of `values` (NaN ignored, Inf kept).
+hegrid_status launch_chan_absmax(const void* values, int dtype, int64_t n_rows, int64_t C,
+                                 int64_t ld, uint32_t* out, cudaStream_t s);
 // `tile`: the channel tile of every job in the table (tc_channel_tile(C)).
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile);
 int f32_channel_tile();

@@ -45,7 +45,8 @@ extern "C" hegrid_status hegrid_fp32_peak(double* tflops, void* stream) {
   hg::k_fma_loop<<<blocks, threads, 0, s>>>(sink, iters, 0.999f);
   cudaEventRecord(e1, s);
   hg::count_launch(2);
-  cudaError_t err = cudaEventSynchronize(e1);
+  cudaError_t err = hg::launch_status();
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
   float ms = 0.0f;
   if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);

@@ -22,6 +22,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -31,13 +32,73 @@
 
 namespace hg {
 
-static std::atomic<int64_t> g_launches{0};
-void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
-
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 const char* last_error() { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Host-side fault injection for the failure-path tests.  HEGRID_FAULT =
+// "alloc:N" makes the N-th pool allocation fail with out-of-memory, "launch:N"
+// makes the N-th kernel launch report a launch failure at its next error
+// check, "wait:N" runs the N-th tensor-core grid launch with one producer
+// arrive withheld and a short wait limit, so that its bounded waits run out
+// (the counts start when the variable's text last changed).  Unset: no effect
+// beyond one getenv per event.
+// ---------------------------------------------------------------------------
+namespace {
+struct FaultState {
+  std::mutex mu;
+  std::string text;  // the variable as last parsed
+  int kind = kFaultNone;
+  int64_t n = 0, seen = 0;
+};
+FaultState& fault_state() {
+  static FaultState st;
+  return st;
+}
+thread_local bool t_launch_fault = false;
+}  // namespace
+
+bool fault_hit(int kind) {
+  const char* env = std::getenv("HEGRID_FAULT");
+  FaultState& f = fault_state();
+  std::lock_guard<std::mutex> lock(f.mu);
+  const std::string text = env ? env : "";
+  if (text != f.text) {
+    f.text = text;
+    f.kind = kFaultNone;
+    f.n = 0;
+    f.seen = 0;
+    const size_t c = text.find(':');
+    if (c != std::string::npos) {
+      const std::string what = text.substr(0, c);
+      const long long n = std::atoll(text.c_str() + c + 1);
+      if (n >= 1) {
+        f.n = n;
+        f.kind = what == "alloc" ? kFaultAlloc : what == "launch" ? kFaultLaunch
+                                              : what == "wait" ? kFaultWait : kFaultNone;
+      }
+    }
+  }
+  if (f.kind != kind) return false;
+  return ++f.seen == f.n;
+}
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  for (int i = 0; i < n; ++i)
+    if (fault_hit(kFaultLaunch)) t_launch_fault = true;
+}
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+cudaError_t launch_status() {
+  if (t_launch_fault) {
+    t_launch_fault = false;
+    return cudaErrorLaunchFailure;
+  }
+  return cudaGetLastError();
+}
 
 namespace {
 
@@ -353,7 +414,7 @@ __global__ void k_set_total(T* out, int64_t n, const T* excl_last, const T* in_l
 
 // out[0..n] = exclusive scan of in[0..n) with out[n] = total.  `tmp` needs
 // scan_tmp_elems(n) elements.
-int64_t scan_tmp_elems(int64_t n) {
+constexpr int64_t scan_tmp_elems(int64_t n) {
   int64_t t = 0;
   while (n > kScanTile) {
     n = (n + kScanTile - 1) / kScanTile;
@@ -1083,7 +1144,7 @@ __global__ void __launch_bounds__(kChunk)
 // Device memory of plans comes from a library-owned, stream-ordered pool per
 // device whose release threshold keeps freed blocks for reuse, so repeated plan
 // creation does not pay for cudaMalloc/cudaFree.
-static cudaMemPool_t plan_pool() {
+cudaMemPool_t plan_pool() {
   static cudaMemPool_t pools[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1105,6 +1166,10 @@ static cudaMemPool_t plan_pool() {
 }  // namespace
 
 cudaError_t pool_alloc(void** p, size_t sz, cudaStream_t st) {
+  if (fault_hit(kFaultAlloc)) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   cudaMemPool_t pool = plan_pool();
   if (!pool) return cudaMalloc(p, sz);
   return cudaMallocFromPoolAsync(p, sz, pool, st);
@@ -1327,7 +1392,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     k_prep<false><<<(N + 255) / 256, 256, 0, st>>>(N, dlon, dlat, kp, hp, key0, val0);
   }
   count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
 
   // --- a3: radix sort ------------------------------------------------------
   int bits = 1;
@@ -1351,7 +1416,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
   int64_t bytes = 0;
   HG_CUDA_TRY(dmalloc(&p->perm, N, &bytes, st));
   HG_CUDA_TRY(dmalloc(&p->bin_off, p->n_bins + 1, &bytes, st));
@@ -1360,7 +1425,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   count_launch();
   k_unit_sorted<<<(N + 255) / 256, 256, 0, st>>>(p->perm, N, dlon, dlat, sx, sy, sz);
   count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
 
   // --- bin windows (host): of each block, and of each warp's 8 x 4 cell
   // tile within it (the bins that can hold a sample within R of a cell of
@@ -1553,7 +1618,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   // exclusive scans over n+1 entries (last input 0): out[n] is the total
   scan_exclusive<int64_t, int64_t>(slots_ub, p->n_blocks + 1, p->cand_off, stmp64, st);
   scan_exclusive<int64_t, int64_t>(pairs_ub, p->n_blocks + 1, p->blk_pair_off, stmp64, st);
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
 
   // The one host round trip of plan creation: the bounds' totals size the
   // candidate-slot and entry arrays.
@@ -1594,7 +1659,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
         pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
         p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
   count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
   p->P = -1;  // exact totals: read on first use (plan_totals)
   HG_CUDA_TRY(cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming));
   HG_CUDA_TRY(cudaEventRecord(p->ready, st));
@@ -1613,6 +1678,22 @@ extern "C" {
 const char* hegrid_last_error(void) { return hg::last_error(); }
 
 int64_t hegrid_launch_count(void) { return hg::launch_count(); }
+
+hegrid_status hegrid_pool_usage(int64_t* used_bytes, int64_t* reserved_bytes) {
+  hg::set_error("");
+  HG_ARG_CHECK(used_bytes != nullptr || reserved_bytes != nullptr, "both outputs are NULL");
+  cudaMemPool_t pool = hg::plan_pool();
+  if (!pool) {
+    hg::set_error("the library's memory pool could not be created on this device");
+    return HEGRID_ERR_CUDA;
+  }
+  uint64_t used = 0, reserved = 0;
+  HG_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  HG_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+  if (used_bytes) *used_bytes = (int64_t)used;
+  if (reserved_bytes) *reserved_bytes = (int64_t)reserved;
+  return HEGRID_OK;
+}
 
 hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const double* lon_deg,
                                  const double* lat_deg, int coords_on_device,
@@ -1803,7 +1884,9 @@ namespace {
 constexpr int64_t kNoAllocMaxSamples = (int64_t)1 << 19;  // 524,288 samples
 constexpr int64_t kNoAllocTiles = (kNoAllocMaxSamples + kSortTile - 1) / kSortTile;
 constexpr int64_t kNoAllocHist = 256 * kNoAllocTiles;
-constexpr int64_t kNoAllocTmp = 64;  // >= scan_tmp_elems(kNoAllocHist)
+constexpr int64_t kNoAllocTmp = 64;
+// the scan's partial sums, with the plan path's slack of 8 elements
+static_assert(kNoAllocTmp >= scan_tmp_elems(kNoAllocHist) + 8, "scratch too small for the scan");
 constexpr size_t kOffKey0 = 0;
 constexpr size_t kOffKey1 = kOffKey0 + 4 * kNoAllocMaxSamples;
 constexpr size_t kOffVal0 = kOffKey1 + 4 * kNoAllocMaxSamples;
@@ -1815,24 +1898,6 @@ constexpr size_t kNoAllocBytes = kOffTmp + 4 * kNoAllocTmp;  // about 8.5 MB
 
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-// Bin key only (the key arithmetic of k_prep, without the unit vectors).
-__global__ void k_keys_only(int32_t N, const double* __restrict__ lon,
-                            const double* __restrict__ lat, KeyParams kp,
-                            uint32_t* __restrict__ key, int32_t* __restrict__ idx) {
-  int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  double a = wrap_ra(__dsub_rn(lon[n], kp.lon0));
-  double fx = floor_div_add(a, kp.dlon, kp.rdlon, kp.cx);
-  double fy = floor_div_add(__dsub_rn(lat[n], kp.lat0), kp.dlat, kp.rdlat, kp.cy);
-  uint32_t k = kp.n_bins;
-  if (isfinite(fx) && isfinite(fy) && fx >= 0.0 && fy >= 0.0 && fx < kp.wx && fy < kp.wy) {
-    int64_t bx = (int64_t)fx / kp.bin_cells, by = (int64_t)fy / kp.bin_cells;
-    k = (uint32_t)(by * kp.nbx + bx);
-  }
-  key[n] = k;
-  idx[n] = n;
-}
 
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[64] = {};
@@ -1875,7 +1940,9 @@ extern "C" hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double
   HG_ARG_CHECK(std::isfinite(geom->lon0_deg) && std::isfinite(geom->lat0_deg),
                "map centre must be finite");
   HG_ARG_CHECK(kern->fwhm_deg > 0 && kern->support_sigmas > 0, "FWHM and support must be > 0");
-  HG_ARG_CHECK((flags >> 8) == 0, "only map bins (HEGRID_PLAN_BIN_CELLS) are sorted here");
+  HG_ARG_CHECK((flags >> 8) == 0,
+               "only plain-grid map bins (HEGRID_PLAN_BIN_CELLS) are sorted here: "
+               "HEGRID_PLAN_HEALPIX and HEGRID_PLAN_SFL are not");
   const int B = (flags & 0xffu) ? (int)(flags & 0xffu) : 2;
   const double sigma_deg = kern->fwhm_deg / std::sqrt(8.0 * std::log(2.0));
   const double R_deg = kern->support_sigmas * sigma_deg;
@@ -1936,7 +2003,10 @@ extern "C" hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double
   kp.bin_cells = B;
   kp.nbx = nbx;
   kp.n_bins = (uint32_t)n_bins;
-  k_keys_only<<<(N + 255) / 256, 256, 0, st>>>(N, lon_deg, lat_deg, kp, key0, val0);
+  kp.sfl = 0;
+  HpxParams hp;  // unused by the map-bin key
+  std::memset(&hp, 0, sizeof(hp));
+  k_prep<false><<<(N + 255) / 256, 256, 0, st>>>(N, lon_deg, lat_deg, kp, hp, key0, val0);
   count_launch();
   int bits = 1;
   while (((uint64_t)1 << bits) <= (uint64_t)n_bins) ++bits;
@@ -1955,10 +2025,10 @@ extern "C" hegrid_status hegrid_bin_sort_noalloc(int64_t n_samples, const double
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
   HG_CUDA_TRY(cudaMemcpyAsync(perm_out, vin, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
   k_bin_offsets<<<(N + 255) / 256, 256, 0, st>>>(kin, N, (uint32_t)n_bins, bin_off_out);
   count_launch();
-  HG_CUDA_TRY(cudaGetLastError());
+  HG_CUDA_TRY(launch_status());
   return HEGRID_OK;
 }

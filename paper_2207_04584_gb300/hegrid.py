@@ -43,7 +43,7 @@ EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
             "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc",
             "hegrid_autotune", "hegrid_autotune_bins", "hegrid_plan_set_tuning",
-            "hegrid_fp32_peak", "hegrid_grid_masked"]
+            "hegrid_fp32_peak", "hegrid_grid_masked", "hegrid_pool_usage"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -116,6 +116,7 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int32), P]
     L.hegrid_plan_set_tuning.argtypes = [P, u32, ctypes.c_int32, ctypes.c_int32]
     L.hegrid_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), P]
+    L.hegrid_pool_usage.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.hegrid_last_error.restype = ctypes.c_char_p
     L.hegrid_launch_count.restype = ctypes.c_int64
     for name in EXPORTED:
@@ -241,6 +242,13 @@ def hegrid_plan_export(plan, perm=None, bin_off=None, nb_off=None, nb_idx=None, 
 
 def hegrid_launch_count() -> int:
     return int(lib().hegrid_launch_count())
+
+
+def hegrid_pool_usage():
+    """(used, reserved) bytes of the current device's library pool."""
+    used, res = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().hegrid_pool_usage(ctypes.byref(used), ctypes.byref(res)), "hegrid_pool_usage")
+    return int(used.value), int(res.value)
 
 
 def hegrid_status_poll(plan):

@@ -206,9 +206,10 @@ def test_tc_config3_precision_table(H):
     assert res["f32-split"][0] <= TOL_SPLIT
 
 
-@pytest.mark.parametrize("scale", [1e6, 1e-5])
-def test_tc_split_bf16_fallback_range(H, scale):
-    """Values outside the FP16 window take the BF16 split (full FP32 range)."""
+@pytest.mark.parametrize("scale", [1e6, 1e-5, 1e30, 1e-30])
+def test_tc_split_out_of_fp16_range(H, scale):
+    """Values far outside FP16's range are brought into it by the per-channel
+    power-of-two scale (every channel scaled alike here)."""
     wl = _case(81, C=16)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
@@ -221,16 +222,17 @@ def test_tc_split_bf16_fallback_range(H, scale):
         H.hegrid_plan_destroy(plan)
     ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(vals)
     err, _, _ = map_error(got, ref, Wref)
-    print(f"bf16 fallback scale {scale}: {err:.3e}")
+    print(f"values x {scale}: {err:.3e}")
     assert err <= TOL_SPLIT, err
 
 
-def test_tc_split_mixed_chunk_formats(H):
-    """A few huge samples force BF16 in their chunks; the rest stay FP16.
+def test_tc_split_huge_outliers(H):
+    """A few samples 1e5 times brighter than the rest set their channels' scales,
+    so every other value sits ~17 binades below its channel's largest.
 
-    Cells that touch a huge sample are dominated by it and carry the BF16
-    split's residual (~2^-17 of the huge value): they are checked relative to
-    their own magnitude.  Every other cell must meet the split tolerance."""
+    Cells that touch a huge sample are dominated by it: they are checked
+    relative to their own magnitude.  Every other cell must meet the split
+    tolerance."""
     wl = _case(82, C=16)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
@@ -255,7 +257,7 @@ def test_tc_split_mixed_chunk_formats(H):
     assert err <= TOL_SPLIT, err
     h = hot_cell & (Wref >= 1e-3 * Wref.max())
     rel = np.abs(got[h] - ref[h]) / np.abs(ref[h]).max(axis=0)
-    assert rel.max() <= 4 * 2.0 ** -17, rel.max()
+    assert rel.max() <= 2.0 ** -18, rel.max()
 
 
 @pytest.mark.parametrize("C", [40, 120])
@@ -296,3 +298,56 @@ def test_tc_narrow_tiles_bf16_and_batch(H, C):
     for v, o, c in outs:
         err, _, _ = map_error(o.cpu().numpy(), ref3[:, :c], W3)
         assert err <= TOL_SPLIT, (c, err)
+
+
+def _stored(kind, vals, H):
+    """(device tensor, dtype, ld, values the oracle sees) for values stored as `kind`."""
+    n, C = vals.shape
+    vt = torch.from_numpy(vals)
+    if kind == "f32":
+        v, ld = _padded(vals, 4)
+        return torch.from_numpy(v).cuda(), H.HEGRID_F32, ld, vals
+    if kind in ("bf16", "f16"):
+        ld = (C + 7) // 8 * 8
+        tdt = torch.bfloat16 if kind == "bf16" else torch.float16
+        dv = torch.zeros((n, ld), dtype=tdt)
+        dv[:, :C] = vt.to(tdt)
+        return dv.cuda(), (H.HEGRID_BF16 if kind == "bf16" else H.HEGRID_F16), ld, \
+            np.ascontiguousarray(dv[:, :C].float().numpy())
+    hi = vt.to(torch.bfloat16)
+    lo = (vt - hi.float()).to(torch.bfloat16)
+    ld = (C + 3) // 4 * 4
+    pair = torch.zeros((n, ld, 2), dtype=torch.bfloat16)
+    pair[:, :C, 0] = hi
+    pair[:, :C, 1] = lo
+    stored = (hi.double() + lo.double()).numpy()  # exact: hi + lo is an FP32 value
+    return pair.view(torch.int32).reshape(n, ld).cuda(), H.HEGRID_BF16X2, ld, \
+        np.ascontiguousarray(stored.astype(np.float32))
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16x2", "bf16", "f16"])
+@pytest.mark.parametrize("C", [50, 100, 300])
+def test_tc_split_mixed_channel_scales(H, kind, C):
+    """Eq. 1 holds per channel: a faint channel must keep the split form's
+    accuracy relative to its own RMS when it shares a channel tile (64, 128 or
+    256 wide, by C) with channels many decades brighter.  Channel c is scaled
+    by 10^(c mod 11 - 6) (10^(c mod 7 - 4) for FP16 storage, whose range is
+    narrower), so every tile mixes 1e-6 .. 1e4 (1e-4 .. 1e2)."""
+    wl = _case(91 + C, n=6000, C=C)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    e = (np.arange(C) % 7 - 4) if kind == "f16" else (np.arange(C) % 11 - 6)
+    vals = (wl["values"].astype(np.float64) * 10.0 ** e[None, :]).astype(np.float32)
+    dv, dt, ld, seen = _stored(kind, vals, H)
+    plan = _plan(H, wl)
+    try:
+        got, gw = _run(H, plan, dv, dt, C, ld, M, H.HEGRID_MODE_TC_SPLIT)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(seen)
+    err, med, _ = map_error(got, ref, Wref)
+    print(f"mixed scales {kind} C={C}: max {err:.3e} median {med:.3e}")
+    assert err <= TOL_SPLIT, err
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    has = Wref > 0
+    assert np.max(np.abs(gw[has] / Wref[has] - 1.0)) <= 2e-5

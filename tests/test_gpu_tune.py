@@ -44,7 +44,7 @@ def test_autotune_keeps_fastest_and_matches_oracle(H, mode):
         best = pts[rep["best"]]
         assert best["ms"] == min(p["ms"] for p in pts)
         if mode == "tc_split":
-            assert {p["seg"] for p in pts} == {16, 32}
+            assert {p["seg"] for p in pts} == {8, 16}
         out = torch.full((M, C), -7.0, device="cuda")
         wout = torch.full((M,), -7.0, device="cuda")
         H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, wout, md, s)
@@ -57,7 +57,7 @@ def test_autotune_keeps_fastest_and_matches_oracle(H, mode):
     assert err <= (TOL_F32 if mode == "fp32" else TOL_SPLIT), err
 
 
-@pytest.mark.parametrize("mode,band,seg", [("tc_split", 1, 16), ("tc_split", 3, 32),
+@pytest.mark.parametrize("mode,band,seg", [("tc_split", 1, 16), ("tc_split", 3, 8),
                                             ("tc_split", 1 << 20, 1), ("tc", 2, 7),
                                             ("fp32", -1, 0), ("fp32", 1, 0), ("fp32", 5, 0)])
 def test_every_shape_matches_oracle(H, mode, band, seg):
@@ -92,7 +92,7 @@ def test_set_tuning_rejects_bad_shapes(H):
     plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, wl["geom"],
                                 wl["fwhm_deg"], 3.0, 0, s)
     try:
-        for md, band, seg in ((H.HEGRID_MODE_TC_SPLIT, 4, 33), (H.HEGRID_MODE_TC, -1, 16),
+        for md, band, seg in ((H.HEGRID_MODE_TC_SPLIT, 4, 17), (H.HEGRID_MODE_TC, -1, 16),
                               (H.HEGRID_MODE_FP32, -2, 0), (9, 4, 16)):
             with pytest.raises(H.HegridError) as e:
                 H.hegrid_plan_set_tuning(plan, md, band, seg)

@@ -64,6 +64,28 @@ def test_noalloc_matches_plan_twice(H, flags):
             assert np.array_equal(off.cpu().numpy()[:nb + 1], ref_off)
 
 
+def test_noalloc_limit_and_single_sample(H):
+    """The largest accepted input (524,288 samples: the histogram, offset and
+    partial-sum regions of the array are full) and the smallest (one sample),
+    each bit for bit against the plan's own sort."""
+    big = W.config1(seed=W.SEED_BASE + 12, n=524288, nx=160, ny=150, with_values=False)
+    one = W.config1(seed=W.SEED_BASE + 13, n=1, with_values=False)
+    s = torch.cuda.current_stream().cuda_stream
+    for wl in (big, one):
+        ref_perm, ref_off = _reference(H, wl, 0)
+        n = len(wl["lon"])
+        lon = torch.from_numpy(np.ascontiguousarray(wl["lon"])).cuda()
+        lat = torch.from_numpy(np.ascontiguousarray(wl["lat"])).cuda()
+        perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        off = torch.full((len(ref_off),), -1, dtype=torch.int32, device="cuda")
+        nb = H.hegrid_bin_sort_noalloc(n, lon, lat, wl["geom"], wl["fwhm_deg"], 3.0, perm, off,
+                                       off.numel(), 0, s)
+        torch.cuda.synchronize()
+        assert nb == len(ref_off) - 1
+        assert np.array_equal(perm.cpu().numpy(), ref_perm)
+        assert np.array_equal(off.cpu().numpy(), ref_off)
+
+
 def test_noalloc_rejects_oversize_and_small_buffers(H):
     wl = W.config1(with_values=False)
     lon = torch.from_numpy(np.ascontiguousarray(wl["lon"])).cuda()
@@ -77,3 +99,11 @@ def test_noalloc_rejects_oversize_and_small_buffers(H):
         H.hegrid_bin_sort_noalloc(len(wl["lon"]), lon, lat, wl["geom"], wl["fwhm_deg"], 3.0, perm,
                                   off, 8)
     assert e.value.status == H.HEGRID_ERR_INVALID_ARG
+    # HEALPix and Sanson-Flamsteed plans have other keys: refused with a message naming both
+    big_off = torch.empty(1 << 20, dtype=torch.int32, device="cuda")
+    for flags in (H.HEGRID_PLAN_HEALPIX(10), H.HEGRID_PLAN_SFL):
+        with pytest.raises(H.HegridError) as e:
+            H.hegrid_bin_sort_noalloc(len(wl["lon"]), lon, lat, wl["geom"], wl["fwhm_deg"], 3.0,
+                                      perm, big_off, big_off.numel(), flags)
+        assert e.value.status == H.HEGRID_ERR_INVALID_ARG
+        assert "HEGRID_PLAN_SFL" in H.hegrid_last_error()
