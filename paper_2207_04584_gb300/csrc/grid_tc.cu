@@ -71,15 +71,15 @@ constexpr int kProducers = kProducerWarps * 32;
 // the tiles and storing the entries).
 constexpr int kGroupWarps = kProducerWarps / 2;
 constexpr int kGroup = kGroupWarps * 32;
+constexpr int kAhead = 8;  // weight entries per A builder loaded ahead of their stores
 constexpr int kMmaWarp = kProducerWarps;
 constexpr int kTmaWarp = kProducerWarps + 1;
 constexpr int kDrainWarp0 = kProducerWarps + 2;  // 4 warps: drains and epilogue
-constexpr int kThreads = (kProducerWarps + 6) * 32;
+constexpr int kEntWarp = kProducerWarps + 6;     // stages the weight entries
+constexpr int kThreads = (kProducerWarps + 7) * 32;
 constexpr int kK = 32;                     // candidates per sub-chunk (64-byte rows of 16-bit values)
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
-constexpr int kRawStages = 3;              // staged sample rows + weight entries ring
-constexpr int kEntCap1 = 1792;             // weight entries staged per sub-chunk (more: from global)
 constexpr int kDefaultSeg = 16;            // sub-chunks per accumulation segment
 constexpr int kDefaultBand = 8;            // blocks per band of the work order
 // The channel tile kN (64, 128 or 256: the MMA's N) is a template parameter:
@@ -96,7 +96,11 @@ struct TcShape {
   static constexpr int kCK = kK * kS;
   static constexpr int kRawPitch = kN * 4;
   static constexpr uint32_t kTmemCols = 2 * kN;
-  static constexpr int kEntCap = kEntCap1 * kS;
+  // staged-row ring and weight-entry ring depths, entries staged per chunk
+  // (more come from global memory): as deep and large as shared memory allows
+  static constexpr int kRawStages = kN == 256 ? 2 : kN == 128 ? 4 : 3;
+  static constexpr int kEntStages = 3;
+  static constexpr int kEntCap = 3584;
   static constexpr int kEntStage = kEntCap - 8;  // leaves room for 16-byte alignment
   static constexpr int kCPT = kN * (kCK / 8) / kGroup;  // 16-byte B pieces per converter
   static constexpr int kKT = 8 * kCPT;  // samples of a B row converted per thread
@@ -118,11 +122,12 @@ struct __align__(512) TcSmem {
   using Sh = TcShape<kN, kS>;
   uint8_t A[kStages][2][kS][kM * 64];  // [stage][hi, lo][sub-chunk]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kS][kN * 64];  // [stage][hi, lo][sub-chunk]: values, K-major, 64B swizzle
-  uint8_t raw[kRawStages][Sh::kCK * Sh::kRawPitch];  // staged sample rows as stored
-  uint8_t eck[kRawStages][Sh::kEntCap * 2];  // staged entry tile offsets (16-byte aligned window)
-  uint8_t ew[kRawStages][Sh::kEntCap * 4];   // staged entry weights (16-byte aligned window)
-  EntInfo einfo[kRawStages];
-  uint64_t raw_full[kRawStages], raw_empty[kRawStages], ent_empty[kRawStages];
+  uint8_t raw[Sh::kRawStages][Sh::kCK * Sh::kRawPitch];  // staged sample rows as stored
+  uint8_t eck[Sh::kEntStages][Sh::kEntCap * 2];  // staged entry tile offsets (16-byte aligned window)
+  uint8_t ew[Sh::kEntStages][Sh::kEntCap * 4];   // staged entry weights (16-byte aligned window)
+  EntInfo einfo[Sh::kEntStages];
+  uint64_t raw_full[Sh::kRawStages], raw_empty[Sh::kRawStages];
+  uint64_t ent_full[Sh::kEntStages], ent_empty[Sh::kEntStages];
   uint64_t ab_full[kStages], ab_empty[kStages];
   // MMA -> drains: a segment's MMAs are complete.  Two barriers used by
   // alternate segments: with the regions swapping roles per item the MMA
@@ -243,8 +248,8 @@ __device__ __forceinline__ bool convert_item(TcSmem<kN, kS>& S, const GridJob& J
     sc = pow2f(chan_scale_exp(__ldg(J.chmax + c0 + row)));
   for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
     const int s = g % kStages;
-    const int rs = gr % kRawStages;
-    if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err, lim)) return false;
+    const int rs = gr % Sh::kRawStages;
+    if (!mbar_wait(&S.raw_full[rs], (gr / Sh::kRawStages) & 1u, err, lim)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err, lim)) return false;
     // rows of a sub-chunk that the last chunk lacks are not staged: zeros
     const bool present = kS == 1 || q0 * 8 < (n_sub - j * kS) * kK;
@@ -302,14 +307,15 @@ template <bool SPLIT, int kN, int kS>
 __device__ __forceinline__ bool build_a_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
                                              uint32_t& g, uint32_t& gr, int32_t* err,
                                              uint64_t lim) {
+  using Sh = TcShape<kN, kS>;
   constexpr uint32_t kSubTile = kM * 64;       // A[s][h][1] follows A[s][h][0]
   constexpr uint32_t kLoTile = kS * kSubTile;  // A[s][1] follows A[s][0]
   const int t = threadIdx.x - kGroup;  // 0 .. kGroup-1
   const PlanView& pv = J.pv;
   for (int j = 0; j < n_chunks; ++j, ++g, ++gr) {
     const int s = g % kStages;
-    const int rs = gr % kRawStages;
-    if (!mbar_wait(&S.raw_full[rs], (gr / kRawStages) & 1u, err, lim)) return false;
+    const int rs = gr % Sh::kEntStages;
+    if (!mbar_wait(&S.ent_full[rs], (gr / Sh::kEntStages) & 1u, err, lim)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err, lim)) return false;
     const uint32_t ah = smem_u32(S.A[s][0]);
     // zero (the stores follow the group's barrier)
@@ -319,47 +325,59 @@ __device__ __forceinline__ bool build_a_item(TcSmem<kN, kS>& S, const GridJob& J
       if (SPLIT) st_shared_v4(ah + kLoTile + i * 16, 0u, 0u, 0u, 0u);
     }
     // the chunk's weight entries (staged in shared memory by the row stager;
-    // any beyond the staging capacity come from global memory): entries t
-    // and t + kGroup are loaded before the barrier
+    // any beyond the staging capacity come from global memory).  Each thread
+    // takes entries t, t + kGroup, ...; kAhead of them are loaded before the
+    // barrier and the rest kAhead at a time, every batch's loads ahead of its
+    // stores, so a dense chunk waits for global memory once per batch, not
+    // once per entry.
     const EntInfo ei = S.einfo[rs];
     const uint32_t eck = smem_u32(S.eck[rs]) + ei.ck_off, ew = smem_u32(S.ew[rs]) + ei.w_off;
-    auto entry = [&](int i, uint32_t& off, float& w) {
-      if (i < ei.ns) {
-        off = ld_shared_u16(eck + 2 * i);
-        w = __uint_as_float(ld_shared_u32(ew + 4 * i));
-      } else {
-        off = __ldg(pv.ent_ck + ei.e_lo + i);
-        w = __ldg(pv.ent_w + ei.e_lo + i);
+    uint32_t eo[kAhead];
+    float ev[kAhead];
+    auto load_batch = [&](int i0) {
+#pragma unroll
+      for (int k = 0; k < kAhead; ++k) {
+        const int i = i0 + k * kGroup;
+        eo[k] = 0u;
+        ev[k] = 0.0f;
+        if (i < ei.ns) {
+          eo[k] = ld_shared_u16(eck + 2 * i);
+          ev[k] = __uint_as_float(ld_shared_u32(ew + 4 * i));
+        } else if (i < ei.n) {
+          eo[k] = __ldg(pv.ent_ck + ei.e_lo + i);
+          ev[k] = __ldg(pv.ent_w + ei.e_lo + i);
+        }
       }
     };
-    uint32_t o0 = 0u, o1 = 0u;
-    float w0 = 0.0f, w1 = 0.0f;
-    if (t < ei.n) entry(t, o0, w0);
-    if (t + kGroup < ei.n) entry(t + kGroup, o1, w1);
+    // stores entries i0 + k kGroup (k < kAhead) of the loaded batch: scaled
+    // by kTcWeightScale, split into FP16 halves, two at a time
+    auto store_batch = [&](int i0) {
+#pragma unroll
+      for (int k = 0; k < kAhead; k += 2) {
+        const int i = i0 + k * kGroup;
+        uint32_t p0 = eo[k], p1 = eo[k + 1];
+        uint32_t h2, l2;
+        split2<true>(ev[k] * kTcWeightScale, ev[k + 1] * kTcWeightScale, h2, l2);
+        if (kS > 1) {
+          p0 += i >= ei.n0 ? kSubTile : 0u;
+          p1 += i + kGroup >= ei.n0 ? kSubTile : 0u;
+        }
+        if (i < ei.n) {
+          st_shared_u16(ah + p0, (uint16_t)(h2 & 0xffffu));
+          if (SPLIT) st_shared_u16(ah + kLoTile + p0, (uint16_t)(l2 & 0xffffu));
+        }
+        if (i + kGroup < ei.n) {
+          st_shared_u16(ah + p1, (uint16_t)(h2 >> 16));
+          if (SPLIT) st_shared_u16(ah + kLoTile + p1, (uint16_t)(l2 >> 16));
+        }
+      }
+    };
+    load_batch(t);
     named_bar_a_builders();
-    auto put2 = [&](int i0, uint32_t p0, float v0, uint32_t p1, float v1) {
-      uint32_t h2, l2;
-      split2<true>(v0 * kTcWeightScale, v1 * kTcWeightScale, h2, l2);
-      if (kS > 1) {
-        p0 += i0 >= ei.n0 ? kSubTile : 0u;
-        p1 += i0 + kGroup >= ei.n0 ? kSubTile : 0u;
-      }
-      if (i0 < ei.n) {
-        st_shared_u16(ah + p0, (uint16_t)(h2 & 0xffffu));
-        if (SPLIT) st_shared_u16(ah + kLoTile + p0, (uint16_t)(l2 & 0xffffu));
-      }
-      if (i0 + kGroup < ei.n) {
-        st_shared_u16(ah + p1, (uint16_t)(h2 >> 16));
-        if (SPLIT) st_shared_u16(ah + kLoTile + p1, (uint16_t)(l2 >> 16));
-      }
-    };
-    put2(t, o0, w0, o1, w1);
-    for (int i = t + 2 * kGroup; i < ei.n; i += 2 * kGroup) {
-      uint32_t p0 = 0u, p1 = 0u;
-      float v0 = 0.0f, v1 = 0.0f;
-      entry(i, p0, v0);
-      if (i + kGroup < ei.n) entry(i + kGroup, p1, v1);
-      put2(i, p0, v0, p1, v1);
+    store_batch(t);
+    for (int i0 = t + kAhead * kGroup; i0 < ei.n; i0 += kAhead * kGroup) {
+      load_batch(i0);
+      store_batch(i0);
     }
     // the entries are read; the A tiles are written (visible to the MMA)
     __syncwarp();
@@ -387,9 +405,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   const bool withhold = jt.inject != 0 && warp == 0;
 
   if (tid == 0) {
-    for (int i = 0; i < kRawStages; ++i) {
+    for (int i = 0; i < Sh::kRawStages; ++i) {
       mbar_init(&S.raw_full[i], 1);
       mbar_init(&S.raw_empty[i], kGroupWarps);  // the B converters
+    }
+    for (int i = 0; i < Sh::kEntStages; ++i) {
+      mbar_init(&S.ent_full[i], 1);
       mbar_init(&S.ent_empty[i], kGroupWarps);  // the A builders
     }
     for (int i = 0; i < kStages; ++i) {
@@ -455,8 +476,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       }
       int64_t sob = 0;
       for (int j = 0; j < n_chunks; ++j, ++gr) {
-        const int r = gr % kRawStages;
-        const uint32_t u = gr / kRawStages;
+        const int r = gr % Sh::kRawStages;
+        const uint32_t u = gr / Sh::kRawStages;
         const int jb = j % kBatch;
         if (jb == 0) sob = j * kS + lane <= n_sub ? __ldg(so + j * kS + lane) : 0;
         const int nsj = min(kS, n_sub - j * kS);  // sub-chunks in this chunk
@@ -472,8 +493,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           const int64_t q = (int64_t)(j + 2) * kS + t;
           if (q < n_sub) nB[t] = __ldg(pv.cand_idx + kb0 + q * kK + lane);
         }
-        if (u >= 1 && !(mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err, lim) &&
-                        mbar_wait(&S.ent_empty[r], (u - 1) & 1u, err, lim))) {
+        if (u >= 1 && !mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err, lim)) {
+          bail = true;
+          break;
+        }
+        const int ne = (int)(e_hi - e_lo);
+        const int ns = ne < Sh::kEntStage ? ne : Sh::kEntStage;
+        const int64_t a0 = (e_lo * 2) & ~(int64_t)15, b0 = (e_lo * 4) & ~(int64_t)15;
+        const uint32_t abytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 2 + 15) & ~(int64_t)15) - a0) : 0u;
+        const uint32_t wbytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 4 + 15) & ~(int64_t)15) - b0) : 0u;
+        if (lane == 0) mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * (uint32_t)(kK * nsj));
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+          const int q4 = (lane & 7) * 4;
+          const int32_t r0 = __shfl_sync(0xffffffffu, n[t], q4);
+          const int32_t r1 = __shfl_sync(0xffffffffu, n[t], q4 + 1);
+          const int32_t r2 = __shfl_sync(0xffffffffu, n[t], q4 + 2);
+          const int32_t r3 = __shfl_sync(0xffffffffu, n[t], q4 + 3);
+          if (lane < 8 && t < nsj)
+            tma_gather4(&S.raw[r][(t * kK + lane * 4) * row_bytes], tmap, (int32_t)c0, r0, r1, r2,
+                        r3, &S.raw_full[r]);
+        }
+      }
+      continue;
+    }
+
+    if (warp == kEntWarp) {
+      // ---------------- entry stager ----------------
+      constexpr int kBatch = 31 / kS;
+      const int64_t* __restrict__ so = pv.sub_off + kb0 / kK;
+      int64_t sob = 0;
+      for (int j = 0; j < n_chunks; ++j, ++gr) {
+        const int r = gr % Sh::kEntStages;
+        const uint32_t u = gr / Sh::kEntStages;
+        const int jb = j % kBatch;
+        if (jb == 0) sob = j * kS + lane <= n_sub ? __ldg(so + j * kS + lane) : 0;
+        const int nsj = min(kS, n_sub - j * kS);  // sub-chunks in this chunk
+        const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb * kS);
+        const int64_t e_mid = kS == 1 ? e_lo : __shfl_sync(0xffffffffu, sob, jb * kS + 1);
+        const int64_t e_end = __shfl_sync(0xffffffffu, sob, jb * kS + kS);
+        const int64_t e_hi = nsj == kS ? e_end : e_mid;
+        if (u >= 1 && !mbar_wait(&S.ent_empty[r], (u - 1) & 1u, err, lim)) {
           bail = true;
           break;
         }
@@ -491,26 +552,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
           ei.ck_off = (uint32_t)(e_lo * 2 - a0);
           ei.w_off = (uint32_t)(e_lo * 4 - b0);
           S.einfo[r] = ei;
-          mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * (uint32_t)(kK * nsj) + abytes + wbytes);
+          mbar_arrive_expect_tx(&S.ent_full[r], abytes + wbytes);
         }
         __syncwarp();
-#pragma unroll
-        for (int t = 0; t < kS; ++t) {
-          const int q4 = (lane & 7) * 4;
-          const int32_t r0 = __shfl_sync(0xffffffffu, n[t], q4);
-          const int32_t r1 = __shfl_sync(0xffffffffu, n[t], q4 + 1);
-          const int32_t r2 = __shfl_sync(0xffffffffu, n[t], q4 + 2);
-          const int32_t r3 = __shfl_sync(0xffffffffu, n[t], q4 + 3);
-          if (lane < 8 && t < nsj)
-            tma_gather4(&S.raw[r][(t * kK + lane * 4) * row_bytes], tmap, (int32_t)c0, r0, r1, r2,
-                        r3, &S.raw_full[r]);
-        }
         if (lane == 0 && abytes)
           bulk_g2s(S.eck[r], reinterpret_cast<const uint8_t*>(pv.ent_ck) + a0, abytes,
-                   &S.raw_full[r]);
+                   &S.ent_full[r]);
         if (lane == 1 && wbytes)
           bulk_g2s(S.ew[r], reinterpret_cast<const uint8_t*>(pv.ent_w) + b0, wbytes,
-                   &S.raw_full[r]);
+                   &S.ent_full[r]);
       }
       continue;
     }
@@ -573,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
       continue;
     }
 
-    if (warp >= kDrainWarp0) {
+    if (warp >= kDrainWarp0 && warp < kDrainWarp0 + 4) {
       // ---------------- drains and epilogue ----------------
       const int quarter = warp & 3;  // TMEM lane quarter this warp may access
       const int row = quarter * 32 + lane;
@@ -623,13 +673,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         }
       }
       if (bail) break;
-      // epilogue: map = (total / W) * 2^-k_c, W from the plan's compensated
+      // epilogue: map = total / W * 2^-k_c, W from the plan's compensated
       // sums: FP32 weights for the split form (the hi+lo split differs from
       // them by at most 2^-22 per weight, at random), FP16-rounded weights for
       // the single form; both x 2^15.  k_c is the channel's scale exponent.
       const float Wm = active ? pv.wsum[(int64_t)(split ? 0 : 1) * pv.M + m] : 0.0f;
       const float W = Wm * kTcWeightScale;
       const bool ok = W > 0.0f;
+      // one reciprocal per cell: t * (1/W) * 2^-k is within one ulp of t / W * 2^-k
+      const float rW = ok ? __frcp_rn(W) : 0.0f;
       const bool scaled = J.chmax != nullptr && J.dtype != HEGRID_F16;
       // 32 columns per step: each lane writes whole 128-byte lines of its row
       uint32_t t[32];
@@ -644,8 +696,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
                                 : 1.0f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
+          // the second product is exact (a power of two on a normal value)
           const float inv = __shfl_sync(0xffffffffu, inv_l, i);
-          t[i] = __float_as_uint(ok ? __fmul_rn(__fdiv_rn(__uint_as_float(t[i]), W), inv) : qnan);
+          t[i] = __float_as_uint(ok ? __fmul_rn(__fmul_rn(__uint_as_float(t[i]), rW), inv) : qnan);
         }
         if (active) {
           if (cbase + 32 <= C && (((uintptr_t)(out + cbase) & 15u) == 0)) {
