@@ -262,7 +262,8 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * hegrid_grid_batched, hegrid_batch_create and hegrid_grid_stream calls on
  * this plan use it.  Shapes: the work order's band width in cell-block
  * columns (which blocks run concurrently and so share sample rows in L2),
- * and for the tensor-core modes the accumulation segment length (8 or 16
+ * for the tensor-core modes also the order of channel tiles (negative band:
+ * the tiles of a block side by side) and the accumulation segment length (8 or 16
  * sub-chunks of 32 candidates; both keep the split form well inside its error
  * bound: the tensor core's FP32 accumulate loses about 2^-22 of the running
  * sum per MMA, so the error grows with the segment).  values,
@@ -289,8 +290,11 @@ hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtyp
 
 /*
  * hegrid_plan_set_tuning -- set the launch shape hegrid_autotune would keep
- * (for instance one found in an earlier run; the tuning of Sec. 5.3).  band: blocks per band, >= 1
- * (0: default; FP32 mode also -1: the channel tiles of a block back to back);
+ * (for instance one found in an earlier run; the tuning of Sec. 5.3).  band: blocks per band
+ * (0: default).  FP32 mode: >= 1, or -1: the channel tiles of a block back to back.
+ * Tensor-core modes: > 0 runs the channel tiles one after another over all
+ * blocks, < 0 runs the channel tiles of each block side by side (bands of
+ * -band block columns), so that they share the block's weight entries in L2;
  * seg: 32-candidate sub-chunks per accumulation segment for the tensor-core
  * modes, 1..16 (0: default 16; longer segments would leave the split form
  * too little margin inside its error bound).  The 64-channel tile moves two sub-chunks per step and rounds

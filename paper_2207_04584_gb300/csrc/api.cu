@@ -110,72 +110,97 @@ __global__ void __launch_bounds__(256) k_mask_divide(float* __restrict__ map, in
   }
 }
 
-// Largest |v| of each channel, for the tensor-core forms' per-channel scale:
-// out[c] = max(out[c], |v[n, c]| over this CTA's rows) as the bits of a
-// non-negative float (they order like the floats; NaN is dropped by fmaxf,
-// Inf kept).  Each thread reads 16-byte vectors (kVec values) of one channel
-// group, `cols` groups per CTA side by side and 256 / cols rows at a time;
-// blockIdx.y selects the channel groups, blockIdx.x the row range.  One
-// atomicMax per channel and CTA, after a shared-memory reduction over the
-// CTA's rows.
+// Largest |v| of each channel, for the tensor-core forms' per-channel scale,
+// for every entry of a batch in one launch: out[c] = max(out[c], |v[n, c]|
+// over a CTA's rows) as the bits of a non-negative float (they order like the
+// floats; NaN is dropped by fmaxf, Inf kept).  Each thread reads 16-byte
+// vectors (kVec values) of one channel group, `cols` groups per CTA side by
+// side and 256 / cols rows at a time; an entry's CTAs cover its channel groups
+// (gy) times its row ranges (gx).  One atomicMax per channel and CTA, after a
+// shared-memory reduction over the CTA's rows.
+struct AbsmaxJob {
+  const void* values;
+  uint32_t* out;
+  int64_t N, C, ld, rows_per_cta;
+  int32_t dtype, nvec, cols, gy;
+  int64_t block_base;  // first CTA of this entry
+};
+constexpr int kMaxAbsmaxJobs = kMaxJobs;
+struct AbsmaxTable {
+  int32_t n;
+  AbsmaxJob job[kMaxAbsmaxJobs];
+};
+
 template <int DT>
-__global__ void __launch_bounds__(256) k_chan_absmax(const void* __restrict__ values, int64_t N,
-                                                     int64_t C, int64_t ld, int nvec, int cols,
-                                                     int64_t rows_per_cta,
-                                                     uint32_t* __restrict__ out) {
+__device__ __forceinline__ void absmax_rows(const AbsmaxJob& J, int64_t cv, int64_t r0, int64_t r1,
+                                            int rl, int rpt, float (&m)[8]) {
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;
-  constexpr int kVec = kWide ? 4 : 8;  // values per 16 bytes
-  __shared__ float red[256][kVec];
-  const int tid = threadIdx.x;
-  const int rpt = 256 / cols;  // rows read side by side
-  const int cslot = tid % cols, rl = tid / cols;
-  const int64_t cv = (int64_t)blockIdx.y * cols + cslot;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
-  const int64_t r1 = r0 + rows_per_cta < N ? r0 + rows_per_cta : N;
-  float m[kVec];
-#pragma unroll
-  for (int e = 0; e < kVec; ++e) m[e] = 0.0f;
-  if (rl < rpt && cv < nvec) {
-    const uint4* base = reinterpret_cast<const uint4*>(
-        static_cast<const char*>(values) + (cv * 16));
-    const int64_t pitch = ld * (kWide ? 4 : 2) / 16;  // row pitch in 16-byte vectors
+  const uint4* base =
+      reinterpret_cast<const uint4*>(static_cast<const char*>(J.values) + (cv * 16));
+  const int64_t pitch = J.ld * (kWide ? 4 : 2) / 16;  // row pitch in 16-byte vectors
 #pragma unroll 4
-    for (int64_t r = r0 + rl; r < r1; r += rpt) {
-      const uint4 q = __ldcs(base + r * pitch);
-      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  for (int64_t r = r0 + rl; r < r1; r += rpt) {
+    const uint4 q = __ldcs(base + r * pitch);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (DT == HEGRID_F32) {
-          m[i] = fmaxf(m[i], fabsf(__uint_as_float(w[i])));
-        } else if (DT == HEGRID_BF16X2) {
-          const float v = __uint_as_float(w[i] << 16) + __uint_as_float(w[i] & 0xffff0000u);
-          m[i] = fmaxf(m[i], fabsf(v));
-        } else if (DT == HEGRID_BF16) {
-          m[2 * i] = fmaxf(m[2 * i], fabsf(__uint_as_float(w[i] << 16)));
-          m[2 * i + 1] = fmaxf(m[2 * i + 1], fabsf(__uint_as_float(w[i] & 0xffff0000u)));
-        } else {  // F16
-          const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
-          m[2 * i] = fmaxf(m[2 * i], fabsf(f.x));
-          m[2 * i + 1] = fmaxf(m[2 * i + 1], fabsf(f.y));
-        }
+    for (int i = 0; i < 4; ++i) {
+      if (DT == HEGRID_F32) {
+        m[i] = fmaxf(m[i], fabsf(__uint_as_float(w[i])));
+      } else if (DT == HEGRID_BF16X2) {
+        const float v = __uint_as_float(w[i] << 16) + __uint_as_float(w[i] & 0xffff0000u);
+        m[i] = fmaxf(m[i], fabsf(v));
+      } else if (DT == HEGRID_BF16) {
+        m[2 * i] = fmaxf(m[2 * i], fabsf(__uint_as_float(w[i] << 16)));
+        m[2 * i + 1] = fmaxf(m[2 * i + 1], fabsf(__uint_as_float(w[i] & 0xffff0000u)));
+      } else {  // F16
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+        m[2 * i] = fmaxf(m[2 * i], fabsf(f.x));
+        m[2 * i + 1] = fmaxf(m[2 * i + 1], fabsf(f.y));
       }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_chan_absmax(const __grid_constant__ AbsmaxTable tab) {
+  __shared__ float red[256][8];
+  int j = 0;
+  while (j + 1 < tab.n && tab.job[j + 1].block_base <= (int64_t)blockIdx.x) ++j;
+  const AbsmaxJob& J = tab.job[j];
+  const int64_t local = (int64_t)blockIdx.x - J.block_base;
+  const int64_t bx = local / J.gy, by = local - bx * J.gy;
+  const int tid = threadIdx.x;
+  const int cols = J.cols, rpt = 256 / cols;  // rows read side by side
+  const int cslot = tid % cols, rl = tid / cols;
+  const int64_t cv = by * cols + cslot;
+  const int64_t r0 = bx * J.rows_per_cta;
+  const int64_t r1 = r0 + J.rows_per_cta < J.N ? r0 + J.rows_per_cta : J.N;
+  const bool wide = J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2;
+  const int vec = wide ? 4 : 8;  // values per 16 bytes
+  float m[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) m[e] = 0.0f;
+  if (rl < rpt && cv < J.nvec) {
+    switch (J.dtype) {
+      case HEGRID_F32: absmax_rows<HEGRID_F32>(J, cv, r0, r1, rl, rpt, m); break;
+      case HEGRID_BF16X2: absmax_rows<HEGRID_BF16X2>(J, cv, r0, r1, rl, rpt, m); break;
+      case HEGRID_BF16: absmax_rows<HEGRID_BF16>(J, cv, r0, r1, rl, rpt, m); break;
+      default: absmax_rows<HEGRID_F16>(J, cv, r0, r1, rl, rpt, m); break;
     }
   }
   if (rpt > 1) {
 #pragma unroll
-    for (int e = 0; e < kVec; ++e) red[tid][e] = m[e];
+    for (int e = 0; e < 8; ++e) red[tid][e] = m[e];
     __syncthreads();
     if (tid < cols) {
       for (int k = 1; k < rpt; ++k)
 #pragma unroll
-        for (int e = 0; e < kVec; ++e) m[e] = fmaxf(m[e], red[k * cols + tid][e]);
+        for (int e = 0; e < 8; ++e) m[e] = fmaxf(m[e], red[k * cols + tid][e]);
     }
   }
-  if (rl == 0 && cv < nvec) {
-#pragma unroll
-    for (int e = 0; e < kVec; ++e) {
-      const int64_t c = cv * kVec + e;
-      if (c < C && m[e] > 0.0f) atomicMax(out + c, __float_as_uint(m[e]));
+  if (rl == 0 && cv < J.nvec) {
+    for (int e = 0; e < vec; ++e) {
+      const int64_t c = cv * vec + e;
+      if (c < J.C && m[e] > 0.0f) atomicMax(J.out + c, __float_as_uint(m[e]));
     }
   }
 }
@@ -228,7 +253,7 @@ GridJob make_job(const hegrid_plan* plan, const hegrid_grid_args& a, int64_t cti
     j.band = plan->tune_f32_band;
     j.seg = 1;
   } else {
-    j.band = plan->tune_tc_band > 0 ? plan->tune_tc_band : tc_default_band();
+    j.band = plan->tune_tc_band != 0 ? plan->tune_tc_band : tc_default_band();
     j.seg = plan->tune_tc_seg > 0 ? plan->tune_tc_seg : tc_default_seg();
   }
   return j;
@@ -328,6 +353,7 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
     HG_CUDA_TRY(pool_alloc((void**)&chmax, sizeof(uint32_t) * (size_t)n_scaled, s));
   const bool own = chmax != chmax_buf;
   hegrid_status st = HEGRID_OK;
+  std::vector<AbsmaxRequest> amax;
   auto run = [&]() -> hegrid_status {
     if (n_scaled > 0)
       HG_CUDA_TRY(cudaMemsetAsync(chmax, 0, sizeof(uint32_t) * (size_t)n_scaled, s));
@@ -345,12 +371,20 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
       if (e != HEGRID_OK) return e;
       if (args[i].dtype != HEGRID_F16) {
         fam.back().chmax = chmax + at;
-        e = launch_chan_absmax(args[i].values, (int)args[i].dtype, plans[i]->N,
-                               args[i].n_channels, args[i].ld_values, chmax + at, s);
-        if (e != HEGRID_OK) return e;
+        AbsmaxRequest r;
+        r.values = args[i].values;
+        r.dtype = (int)args[i].dtype;
+        r.n_rows = plans[i]->N;
+        r.C = args[i].n_channels;
+        r.ld = args[i].ld_values;
+        r.out = chmax + at;
+        amax.push_back(r);
         at += args[i].n_channels;
       }
     }
+    // every entry's channel maxima in one launch, ahead of the grid kernels
+    hegrid_status e = launch_chan_absmax((int)amax.size(), amax.data(), s);
+    if (e != HEGRID_OK) return e;
     if (!f32.empty()) {
       hegrid_status e = launch_family(f32, false, s);
       if (e != HEGRID_OK) return e;
@@ -369,42 +403,44 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
 
 }  // namespace
 
-hegrid_status launch_chan_absmax(const void* values, int dtype, int64_t n_rows, int64_t C,
-                                 int64_t ld, uint32_t* out, cudaStream_t s) {
-  const int vec = (dtype == HEGRID_F32 || dtype == HEGRID_BF16X2) ? 4 : 8;
-  const int64_t nvec = (C + vec - 1) / vec;  // within ld: ld * element size is a multiple of 16
-  const int cols = (int)std::min<int64_t>(nvec, 256);
-  const int rpt = 256 / cols;
-  const int64_t gy = (nvec + cols - 1) / cols;
+hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s) {
+  if (n <= 0) return HEGRID_OK;
   int dev = 0, n_sm = 0;
   HG_CUDA_TRY(cudaGetDevice(&dev));
   HG_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  // about 8 CTAs per SM over all channel groups, each thread >= 32 rows
-  int64_t gx = std::max<int64_t>(1, (8 * (int64_t)n_sm + gy - 1) / gy);
-  gx = std::min<int64_t>(gx, std::max<int64_t>(1, n_rows / (32 * (int64_t)rpt)));
-  HG_ARG_CHECK(gy <= 65535, "too many channels");
-  const int64_t rows_per_cta = (n_rows + gx - 1) / gx;
-  const dim3 grid((unsigned)gx, (unsigned)gy);
-  switch (dtype) {
-    case HEGRID_F32:
-      k_chan_absmax<HEGRID_F32><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
-                                                     rows_per_cta, out);
-      break;
-    case HEGRID_BF16X2:
-      k_chan_absmax<HEGRID_BF16X2><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
-                                                        rows_per_cta, out);
-      break;
-    case HEGRID_BF16:
-      k_chan_absmax<HEGRID_BF16><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
-                                                      rows_per_cta, out);
-      break;
-    default:
-      k_chan_absmax<HEGRID_F16><<<grid, 256, 0, s>>>(values, n_rows, C, ld, (int)nvec, cols,
-                                                     rows_per_cta, out);
-      break;
+  for (int base = 0; base < n; base += kMaxAbsmaxJobs) {
+    AbsmaxTable tab;
+    std::memset(&tab, 0, sizeof(tab));
+    tab.n = std::min(kMaxAbsmaxJobs, n - base);
+    int64_t blocks = 0;
+    for (int i = 0; i < tab.n; ++i) {
+      const AbsmaxRequest& r = req[base + i];
+      AbsmaxJob& J = tab.job[i];
+      const int vec = (r.dtype == HEGRID_F32 || r.dtype == HEGRID_BF16X2) ? 4 : 8;
+      // channel groups of 16 bytes (within ld: ld * element size is a multiple of 16)
+      const int64_t nvec = (r.C + vec - 1) / vec;
+      J.values = r.values;
+      J.out = r.out;
+      J.N = r.n_rows;
+      J.C = r.C;
+      J.ld = r.ld;
+      J.dtype = r.dtype;
+      J.nvec = (int32_t)nvec;
+      J.cols = (int32_t)std::min<int64_t>(nvec, 256);
+      const int rpt = 256 / J.cols;
+      J.gy = (int32_t)((nvec + J.cols - 1) / J.cols);
+      // about 8 CTAs per SM over all channel groups, each thread >= 32 rows
+      int64_t gx = std::max<int64_t>(1, (8 * (int64_t)n_sm + J.gy - 1) / J.gy);
+      gx = std::min<int64_t>(gx, std::max<int64_t>(1, r.n_rows / (32 * (int64_t)rpt)));
+      J.rows_per_cta = (r.n_rows + gx - 1) / gx;
+      J.block_base = blocks;
+      blocks += gx * J.gy;
+    }
+    HG_ARG_CHECK(blocks < ((int64_t)1 << 31), "too many channel-maximum blocks");
+    k_chan_absmax<<<(unsigned)blocks, 256, 0, s>>>(tab);
+    count_launch();
+    HG_CUDA_TRY(launch_status());
   }
-  count_launch();
-  HG_CUDA_TRY(launch_status());
   return HEGRID_OK;
 }
 
@@ -715,7 +751,7 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   // candidate shapes
   std::vector<hegrid_tune_point> pts;
   auto add = [&](int band, int seg) {
-    band = std::min(band, plan->nbx_b);
+    band = band < 0 ? -std::min(-band, plan->nbx_b) : std::min(band, plan->nbx_b);
     for (const auto& q : pts)
       if (q.band == band && q.seg == seg) return;
     hegrid_tune_point q;
@@ -726,8 +762,14 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   };
   const int bands[] = {2, 4, 8, 16, 1 << 30};
   if (tc) {
-    for (int seg : {8, 16})
-      for (int b : bands) add(b, seg);
+    // both work orders (channel tiles slowest / fastest) at segments of 16,
+    // and the shorter segment at one band of each
+    for (int b : bands) {
+      add(b, 16);
+      add(-b, 16);
+    }
+    add(4, 8);
+    add(-4, 8);
   } else {
     add(0, 1);
     for (int b : bands) add(b, 1);
@@ -809,7 +851,7 @@ hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t b
     plan->tune_f32_band = band;
   } else {
     HG_ARG_CHECK(mode == HEGRID_MODE_TC || mode == HEGRID_MODE_TC_SPLIT, "unknown mode");
-    HG_ARG_CHECK(band >= 0, "band must be >= 0");
+    HG_ARG_CHECK(band != INT32_MIN, "band out of range");
     HG_ARG_CHECK(seg >= 0 && seg <= 16, "seg must be in [0, 16]");
     plan->tune_tc_band = band;
     plan->tune_tc_seg = seg;

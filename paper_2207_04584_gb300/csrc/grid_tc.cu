@@ -81,7 +81,7 @@ constexpr int kK = 32;                     // candidates per sub-chunk (64-byte 
 constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kDefaultSeg = 16;            // sub-chunks per accumulation segment
-constexpr int kDefaultBand = 8;            // blocks per band of the work order
+constexpr int kDefaultBand = -8;  // work order: bands of 8 block columns, channel tiles fastest
 // The channel tile kN (64, 128 or 256: the MMA's N) is a template parameter:
 // the launcher takes the narrowest tile that holds C (256 above it), so few
 // channels do not pay for 256-column tiles.  So is kS, the 32-candidate
@@ -148,14 +148,22 @@ __device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
   return j;
 }
 
-// Work order inside a job: channel tiles slowest, then cell blocks in bands
-// of J.band block columns, so concurrently running CTAs share candidates in L2.
+// Work order inside a job: cell blocks in bands of |J.band| block columns, so
+// concurrently running CTAs share candidate rows in L2, and the channel tiles
+// either slowest (J.band > 0) or fastest (J.band < 0: the tiles of a block run
+// side by side and share its weight entries in L2).
 __device__ __forceinline__ void item_coords(const GridJob& J, int64_t local, int64_t& b,
                                             int64_t& ct) {
   const int64_t nb = J.pv.n_blocks;
-  ct = local / nb;
-  const int64_t bo = local - ct * nb;
-  const int64_t kBand = J.band;
+  int64_t bo;
+  if (J.band < 0) {
+    ct = local % J.n_ctiles;
+    bo = local / J.n_ctiles;
+  } else {
+    ct = local / nb;
+    bo = local - ct * nb;
+  }
+  const int64_t kBand = J.band < 0 ? -(int64_t)J.band : J.band;
   const int64_t per_band = kBand * J.pv.nby_b;
   const int64_t band = bo / per_band;
   const int64_t t = bo - band * per_band;

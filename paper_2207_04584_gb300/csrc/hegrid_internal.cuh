@@ -186,10 +186,16 @@ struct JobTable {
 };
 
 hegrid_status launch_grid_f32(const JobTable& jt, cudaStream_t s);
-// out[c] (zeroed by the caller) = max(out[c], largest |v| of channel c) as
-// float bits, for the C channels of `values` (NaN ignored, Inf kept).
-hegrid_status launch_chan_absmax(const void* values, int dtype, int64_t n_rows, int64_t C,
-                                 int64_t ld, uint32_t* out, cudaStream_t s);
+// For each request: out[c] (zeroed by the caller) = max(out[c], largest |v|
+// of channel c) as float bits, for the C channels of `values` (NaN ignored,
+// Inf kept); all requests in one launch (kMaxJobs per launch).
+struct AbsmaxRequest {
+  const void* values;
+  int dtype;
+  int64_t n_rows, C, ld;
+  uint32_t* out;
+};
+hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s);
 // `tile`: the channel tile of every job in the table (tc_channel_tile(C)).
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile);
 int f32_channel_tile();

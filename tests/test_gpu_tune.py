@@ -58,6 +58,7 @@ def test_autotune_keeps_fastest_and_matches_oracle(H, mode):
 
 
 @pytest.mark.parametrize("mode,band,seg", [("tc_split", 1, 16), ("tc_split", 3, 8),
+                                            ("tc_split", -2, 16), ("tc_split", -1 << 20, 8),
                                             ("tc_split", 1 << 20, 1), ("tc", 2, 7),
                                             ("fp32", -1, 0), ("fp32", 1, 0), ("fp32", 5, 0)])
 def test_every_shape_matches_oracle(H, mode, band, seg):
@@ -92,7 +93,7 @@ def test_set_tuning_rejects_bad_shapes(H):
     plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, wl["geom"],
                                 wl["fwhm_deg"], 3.0, 0, s)
     try:
-        for md, band, seg in ((H.HEGRID_MODE_TC_SPLIT, 4, 17), (H.HEGRID_MODE_TC, -1, 16),
+        for md, band, seg in ((H.HEGRID_MODE_TC_SPLIT, 4, 17), (H.HEGRID_MODE_TC, -1, -3),
                               (H.HEGRID_MODE_FP32, -2, 0), (9, 4, 16)):
             with pytest.raises(H.HegridError) as e:
                 H.hegrid_plan_set_tuning(plan, md, band, seg)
