@@ -268,32 +268,37 @@ def config4_fields(seed=SEED_BASE + 4, n_fields=64, max_bytes=150e9, n_range=(1e
                    side_choices=(64, 128, 256, 512, 1024), c_range=(64, 4096)):
     """Parameters of the batched uneven fields (no samples drawn yet).
 
-    Resamples (seeded) until the estimated device footprint is <= max_bytes.
+    Each field's device footprint is estimated (values at their stored width,
+    the FP32 map, about 7 bytes per in-radius pair for the plan's weight
+    entries and candidate lists, 40 bytes per sample for the rest of the
+    plan); while the total exceeds max_bytes the largest field is drawn anew
+    (seeded), so the set is found in a few draws.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
-    while True:
-        fields = []
-        total = 0.0
-        for i in range(n_fields):
-            n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
-            side = int(side_choices[int(rng.integers(len(side_choices)))])
-            cell = float(rng.choice([0.5, 1.0])) * ARCMIN
-            lc2 = rng.uniform(math.log2(c_range[0]), math.log2(c_range[1]))
-            C = int(2 ** int(round(lc2)))
-            dtype = "f32" if rng.uniform() < 0.5 else "bf16"
-            fwhm = rng.uniform(2.9, 6.0) * ARCMIN
-            pattern = ["drift", "raster", "uniform"][int(rng.integers(3))]
-            lon0 = float(rng.uniform(10.0, 350.0))
-            lat0 = float(rng.uniform(-60.0, 60.0))
-            M = side * side
-            eb = 4 if dtype == "f32" else 2
-            pairs_est = n * 3.0 * (math.pi * (3 * fwhm / 2.3548) ** 2) / (cell * cell)
-            total += n * C * eb + M * C * 4 + pairs_est * 14 + n * 40
-            fields.append({"n": n, "side": side, "cell_deg": cell, "C": C, "dtype": dtype,
-                           "fwhm_deg": fwhm, "pattern": pattern, "lon0": lon0, "lat0": lat0,
-                           "seed": int(rng.integers(2**62))})
-        if total <= max_bytes:
-            return fields, total
+
+    def draw():
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        side = int(side_choices[int(rng.integers(len(side_choices)))])
+        cell = float(rng.choice([0.5, 1.0])) * ARCMIN
+        lc2 = rng.uniform(math.log2(c_range[0]), math.log2(c_range[1]))
+        C = int(2 ** int(round(lc2)))
+        dtype = "f32" if rng.uniform() < 0.5 else "bf16"
+        fwhm = rng.uniform(2.9, 6.0) * ARCMIN
+        pattern = ["drift", "raster", "uniform"][int(rng.integers(3))]
+        lon0 = float(rng.uniform(10.0, 350.0))
+        lat0 = float(rng.uniform(-60.0, 60.0))
+        eb = 4 if dtype == "f32" else 2
+        pairs_est = n * math.pi * (3 * fwhm / 2.3548) ** 2 / (cell * cell)
+        est = n * C * eb + side * side * C * 4 + pairs_est * 7 + n * 40
+        return {"n": n, "side": side, "cell_deg": cell, "C": C, "dtype": dtype,
+                "fwhm_deg": fwhm, "pattern": pattern, "lon0": lon0, "lat0": lat0,
+                "seed": int(rng.integers(2**62)), "bytes_est": est}
+
+    fields = [draw() for _ in range(n_fields)]
+    while sum(f["bytes_est"] for f in fields) > max_bytes:
+        big = max(range(n_fields), key=lambda i: fields[i]["bytes_est"])
+        fields[big] = draw()
+    return fields, sum(f["bytes_est"] for f in fields)
 
 
 def field_samples(f, with_values=True):
