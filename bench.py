@@ -109,9 +109,9 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "fbae6c5a8a120b7d82747e087b69a581c3743b25a06265ab74afe59b1fe2347b",
-                  "bytes": 4 * (8.595043e9 + 0.366710e9),
-                  "capture": "profiles/k_grid_tc_fast_drift_c256.md (C=256 x 4 channel tiles)"},
+                  "sha256": "4a1eb0c2c484f7a680c3e9d025f4eea564d03da12bc3d621c19dbb9367430593",
+                  "bytes": 36.274460928e9 + 1.475841280e9,
+                  "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench launch, C=1024)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
@@ -532,6 +532,46 @@ def run_config3(args, H, torch, dev, rank):
                 "clocks": clk, "gen_s": t_gen}), flush=True)
 
 
+def run_profile_case(args, H, torch, dev, rank):
+    """Small cases of the tensor-core grid kernel for profiler captures (a few GB on the
+    device): profile-drift is the drift scan over 2.5 x 2.5 deg at (30, 41) (the bench
+    workload's density and kernel) with 256 FP32 channels; profile-cfg3 is config 3 with
+    its 16,384 channels stored as BF16.  Four split-form grid calls on one plan; prints
+    the time of the last."""
+    s = torch.cuda.current_stream(dev).cuda_stream
+    if args.workload == "profile-drift":
+        wl = W.config2(C=256, size_deg=2.5)
+        vals = torch.from_numpy(wl["values"]).to(dev)
+        dt = H.HEGRID_F32
+    else:
+        wl = W.config3()
+        vals = torch.from_numpy(wl["values"]).to(torch.bfloat16).to(dev)
+        dt = H.HEGRID_BF16
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    N, C = wl["values"].shape
+    lon = torch.from_numpy(wl["lon"]).to(dev)
+    lat = torch.from_numpy(wl["lat"]).to(dev)
+    plan = H.hegrid_plan_create(N, lon, lat, 1, g, wl["fwhm_deg"], 3.0, 0, s)
+    try:
+        out = torch.empty((M, C), device=dev)
+        for _ in range(3):
+            H.hegrid_grid(plan, vals, dt, C, C, out, C, None, H.HEGRID_MODE_TC_SPLIT, s)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        H.hegrid_grid(plan, vals, dt, C, C, out, C, None, H.HEGRID_MODE_TC_SPLIT, s)
+        b.record()
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+        info = H.hegrid_plan_info(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    if rank == 0:
+        print(json.dumps({"report": args.workload, "N": N, "C": C, "M": M,
+                          "pairs": info["n_pairs"], "grid_ms": a.elapsed_time(b)}), flush=True)
+
+
 # Table 3 (Sec. 5.2): HEGrid's end-to-end times in seconds on a V100 for the simulated
 # survey (50 channels) at each sample count; context only (another machine, and the paper's
 # times include reading the input files).
@@ -839,10 +879,12 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch shapes, bin edge 2)")
     ap.add_argument("--workload", default="config2",
-                    choices=["config2", "config3", "config4", "config5", "sim", "sweep"],
+                    choices=["config2", "config3", "config4", "config5", "sim", "sweep",
+                             "profile-drift", "profile-cfg3"],
                     help="config2 (default): the bench line; config3: 16,384 channels stored "
                          "as BF16, FP16, BF16 hi/lo and FP32, one line per stored type and "
-                         "tensor-core form; config4: 64 uneven fields in one "
+                         "tensor-core form; profile-drift / profile-cfg3: small cases of the "
+                         "grid kernel for profiler captures; config4: 64 uneven fields in one "
                          "graph-captured batch; config5: 65,536 BF16 channels streamed from "
                          "pinned host memory; sim: the paper's 60x20 deg simulated survey "
                          "at every sample count of Table 3, plan + grid, device and end to "
@@ -881,6 +923,8 @@ def main():
     H.lib()
     if args.workload == "config3":
         return run_config3(args, H, torch, dev, rank)
+    if args.workload.startswith("profile-"):
+        return run_profile_case(args, H, torch, dev, rank)
     if args.workload == "config4":
         return run_config4(args, H, torch, dev, rank)
     if args.workload == "config5":
