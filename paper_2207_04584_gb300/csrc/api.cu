@@ -362,6 +362,8 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
       if (wait_ready) HG_CUDA_TRY(cudaStreamWaitEvent(s, plans[i]->ready, 0));
       if (args[i].mode == HEGRID_MODE_FP32) {
         f32.push_back(make_job(plans[i], args[i], f32_channel_tile()));
+        hegrid_status e = encode_rows_map(f32.back(), f32_channel_tile());
+        if (e != HEGRID_OK) return e;
         continue;
       }
       const int tile = tc_channel_tile(args[i].n_channels);

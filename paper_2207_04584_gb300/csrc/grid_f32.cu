@@ -5,9 +5,10 @@
 // in a fixed stride, in the job's work order (the channel tiles of a block
 // back to back, or channel tiles slowest with the blocks in bands of block
 // columns).  For each K chunk of 32 candidate samples of the block:
-//   * warp 0 stages the 32 sample rows (FP32, channel-contiguous) and the
-//     chunk's weight entries into shared memory with bulk async copies (TMA
-//     engine, one row per lane, two entry windows) completing on an mbarrier,
+//   * warp 0 stages the 32 sample rows (FP32, channel-contiguous; eight
+//     four-row TMA tensor gathers of the 128-channel tile) and the chunk's
+//     weight entries (two bulk copies of 16-byte aligned windows) into shared
+//     memory, completing on an mbarrier,
 //     double-buffered: chunk j + 1 is staged while chunk j is computed;
 //     one CTA barrier per chunk (after the scatter; each warp clears its own
 //     columns of the weight tile after computing);
@@ -37,6 +38,7 @@ constexpr int kThreads = 256;
 constexpr int kKC = 32;   // candidates per K chunk
 constexpr int kCT = 128;  // channels per tile
 constexpr int kFlush = 4;   // chunks per register partial sum (then added to the TMEM total)
+constexpr int kEB = 4;      // weight entries per thread loaded ahead of their stores
 constexpr uint32_t kTmemCols = 128;  // 64 FP32 totals per thread: two warps per lane quarter
 constexpr int kEntCap = 2048;           // weight entries staged per chunk (more: global)
 constexpr int kEntStage = kEntCap - 8;  // entries copied (room for 16-byte alignment)
@@ -133,8 +135,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     const int64_t c0 = ct * kCT;
     const int cw = (int)(J.C - c0 < kCT ? J.C - c0 : kCT);
-    const uint32_t row_bytes = (uint32_t)(((cw + 3) & ~3) * 4);
-    const float* __restrict__ vals = static_cast<const float*>(J.values);
     const int bbx = (int)(b % pv.nbx_b), bby = (int)(b / pv.nbx_b);
     const int64_t kb0 = pv.cand_off[b];
     const int n_chunks = pv.cand_cnt[b] / kKC;
@@ -170,13 +170,19 @@ __global__ void __launch_bounds__(kThreads, 2)
         w.ck_off = (uint32_t)(e_lo * 2 - a0);
         w.w_off = (uint32_t)(e_lo * 4 - b0);
         S.win[s] = w;
-        mbar_arrive_expect_tx(&S.bar[s], row_bytes * kKC + ab + wb);
+        mbar_arrive_expect_tx(&S.bar[s], kKC * kCT * 4 + ab + wb);
       }
       __syncwarp();
       const int32_t n = n_cur;
       n_cur = n_next;
       if (j + 2 < n_chunks) n_next = pv.cand_idx[kb0 + (int64_t)(j + 2) * kKC + lane];
-      bulk_g2s(&S.V[s][lane][0], vals + (int64_t)n * J.ld_values + c0, row_bytes, &S.bar[s]);
+      // the 32 rows by eight four-row tensor gathers (channels past C arrive as zeros)
+      {
+        const int q4 = (lane & 7) * 4;
+        const int32_t r0 = __shfl_sync(0xffffffffu, n, q4), r1 = __shfl_sync(0xffffffffu, n, q4 + 1);
+        const int32_t r2 = __shfl_sync(0xffffffffu, n, q4 + 2), r3 = __shfl_sync(0xffffffffu, n, q4 + 3);
+        if (lane < 8) tma_gather4(&S.V[s][q4][0], &J.rows, (int32_t)c0, r0, r1, r2, r3, &S.bar[s]);
+      }
       if (lane == 0 && ab)
         bulk_g2s(S.eck[s], reinterpret_cast<const uint8_t*>(pv.ent_ck) + a0, ab, &S.bar[s]);
       if (lane == 1 && wb)
@@ -221,23 +227,36 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (staged) {
         const EntWin w = S.win[s];
         const uint32_t eck = smem_u32(S.eck[s]) + w.ck_off, ew = smem_u32(S.ew[s]) + w.w_off;
-        for (int i = tid; i < w.n; i += kThreads) {
-          uint32_t ck;
-          float wt;
-          if (i < w.ns) {
-            uint16_t h;
-            asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(eck + 2 * i));
-            ck = h;
-            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(wt) : "r"(ew + 4 * i));
-          } else {
-            ck = pv.ent_ck[w.e_lo + i];
-            wt = pv.ent_w[w.e_lo + i];
+        // kEB entries per thread at a time, all loaded before any is stored, so
+        // that entries beyond the staged ones (dense chunks) wait for global
+        // memory once per batch rather than once per entry
+        for (int i0 = tid; i0 < w.n; i0 += kEB * kThreads) {
+          uint32_t ck[kEB];
+          float wt[kEB];
+#pragma unroll
+          for (int b = 0; b < kEB; ++b) {
+            const int i = i0 + b * kThreads;
+            ck[b] = 0u;
+            wt[b] = 0.0f;
+            if (i < w.ns) {
+              uint16_t h;
+              asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(eck + 2 * i));
+              ck[b] = h;
+              asm volatile("ld.shared.f32 %0, [%1];" : "=f"(wt[b]) : "r"(ew + 4 * i));
+            } else if (i < w.n) {
+              ck[b] = __ldg(pv.ent_ck + w.e_lo + i);
+              wt[b] = __ldg(pv.ent_w + w.e_lo + i);
+            }
           }
-          int col, k;
-          tile_rk(ck, col, k);
-          const int tc = cell_to_col(col % HG_BX, col / HG_BX);
-          S.Wt[s][k][tc] = wt;
-          atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
+#pragma unroll
+          for (int b = 0; b < kEB; ++b) {
+            if (i0 + b * kThreads >= w.n) break;
+            int col, k;
+            tile_rk(ck[b], col, k);
+            const int tc = cell_to_col(col % HG_BX, col / HG_BX);
+            S.Wt[s][k][tc] = wt[b];
+            atomicOr(&S.pmask[s][k], 1u << (tc >> 4));
+          }
         }
       }
       if (__syncthreads_or(!staged)) {

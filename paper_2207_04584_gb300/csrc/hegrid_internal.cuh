@@ -152,8 +152,8 @@ struct hegrid_plan {
 namespace hg {
 
 struct GridJob {
-  // Tensor map of the values (rows = samples, 256-channel boxes one row
-  // high) for the tensor-core kernel's row gathers; unused by the FP32 kernel.
+  // Tensor map of the values (rows = samples, boxes of one channel tile, one
+  // row high) for the grid kernels' row gathers.
   CUtensorMap rows;
   PlanView pv;
   const void* values;
