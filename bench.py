@@ -631,8 +631,10 @@ def run_sim(args, H, torch, dev, rank):
             if not args.no_tune:
                 rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, ldv, md, sh)
                 best = rep["points"][rep["best"]]
-                q = {"band": best["band"], "seg": best["seg"], "ms": best["ms"]}
-                H.hegrid_plan_set_tuning(p, md, best["band"], best["seg"])
+                q = {"band": best["band"], "seg": best["seg"], "group": best["group"],
+                     "kernel": best["kernel"], "ms": best["ms"]}
+                H.hegrid_plan_set_tuning(p, md, best["band"], best["seg"], best["group"],
+                                         best["kernel"])
             H.hegrid_grid(p, vals_d, H.HEGRID_F32, C, ldv, map_d, C, w_d, md, sh)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -652,7 +654,8 @@ def run_sim(args, H, torch, dev, rank):
     def new_plan(n, lon, lat, on_device):
         pl = H.hegrid_plan_create(n, lon, lat, on_device, g, wl["fwhm_deg"], 3.0, flags, sh)
         if "band" in shape:
-            H.hegrid_plan_set_tuning(pl, mode, shape["band"], shape["seg"])
+            H.hegrid_plan_set_tuning(pl, mode, shape["band"], shape["seg"], shape.get("group", 0),
+                                     shape.get("kernel", 0))
         return pl
 
     link = _link(torch, dev, stream)
@@ -809,7 +812,8 @@ def run_sweep(args, H, torch, dev, rank):
     try:
         for nm, md in (("tc_split", H.HEGRID_MODE_TC_SPLIT), ("fp32", H.HEGRID_MODE_FP32)):
             rep = H.hegrid_autotune(p, vals_d, H.HEGRID_F32, C, C, md, sh)
-            shapes[nm] = [{"band": q["band"], "seg": q["seg"], "grid_ms": q["ms"]}
+            shapes[nm] = [{"band": q["band"], "seg": q["seg"], "group": q["group"],
+                           "kernel": q["kernel"], "grid_ms": q["ms"]}
                           for q in rep["points"]]
         # streaming: the same plan, C channels from pinned host memory in k chunks
         host_map = torch.empty((M, C), dtype=torch.float32, pin_memory=True)
@@ -986,9 +990,10 @@ def main():
         finally:
             H.hegrid_plan_destroy(p)
         best = rep["points"][rep["best"]]
-        tune = {"bin_cells": bin_cells, "band": best["band"], "seg": best["seg"],
+        tune = {"bin_cells": bin_cells, "band": best["band"], "seg": best["seg"], "group": best["group"],
+                "kernel": best["kernel"],
                 "plan_ms_by_bin": [round(x, 3) for x in bin_ms],
-                "grid_ms_by_shape": [[q["band"], q["seg"], round(q["ms"], 3)]
+                "grid_ms_by_shape": [[q["band"], q["seg"], q["group"], q["kernel"], round(q["ms"], 3)]
                                      for q in rep["points"]],
                 "seconds": round(time.perf_counter() - t_tune, 2)}
     flags = tune.get("bin_cells", hpx_flag)
@@ -996,7 +1001,8 @@ def main():
     def new_plan(lon, lat, on_device):
         p = H.hegrid_plan_create(N, lon, lat, on_device, g, wl["fwhm_deg"], 3.0, flags, sh)
         if tune:
-            H.hegrid_plan_set_tuning(p, mode, tune["band"], tune["seg"])
+            H.hegrid_plan_set_tuning(p, mode, tune["band"], tune["seg"], tune["group"],
+                                     tune["kernel"])
         return p
 
     ev = []

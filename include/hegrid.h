@@ -262,7 +262,8 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * hegrid_grid_batched, hegrid_batch_create and hegrid_grid_stream calls on
  * this plan use it.  Shapes: the work order's band width in cell-block
  * columns (which blocks run concurrently and so share sample rows in L2),
- * for the tensor-core modes also the order of channel tiles (negative band:
+ * for the tensor-core modes also the kernel (cell-major, and channel-major
+ * when n_channels > 64), the order of channel tiles (negative band:
  * the tiles of a block side by side) and the accumulation segment length (8 or 16
  * sub-chunks of 32 candidates; both keep the split form well inside its error
  * bound: the tensor core's FP32 accumulate loses about 2^-22 of the running
@@ -274,11 +275,13 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * the one kept.  Errors: INVALID_ARG (plan NULL, and the checks of
  * hegrid_grid); UNSUPPORTED, OOM (the scratch map) and CUDA as for hegrid_grid.
  */
-#define HEGRID_TUNE_MAX 16
+#define HEGRID_TUNE_MAX 40
 typedef struct {
-  int32_t band; /* blocks per band (0: the channel tiles of a block back to back) */
-  int32_t seg;  /* 32-candidate sub-chunks per accumulation segment (tensor-core modes) */
-  float ms;     /* time per grid call */
+  int32_t band;   /* blocks per band (0: the channel tiles of a block back to back) */
+  int32_t seg;    /* 32-candidate sub-chunks per accumulation segment (tensor-core modes) */
+  int32_t group;  /* channel tiles side by side when band < 0 (tensor-core modes; 0: all) */
+  int32_t kernel; /* tensor-core kernel: 1 cell-major, 2 channel-major (0: default) */
+  float ms;       /* time per grid call */
 } hegrid_tune_point;
 typedef struct {
   int32_t n, best;
@@ -294,14 +297,27 @@ hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtyp
  * (0: default).  FP32 mode: >= 1, or -1: the channel tiles of a block back to back.
  * Tensor-core modes: > 0 runs the channel tiles one after another over all
  * blocks, < 0 runs the channel tiles of each block side by side (bands of
- * -band block columns), so that they share the block's weight entries in L2;
+ * -band block columns), so that they share the block's weight entries in L2:
+ * `group` tiles at a time (0: all of them; the groups follow one another over
+ * all blocks, so that fewer blocks run at once and more of them share sample
+ * rows in L2); group is ignored for band > 0 and for FP32 mode.
+ * kernel (tensor-core modes): 1 runs the cell-major kernel (cells x channels
+ * per MMA, weight tiles built in shared memory from the plan's entries, one
+ * per channel tile); 2 the channel-major kernel (channels x cells per MMA,
+ * the values gathered into shared memory and stored into tensor memory as
+ * the MMA's A operand, the weights from dense tiles built once per plan,
+ * 128-channel tiles: the first grid call that
+ * runs it builds them, 16 KB per 32 candidate slots, on its stream, outside
+ * a stream capture, where the cell-major kernel runs until they exist);
+ * 0: the default, the cell-major kernel.  FP32 mode ignores it.
  * seg: 32-candidate sub-chunks per accumulation segment for the tensor-core
  * modes, 1..16 (0: default 16; longer segments would leave the split form
  * too little margin inside its error bound).  The 64-channel tile moves two sub-chunks per step and rounds
  * seg down to an even count (at least 2).
- * INVALID_ARG otherwise.
+ * INVALID_ARG otherwise (also group < 0, kernel outside 0..2).
  */
-hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t band, int32_t seg);
+hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t band, int32_t seg,
+                                     int32_t group, int32_t kernel);
 
 /*
  * hegrid_autotune_bins -- time hegrid_plan_create (plus destroy) for bin edges

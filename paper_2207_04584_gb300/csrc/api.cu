@@ -255,6 +255,11 @@ GridJob make_job(const hegrid_plan* plan, const hegrid_grid_args& a, int64_t cti
   } else {
     j.band = plan->tune_tc_band != 0 ? plan->tune_tc_band : tc_default_band();
     j.seg = plan->tune_tc_seg > 0 ? plan->tune_tc_seg : tc_default_seg();
+    j.group = plan->tune_tc_band != 0 ? plan->tune_tc_group : tc_default_group();
+    // the block's height over its candidate window's (R on each side, plus up
+    // to one bin of rounding), in map rows
+    const double r_rows = plan->R_deg / plan->geom.dlat_deg;
+    j.rot = (float)(HG_BY / (HG_BY + 2.0 * r_rows + plan->bin_cells));
   }
   return j;
 }
@@ -300,7 +305,52 @@ hegrid_status encode_rows_map(GridJob& j, int tile) {
   return HEGRID_OK;
 }
 
-// Launch all jobs of one kernel family (one tensor-core channel tile),
+// Builds the plan's dense weight tiles (once; serialised by a host mutex)
+// on stream s, after which `ready` is re-recorded on s so that every later
+// user of the plan waits for them too.
+hegrid_status ensure_wtiles(hegrid_plan* p, cudaStream_t s) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (p->wtiles) return HEGRID_OK;
+  const int64_t bytes = tcm_wtile_bytes(p->slots);
+  uint8_t* wt = nullptr;
+  HG_CUDA_TRY(pool_alloc((void**)&wt, (size_t)std::max<int64_t>(bytes, 16), s));
+  hegrid_plan tmp = *p;
+  tmp.wtiles = wt;
+  hegrid_status st = launch_build_wtiles(tmp.view(), wt, s);
+  if (st != HEGRID_OK) {
+    cudaFreeAsync(wt, s);
+    return st;
+  }
+  HG_CUDA_TRY(cudaEventRecord(p->ready, s));
+  p->wtiles = wt;
+  p->bytes += bytes;
+  return HEGRID_OK;
+}
+
+// Whether the tensor-core job (plan, a) runs on the channel-major kernel:
+// the plan's choice (tune_tc_kernel: 2, set by the caller or kept by the
+// autotuner; the default is the cell-major kernel); the weight tiles are
+// built here if needed, except inside a stream capture (where the cell-major
+// kernel runs unless they exist).
+hegrid_status use_channel_major(hegrid_plan* p, const hegrid_grid_args& a, cudaStream_t s,
+                                bool* cm) {
+  *cm = false;
+  (void)a;
+  if (p->tune_tc_kernel != 2) return HEGRID_OK;
+  if (!p->wtiles) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HG_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return HEGRID_OK;
+    hegrid_status e = ensure_wtiles(p, s);
+    if (e != HEGRID_OK) return e;
+  }
+  *cm = true;
+  return HEGRID_OK;
+}
+
+// Launch all jobs of one kernel family (tile > 0: the cell-major
+// tensor-core kernel of that channel tile; tile < 0: the channel-major one),
 // kMaxJobs per launch.
 hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStream_t s,
                             int tile = 0) {
@@ -317,7 +367,9 @@ hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStrea
       items += jt.job[i].pv.n_blocks * jt.job[i].n_ctiles;
     }
     jt.n_items = items;
-    hegrid_status st = tc ? launch_grid_tc(jt, s, tile) : launch_grid_f32(jt, s);
+    hegrid_status st = !tc ? launch_grid_f32(jt, s)
+                       : tile < 0 ? launch_grid_tcm(jt, s)
+                                  : launch_grid_tc(jt, s, tile);
     if (st != HEGRID_OK) return st;
   }
   return HEGRID_OK;
@@ -340,8 +392,9 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
                         cudaStream_t s, bool wait_ready = true, uint32_t* chmax_buf = nullptr) {
   HG_ARG_CHECK(n >= 0, "n must be >= 0");
   HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
-  // tensor-core jobs grouped by channel tile (64, 128, 256): one launch each
-  std::vector<GridJob> f32, tc[3];
+  // tensor-core jobs grouped by kernel and channel tile (cell-major 64, 128,
+  // 256; channel-major 128): one launch each
+  std::vector<GridJob> f32, tc[3], tcm;
   const int tiles[3] = {64, 128, 256};
   for (int i = 0; i < n; ++i) {
     hegrid_status st = check_args(plans[i], args[i]);
@@ -366,11 +419,18 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
         if (e != HEGRID_OK) return e;
         continue;
       }
-      const int tile = tc_channel_tile(args[i].n_channels);
-      std::vector<GridJob>& fam = tc[tile == 64 ? 0 : tile == 128 ? 1 : 2];
+      bool cm = false;
+      {
+        hegrid_status e = use_channel_major(plans[i], args[i], s, &cm);
+        if (e != HEGRID_OK) return e;
+      }
+      const int tile = cm ? tcm_channel_tile() : tc_channel_tile(args[i].n_channels);
+      std::vector<GridJob>& fam = cm ? tcm : tc[tile == 64 ? 0 : tile == 128 ? 1 : 2];
       fam.push_back(make_job(plans[i], args[i], tile));
-      hegrid_status e = encode_rows_map(fam.back(), tile);
-      if (e != HEGRID_OK) return e;
+      {
+        hegrid_status e = encode_rows_map(fam.back(), tile);
+        if (e != HEGRID_OK) return e;
+      }
       if (args[i].dtype != HEGRID_F16) {
         fam.back().chmax = chmax + at;
         AbsmaxRequest r;
@@ -394,6 +454,10 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
     for (int t = 0; t < 3; ++t) {
       if (tc[t].empty()) continue;
       hegrid_status e = launch_family(tc[t], true, s, tiles[t]);
+      if (e != HEGRID_OK) return e;
+    }
+    if (!tcm.empty()) {
+      hegrid_status e = launch_family(tcm, true, s, -1);
       if (e != HEGRID_OK) return e;
     }
     return HEGRID_OK;
@@ -752,13 +816,15 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   const bool tc = mode != HEGRID_MODE_FP32;
   // candidate shapes
   std::vector<hegrid_tune_point> pts;
-  auto add = [&](int band, int seg) {
+  auto add = [&](int band, int seg, int group, int kernel) {
     band = band < 0 ? -std::min(-band, plan->nbx_b) : std::min(band, plan->nbx_b);
     for (const auto& q : pts)
-      if (q.band == band && q.seg == seg) return;
+      if (q.band == band && q.seg == seg && q.group == group && q.kernel == kernel) return;
     hegrid_tune_point q;
     q.band = band;
     q.seg = seg;
+    q.group = group;
+    q.kernel = kernel;
     q.ms = -1.0f;
     pts.push_back(q);
   };
@@ -766,15 +832,25 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   if (tc) {
     // both work orders (channel tiles slowest / fastest) at segments of 16,
     // and the shorter segment at one band of each
-    for (int b : bands) {
-      add(b, 16);
-      add(-b, 16);
+    // both kernels (channel-major only where its 128-channel tiles fill),
+    // both orders of the channel tiles (slowest / side by side: all of a
+    // block's, or in pairs) at segments of 16, and the shorter segment at one
+    // band of each
+    const bool cm = n_channels > 64;
+    for (int kern = cm ? 2 : 1; kern >= 1; --kern) {
+      for (int b : bands) {
+        add(b, 16, 0, kern);
+        add(-b, 16, 0, kern);
+      }
+      add(4, 8, 0, kern);
+      add(-4, 8, 0, kern);
+      add(-2, 16, 2, kern);
+      add(-4, 16, 2, kern);
+      add(-8, 16, 2, kern);
     }
-    add(4, 8);
-    add(-4, 8);
   } else {
-    add(0, 1);
-    for (int b : bands) add(b, 1);
+    add(0, 1, 0, 0);
+    for (int b : bands) add(b, 1, 0, 0);
   }
   // scratch map (discarded)
   float* scratch = nullptr;
@@ -789,13 +865,16 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   a.ld_map = n_channels;
   a.weight_out = nullptr;
   a.mode = mode;
-  const int32_t keep[3] = {plan->tune_f32_band, plan->tune_tc_band, plan->tune_tc_seg};
+  const int32_t keep[5] = {plan->tune_f32_band, plan->tune_tc_band, plan->tune_tc_seg,
+                           plan->tune_tc_group, plan->tune_tc_kernel};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   hegrid_status st = HEGRID_OK;
   auto fail = [&](hegrid_status code) {
     plan->tune_f32_band = keep[0];
     plan->tune_tc_band = keep[1];
     plan->tune_tc_seg = keep[2];
+    plan->tune_tc_group = keep[3];
+    plan->tune_tc_kernel = keep[4];
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFreeAsync(scratch, s);
@@ -811,6 +890,8 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
     if (tc) {
       plan->tune_tc_band = pts[i].band;
       plan->tune_tc_seg = pts[i].seg;
+      plan->tune_tc_group = pts[i].group;
+      plan->tune_tc_kernel = pts[i].kernel;
     } else {
       plan->tune_f32_band = pts[i].band > 0 ? pts[i].band : -1;
     }
@@ -831,6 +912,8 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   if (tc) {
     plan->tune_tc_band = pts[best].band;
     plan->tune_tc_seg = pts[best].seg;
+    plan->tune_tc_group = pts[best].group;
+    plan->tune_tc_kernel = pts[best].kernel;
   } else {
     plan->tune_f32_band = pts[best].band > 0 ? pts[best].band : -1;
   }
@@ -845,7 +928,8 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
   return HEGRID_OK;
 }
 
-hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t band, int32_t seg) {
+hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t band, int32_t seg,
+                                     int32_t group, int32_t kernel) {
   hg::set_error("");
   HG_ARG_CHECK(plan != nullptr, "plan is NULL");
   if (mode == HEGRID_MODE_FP32) {
@@ -855,8 +939,12 @@ hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t b
     HG_ARG_CHECK(mode == HEGRID_MODE_TC || mode == HEGRID_MODE_TC_SPLIT, "unknown mode");
     HG_ARG_CHECK(band != INT32_MIN, "band out of range");
     HG_ARG_CHECK(seg >= 0 && seg <= 16, "seg must be in [0, 16]");
+    HG_ARG_CHECK(group >= 0, "group must be >= 0");
+    HG_ARG_CHECK(kernel >= 0 && kernel <= 2, "kernel must be 0, 1 or 2");
     plan->tune_tc_band = band;
     plan->tune_tc_seg = seg;
+    plan->tune_tc_group = group;
+    plan->tune_tc_kernel = kernel;
   }
   return HEGRID_OK;
 }

@@ -36,8 +36,9 @@
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warp 17     stages the chunk's sample rows (raw, as stored; eight
-//               four-row TMA tensor gathers per sub-chunk) and its weight
-//               entries (bulk copies) into a 3-deep shared-memory ring;
+//               four-row TMA tensor gathers per sub-chunk) into a ring;
+//   warp 22     stages the chunk's weight entries (bulk copies) into a
+//               3-deep ring of their own;
 //   warps 0-7   convert a staged chunk into the B tiles (row = channel; 16-byte
 //               pieces of 8 samples; no barrier among them);
 //   warps 8-15  zero the A tiles and store the chunk's weight entries into
@@ -82,6 +83,7 @@ constexpr int kM = HG_BLOCK_CELLS;         // cells per block
 constexpr int kStages = 2;                 // A/B tile ring
 constexpr int kDefaultSeg = 16;            // sub-chunks per accumulation segment
 constexpr int kDefaultBand = -8;  // work order: bands of 8 block columns, channel tiles fastest
+constexpr int kDefaultGroup = 0;  // ... all of a block's channel tiles side by side
 // The channel tile kN (64, 128 or 256: the MMA's N) is a template parameter:
 // the launcher takes the narrowest tile that holds C (256 above it), so few
 // channels do not pay for 256-column tiles.  So is kS, the 32-candidate
@@ -150,15 +152,20 @@ __device__ __forceinline__ int find_job(const JobTable& jt, int64_t item) {
 
 // Work order inside a job: cell blocks in bands of |J.band| block columns, so
 // concurrently running CTAs share candidate rows in L2, and the channel tiles
-// either slowest (J.band > 0) or fastest (J.band < 0: the tiles of a block run
-// side by side and share its weight entries in L2).
+// either slowest (J.band > 0) or in groups of J.group (0: all) run side by
+// side (J.band < 0: the tiles of a group share the block's weight entries in
+// L2; the groups follow one another over all blocks).
 __device__ __forceinline__ void item_coords(const GridJob& J, int64_t local, int64_t& b,
                                             int64_t& ct) {
   const int64_t nb = J.pv.n_blocks;
   int64_t bo;
   if (J.band < 0) {
-    ct = local % J.n_ctiles;
-    bo = local / J.n_ctiles;
+    const int64_t G = J.group > 0 && J.group < J.n_ctiles ? J.group : J.n_ctiles;
+    const int64_t grp = local / (G * nb);  // every group before the last is full
+    const int64_t r = local - grp * G * nb;
+    const int64_t Gg = min(G, J.n_ctiles - grp * G);
+    ct = grp * G + r % Gg;
+    bo = r / Gg;
   } else {
     ct = local / nb;
     bo = local - ct * nb;
@@ -169,6 +176,21 @@ __device__ __forceinline__ void item_coords(const GridJob& J, int64_t local, int
   const int64_t t = bo - band * per_band;
   const int64_t bw = min(kBand, (int64_t)J.pv.nbx_b - band * kBand);
   b = (t / bw) * J.pv.nbx_b + band * kBand + (t % bw);
+}
+
+// First chunk of block b's sweep.  A block's candidates run through its bin
+// window row by row, so the block above another (which runs at the same time
+// in the work order) reaches the rows the two share a fraction
+// J.rot = (block height) / (window height) of its sweep earlier; starting
+// each block's sweep at the fraction frac(-row * J.rot) of its chunks (and
+// wrapping around) has the blocks of neighbouring rows read their shared
+// sample rows at about the same time, while they are in L2.  J.rot = 0: no
+// rotation.  Every role of the CTA computes the same value.
+__device__ __forceinline__ int sweep_start(const GridJob& J, int64_t b, int n_chunks) {
+  if (J.rot <= 0.0f || n_chunks < 2) return 0;
+  float f = -(float)(b / J.pv.nbx_b) * J.rot;
+  f -= floorf(f);
+  return min((int)(f * (float)n_chunks), n_chunks - 1);
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
@@ -240,8 +262,9 @@ __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) 
 // Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT, int kN, int kS>
 __device__ __forceinline__ bool convert_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
-                                             int n_sub, int64_t c0, uint32_t& g, uint32_t& gr,
-                                             int32_t* err, uint64_t lim, bool withhold) {
+                                             int n_sub, int j0, int64_t c0, uint32_t& g,
+                                             uint32_t& gr, int32_t* err, uint64_t lim,
+                                             bool withhold) {
   using Sh = TcShape<kN, kS>;
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
@@ -260,7 +283,8 @@ __device__ __forceinline__ bool convert_item(TcSmem<kN, kS>& S, const GridJob& J
     if (!mbar_wait(&S.raw_full[rs], (gr / Sh::kRawStages) & 1u, err, lim)) return false;
     if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err, lim)) return false;
     // rows of a sub-chunk that the last chunk lacks are not staged: zeros
-    const bool present = kS == 1 || q0 * 8 < (n_sub - j * kS) * kK;
+    const int pj = j + j0 < n_chunks ? j + j0 : j + j0 - n_chunks;  // chunk of the sweep
+    const bool present = kS == 1 || q0 * 8 < (n_sub - pj * kS) * kK;
     const uint32_t rb = smem_u32(S.raw[rs]) + q0 * 8 * kPitch;
     const uint32_t bh = smem_u32(S.B[s][0]), bl = smem_u32(S.B[s][1]);
 #pragma unroll
@@ -464,52 +488,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
     const int eb = (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) ? 4 : 2;
 
+    // the sweep's j-th chunk (sweep_start: the sweep begins at chunk j0 and wraps)
+    const int j0 = sweep_start(J, b, n_chunks);
+    auto phys = [&](int jl) { return jl + j0 < n_chunks ? jl + j0 : jl + j0 - n_chunks; };
+
     if (warp == kTmaWarp) {
-      // ---------------- row and entry stager ----------------
+      // ---------------- row stager ----------------
       // Per chunk: the 32 kS sample rows (8 kS four-row tensor gathers of the
-      // channel tile; channels past C arrive as zeros) and the chunk's
-      // weight entries (two bulk copies of 16-byte aligned windows), all
-      // completing on raw_full.  Candidate indices are loaded two chunks
-      // ahead, sub-chunk offsets 31 / kS chunks at a time.
-      constexpr int kBatch = 31 / kS;
+      // channel tile; channels past C arrive as zeros), completing on
+      // raw_full.  Candidate indices are loaded two chunks ahead.
       const uint32_t row_bytes = (uint32_t)(kN * eb);
       const void* tmap = &J.rows;
-      const int64_t* __restrict__ so = pv.sub_off + kb0 / kK;
-      // this lane's candidate of each sub-chunk of chunk j (nA) and j + 1 (nB)
+      // this lane's candidate of each sub-chunk of the sweep's chunk j (nA) and j + 1 (nB)
       int32_t nA[kS], nB[kS];
+      {
+        const int p0 = phys(0), p1 = n_chunks > 1 ? phys(1) : 0;
 #pragma unroll
-      for (int t = 0; t < kS; ++t) {
-        nA[t] = t < n_sub ? __ldg(pv.cand_idx + kb0 + t * kK + lane) : 0;
-        nB[t] = kS + t < n_sub ? __ldg(pv.cand_idx + kb0 + (kS + t) * kK + lane) : 0;
+        for (int t = 0; t < kS; ++t) {
+          nA[t] = p0 * kS + t < n_sub ? __ldg(pv.cand_idx + kb0 + (int64_t)(p0 * kS + t) * kK + lane) : 0;
+          nB[t] = n_chunks > 1 && p1 * kS + t < n_sub
+                      ? __ldg(pv.cand_idx + kb0 + (int64_t)(p1 * kS + t) * kK + lane)
+                      : 0;
+        }
       }
-      int64_t sob = 0;
       for (int j = 0; j < n_chunks; ++j, ++gr) {
         const int r = gr % Sh::kRawStages;
         const uint32_t u = gr / Sh::kRawStages;
-        const int jb = j % kBatch;
-        if (jb == 0) sob = j * kS + lane <= n_sub ? __ldg(so + j * kS + lane) : 0;
-        const int nsj = min(kS, n_sub - j * kS);  // sub-chunks in this chunk
-        const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb * kS);
-        const int64_t e_mid = kS == 1 ? e_lo : __shfl_sync(0xffffffffu, sob, jb * kS + 1);
-        const int64_t e_end = __shfl_sync(0xffffffffu, sob, jb * kS + kS);
-        const int64_t e_hi = nsj == kS ? e_end : e_mid;
+        const int pj = phys(j);
+        const int nsj = min(kS, n_sub - pj * kS);  // sub-chunks in this chunk
+        const int p2 = j + 2 < n_chunks ? phys(j + 2) : -1;
         int32_t n[kS];  // this lane's rows
 #pragma unroll
         for (int t = 0; t < kS; ++t) {
           n[t] = nA[t];
           nA[t] = nB[t];
-          const int64_t q = (int64_t)(j + 2) * kS + t;
-          if (q < n_sub) nB[t] = __ldg(pv.cand_idx + kb0 + q * kK + lane);
+          if (p2 >= 0 && p2 * kS + t < n_sub)
+            nB[t] = __ldg(pv.cand_idx + kb0 + (int64_t)(p2 * kS + t) * kK + lane);
         }
         if (u >= 1 && !mbar_wait(&S.raw_empty[r], (u - 1) & 1u, err, lim)) {
           bail = true;
           break;
         }
-        const int ne = (int)(e_hi - e_lo);
-        const int ns = ne < Sh::kEntStage ? ne : Sh::kEntStage;
-        const int64_t a0 = (e_lo * 2) & ~(int64_t)15, b0 = (e_lo * 4) & ~(int64_t)15;
-        const uint32_t abytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 2 + 15) & ~(int64_t)15) - a0) : 0u;
-        const uint32_t wbytes = ns > 0 ? (uint32_t)((((e_lo + ns) * 4 + 15) & ~(int64_t)15) - b0) : 0u;
         if (lane == 0) mbar_arrive_expect_tx(&S.raw_full[r], row_bytes * (uint32_t)(kK * nsj));
         __syncwarp();
 #pragma unroll
@@ -529,15 +548,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
 
     if (warp == kEntWarp) {
       // ---------------- entry stager ----------------
+      // Sub-chunk offsets are loaded 31 / kS chunks at a time (lane i holds
+      // the offset of sub-chunk pb kS + i; reloaded where the sweep wraps).
       constexpr int kBatch = 31 / kS;
       const int64_t* __restrict__ so = pv.sub_off + kb0 / kK;
       int64_t sob = 0;
+      int pb = 0;  // chunk whose first sub-chunk lane 0's offset belongs to
       for (int j = 0; j < n_chunks; ++j, ++gr) {
         const int r = gr % Sh::kEntStages;
         const uint32_t u = gr / Sh::kEntStages;
-        const int jb = j % kBatch;
-        if (jb == 0) sob = j * kS + lane <= n_sub ? __ldg(so + j * kS + lane) : 0;
-        const int nsj = min(kS, n_sub - j * kS);  // sub-chunks in this chunk
+        const int pj = phys(j);
+        if (j == 0 || pj == 0 || pj - pb >= kBatch) {
+          pb = pj;
+          sob = pb * kS + lane <= n_sub ? __ldg(so + pb * kS + lane) : 0;
+        }
+        const int jb = pj - pb;
+        const int nsj = min(kS, n_sub - pj * kS);  // sub-chunks in this chunk
         const int64_t e_lo = __shfl_sync(0xffffffffu, sob, jb * kS);
         const int64_t e_mid = kS == 1 ? e_lo : __shfl_sync(0xffffffffu, sob, jb * kS + 1);
         const int64_t e_end = __shfl_sync(0xffffffffu, sob, jb * kS + kS);
@@ -604,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
         tc_fence_after();
         if (lane == 0) {
           const uint32_t d = tmem + dcol;
-          const int nsj = min(kS, n_sub - j * kS);
+          const int nsj = min(kS, n_sub - phys(j) * kS);
 #pragma unroll
           for (int t = 0; t < kS; ++t) {
             if (t >= nsj) break;
@@ -740,17 +766,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
                    : build_a_item<false, kN, kS>(S, J, n_chunks, g, gr, err, lim);
       } else if (split) {  // B converters
         switch (J.dtype) {
-          case HEGRID_F32: ok = convert_item<HEGRID_F32, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_F16: ok = convert_item<HEGRID_F16, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
-          default: ok = convert_item<HEGRID_BF16X2, true, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F32: ok = convert_item<HEGRID_F32, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F16: ok = convert_item<HEGRID_F16, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          default: ok = convert_item<HEGRID_BF16X2, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = convert_item<HEGRID_F32, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_F16: ok = convert_item<HEGRID_F16, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
-          default: ok = convert_item<HEGRID_BF16X2, false, kN, kS>(S, J, n_chunks, n_sub, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F32: ok = convert_item<HEGRID_F32, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F16: ok = convert_item<HEGRID_F16, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          default: ok = convert_item<HEGRID_BF16X2, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
         }
       }
       bail = !ok;
@@ -795,6 +821,7 @@ hegrid_status launch_tile(const JobTable& jt, cudaStream_t s) {
 int tc_channel_tile(int64_t C) { return C <= 64 ? 64 : C <= 128 ? 128 : 256; }
 int tc_default_band() { return kDefaultBand; }
 int tc_default_seg() { return kDefaultSeg; }
+int tc_default_group() { return kDefaultGroup; }
 
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile) {
   switch (tile) {

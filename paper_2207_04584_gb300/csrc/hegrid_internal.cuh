@@ -91,6 +91,10 @@ struct PlanView {
                             // (a block's last sub-chunk is followed by its end sentinel)
   const uint16_t* ent_ck;   // [P] entry: tile_off(block-local cell, candidate & 31)
   const float* ent_w;       // [P] FP32 weight of the entry
+  // [slots/32] dense weight tiles of the channel-major tensor-core kernel
+  // (16 KB per sub-chunk: FP16 hi then lo halves of the weights x 2^15, 128
+  // cells x 32 candidates, K-major, 64-byte swizzle); NULL until built
+  const uint8_t* wtiles;
   int32_t* err_word;        // device error word (bounded waits)
 };
 
@@ -120,8 +124,15 @@ struct hegrid_plan {
   int32_t* err_word;
   int64_t bytes;
   // Launch shapes chosen by hegrid_autotune (0: defaults): FP32 band, tensor
-  // core band and segment length.
-  int32_t tune_f32_band, tune_tc_band, tune_tc_seg;
+  // core band, segment length and channel-tile group.
+  int32_t tune_f32_band, tune_tc_band, tune_tc_seg, tune_tc_group;
+  // Tensor-core kernel: 0 (default) and 1: cell-major; 2: channel-major
+  // (where its weight tiles exist or can be built).
+  int32_t tune_tc_kernel;
+  // Dense weight tiles of the channel-major kernel (owned; built by the first
+  // grid call that runs it, on that call's stream, which then re-records
+  // `ready`).
+  uint8_t* wtiles;
   // Recorded on the creation stream after the last plan kernel.  The plan's
   // memory comes from a stream-ordered pool, so every other stream must wait
   // on this event before touching it.
@@ -141,6 +152,7 @@ struct hegrid_plan {
     v.sub_off = sub_off;
     v.ent_ck = ent_ck;
     v.ent_w = ent_w;
+    v.wtiles = wtiles;
     v.err_word = err_word;
     return v;
   }
@@ -171,6 +183,11 @@ struct GridJob {
   // (0: channel tiles fastest, FP32 kernel only) and chunks per accumulation
   // segment (tensor-core kernel).
   int32_t band, seg;
+  // Tensor-core kernel: channel tiles run side by side in groups of `group`
+  // (band < 0; 0: all of a block's tiles), and the sweep over a block's
+  // candidates starts at the fraction frac(-row * rot) of it (0: no rotation).
+  int32_t group;
+  float rot;
   int64_t n_ctiles;   // channel tiles
   int64_t item_base;  // first work item of this job in the queue
 };
@@ -204,5 +221,13 @@ int f32_channel_tile();
 int tc_channel_tile(int64_t C);
 int tc_default_band();
 int tc_default_seg();
+int tc_default_group();
+// Channel-major tensor-core kernel (grid_tcm.cu): its channel tile (128), the
+// bytes of a plan's dense weight tiles for `slots` candidate slots, their
+// build, and the grid launch (every job's plan must have its tiles).
+int tcm_channel_tile();
+int64_t tcm_wtile_bytes(int64_t slots);
+hegrid_status launch_build_wtiles(const PlanView& pv, uint8_t* wtiles, cudaStream_t s);
+hegrid_status launch_grid_tcm(const JobTable& jt, cudaStream_t s);
 
 }  // namespace hg

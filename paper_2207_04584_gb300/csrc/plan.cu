@@ -1188,7 +1188,8 @@ static cudaError_t dmalloc(T** p, int64_t n, int64_t* bytes, cudaStream_t st) {
 
 void free_plan_arrays(hegrid_plan* p, cudaStream_t st) {
   void* arrays[] = {p->perm,   p->bin_off, p->cand_off, p->blk_pair_off, p->cand_cnt, p->cand_idx,
-                    p->sub_off, p->ent_ck,  p->ent_w,    p->wsum,         p->totals,   p->err_word};
+                    p->sub_off, p->ent_ck,  p->ent_w,    p->wsum,         p->totals,   p->err_word,
+                    p->wtiles};
   for (void* a : arrays)
     if (a) cudaFreeAsync(a, st);
 }

@@ -63,11 +63,12 @@ class hegrid_grid_args(ctypes.Structure):
                 ("mode", ctypes.c_uint32)]
 
 
-HEGRID_TUNE_MAX = 16
+HEGRID_TUNE_MAX = 40
 
 
 class hegrid_tune_point(ctypes.Structure):
-    _fields_ = [("band", ctypes.c_int32), ("seg", ctypes.c_int32), ("ms", ctypes.c_float)]
+    _fields_ = [("band", ctypes.c_int32), ("seg", ctypes.c_int32), ("group", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("ms", ctypes.c_float)]
 
 
 class hegrid_tune_report(ctypes.Structure):
@@ -114,7 +115,8 @@ def lib():
     L.hegrid_autotune_bins.argtypes = [i64, P, P, c_int, ctypes.POINTER(hegrid_map_geom),
                                        ctypes.POINTER(hegrid_kernel), P,
                                        ctypes.POINTER(ctypes.c_int32), P]
-    L.hegrid_plan_set_tuning.argtypes = [P, u32, ctypes.c_int32, ctypes.c_int32]
+    L.hegrid_plan_set_tuning.argtypes = [P, u32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32]
     L.hegrid_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), P]
     L.hegrid_pool_usage.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.hegrid_last_error.restype = ctypes.c_char_p
@@ -276,7 +278,8 @@ def hegrid_autotune(plan, values, dtype, n_channels, ld_values, mode, stream=Non
     r = hegrid_tune_report()
     _check(lib().hegrid_autotune(plan, _ptr(values), int(dtype), int(n_channels), int(ld_values),
                                  int(mode), _ptr(stream), ctypes.byref(r)), "hegrid_autotune")
-    pts = [{"band": r.pt[i].band, "seg": r.pt[i].seg, "ms": r.pt[i].ms} for i in range(r.n)]
+    pts = [{"band": r.pt[i].band, "seg": r.pt[i].seg, "group": r.pt[i].group,
+            "kernel": r.pt[i].kernel, "ms": r.pt[i].ms} for i in range(r.n)]
     return {"points": pts, "best": r.best}
 
 
@@ -294,8 +297,9 @@ def hegrid_autotune_bins(n_samples, lon_deg, lat_deg, coords_on_device, geom, fw
     return best.value, list(ms)
 
 
-def hegrid_plan_set_tuning(plan, mode, band, seg=0):
-    return _check(lib().hegrid_plan_set_tuning(plan, int(mode), int(band), int(seg)),
+def hegrid_plan_set_tuning(plan, mode, band, seg=0, group=0, kernel=0):
+    return _check(lib().hegrid_plan_set_tuning(plan, int(mode), int(band), int(seg), int(group),
+                                               int(kernel)),
                   "hegrid_plan_set_tuning")
 
 

@@ -163,3 +163,84 @@ def test_grid_faults_leak_nothing(H, fault, what, status):
         H.hegrid_status_poll(plan)
     finally:
         H.hegrid_plan_destroy(plan)
+
+
+def test_channel_major_wait_timeout(H, fault):
+    """The channel-major tensor-core kernel's bounded waits: one value warp
+    withholds its first arrive, every role gives up, TIMEOUT is reported and
+    the plan grids correctly afterwards."""
+    wl = W.config1(n=6000, C=200, nx=48, ny=40)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    s = torch.cuda.current_stream().cuda_stream
+    v = torch.from_numpy(wl["values"]).cuda()
+    out = torch.zeros((M, 200), device="cuda")
+    plan = _plan(H, wl)
+    try:
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, 2)
+        fault("wait:1")
+        H.hegrid_grid(plan, v, H.HEGRID_F32, 200, 200, out, 200, None, H.HEGRID_MODE_TC_SPLIT, s)
+        torch.cuda.synchronize()
+        fault(None)
+        with pytest.raises(H.HegridError) as e:
+            H.hegrid_status_poll(plan)
+        assert e.value.status == H.HEGRID_ERR_TIMEOUT
+    finally:
+        H.hegrid_plan_destroy(plan)
+    plan = _plan(H, wl)
+    try:
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, 2)
+        H.hegrid_grid(plan, v, H.HEGRID_F32, 200, 200, out, 200, None, H.HEGRID_MODE_TC_SPLIT, s)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
+    assert err <= 5e-5, err
+
+
+@pytest.mark.parametrize("what,status", [("alloc:1", "HEGRID_ERR_OOM"),
+                                         ("alloc:2", "HEGRID_ERR_OOM"),
+                                         ("launch:1", "HEGRID_ERR_CUDA"),
+                                         ("launch:2", "HEGRID_ERR_CUDA"),
+                                         ("launch:3", "HEGRID_ERR_CUDA")])
+def test_channel_major_first_call_faults_leak_nothing(H, fault, what, status):
+    """The first channel-major grid call on a plan allocates the channel maxima
+    (allocation 1) and the plan's dense weight tiles (2), then launches the
+    tile build (launch 1), the maxima pass (2) and the grid kernel (3).  A
+    failure anywhere returns its status; the tiles stay with the plan only if
+    they were built (then the plan owns and later frees them), and the next
+    call succeeds."""
+    wl = W.config1(n=6000, C=200, nx=48, ny=40)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    s = torch.cuda.current_stream().cuda_stream
+    v = torch.from_numpy(wl["values"]).cuda()
+    out = torch.zeros((M, 200), device="cuda")
+    base0 = _used(H)
+    plan = _plan(H, wl)
+    try:
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, 2)
+        base = _used(H)
+        b0 = H.hegrid_plan_info(plan)["bytes"]
+        fault(what)
+        with pytest.raises(H.HegridError) as e:
+            H.hegrid_grid(plan, v, H.HEGRID_F32, 200, 200, out, 200, None,
+                          H.HEGRID_MODE_TC_SPLIT, s)
+        fault(None)
+        assert e.value.status == getattr(H, status)
+        built = H.hegrid_plan_info(plan)["bytes"] - b0  # the tiles, if they were built
+        if what in ("alloc:1", "alloc:2", "launch:1"):
+            assert built == 0 and _used(H) == base
+        else:
+            assert built > 0 and _used(H) > base
+        H.hegrid_grid(plan, v, H.HEGRID_F32, 200, 200, out, 200, None, H.HEGRID_MODE_TC_SPLIT, s)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    assert _used(H) == base0
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
+    assert err <= 5e-5, err

@@ -31,10 +31,15 @@ def H():
     return hegrid
 
 
-def _plan(H, wl):
-    return H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
-                                np.ascontiguousarray(wl["lat"]), 0, wl["geom"], wl["fwhm_deg"],
-                                wl.get("support", 3.0), 0, torch.cuda.current_stream().cuda_stream)
+def _plan(H, wl, kernel=0):
+    """A plan whose tensor-core calls run `kernel` (0: default, 1: cell-major,
+    2: channel-major)."""
+    p = H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
+                             np.ascontiguousarray(wl["lat"]), 0, wl["geom"], wl["fwhm_deg"],
+                             wl.get("support", 3.0), 0, torch.cuda.current_stream().cuda_stream)
+    if kernel:
+        H.hegrid_plan_set_tuning(p, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, kernel)
+    return p
 
 
 def _run(H, plan, vdev, dtype, C, ld, M, mode):
@@ -85,14 +90,16 @@ def test_tc_f32_config1(H, mode, tol):
     assert np.max(np.abs(gw[has] / Wref[has] - 1.0)) <= wtol
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("C", [1, 5, 64, 65, 100, 128, 129, 256, 257, 300])
-def test_tc_split_ragged_channels(H, C):
-    """Every channel-tile width (64, 128, 256) and its edges, ragged and full."""
+def test_tc_split_ragged_channels(H, C, kernel):
+    """Every channel-tile width (64, 128, 256 cell-major; 128 channel-major)
+    and its edges, ragged and full."""
     wl = _case(51, C=C)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
     v, ld = _padded(wl["values"], 4)
-    plan = _plan(H, wl)
+    plan = _plan(H, wl, kernel)
     try:
         got, _ = _run(H, plan, torch.from_numpy(v).cuda(), H.HEGRID_F32, C, ld, M,
                       H.HEGRID_MODE_TC_SPLIT)
@@ -325,9 +332,10 @@ def _stored(kind, vals, H):
         np.ascontiguousarray(stored.astype(np.float32))
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("kind", ["f32", "bf16x2", "bf16", "f16"])
 @pytest.mark.parametrize("C", [50, 100, 300])
-def test_tc_split_mixed_channel_scales(H, kind, C):
+def test_tc_split_mixed_channel_scales(H, kind, C, kernel):
     """Eq. 1 holds per channel: a faint channel must keep the split form's
     accuracy relative to its own RMS when it shares a channel tile (64, 128 or
     256 wide, by C) with channels many decades brighter.  Channel c is scaled
@@ -339,7 +347,7 @@ def test_tc_split_mixed_channel_scales(H, kind, C):
     e = (np.arange(C) % 7 - 4) if kind == "f16" else (np.arange(C) % 11 - 6)
     vals = (wl["values"].astype(np.float64) * 10.0 ** e[None, :]).astype(np.float32)
     dv, dt, ld, seen = _stored(kind, vals, H)
-    plan = _plan(H, wl)
+    plan = _plan(H, wl, kernel)
     try:
         got, gw = _run(H, plan, dv, dt, C, ld, M, H.HEGRID_MODE_TC_SPLIT)
     finally:
@@ -351,3 +359,37 @@ def test_tc_split_mixed_channel_scales(H, kind, C):
     assert np.array_equal(np.isnan(got), np.isnan(ref))
     has = Wref > 0
     assert np.max(np.abs(gw[has] / Wref[has] - 1.0)) <= 2e-5
+
+
+@pytest.mark.parametrize("C", [100, 300])
+@pytest.mark.parametrize("kind", ["f32", "bf16x2", "bf16", "f16"])
+@pytest.mark.parametrize("mode", ["split", "single"])
+def test_channel_major_equals_cell_major(H, C, kind, mode):
+    """The channel-major kernel (values as the MMA's A operand in tensor memory,
+    weights from the plan's dense tiles) forms the same products as the
+    cell-major kernel and adds them in the same segments; only the tensor
+    core's internal summation order differs with the MMA shape.  So the maps
+    agree to a few units of FP32 rounding relative to each channel's RMS,
+    with the same NaN pattern, and the weight maps (the plan's) are equal; a
+    repeated cell-major call is bit-identical to the first."""
+    wl = _case(71 + C, n=9000, nx=56, ny=32, C=C)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    dv, dt, ld, _ = _stored(kind, wl["values"], H)
+    md = H.HEGRID_MODE_TC_SPLIT if mode == "split" else H.HEGRID_MODE_TC
+    maps = []
+    plan = _plan(H, wl)
+    try:
+        for kernel in (1, 2, 1):
+            H.hegrid_plan_set_tuning(plan, md, -4, 16, 0, kernel)
+            maps.append(_run(H, plan, dv, dt, C, ld, M, md))
+    finally:
+        H.hegrid_plan_destroy(plan)
+    (a, wa), (b, wb), (c, wc) = maps
+    assert np.array_equal(a, c, equal_nan=True)
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    ok = ~np.isnan(a[:, 0])
+    rms = np.sqrt(np.mean(a[ok].astype(np.float64) ** 2, axis=0))
+    diff = np.max(np.abs(a[ok].astype(np.float64) - b[ok]), axis=0) / rms
+    assert diff.max() <= 2e-6, diff.max()
+    assert np.array_equal(wa, wb) and np.array_equal(wa, wc)

@@ -87,6 +87,33 @@ def test_every_shape_matches_oracle(H, mode, band, seg):
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("band,seg,group", [(-2, 16, 2), (-4, 8, 2), (-1 << 20, 16, 1),
+                                            (-2, 16, 0), (3, 16, 0), (-3, 16, 5)])
+def test_channel_tile_groups_match_oracle(H, band, seg, group):
+    """Channel tiles side by side in groups (a last group with fewer tiles; a
+    group wider than the tiles) and the rotated candidate sweeps of the
+    tensor-core work order give the oracle's map in every channel tile."""
+    wl = W.config1(n=12000, C=700, nx=70, ny=40)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    C = wl["values"].shape[1]
+    s = torch.cuda.current_stream().cuda_stream
+    plan = H.hegrid_plan_create(len(wl["lon"]), wl["lon"], wl["lat"], 0, g, wl["fwhm_deg"], 3.0,
+                                0, s)
+    try:
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, band, seg, group)
+        v = torch.from_numpy(wl["values"]).cuda()
+        out = torch.full((M, C), -7.0, device="cuda")
+        H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, None, H.HEGRID_MODE_TC_SPLIT, s)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], g, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(out.cpu().numpy(), ref, Wref)
+    assert err <= TOL_SPLIT, err
+
+
 def test_set_tuning_rejects_bad_shapes(H):
     wl = W.config1(n=2000, C=4, nx=20, ny=20)
     s = torch.cuda.current_stream().cuda_stream
@@ -98,6 +125,9 @@ def test_set_tuning_rejects_bad_shapes(H):
             with pytest.raises(H.HegridError) as e:
                 H.hegrid_plan_set_tuning(plan, md, band, seg)
             assert e.value.status == H.HEGRID_ERR_INVALID_ARG
+        with pytest.raises(H.HegridError) as e:
+            H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, -4, 16, -1)
+        assert e.value.status == H.HEGRID_ERR_INVALID_ARG
     finally:
         H.hegrid_plan_destroy(plan)
 
