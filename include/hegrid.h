@@ -147,6 +147,43 @@ hegrid_status hegrid_grid(hegrid_plan *plan, const void *values, hegrid_dtype dt
                           int64_t n_channels, int64_t ld_values, float *map_out, int64_t ld_map,
                           float *weight_out, uint32_t mode, void *stream);
 
+/*
+ * hegrid_chan_maxima -- the largest |v| of each channel of `values` (as FP32
+ * bits; NaN ignored), the statistic that sets each channel's power-of-two
+ * scale in the tensor-core modes (see hegrid_grid; the scale is part of the
+ * FP16 conversion that Eq. 1's products go through on the tensor cores, the
+ * paper has no counterpart).  It depends on the values only, not on a plan,
+ * so a caller can run it on another stream while the plan is being created
+ * and pass the result to hegrid_grid_prescaled.  Asynchronous on `stream`.
+ *
+ * values     device [n_samples x ld_values] of `dtype`, as for hegrid_grid.
+ * chmax_out  device uint32 [n_channels], written (caller-owned).
+ *
+ * Errors: INVALID_ARG (NULL pointers, n_samples < 1, n_channels < 1, bad
+ * ld/alignment/dtype); CUDA (launch failure).
+ */
+hegrid_status hegrid_chan_maxima(const void *values, hegrid_dtype dtype, int64_t n_samples,
+                                 int64_t n_channels, int64_t ld_values, uint32_t *chmax_out,
+                                 void *stream);
+
+/*
+ * hegrid_grid_prescaled -- hegrid_grid with the channel maxima already
+ * computed by hegrid_chan_maxima on the same values (device [n_channels],
+ * complete in stream order before this call's work, e.g. through an event):
+ * the tensor-core modes skip their own pass over the values and the scratch
+ * for the maxima.  Maxima of other values give wrong maps (values above a
+ * channel's stated maximum overflow its FP16 scale).  chmax may be NULL for
+ * HEGRID_MODE_FP32 and for HEGRID_F16 values, which are not scaled.  The map
+ * is identical to hegrid_grid's on the same inputs.
+ *
+ * Errors: as for hegrid_grid; INVALID_ARG also for chmax NULL where it is
+ * needed.
+ */
+hegrid_status hegrid_grid_prescaled(hegrid_plan *plan, const void *values, hegrid_dtype dtype,
+                                    int64_t n_channels, int64_t ld_values, const uint32_t *chmax,
+                                    float *map_out, int64_t ld_map, float *weight_out,
+                                    uint32_t mode, void *stream);
+
 /* Free the plan and all of its device memory (synchronises the device).
  * NULL is a no-op.  Returns OK.  (Library service; no step of the paper.) */
 hegrid_status hegrid_plan_destroy(hegrid_plan *plan);

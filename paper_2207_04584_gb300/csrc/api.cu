@@ -387,9 +387,11 @@ int64_t scaled_channels(int n, const hegrid_grid_args* args) {
 // wait_ready: make `s` wait for each plan's creation (false inside a graph
 // capture, where the caller has synchronised the plans on the host instead).
 // chmax_buf: room for scaled_channels() channel maxima, or NULL to take it
-// from the pool for this call.
+// from the pool for this call; chmax_ready: chmax_buf already holds them
+// (hegrid_chan_maxima), so the maximum pass is skipped.
 hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args* args,
-                        cudaStream_t s, bool wait_ready = true, uint32_t* chmax_buf = nullptr) {
+                        cudaStream_t s, bool wait_ready = true, uint32_t* chmax_buf = nullptr,
+                        bool chmax_ready = false) {
   HG_ARG_CHECK(n >= 0, "n must be >= 0");
   HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
   // tensor-core jobs grouped by kernel and channel tile (cell-major 64, 128,
@@ -408,7 +410,7 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
   hegrid_status st = HEGRID_OK;
   std::vector<AbsmaxRequest> amax;
   auto run = [&]() -> hegrid_status {
-    if (n_scaled > 0)
+    if (n_scaled > 0 && !chmax_ready)
       HG_CUDA_TRY(cudaMemsetAsync(chmax, 0, sizeof(uint32_t) * (size_t)n_scaled, s));
     int64_t at = 0;
     for (int i = 0; i < n; ++i) {
@@ -445,8 +447,10 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
       }
     }
     // every entry's channel maxima in one launch, ahead of the grid kernels
-    hegrid_status e = launch_chan_absmax((int)amax.size(), amax.data(), s);
-    if (e != HEGRID_OK) return e;
+    if (!chmax_ready) {
+      hegrid_status e = launch_chan_absmax((int)amax.size(), amax.data(), s);
+      if (e != HEGRID_OK) return e;
+    }
     if (!f32.empty()) {
       hegrid_status e = launch_family(f32, false, s);
       if (e != HEGRID_OK) return e;
@@ -534,6 +538,51 @@ hegrid_status hegrid_grid(hegrid_plan* plan, const void* values, hegrid_dtype dt
   a.mode = mode;
   hegrid_plan* p[1] = {plan};
   return hg::grid_many(1, p, &a, (cudaStream_t)stream);
+}
+
+hegrid_status hegrid_chan_maxima(const void* values, hegrid_dtype dtype, int64_t n_samples,
+                                 int64_t n_channels, int64_t ld_values, uint32_t* chmax_out,
+                                 void* stream) {
+  hg::set_error("");
+  HG_ARG_CHECK(values != nullptr && chmax_out != nullptr, "values or chmax_out is NULL");
+  HG_ARG_CHECK(n_samples >= 1, "n_samples must be >= 1");
+  HG_ARG_CHECK(n_channels >= 1, "n_channels must be >= 1");
+  const int eb = hg::elem_bytes((int)dtype);
+  HG_ARG_CHECK(eb > 0, "unknown dtype");
+  HG_ARG_CHECK(ld_values >= n_channels, "ld_values < n_channels");
+  HG_ARG_CHECK((ld_values * eb) % 16 == 0, "ld_values * element size must be a multiple of 16");
+  HG_ARG_CHECK(((uintptr_t)values & 15u) == 0, "values must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  HG_CUDA_TRY(cudaMemsetAsync(chmax_out, 0, sizeof(uint32_t) * (size_t)n_channels, s));
+  hg::AbsmaxRequest r;
+  r.values = values;
+  r.dtype = (int)dtype;
+  r.n_rows = n_samples;
+  r.C = n_channels;
+  r.ld = ld_values;
+  r.out = chmax_out;
+  return hg::launch_chan_absmax(1, &r, s);
+}
+
+hegrid_status hegrid_grid_prescaled(hegrid_plan* plan, const void* values, hegrid_dtype dtype,
+                                    int64_t n_channels, int64_t ld_values, const uint32_t* chmax,
+                                    float* map_out, int64_t ld_map, float* weight_out,
+                                    uint32_t mode, void* stream) {
+  hg::set_error("");
+  hegrid_grid_args a;
+  a.values = values;
+  a.dtype = dtype;
+  a.n_channels = n_channels;
+  a.ld_values = ld_values;
+  a.map_out = map_out;
+  a.ld_map = ld_map;
+  a.weight_out = weight_out;
+  a.mode = mode;
+  hegrid_plan* p[1] = {plan};
+  const bool need = mode != HEGRID_MODE_FP32 && dtype != HEGRID_F16;
+  HG_ARG_CHECK(!need || chmax != nullptr, "chmax is NULL");
+  return hg::grid_many(1, p, &a, (cudaStream_t)stream, true, const_cast<uint32_t*>(chmax),
+                       need);
 }
 
 hegrid_status hegrid_grid_masked(hegrid_plan* plan, const void* values, hegrid_dtype dtype,

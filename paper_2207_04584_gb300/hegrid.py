@@ -43,7 +43,8 @@ EXPORTED = ["hegrid_plan_create", "hegrid_grid", "hegrid_plan_destroy", "hegrid_
             "hegrid_grid_stream", "hegrid_plan_info", "hegrid_plan_export", "hegrid_status_poll",
             "hegrid_launch_count", "hegrid_last_error", "hegrid_bin_sort_noalloc",
             "hegrid_autotune", "hegrid_autotune_bins", "hegrid_plan_set_tuning",
-            "hegrid_fp32_peak", "hegrid_grid_masked", "hegrid_pool_usage"]
+            "hegrid_fp32_peak", "hegrid_grid_masked", "hegrid_pool_usage",
+            "hegrid_chan_maxima", "hegrid_grid_prescaled"]
 
 
 class hegrid_map_geom(ctypes.Structure):
@@ -100,6 +101,8 @@ def lib():
                                      ctypes.POINTER(hegrid_kernel), u32, P]
     L.hegrid_grid.argtypes = [P, P, c_int, i64, i64, P, i64, P, u32, P]
     L.hegrid_grid_masked.argtypes = [P, P, c_int, i64, i64, P, i64, P, u32, P]
+    L.hegrid_chan_maxima.argtypes = [P, c_int, i64, i64, i64, P, P]
+    L.hegrid_grid_prescaled.argtypes = [P, P, c_int, i64, i64, P, P, i64, P, u32, P]
     L.hegrid_plan_destroy.argtypes = [P]
     L.hegrid_grid_batched.argtypes = [c_int, PP, ctypes.POINTER(hegrid_grid_args), P]
     L.hegrid_batch_create.argtypes = [PP, c_int, PP, ctypes.POINTER(hegrid_grid_args), P]
@@ -174,6 +177,22 @@ def hegrid_grid(plan, values, dtype, n_channels, ld_values, map_out, ld_map, wei
     return _check(lib().hegrid_grid(plan, _ptr(values), int(dtype), int(n_channels),
                                     int(ld_values), _ptr(map_out), int(ld_map), _ptr(weight_out),
                                     int(mode), _ptr(stream)), "hegrid_grid")
+
+
+def hegrid_chan_maxima(values, dtype, n_samples, n_channels, ld_values, chmax_out, stream=None):
+    """Per-channel largest |v| (FP32 bits) into chmax_out (device uint32 [C])."""
+    return _check(lib().hegrid_chan_maxima(_ptr(values), int(dtype), int(n_samples),
+                                           int(n_channels), int(ld_values), _ptr(chmax_out),
+                                           _ptr(stream)), "hegrid_chan_maxima")
+
+
+def hegrid_grid_prescaled(plan, values, dtype, n_channels, ld_values, chmax, map_out, ld_map,
+                          weight_out, mode, stream=None):
+    """hegrid_grid with channel maxima from hegrid_chan_maxima."""
+    return _check(lib().hegrid_grid_prescaled(plan, _ptr(values), int(dtype), int(n_channels),
+                                              int(ld_values), _ptr(chmax), _ptr(map_out),
+                                              int(ld_map), _ptr(weight_out), int(mode),
+                                              _ptr(stream)), "hegrid_grid_prescaled")
 
 
 def hegrid_grid_masked(plan, values, dtype, n_channels, ld_values, map_out, ld_map, wc_out,

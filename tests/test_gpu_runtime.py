@@ -190,3 +190,58 @@ def test_stream_unaligned_rows(H, dtype, cc, n_chunks):
     a, b = ref.cpu().numpy(), hmap.numpy()
     assert np.array_equal(np.isnan(a), np.isnan(b))
     assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kind", ["f32", "bf16", "f16"])
+def test_grid_prescaled_overlapped_with_plan(H, kernel, kind):
+    """The channel maxima computed on a second stream while the plan is built
+    (hegrid_chan_maxima), then hegrid_grid_prescaled: the maxima are each
+    channel's largest |v| bit for bit, and the map and weight map equal
+    hegrid_grid's element for element, for both tensor-core kernels."""
+    wl = W.config1(n=15000, C=300, nx=70, ny=50)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    C = 300
+    vt = torch.from_numpy(wl["values"])
+    dt = {"f32": (torch.float32, H.HEGRID_F32), "bf16": (torch.bfloat16, H.HEGRID_BF16),
+          "f16": (torch.float16, H.HEGRID_F16)}[kind]
+    ld = 304
+    v = torch.zeros((len(wl["lon"]), ld), dtype=dt[0])
+    v[:, :C] = vt.to(dt[0])
+    v = v.cuda()
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    chmax = torch.empty(C, dtype=torch.int32, device="cuda")
+    ready = torch.cuda.Event()
+    ready.record(main)
+    side.wait_event(ready)
+    H.hegrid_chan_maxima(v, dt[1], v.shape[0], C, ld, chmax, side.cuda_stream)
+    done = torch.cuda.Event()
+    done.record(side)
+    plan = H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
+                                np.ascontiguousarray(wl["lat"]), 0, g, wl["fwhm_deg"], 3.0, 0,
+                                main.cuda_stream)
+    try:
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, kernel)
+        main.wait_event(done)
+        a = torch.full((M, C), -7.0, device="cuda")
+        wa = torch.full((M,), -7.0, device="cuda")
+        H.hegrid_grid_prescaled(plan, v, dt[1], C, ld, chmax, a, C, wa, H.HEGRID_MODE_TC_SPLIT,
+                                main.cuda_stream)
+        b = torch.full((M, C), -7.0, device="cuda")
+        wb = torch.full((M,), -7.0, device="cuda")
+        H.hegrid_grid(plan, v, dt[1], C, ld, b, C, wb, H.HEGRID_MODE_TC_SPLIT, main.cuda_stream)
+        torch.cuda.synchronize()
+        H.hegrid_status_poll(plan)
+        if kind != "f16":  # scaled values need the maxima
+            with pytest.raises(H.HegridError) as e:
+                H.hegrid_grid_prescaled(plan, v, dt[1], C, ld, None, a, C, wa,
+                                        H.HEGRID_MODE_TC_SPLIT, main.cuda_stream)
+            assert e.value.status == H.HEGRID_ERR_INVALID_ARG
+    finally:
+        H.hegrid_plan_destroy(plan)
+    ref = v[:, :C].float().abs().amax(dim=0)
+    assert torch.equal(chmax.cpu(), ref.cpu().view(torch.int32))
+    assert torch.equal(torch.nan_to_num(a, nan=-1.0), torch.nan_to_num(b, nan=-1.0))
+    assert torch.equal(wa, wb)
