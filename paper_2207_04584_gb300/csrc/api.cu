@@ -473,7 +473,8 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
 
 }  // namespace
 
-hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s) {
+hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s,
+                                 int ctas_per_sm) {
   if (n <= 0) return HEGRID_OK;
   int dev = 0, n_sm = 0;
   HG_CUDA_TRY(cudaGetDevice(&dev));
@@ -499,8 +500,8 @@ hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s
       J.cols = (int32_t)std::min<int64_t>(nvec, 256);
       const int rpt = 256 / J.cols;
       J.gy = (int32_t)((nvec + J.cols - 1) / J.cols);
-      // about 8 CTAs per SM over all channel groups, each thread >= 32 rows
-      int64_t gx = std::max<int64_t>(1, (8 * (int64_t)n_sm + J.gy - 1) / J.gy);
+      // about ctas_per_sm CTAs per SM over all channel groups, each thread >= 32 rows
+      int64_t gx = std::max<int64_t>(1, (ctas_per_sm * (int64_t)n_sm + J.gy - 1) / J.gy);
       gx = std::min<int64_t>(gx, std::max<int64_t>(1, r.n_rows / (32 * (int64_t)rpt)));
       J.rows_per_cta = (r.n_rows + gx - 1) / gx;
       J.block_base = blocks;

@@ -212,7 +212,8 @@ struct AbsmaxRequest {
   int64_t n_rows, C, ld;
   uint32_t* out;
 };
-hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s);
+hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s,
+                                 int ctas_per_sm = 8);
 // `tile`: the channel tile of every job in the table (tc_channel_tile(C)).
 hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile);
 int f32_channel_tile();
