@@ -109,15 +109,17 @@ TRAFFIC = {
     "k_grid_tc": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                               "paper_2207_04584_gb300/csrc/ptx.cuh",
                               "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                  "sha256": "4a1eb0c2c484f7a680c3e9d025f4eea564d03da12bc3d621c19dbb9367430593",
-                  "bytes": 36.274460928e9 + 1.475841280e9,
-                  "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench launch, C=1024)"},
+                  "sha256": "df3138a45841893a091a6afd07b5f9b691fdd520529884f23bc6f6d69ad8c7b3",
+                  "bytes": 32.899492224e9 + 1.472701696e9,
+                  "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench's tuned launch, "
+                             "C=1024; mean of 4)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": "94341235311b9b30b72b4f47e6eb70ff3f50530850303a335f2d4d68f7969c92",
-                   "bytes": 4 * (6.582210e9 + 0.363151e9),
-                   "capture": "profiles/k_grid_f32_fast_drift_c256.md (C=256 x 4)"},
+                   "sha256": "00e4237e8ae40b64adf72dc8b7e533bff35beb024114e47bce159560576459ef",
+                   "bytes": 32.590529728e9 + 1.469339008e9,
+                   "capture": "profiles/k_grid_f32_fast_drift_c256.md (the bench's FP32-form "
+                              "launch, C=1024; mean of 4)"},
 }
 
 
@@ -216,6 +218,13 @@ def workload_desc(N, C):
             "at 0.5', FWHM 2.9', R=3 sigma")
 
 
+def workload_config(N, C, M, world):
+    """The `config` of both arms' bench lines: the workload alone (the form,
+    tuning and binning of the GPU arm are reported beside it)."""
+    return {"workload": workload_desc(N, C), "N": N, "C": C, "M": M,
+            "l2": "inputs larger than L2 (values 8 GB)", "parallelism": f"replicas x{world}"}
+
+
 REF_SLICE = 256  # channels per reference-arm step
 
 
@@ -244,10 +253,10 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(N, C), "N": N, "C": C,
-                       "M": wl["geom"]["nx"] * wl["geom"]["ny"], "seed": W.SEED_BASE + 2,
-                       "step": f"the whole map for {REF_SLICE} of the {C} channels "
-                               "(slices cycled)"},
+            "config": workload_config(N, C, wl["geom"]["nx"] * wl["geom"]["ny"], 1),
+            "seed": W.SEED_BASE + 2,
+            "reference_step": f"the whole map for {REF_SLICE} of the {C} channels "
+                              "(slices cycled)",
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle",
                              "cores": rec["cores"],
                              "sample": f"each step: {rec['sample']} (channel slice of "
@@ -554,6 +563,8 @@ def run_profile_case(args, H, torch, dev, rank):
     lat = torch.from_numpy(wl["lat"]).to(dev)
     plan = H.hegrid_plan_create(N, lon, lat, 1, g, wl["fwhm_deg"], 3.0, 0, s)
     try:
+        if args.tc_kernel:
+            H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, args.tc_kernel)
         out = torch.empty((M, C), device=dev)
         for _ in range(3):
             H.hegrid_grid(plan, vals, dt, C, C, out, C, None, H.HEGRID_MODE_TC_SPLIT, s)
@@ -903,6 +914,9 @@ def main():
     ap.add_argument("--sim-span", type=float, default=60.0,
                     help="sim workload: RA span of the field in degrees (60: the paper's; "
                          "smaller: a cut of it, for profiler captures)")
+    ap.add_argument("--tc-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="profile-drift / profile-cfg3: tensor-core kernel (1 cell-major, "
+                         "2 channel-major; 0 the library's default)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (no per-form timings, accuracy check, e2e or CPU "
                          "baseline): the command used for profiler captures")
@@ -1173,12 +1187,10 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": FORM_DTYPE[mode_name], "data": "synthetic",
-                "config": {"workload": workload_desc(N, C),
-                           "mode": mode_name, "N": N, "C": C, "M": M, "pairs": P,
-                           "l2": "inputs larger than L2 (values 8 GB)", "tuning": tune,
-                           "binning": (f"HEALPix RING nside {1 << args.healpix}" if args.healpix
-                                       else "map bins"),
-                           "parallelism": f"replicas x{world}"},
+                "config": workload_config(N, C, M, world),
+                "form": mode_name, "pairs": P, "tuning": tune,
+                "binning": (f"HEALPix RING nside {1 << args.healpix}" if args.healpix
+                            else "map bins"),
                 "plan_ms": t_plan * 1e3, "grid_ms": t_grid * 1e3,
                 "step_structure": ("plan creation, with the per-channel maxima of the values "
                                    "on a side stream beside it (hegrid_chan_maxima), then "

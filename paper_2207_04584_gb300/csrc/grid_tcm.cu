@@ -52,13 +52,18 @@ namespace {
 constexpr int kCM = 128;             // channels per item (the MMA's M, TMEM lanes)
 constexpr int kCN = HG_BLOCK_CELLS;  // cells per block (the MMA's N)
 constexpr int kCK = 32;              // candidates per sub-chunk
-// Ring depths: value operands in TMEM (kAStg), weight tiles (kBStg) and
-// sample rows (kRStg) in shared memory.  The TMEM and weight-tile stages are
-// released by the MMAs' completion, which comes in issue rounds of kRound
-// sub-chunks, so they hold two rounds; the rows are released as soon as the
-// value warps have read them.
-constexpr int kAStg = 8;
-constexpr int kBStg = 8;
+// Rings: the value operands in TMEM and the weight tiles in shared memory
+// are held in two round slots of kRound stages each (kAStg = kBStg = 2 kRound):
+// the MMA warp issues a round's MMAs behind one fence and releases the
+// round's stages with one tcgen05.commit (a commit costs the issuing thread
+// ~300 cycles before its next tcgen05 instruction, measured with clock
+// stamps, so the kernel commits once per round, not once per stage).  A
+// round never spans two accumulation segments; a short round leaves its
+// slot's remaining stages unused.  The sample rows (kRStg stages) are
+// released as soon as the value warps have read them.
+constexpr int kRound = 4;  // sub-chunks per MMA issue round
+constexpr int kAStg = 2 * kRound;
+constexpr int kBStg = 2 * kRound;
 constexpr int kRStg = 5;
 constexpr int kValWarps = 8;
 constexpr int kMmaW = 8;
@@ -75,8 +80,7 @@ constexpr uint32_t kTmemColsCM = 512;
 static_assert(kACol0 + kAStg * kAStageCols <= kTmemColsCM, "TMEM columns");
 constexpr int kDefaultSegCM = 16;
 constexpr int kPrefetch = 12;  // weight tiles prefetched into L2 this many sub-chunks ahead
-constexpr int kRound = 4;      // sub-chunks per MMA issue round
-static_assert(kRound <= kAStg && kRound <= kBStg, "an issue round must fit the rings");
+
 
 constexpr uint32_t kRawStage = (uint32_t)kCK * kCM * 4u;  // 32 rows x 128 channels x <= 4 bytes
 
@@ -86,9 +90,8 @@ struct __align__(1024) CmSmem {
   uint64_t raw_full[kRStg];       // row gathers -> value warps
   uint64_t raw_empty[kRStg];      // value warps -> row stager: the stage's rows are read
   uint64_t a_full[kAStg];         // value warps -> MMA: the stage's values are in TMEM
-  uint64_t a_empty[kAStg];        // MMA -> value warps: the stage's MMAs are complete
   uint64_t b_full[kBStg];         // bulk copy -> MMA: the stage's weight tiles landed
-  uint64_t b_empty[kBStg];        // MMA -> weight-tile stager: the stage's MMAs are complete
+  uint64_t round_empty[2];        // MMA -> value warps, tile stager: a round slot's MMAs are complete
   uint64_t segdone[2];
   uint64_t regfree[2];
   uint32_t tmem_base;
@@ -186,11 +189,24 @@ __device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
   return v;
 }
 
+// Issue rounds: sub-chunk j of an item (segments of kSeg sub-chunks) lies in
+// round j / kSeg * ceil(kSeg / kRound) + (j % kSeg) / kRound of the item, at
+// slot (j % kSeg) % kRound; an item of n sub-chunks takes
+// rounds_of(n, kSeg) rounds.  Round R uses stages (R & 1) kRound + slot.
+__device__ __forceinline__ int rounds_per_seg(int kSeg) { return (kSeg + kRound - 1) / kRound; }
+__device__ __forceinline__ uint32_t rounds_of(int n, int kSeg) {
+  if (n <= 0) return 0u;
+  const int full = (n - 1) / kSeg;  // segments before the last
+  const int last = n - full * kSeg;
+  return (uint32_t)(full * rounds_per_seg(kSeg) + (last + kRound - 1) / kRound);
+}
+
 // Value warps for one work item.  Returns false if a bounded wait gave up.
 template <int DT, bool SPLIT>
-__device__ __forceinline__ bool values_item(CmSmem& S, const GridJob& J, int n_sub, int64_t c0,
-                                            uint32_t tmem, uint32_t& g, int32_t* err,
-                                            uint64_t lim, bool withhold) {
+__device__ __forceinline__ bool values_item(CmSmem& S, const GridJob& J, int n_sub, int kSeg,
+                                            int64_t c0, uint32_t tmem, uint32_t& gr,
+                                            uint32_t R0, int32_t* err, uint64_t lim,
+                                            bool withhold) {
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;
   constexpr bool kVsplit = SPLIT && kWide;
   constexpr uint32_t kEb = kWide ? 4u : 2u;
@@ -202,9 +218,10 @@ __device__ __forceinline__ bool values_item(CmSmem& S, const GridJob& J, int n_s
   if (DT != HEGRID_F16 && J.chmax != nullptr && c < J.C)
     sc = pow2f_cm(chan_scale_exp_cm(__ldg(J.chmax + c)));
   const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-  for (int j = 0; j < n_sub; ++j, ++g) {
-    const int r = (int)(g % kRStg);
-    if (!mbar_wait(&S.raw_full[r], (g / kRStg) & 1u, err, lim)) return false;
+  const int rps = rounds_per_seg(kSeg);
+  for (int j = 0; j < n_sub; ++j, ++gr) {
+    const int r = (int)(gr % kRStg);
+    if (!mbar_wait(&S.raw_full[r], (gr / kRStg) & 1u, err, lim)) return false;
     // this thread's channel in rows 16 h .. 16 h + 15 of the staged sub-chunk
     const uint32_t rb = smem_u32(S.raw[r]) + (uint32_t)(16 * h) * kRow + (uint32_t)(32 * q + lane) * kEb;
     uint32_t v[16];
@@ -231,8 +248,13 @@ __device__ __forceinline__ bool values_item(CmSmem& S, const GridJob& J, int n_s
         lo[e] = 0u;
       }
     }
-    const int s = (int)(g % kAStg);
-    if (g >= kAStg && !mbar_wait(&S.a_empty[s], (g / kAStg - 1) & 1u, err, lim)) return false;
+    const int seg = j / kSeg, jj = j - seg * kSeg;
+    const uint32_t R = R0 + (uint32_t)(seg * rps + jj / kRound);
+    const int s = (int)(R & 1u) * kRound + jj % kRound;
+    // the round slot is free once round R - 2's MMAs are complete
+    if (jj % kRound == 0 && R >= 2u &&
+        !mbar_wait(&S.round_empty[R & 1u], ((R >> 1) - 1u) & 1u, err, lim))
+      return false;
     tc_fence_after();
     const uint32_t a = tl + kACol0 + (uint32_t)s * kAStageCols + 8u * (uint32_t)h;
     tmem_st_x8(a, hi);
@@ -240,7 +262,12 @@ __device__ __forceinline__ bool values_item(CmSmem& S, const GridJob& J, int n_s
     tmem_st_wait();
     tc_fence_before();
     __syncwarp();
-    if (lane == 0 && !(withhold && g == 0)) mbar_arrive(&S.a_full[s]);
+    if (lane == 0 && !(withhold && R == 0u && jj == 0)) mbar_arrive(&S.a_full[s]);
+    // a round cut short by its segment's end: arrive on the slot's unused
+    // stages too, so that every stage completes one phase per round
+    const int seg_end = min((seg + 1) * kSeg, n_sub);
+    if (j == seg_end - 1 && lane == 0)
+      for (int t = jj % kRound + 1; t < kRound; ++t) mbar_arrive(&S.a_full[(int)(R & 1u) * kRound + t]);
   }
   return true;
 }
@@ -259,14 +286,10 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
       mbar_init(&S.raw_full[i], 1);
       mbar_init(&S.raw_empty[i], kValWarps);
     }
-    for (int i = 0; i < kAStg; ++i) {
-      mbar_init(&S.a_full[i], kValWarps);
-      mbar_init(&S.a_empty[i], 1);
-    }
-    for (int i = 0; i < kBStg; ++i) {
-      mbar_init(&S.b_full[i], 1);
-      mbar_init(&S.b_empty[i], 1);
-    }
+    for (int i = 0; i < kAStg; ++i) mbar_init(&S.a_full[i], kValWarps);
+    for (int i = 0; i < kBStg; ++i) mbar_init(&S.b_full[i], 1);
+    mbar_init(&S.round_empty[0], 1);
+    mbar_init(&S.round_empty[1], 1);
     mbar_init(&S.segdone[0], 1);
     mbar_init(&S.segdone[1], 1);
     mbar_init(&S.regfree[0], 4);
@@ -283,7 +306,8 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
   const uint32_t tmem = S.tmem_base;
 
   bool bail = false;
-  uint32_t g = 0;     // sub-chunks through the ring so far
+  uint32_t gr = 0;    // sub-chunks through the row ring so far
+  uint32_t R0 = 0;    // issue rounds so far (before the current item)
   uint32_t n_tm = 0;  // items that used TMEM so far
   uint32_t n_sg = 0;  // accumulation segments so far
   uint32_t uses[2] = {0u, 0u};
@@ -302,6 +326,9 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
     const bool split = J.mode == HEGRID_MODE_TC_SPLIT;
     const bool vsplit = split && (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2);
     const int j0 = sweep_start_cm(J, b, n_sub);
+    const int rps = rounds_per_seg(kSeg);
+    const uint32_t Ri = R0;  // the item's first round
+    R0 += rounds_of(n_sub, kSeg);
 
     if (warp == kRowW) {
       // ---------------- row stager ----------------
@@ -314,12 +341,12 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
         return __ldg(pv.cand_idx + kb0 + (int64_t)phys(jl) * kCK + lane);
       };
       int32_t nA = n_sub > 0 ? cand_of(0) : 0, nB = n_sub > 1 ? cand_of(1) : 0;
-      for (int j = 0; j < n_sub; ++j, ++g) {
-        const int s = (int)(g % kRStg);
+      for (int j = 0; j < n_sub; ++j, ++gr) {
+        const int s = (int)(gr % kRStg);
         const int32_t n = nA;
         nA = nB;
         if (j + 2 < n_sub) nB = cand_of(j + 2);
-        if (g >= kRStg && !mbar_wait(&S.raw_empty[s], (g / kRStg - 1) & 1u, err, lim)) {
+        if (gr >= kRStg && !mbar_wait(&S.raw_empty[s], (gr / kRStg - 1) & 1u, err, lim)) {
           bail = true;
           break;
         }
@@ -347,20 +374,28 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
         for (int j = 0; j < kPrefetch && j < n_sub; ++j)
           prefetch_l2(wt + (int64_t)(j + j0 < n_sub ? j + j0 : j + j0 - n_sub) * kWTileBytes,
                       kWTileBytes);
-      for (int j = 0; j < n_sub; ++j, ++g) {
-        const int s = (int)(g % kBStg);
+      for (int j = 0; j < n_sub; ++j) {
+        const int seg = j / kSeg, jj = j - seg * kSeg;
+        const uint32_t R = Ri + (uint32_t)(seg * rps + jj / kRound);
+        const int s = (int)(R & 1u) * kRound + jj % kRound;
         const int pj = j + j0 < n_sub ? j + j0 : j + j0 - n_sub;
         if (lane == 0 && j + kPrefetch < n_sub) {
           const int jp = j + kPrefetch + j0;
           prefetch_l2(wt + (int64_t)(jp < n_sub ? jp : jp - n_sub) * kWTileBytes, kWTileBytes);
         }
-        if (g >= kBStg && !mbar_wait(&S.b_empty[s], (g / kBStg - 1) & 1u, err, lim)) {
+        if (jj % kRound == 0 && R >= 2u &&
+            !mbar_wait(&S.round_empty[R & 1u], ((R >> 1) - 1u) & 1u, err, lim)) {
           bail = true;
           break;
         }
         if (lane == 0) {
           mbar_arrive_expect_tx(&S.b_full[s], kWTileBytes);
           bulk_g2s(S.B[s], wt + (int64_t)pj * kWTileBytes, kWTileBytes, &S.b_full[s]);
+          // a round cut short by its segment's end: complete the slot's
+          // unused stages' phases too (plain arrivals)
+          if (j == min((seg + 1) * kSeg, n_sub) - 1)
+            for (int t = jj % kRound + 1; t < kRound; ++t)
+              mbar_arrive(&S.b_full[(int)(R & 1u) * kRound + t]);
         }
         __syncwarp();
       }
@@ -369,18 +404,15 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
 
     if (warp == kMmaW) {
       // ---------------- MMA issuer ----------------
-      // Each round waits for up to kRound consecutive sub-chunks of one
-      // segment and issues all their MMAs behind one fence (a round of one
-      // sub-chunk cost ~1,100 cycles however few MMAs it held, measured with
-      // per-role clock stamps; rounds of four take the kernel from 11.5 to
-      // 10.9 ms on the 1,024-channel drift scan).
+      // Each round waits for its (up to kRound) sub-chunks of one segment,
+      // issues all their MMAs behind one fence and releases its round slot
+      // with one commit (one sub-chunk per round cost ~1,100 cycles however
+      // few MMAs it held).
       if (n_sub == 0) continue;
       const uint32_t idS = idesc_f16(0u, kCM, kCN);  // FP16 A and B, FP32 accumulate
       const uint32_t rT = n_tm & 1u, rS = rT ^ 1u;
-      int j = 0, qs = 0;
-      while (j < n_sub && !bail) {
-        // segment qs: sub-chunks [j, je)
-        const int je = min(j + kSeg, n_sub);
+      for (int qs = 0; qs < n_seg && !bail; ++qs) {
+        const int j = qs * kSeg, je = min(j + kSeg, n_sub);
         const uint32_t r = qs == 0 ? rT : rS;
         if (uses[r] > 0 && !mbar_wait(&S.regfree[r], (uses[r] - 1) & 1u, err, lim)) {
           bail = true;
@@ -391,22 +423,19 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
         tc_fence_after();
         for (int j1 = j; j1 < je && !bail; j1 += kRound) {
           const int nr = min(kRound, je - j1);
-          for (int t = 0; t < nr && !bail; ++t) {
-            const uint32_t gt = g + (uint32_t)t;
-            if (!mbar_wait(&S.a_full[gt % kAStg], (gt / kAStg) & 1u, err, lim) ||
-                !mbar_wait(&S.b_full[gt % kBStg], (gt / kBStg) & 1u, err, lim))
+          const uint32_t R = Ri + (uint32_t)(qs * rps + (j1 - j) / kRound);
+          const int s0 = (int)(R & 1u) * kRound;
+          const uint32_t ph = (R >> 1) & 1u;
+          for (int t = 0; t < nr && !bail; ++t)
+            if (!mbar_wait(&S.a_full[s0 + t], ph, err, lim) ||
+                !mbar_wait(&S.b_full[s0 + t], ph, err, lim))
               bail = true;
-          }
           if (bail) break;
           tc_fence_after();
           if (lane == 0) {
-            // all of the round's MMAs, then its commits (each stage is
-            // released when the whole round completes; the rings hold two
-            // rounds)
             for (int t = 0; t < nr; ++t) {
-              const int sa = (int)((g + (uint32_t)t) % kAStg), sb = (int)((g + (uint32_t)t) % kBStg);
-              const uint32_t a = tmem + kACol0 + (uint32_t)sa * kAStageCols;
-              const uint32_t bh = smem_u32(S.B[sb]), bl = bh + kHalfTile;
+              const uint32_t a = tmem + kACol0 + (uint32_t)(s0 + t) * kAStageCols;
+              const uint32_t bh = smem_u32(S.B[s0 + t]), bl = bh + kHalfTile;
 #pragma unroll
               for (int kk = 0; kk < kCK / 16; ++kk) {
                 const uint32_t o = kk * 32;             // bytes into a 64-byte tile row
@@ -417,18 +446,12 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
                 if (vsplit) tc_mma_f16_ts(d, a + 16u + ac, smem_desc_k_sw64(bh + o), idS, 1u);
               }
             }
-            for (int t = 0; t < nr; ++t) {
-              tc_commit(&S.a_empty[(g + (uint32_t)t) % kAStg]);
-              tc_commit(&S.b_empty[(g + (uint32_t)t) % kBStg]);
-            }
+            tc_commit(&S.round_empty[R & 1u]);
             if (j1 + nr == je) tc_commit(&S.segdone[n_sg & 1u]);
           }
           __syncwarp();
-          g += (uint32_t)nr;
         }
         ++n_sg;
-        ++qs;
-        j = je;
       }
       ++n_tm;
       continue;
@@ -527,17 +550,17 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
       bool ok = true;
       if (split) {
         switch (J.dtype) {
-          case HEGRID_F32: ok = values_item<HEGRID_F32, true>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
-          case HEGRID_BF16: ok = values_item<HEGRID_BF16, true>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
-          case HEGRID_F16: ok = values_item<HEGRID_F16, true>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
-          default: ok = values_item<HEGRID_BF16X2, true>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
+          case HEGRID_F32: ok = values_item<HEGRID_F32, true>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
+          case HEGRID_BF16: ok = values_item<HEGRID_BF16, true>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
+          case HEGRID_F16: ok = values_item<HEGRID_F16, true>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
+          default: ok = values_item<HEGRID_BF16X2, true>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = values_item<HEGRID_F32, false>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
-          case HEGRID_BF16: ok = values_item<HEGRID_BF16, false>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
-          case HEGRID_F16: ok = values_item<HEGRID_F16, false>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
-          default: ok = values_item<HEGRID_BF16X2, false>(S, J, n_sub, c0, tmem, g, err, lim, withhold); break;
+          case HEGRID_F32: ok = values_item<HEGRID_F32, false>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
+          case HEGRID_BF16: ok = values_item<HEGRID_BF16, false>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
+          case HEGRID_F16: ok = values_item<HEGRID_F16, false>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
+          default: ok = values_item<HEGRID_BF16X2, false>(S, J, n_sub, kSeg, c0, tmem, gr, Ri, err, lim, withhold); break;
         }
       }
       bail = !ok;
