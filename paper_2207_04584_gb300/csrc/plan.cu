@@ -762,14 +762,6 @@ __global__ void __launch_bounds__(kChunk)
   }
 
   s_mh[cell] = make_float4(mh[0], mh[1], mh[2], 0.0f);
-  // the cell's thresholds of the dot-product test: (|m|^2 - thr) / 2 for the
-  // FP32 band's two ends (FP64, rounded once)
-  float a_in, a_maybe;
-  {
-    const double mm = (double)mh[0] * mh[0] + (double)mh[1] * mh[1] + (double)mh[2] * mh[2];
-    a_in = __double2float_rn(0.5 * (mm - (double)pp.lo_thr));
-    a_maybe = __double2float_rn(0.5 * (mm - (double)pp.hi_thr));
-  }
   s_ml[cell] = make_float4(ml[0], ml[1], ml[2], 0.0f);
   int64_t kcount = 0;  // union size so far (local index of the next candidate)
   int64_t erun = 0;    // entries of the block so far
@@ -799,10 +791,7 @@ __global__ void __launch_bounds__(kChunk)
           lv[i] = __double2float_rn(e[i] - (double)hv[i]);
           s_u[i][t] = u[i];
         }
-        // w: -|n|^2 / 2 of the rounded coordinates (FP64, rounded once), the
-        // candidate's term of the dot-product membership test
-        const double nn = (double)hv[0] * hv[0] + (double)hv[1] * hv[1] + (double)hv[2] * hv[2];
-        s_eh[t] = make_float4(hv[0], hv[1], hv[2], __double2float_rn(-0.5 * nn));
+        s_eh[t] = make_float4(hv[0], hv[1], hv[2], 0.0f);
         s_el[t] = make_float4(lv[0], lv[1], lv[2], 0.0f);
         s_n[t] = perm[s];
       }
@@ -814,10 +803,7 @@ __global__ void __launch_bounds__(kChunk)
       // Phase 1: membership of each staged candidate for this thread's cell.
       // FP32 test first (bit set in `in32` when surely inside, in `maybe`
       // when not surely outside); pairs inside the FP32 error band are
-      // decided in FP64 afterwards.  The test is the chord's
-      // |m - n|^2 = |m|^2 + |n|^2 - 2 m.n <= thr written as
-      // m.n - |n|^2/2 >= (|m|^2 - thr)/2: three FMAs against the staged
-      // -|n|^2/2 and the cell's two thresholds.
+      // decided in FP64 afterwards.
       uint32_t mask[kQ];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
@@ -826,10 +812,11 @@ __global__ void __launch_bounds__(kChunk)
 #pragma unroll 4
         for (int r = r0; r < r1; ++r) {
           const float4 n4 = s_eh[32 * q + r];
-          const float tt = __fmaf_rn(mh[0], n4.x, __fmaf_rn(mh[1], n4.y, __fmaf_rn(mh[2], n4.z, n4.w)));
+          const float dx = mh[0] - n4.x, dy = mh[1] - n4.y, dz = mh[2] - n4.z;
+          const float c2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
           const uint32_t bit = 1u << r;
-          if (tt >= a_in) in32 |= bit;
-          if (tt >= a_maybe) maybe |= bit;
+          if (c2 <= pp.lo_thr) in32 |= bit;
+          if (c2 <= pp.hi_thr) maybe |= bit;
         }
         uint32_t band = active ? maybe & ~in32 : 0u;
         while (band) {
@@ -1572,13 +1559,9 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     double s = std::sin(0.5 * p->R_rad);
     pp.cR2 = 4.0 * s * s;
     // Error band of the FP32 test (relative to c_R^2).  With E the largest
-    // |u - u_block| in the window, c the chord and u = 2^-24: rounding the
-    // block-local coordinates moves c^2 by at most u (7 E/c) c^2; the
-    // dot-product form m.n - |n|^2/2 >= (|m|^2 - thr)/2 adds at most
-    // u (4.5 + 0.5) E^2 for its three FMAs and the rounded -|n|^2/2, and
-    // u (E^2 + c^2)/2 for the rounded threshold, i.e. u (11 E^2 + c^2) on the
-    // scale of c^2.  The band, 2^-20 (8 + 8 E/c + 12 E^2/c^2), is at least 9x
-    // wider than their sum u (1 + 7 E/c + 11 E^2/c^2).
+    // |u - u_block| in the window and c the chord, the FP32 chord^2 from the
+    // rounded block-local coordinates is within 2^-24 (7 E/c + 8) of the exact
+    // value; the band is 2^-20 (8 + 8 E/c), 16x wider.
     double cR = 2.0 * s;
     double wx_cells = HG_BX + 2.0 * (Hmax / g.dlon_deg + 2.0 * B + 1.0);
     double wy_cells = HG_BY + 2.0 * (p->R_deg / g.dlat_deg + 2.0 * B + 1.0);
@@ -1590,7 +1573,7 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
     }
     double E = 0.5 * std::sqrt(wx_cells * wx_cells * g.dlon_deg * g.dlon_deg +
                                wy_cells * wy_cells * g.dlat_deg * g.dlat_deg) * kDeg;
-    double band = std::ldexp(8.0 + 8.0 * E / cR + 12.0 * (E / cR) * (E / cR), -20);
+    double band = std::ldexp(8.0 + 8.0 * E / cR, -20);
     pp.lo_thr = std::nextafter((float)(pp.cR2 * (1.0 - band)), 0.0f);
     pp.hi_thr = std::nextafter((float)(pp.cR2 * (1.0 + band)), 1.0f);
     double k = 1.0 / (2.0 * p->sigma_rad * p->sigma_rad);
