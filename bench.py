@@ -471,6 +471,8 @@ def run_config3(args, H, torch, dev, rank):
     lon_d = torch.from_numpy(wl["lon"]).to(dev)
     lat_d = torch.from_numpy(wl["lat"]).to(dev)
     plan = H.hegrid_plan_create(N, lon_d, lat_d, 1, g, wl["fwhm_deg"], 3.0, 0, sh)
+    if args.tc_kernel:
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, args.tc_kernel)
     out = torch.empty((M, C), device=dev)
     w_d = torch.empty(M, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, device=dev)
@@ -536,6 +538,9 @@ def run_config3(args, H, torch, dev, rank):
                                        "of smooth spectra",
                            "N": N, "C": C, "M": M, "pairs": info["n_pairs"],
                            "stored": rec["stored"], "form": rec["form"],
+                           "tc_kernel": {0: "cell-major (default)", 1: "cell-major",
+                                         2: "channel-major",
+                                         3: "cell-major, dense A tiles"}[args.tc_kernel],
                            "l2": "L2 flushed (a 258 MB buffer zeroed) before every timed call"},
                 **{k: rec[k] for k in rec if k not in ("value", "stored", "form")},
                 "clocks": clk, "gen_s": t_gen}), flush=True)
@@ -914,9 +919,10 @@ def main():
     ap.add_argument("--sim-span", type=float, default=60.0,
                     help="sim workload: RA span of the field in degrees (60: the paper's; "
                          "smaller: a cut of it, for profiler captures)")
-    ap.add_argument("--tc-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="profile-drift / profile-cfg3: tensor-core kernel (1 cell-major, "
-                         "2 channel-major; 0 the library's default)")
+    ap.add_argument("--tc-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="config3 / profile-drift / profile-cfg3: tensor-core kernel (1 "
+                         "cell-major, 2 channel-major, 3 cell-major with dense A tiles; 0 the "
+                         "library's default)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (no per-form timings, accuracy check, e2e or CPU "
                          "baseline): the command used for profiler captures")

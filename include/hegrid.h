@@ -299,8 +299,11 @@ hegrid_status hegrid_plan_export(const hegrid_plan *plan, int32_t *perm, int32_t
  * hegrid_grid_batched, hegrid_batch_create and hegrid_grid_stream calls on
  * this plan use it.  Shapes: the work order's band width in cell-block
  * columns (which blocks run concurrently and so share sample rows in L2),
- * for the tensor-core modes also the kernel (cell-major, and channel-major
- * when n_channels > 64), the order of channel tiles (negative band:
+ * for the tensor-core modes also the kernel (cell-major, cell-major with
+ * dense A tiles, and channel-major when n_channels > 64; the two that read
+ * the plan's dense weight tiles are charged the tiles' build, timed here as a
+ * rebuild into memory the pool already holds, unless the plan held its tiles
+ * before the call), the order of channel tiles (negative band:
  * the tiles of a block side by side) and the accumulation segment length (8 or 16
  * sub-chunks of 32 candidates; both keep the split form well inside its error
  * bound: the tensor core's FP32 accumulate loses about 2^-22 of the running
@@ -317,7 +320,8 @@ typedef struct {
   int32_t band;   /* blocks per band (0: the channel tiles of a block back to back) */
   int32_t seg;    /* 32-candidate sub-chunks per accumulation segment (tensor-core modes) */
   int32_t group;  /* channel tiles side by side when band < 0 (tensor-core modes; 0: all) */
-  int32_t kernel; /* tensor-core kernel: 1 cell-major, 2 channel-major (0: default) */
+  int32_t kernel; /* tensor-core kernel: 1 cell-major, 2 channel-major, 3 cell-major with
+                     dense A tiles (0: default) */
   float ms;       /* time per grid call */
 } hegrid_tune_point;
 typedef struct {
@@ -346,12 +350,14 @@ hegrid_status hegrid_autotune(hegrid_plan *plan, const void *values, hegrid_dtyp
  * 128-channel tiles: the first grid call that
  * runs it builds them, 16 KB per 32 candidate slots, on its stream, outside
  * a stream capture, where the cell-major kernel runs until they exist);
+ * 3 the cell-major kernel with its A tiles copied whole from those dense
+ * tiles (the same maps as 1, bit for bit; all 16 producer warps convert B);
  * 0: the default, the cell-major kernel.  FP32 mode ignores it.
  * seg: 32-candidate sub-chunks per accumulation segment for the tensor-core
  * modes, 1..16 (0: default 16; longer segments would leave the split form
  * too little margin inside its error bound).  The 64-channel tile moves two sub-chunks per step and rounds
  * seg down to an even count (at least 2).
- * INVALID_ARG otherwise (also group < 0, kernel outside 0..2).
+ * INVALID_ARG otherwise (also group < 0, kernel outside 0..3).
  */
 hegrid_status hegrid_plan_set_tuning(hegrid_plan *plan, uint32_t mode, int32_t band, int32_t seg,
                                      int32_t group, int32_t kernel);

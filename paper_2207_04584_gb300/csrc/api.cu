@@ -328,16 +328,16 @@ hegrid_status ensure_wtiles(hegrid_plan* p, cudaStream_t s) {
   return HEGRID_OK;
 }
 
-// Whether the tensor-core job (plan, a) runs on the channel-major kernel:
-// the plan's choice (tune_tc_kernel: 2, set by the caller or kept by the
-// autotuner; the default is the cell-major kernel); the weight tiles are
-// built here if needed, except inside a stream capture (where the cell-major
-// kernel runs unless they exist).
-hegrid_status use_channel_major(hegrid_plan* p, const hegrid_grid_args& a, cudaStream_t s,
-                                bool* cm) {
-  *cm = false;
-  (void)a;
-  if (p->tune_tc_kernel != 2) return HEGRID_OK;
+// The tensor-core kernel a job on plan p runs (1 cell-major, 2 channel-major,
+// 3 cell-major with dense A tiles): the plan's choice (tune_tc_kernel, set
+// by the caller or kept by the autotuner; 0, the default, is 1).  Kernels 2
+// and 3 need the plan's dense weight tiles, built here if missing, except
+// inside a stream capture, where the plain cell-major kernel runs until they
+// exist.
+hegrid_status tc_kernel_of(hegrid_plan* p, cudaStream_t s, int* kern) {
+  *kern = 1;
+  const int k = p->tune_tc_kernel;
+  if (k != 2 && k != 3) return HEGRID_OK;
   if (!p->wtiles) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     HG_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
@@ -345,7 +345,7 @@ hegrid_status use_channel_major(hegrid_plan* p, const hegrid_grid_args& a, cudaS
     hegrid_status e = ensure_wtiles(p, s);
     if (e != HEGRID_OK) return e;
   }
-  *cm = true;
+  *kern = k;
   return HEGRID_OK;
 }
 
@@ -353,7 +353,7 @@ hegrid_status use_channel_major(hegrid_plan* p, const hegrid_grid_args& a, cudaS
 // tensor-core kernel of that channel tile; tile < 0: the channel-major one),
 // kMaxJobs per launch.
 hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStream_t s,
-                            int tile = 0) {
+                            int tile = 0, bool dense_a = false) {
   for (size_t base = 0; base < jobs.size(); base += kMaxJobs) {
     JobTable jt;
     std::memset(&jt, 0, sizeof(jt));
@@ -369,7 +369,7 @@ hegrid_status launch_family(const std::vector<GridJob>& jobs, bool tc, cudaStrea
     jt.n_items = items;
     hegrid_status st = !tc ? launch_grid_f32(jt, s)
                        : tile < 0 ? launch_grid_tcm(jt, s)
-                                  : launch_grid_tc(jt, s, tile);
+                                  : launch_grid_tc(jt, s, tile, dense_a);
     if (st != HEGRID_OK) return st;
   }
   return HEGRID_OK;
@@ -395,8 +395,9 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
   HG_ARG_CHECK(n >= 0, "n must be >= 0");
   HG_ARG_CHECK(n == 0 || (plans && args), "NULL plans or args");
   // tensor-core jobs grouped by kernel and channel tile (cell-major 64, 128,
-  // 256; channel-major 128): one launch each
-  std::vector<GridJob> f32, tc[3], tcm;
+  // 256, with A tiles built or from dense tiles; channel-major 128): one
+  // launch each
+  std::vector<GridJob> f32, tc[3], tcd[3], tcm;
   const int tiles[3] = {64, 128, 256};
   for (int i = 0; i < n; ++i) {
     hegrid_status st = check_args(plans[i], args[i]);
@@ -421,13 +422,15 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
         if (e != HEGRID_OK) return e;
         continue;
       }
-      bool cm = false;
+      int kern = 1;
       {
-        hegrid_status e = use_channel_major(plans[i], args[i], s, &cm);
+        hegrid_status e = tc_kernel_of(plans[i], s, &kern);
         if (e != HEGRID_OK) return e;
       }
+      const bool cm = kern == 2;
       const int tile = cm ? tcm_channel_tile() : tc_channel_tile(args[i].n_channels);
-      std::vector<GridJob>& fam = cm ? tcm : tc[tile == 64 ? 0 : tile == 128 ? 1 : 2];
+      const int ti = tile == 64 ? 0 : tile == 128 ? 1 : 2;
+      std::vector<GridJob>& fam = cm ? tcm : kern == 3 ? tcd[ti] : tc[ti];
       fam.push_back(make_job(plans[i], args[i], tile));
       {
         hegrid_status e = encode_rows_map(fam.back(), tile);
@@ -456,9 +459,14 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
       if (e != HEGRID_OK) return e;
     }
     for (int t = 0; t < 3; ++t) {
-      if (tc[t].empty()) continue;
-      hegrid_status e = launch_family(tc[t], true, s, tiles[t]);
-      if (e != HEGRID_OK) return e;
+      if (!tc[t].empty()) {
+        hegrid_status e = launch_family(tc[t], true, s, tiles[t]);
+        if (e != HEGRID_OK) return e;
+      }
+      if (!tcd[t].empty()) {
+        hegrid_status e = launch_family(tcd[t], true, s, tiles[t], true);
+        if (e != HEGRID_OK) return e;
+      }
     }
     if (!tcm.empty()) {
       hegrid_status e = launch_family(tcm, true, s, -1);
@@ -898,6 +906,12 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
       add(-4, 16, 2, kern);
       add(-8, 16, 2, kern);
     }
+    // the cell-major kernel with dense A tiles, at the shapes that suit the
+    // cell-major kernel
+    add(-2, 16, 0, 3);
+    add(-4, 16, 2, 3);
+    add(-8, 16, 0, 3);
+    add(4, 16, 0, 3);
   } else {
     add(0, 1, 0, 0);
     for (int b : bands) add(b, 1, 0, 0);
@@ -935,6 +949,25 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
     return fail(HEGRID_ERR_CUDA);
   }
   hegrid_plan* pl[1] = {plan};
+  // Kernels 2 and 3 read the plan's dense weight tiles.  If the plan has not
+  // built them yet, they are built here (timed) and that time is added to
+  // those shapes' per-call times: the choice then holds for a plan gridded
+  // once; a plan that already holds its tiles is tuned on per-call times.
+  // The build is timed as a rebuild into the tiles just allocated: the cost a
+  // plan pays when the library's pool already holds the memory (the first
+  // allocation of a process maps it, a one-time cost).
+  float build_ms = 0.0f;
+  if (tc && !plan->wtiles) {
+    if ((st = hg::ensure_wtiles(plan, s)) != HEGRID_OK) return fail(st);
+    if (cudaEventRecord(e0, s) != cudaSuccess) return fail(HEGRID_ERR_CUDA);
+    if ((st = hg::launch_build_wtiles(plan->view(), plan->wtiles, s)) != HEGRID_OK)
+      return fail(st);
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&build_ms, e0, e1) != cudaSuccess) {
+      hg::set_error("timing the weight-tile build failed");
+      return fail(HEGRID_ERR_CUDA);
+    }
+  }
   int best = -1;
   for (size_t i = 0; i < pts.size(); ++i) {
     if (tc) {
@@ -956,7 +989,7 @@ hegrid_status hegrid_autotune(hegrid_plan* plan, const void* values, hegrid_dtyp
       hg::set_error("timing the autotune candidates failed");
       return fail(HEGRID_ERR_CUDA);
     }
-    pts[i].ms = ms / kReps;
+    pts[i].ms = ms / kReps + (pts[i].kernel >= 2 ? build_ms : 0.0f);
     if (best < 0 || pts[i].ms < pts[best].ms) best = (int)i;
   }
   if (tc) {
@@ -990,7 +1023,7 @@ hegrid_status hegrid_plan_set_tuning(hegrid_plan* plan, uint32_t mode, int32_t b
     HG_ARG_CHECK(band != INT32_MIN, "band out of range");
     HG_ARG_CHECK(seg >= 0 && seg <= 16, "seg must be in [0, 16]");
     HG_ARG_CHECK(group >= 0, "group must be >= 0");
-    HG_ARG_CHECK(kernel >= 0 && kernel <= 2, "kernel must be 0, 1 or 2");
+    HG_ARG_CHECK(kernel >= 0 && kernel <= 3, "kernel must be 0, 1, 2 or 3");
     plan->tune_tc_band = band;
     plan->tune_tc_seg = seg;
     plan->tune_tc_group = group;

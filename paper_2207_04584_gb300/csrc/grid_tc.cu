@@ -93,20 +93,24 @@ constexpr int kDefaultGroup = 0;  // ... all of a block's channel tiles side by 
 // per chunk, staged row slot bytes (4-byte elements), TMEM columns (two
 // accumulator regions), staged entries, 16-byte B-tile pieces per converting
 // producer thread and converting threads.
-template <int kN, int kS>
+// kD: the A tiles come whole from the plan's dense weight tiles (one bulk
+// copy per sub-chunk by the entry stager warp: the tiles are the exact image
+// the A builders would assemble) and all 16 producer warps convert B.
+template <int kN, int kS, bool kD>
 struct TcShape {
   static constexpr int kCK = kK * kS;
   static constexpr int kRawPitch = kN * 4;
   static constexpr uint32_t kTmemCols = 2 * kN;
   // staged-row ring and weight-entry ring depths, entries staged per chunk
   // (more come from global memory): as deep and large as shared memory allows
-  static constexpr int kRawStages = kN == 256 ? 2 : kN == 128 ? 4 : 3;
-  static constexpr int kEntStages = 3;
-  static constexpr int kEntCap = 3584;
+  // (with dense A tiles the entry ring is not needed and the rows get its room)
+  static constexpr int kRawStages = kD ? (kN == 256 ? 3 : 6) : (kN == 256 ? 2 : kN == 128 ? 4 : 3);
+  static constexpr int kEntStages = kD ? 1 : 3;
+  static constexpr int kEntCap = kD ? 8 : 3584;
   static constexpr int kEntStage = kEntCap - 8;  // leaves room for 16-byte alignment
-  static constexpr int kCPT = kN * (kCK / 8) / kGroup;  // 16-byte B pieces per converter
-  static constexpr int kKT = 8 * kCPT;  // samples of a B row converted per thread
-  static_assert(kN * (kCK / 8) % kGroup == 0, "B pieces do not divide among the converters");
+  static constexpr int kConv = kD ? kProducers : kGroup;  // B-converting threads
+  static constexpr int kCPT = kN * (kCK / 8) / kConv;  // 16-byte B pieces per converter
+  static_assert(kN * (kCK / 8) % kConv == 0, "B pieces do not divide among the converters");
 };
 
 // Where a staged chunk's weight entries are: e_lo is the global index of its
@@ -119,9 +123,9 @@ struct EntInfo {
   uint32_t ck_off, w_off;
 };
 
-template <int kN, int kS>
+template <int kN, int kS, bool kD>
 struct __align__(512) TcSmem {
-  using Sh = TcShape<kN, kS>;
+  using Sh = TcShape<kN, kS, kD>;
   uint8_t A[kStages][2][kS][kM * 64];  // [stage][hi, lo][sub-chunk]: weights, K-major, 64B swizzle
   uint8_t B[kStages][2][kS][kN * 64];  // [stage][hi, lo][sub-chunk]: values, K-major, 64B swizzle
   uint8_t raw[Sh::kRawStages][Sh::kCK * Sh::kRawPitch];  // staged sample rows as stored
@@ -260,16 +264,16 @@ __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) 
 // of 32-candidate sub-chunks (the last chunk may hold fewer than kS).
 // `withhold` (failure tests) skips the first chunk's ab_full arrive.
 // Returns false if a bounded wait gave up.
-template <int DT, bool SPLIT, int kN, int kS>
-__device__ __forceinline__ bool convert_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
+template <int DT, bool SPLIT, int kN, int kS, bool kD>
+__device__ __forceinline__ bool convert_item(TcSmem<kN, kS, kD>& S, const GridJob& J, int n_chunks,
                                              int n_sub, int j0, int64_t c0, uint32_t& g,
                                              uint32_t& gr, int32_t* err, uint64_t lim,
                                              bool withhold) {
-  using Sh = TcShape<kN, kS>;
+  using Sh = TcShape<kN, kS, kD>;
   constexpr bool kWide = DT == HEGRID_F32 || DT == HEGRID_BF16X2;  // 4-byte elements
   constexpr bool kVsplit = SPLIT && kWide;
   constexpr int kPitch = kWide ? Sh::kRawPitch : Sh::kRawPitch / 2;  // staged rows are packed
-  const int t = threadIdx.x;  // 0 .. kGroup-1
+  const int t = threadIdx.x;  // 0 .. Sh::kConv-1
   // B row (channel c0 + row) and first 16-byte piece (8 samples) this thread
   // converts; pieces 4 u .. 4 u + 3 belong to sub-chunk u.
   const int row = t % kN, q0 = (t / kN) * Sh::kCPT;
@@ -336,10 +340,10 @@ __device__ __forceinline__ bool convert_item(TcSmem<kN, kS>& S, const GridJob& J
 // split into FP16 halves, at the tile offsets the plan precomputed (in the
 // second sub-tile from entry n0 on).  Returns false if a bounded wait gave up.
 template <bool SPLIT, int kN, int kS>
-__device__ __forceinline__ bool build_a_item(TcSmem<kN, kS>& S, const GridJob& J, int n_chunks,
+__device__ __forceinline__ bool build_a_item(TcSmem<kN, kS, false>& S, const GridJob& J, int n_chunks,
                                              uint32_t& g, uint32_t& gr, int32_t* err,
                                              uint64_t lim) {
-  using Sh = TcShape<kN, kS>;
+  using Sh = TcShape<kN, kS, false>;
   constexpr uint32_t kSubTile = kM * 64;       // A[s][h][1] follows A[s][h][0]
   constexpr uint32_t kLoTile = kS * kSubTile;  // A[s][1] follows A[s][0]
   const int t = threadIdx.x - kGroup;  // 0 .. kGroup-1
@@ -421,14 +425,14 @@ __device__ __forceinline__ bool build_a_item(TcSmem<kN, kS>& S, const GridJob& J
   return true;
 }
 
-template <int kN, int kS>
+template <int kN, int kS, bool kD>
 __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__ JobTable jt) {
-  using Sh = TcShape<kN, kS>;
+  using Sh = TcShape<kN, kS, kD>;
   extern __shared__ unsigned char smem_raw[];
   // 64B-swizzled tiles need 512-byte alignment (the swizzle atom); offsetting
   // smem_raw (not an integer round trip) keeps the shared address space.
   const uint32_t pad = (512u - (smem_u32(smem_raw) & 511u)) & 511u;
-  TcSmem<kN, kS>& S = *reinterpret_cast<TcSmem<kN, kS>*>(smem_raw + pad);
+  TcSmem<kN, kS, kD>& S = *reinterpret_cast<TcSmem<kN, kS, kD>*>(smem_raw + pad);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int32_t* err = jt.job[0].pv.err_word;
   const uint64_t lim = jt.wait_ns;  // limit of every bounded wait
@@ -439,14 +443,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   if (tid == 0) {
     for (int i = 0; i < Sh::kRawStages; ++i) {
       mbar_init(&S.raw_full[i], 1);
-      mbar_init(&S.raw_empty[i], kGroupWarps);  // the B converters
+      mbar_init(&S.raw_empty[i], Sh::kConv / 32);  // the B converters
     }
     for (int i = 0; i < Sh::kEntStages; ++i) {
       mbar_init(&S.ent_full[i], 1);
       mbar_init(&S.ent_empty[i], kGroupWarps);  // the A builders
     }
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&S.ab_full[i], kProducerWarps);
+      // the producer warps, and with dense A tiles the A-tile copy's arrival
+      mbar_init(&S.ab_full[i], kD ? kProducerWarps + 1 : kProducerWarps);
       mbar_init(&S.ab_empty[i], 1);
     }
     mbar_init(&S.segdone[0], 1);
@@ -542,6 +547,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
             tma_gather4(&S.raw[r][(t * kK + lane * 4) * row_bytes], tmap, (int32_t)c0, r0, r1, r2,
                         r3, &S.raw_full[r]);
         }
+      }
+      continue;
+    }
+
+    if (kD && warp == kEntWarp) {
+      // ---------------- A-tile stager (dense A tiles) ----------------
+      // Per chunk: once the A/B stage is free, the chunk's sub-chunks' A
+      // tiles (hi, and lo in the split form) straight from the plan's dense
+      // weight tiles into the stage, completing on ab_full with one
+      // expect_tx arrival.
+      const uint8_t* wt = pv.wtiles + (kb0 / kK) * (int64_t)(2 * kM * 64);
+      for (int j = 0; j < n_chunks; ++j, ++g) {
+        const int s = g % kStages;
+        const int pj = phys(j);
+        const int nsj = min(kS, n_sub - pj * kS);
+        if (g >= kStages && !mbar_wait(&S.ab_empty[s], (g / kStages - 1) & 1u, err, lim)) {
+          bail = true;
+          break;
+        }
+        if (lane == 0) {
+          const uint32_t half = (uint32_t)(kM * 64);
+          mbar_arrive_expect_tx(&S.ab_full[s], half * (split ? 2u : 1u) * (uint32_t)nsj);
+          for (int t = 0; t < nsj; ++t) {
+            const uint8_t* src = wt + (int64_t)(pj * kS + t) * (2 * kM * 64);
+            bulk_g2s(S.A[s][0][t], src, half, &S.ab_full[s]);
+            if (split) bulk_g2s(S.A[s][1][t], src + half, half, &S.ab_full[s]);
+          }
+        }
+        __syncwarp();
       }
       continue;
     }
@@ -761,22 +795,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
     if (n_chunks == 0) continue;
     {
       bool ok = true;
-      if (warp >= kGroupWarps) {  // A builders
-        ok = split ? build_a_item<true, kN, kS>(S, J, n_chunks, g, gr, err, lim)
-                   : build_a_item<false, kN, kS>(S, J, n_chunks, g, gr, err, lim);
-      } else if (split) {  // B converters
+      if constexpr (!kD) {
+        if (warp >= kGroupWarps) {  // A builders
+          ok = split ? build_a_item<true, kN, kS>(S, J, n_chunks, g, gr, err, lim)
+                     : build_a_item<false, kN, kS>(S, J, n_chunks, g, gr, err, lim);
+          bail = !ok;
+          ++n_tm;
+          continue;
+        }
+      }
+      if (split) {  // B converters
         switch (J.dtype) {
-          case HEGRID_F32: ok = convert_item<HEGRID_F32, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_F16: ok = convert_item<HEGRID_F16, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
-          default: ok = convert_item<HEGRID_BF16X2, true, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F32: ok = convert_item<HEGRID_F32, true, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, true, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F16: ok = convert_item<HEGRID_F16, true, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          default: ok = convert_item<HEGRID_BF16X2, true, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
         }
       } else {
         switch (J.dtype) {
-          case HEGRID_F32: ok = convert_item<HEGRID_F32, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
-          case HEGRID_F16: ok = convert_item<HEGRID_F16, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
-          default: ok = convert_item<HEGRID_BF16X2, false, kN, kS>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F32: ok = convert_item<HEGRID_F32, false, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_BF16: ok = convert_item<HEGRID_BF16, false, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          case HEGRID_F16: ok = convert_item<HEGRID_F16, false, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
+          default: ok = convert_item<HEGRID_BF16X2, false, kN, kS, kD>(S, J, n_chunks, n_sub, j0, c0, g, gr, err, lim, withhold); break;
         }
       }
       bail = !ok;
@@ -790,14 +830,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_grid_tc(const __grid_constant__
   if (warp == kMmaWarp) tmem_dealloc(tmem, Sh::kTmemCols);
 }
 
-template <int kN, int kS>
+template <int kN, int kS, bool kD>
 hegrid_status launch_tile(const JobTable& jt, cudaStream_t s) {
   static int sms = 0;
-  const size_t smem = sizeof(TcSmem<kN, kS>) + 512;
+  const size_t smem = sizeof(TcSmem<kN, kS, kD>) + 512;
   if (!sms) {
     int dev;
     cudaGetDevice(&dev);
-    HG_CUDA_TRY(cudaFuncSetAttribute(k_grid_tc<kN, kS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HG_CUDA_TRY(cudaFuncSetAttribute(k_grid_tc<kN, kS, kD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
@@ -807,9 +847,9 @@ hegrid_status launch_tile(const JobTable& jt, cudaStream_t s) {
     JobTable t = jt;
     t.inject = 1;
     t.wait_ns = kInjectWaitNs;
-    k_grid_tc<kN, kS><<<(unsigned)grid, kThreads, smem, s>>>(t);
+    k_grid_tc<kN, kS, kD><<<(unsigned)grid, kThreads, smem, s>>>(t);
   } else {
-    k_grid_tc<kN, kS><<<(unsigned)grid, kThreads, smem, s>>>(jt);
+    k_grid_tc<kN, kS, kD><<<(unsigned)grid, kThreads, smem, s>>>(jt);
   }
   count_launch();
   HG_CUDA_TRY(launch_status());
@@ -823,11 +863,14 @@ int tc_default_band() { return kDefaultBand; }
 int tc_default_seg() { return kDefaultSeg; }
 int tc_default_group() { return kDefaultGroup; }
 
-hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile) {
-  switch (tile) {
-    case 64: return launch_tile<64, 2>(jt, s);
-    case 128: return launch_tile<128, 1>(jt, s);
-    case 256: return launch_tile<256, 1>(jt, s);
+hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile, bool dense_a) {
+  switch (tile * 2 + (dense_a ? 1 : 0)) {
+    case 128: return launch_tile<64, 2, false>(jt, s);
+    case 129: return launch_tile<64, 2, true>(jt, s);
+    case 256: return launch_tile<128, 1, false>(jt, s);
+    case 257: return launch_tile<128, 1, true>(jt, s);
+    case 512: return launch_tile<256, 1, false>(jt, s);
+    case 513: return launch_tile<256, 1, true>(jt, s);
     default:
       set_error("unsupported tensor-core channel tile");
       return HEGRID_ERR_UNSUPPORTED;

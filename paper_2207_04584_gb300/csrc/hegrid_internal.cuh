@@ -126,8 +126,9 @@ struct hegrid_plan {
   // Launch shapes chosen by hegrid_autotune (0: defaults): FP32 band, tensor
   // core band, segment length and channel-tile group.
   int32_t tune_f32_band, tune_tc_band, tune_tc_seg, tune_tc_group;
-  // Tensor-core kernel: 0 (default) and 1: cell-major; 2: channel-major
-  // (where its weight tiles exist or can be built).
+  // Tensor-core kernel: 0 (default) and 1: cell-major; 2: channel-major;
+  // 3: cell-major with its A tiles from the dense weight tiles (2 and 3 where
+  // the tiles exist or can be built).
   int32_t tune_tc_kernel;
   // Dense weight tiles of the channel-major kernel (owned; built by the first
   // grid call that runs it, on that call's stream, which then re-records
@@ -214,8 +215,10 @@ struct AbsmaxRequest {
 };
 hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s,
                                  int ctas_per_sm = 8);
-// `tile`: the channel tile of every job in the table (tc_channel_tile(C)).
-hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile);
+// `tile`: the channel tile of every job in the table (tc_channel_tile(C));
+// dense_a: the A tiles come from the plans' dense weight tiles (every job's
+// plan must have them).
+hegrid_status launch_grid_tc(const JobTable& jt, cudaStream_t s, int tile, bool dense_a);
 int f32_channel_tile();
 // Tensor-core channel tile for C channels: the narrowest of 64, 128, 256
 // that holds C, else 256.

@@ -165,10 +165,12 @@ def test_grid_faults_leak_nothing(H, fault, what, status):
         H.hegrid_plan_destroy(plan)
 
 
-def test_channel_major_wait_timeout(H, fault):
-    """The channel-major tensor-core kernel's bounded waits: one value warp
-    withholds its first arrive, every role gives up, TIMEOUT is reported and
-    the plan grids correctly afterwards."""
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_dense_tile_kernels_wait_timeout(H, fault, kernel):
+    """The bounded waits of the kernels that read the dense weight tiles
+    (channel-major; cell-major with dense A tiles): one producer warp withholds
+    its first arrive, every role gives up, TIMEOUT is reported and the plan
+    grids correctly afterwards."""
     wl = W.config1(n=6000, C=200, nx=48, ny=40)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
@@ -177,7 +179,7 @@ def test_channel_major_wait_timeout(H, fault):
     out = torch.zeros((M, 200), device="cuda")
     plan = _plan(H, wl)
     try:
-        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, 2)
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, kernel)
         fault("wait:1")
         H.hegrid_grid(plan, v, H.HEGRID_F32, 200, 200, out, 200, None, H.HEGRID_MODE_TC_SPLIT, s)
         torch.cuda.synchronize()
@@ -189,7 +191,7 @@ def test_channel_major_wait_timeout(H, fault):
         H.hegrid_plan_destroy(plan)
     plan = _plan(H, wl)
     try:
-        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, 2)
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, kernel)
         H.hegrid_grid(plan, v, H.HEGRID_F32, 200, 200, out, 200, None, H.HEGRID_MODE_TC_SPLIT, s)
         torch.cuda.synchronize()
         H.hegrid_status_poll(plan)
@@ -200,13 +202,15 @@ def test_channel_major_wait_timeout(H, fault):
     assert err <= 5e-5, err
 
 
+@pytest.mark.parametrize("kernel", [2, 3])
 @pytest.mark.parametrize("what,status", [("alloc:1", "HEGRID_ERR_OOM"),
                                          ("alloc:2", "HEGRID_ERR_OOM"),
                                          ("launch:1", "HEGRID_ERR_CUDA"),
                                          ("launch:2", "HEGRID_ERR_CUDA"),
                                          ("launch:3", "HEGRID_ERR_CUDA")])
-def test_channel_major_first_call_faults_leak_nothing(H, fault, what, status):
-    """The first channel-major grid call on a plan allocates the channel maxima
+def test_dense_tile_first_call_faults_leak_nothing(H, fault, what, status, kernel):
+    """The first grid call on a plan with a kernel that reads the dense weight
+    tiles (channel-major, or cell-major with dense A tiles) allocates the channel maxima
     (allocation 1) and the plan's dense weight tiles (2), then launches the
     tile build (launch 1), the maxima pass (2) and the grid kernel (3).  A
     failure anywhere returns its status; the tiles stay with the plan only if
@@ -221,7 +225,7 @@ def test_channel_major_first_call_faults_leak_nothing(H, fault, what, status):
     base0 = _used(H)
     plan = _plan(H, wl)
     try:
-        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, 2)
+        H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, kernel)
         base = _used(H)
         b0 = H.hegrid_plan_info(plan)["bytes"]
         fault(what)

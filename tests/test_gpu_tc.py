@@ -90,7 +90,7 @@ def test_tc_f32_config1(H, mode, tol):
     assert np.max(np.abs(gw[has] / Wref[has] - 1.0)) <= wtol
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("C", [1, 5, 64, 65, 100, 128, 129, 256, 257, 300])
 def test_tc_split_ragged_channels(H, C, kernel):
     """Every channel-tile width (64, 128, 256 cell-major; 128 channel-major)
@@ -332,7 +332,7 @@ def _stored(kind, vals, H):
         np.ascontiguousarray(stored.astype(np.float32))
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("kind", ["f32", "bf16x2", "bf16", "f16"])
 @pytest.mark.parametrize("C", [50, 100, 300])
 def test_tc_split_mixed_channel_scales(H, kind, C, kernel):
@@ -393,3 +393,28 @@ def test_channel_major_equals_cell_major(H, C, kind, mode):
     diff = np.max(np.abs(a[ok].astype(np.float64) - b[ok]), axis=0) / rms
     assert diff.max() <= 2e-6, diff.max()
     assert np.array_equal(wa, wb) and np.array_equal(wa, wc)
+
+
+@pytest.mark.parametrize("C", [40, 100, 300])
+@pytest.mark.parametrize("kind", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("mode", ["split", "single"])
+def test_dense_a_tiles_equal_built_a_tiles(H, C, kind, mode):
+    """The cell-major kernel with its A tiles copied from the plan's dense
+    weight tiles (kernel 3) multiplies exactly the A tiles its A builders would
+    assemble from the entries (kernel 1), at every channel-tile width (64 with
+    two sub-chunks per chunk, 128, 256): maps and weight maps equal bit for bit."""
+    wl = _case(131 + C, n=9000, nx=56, ny=32, C=C)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    dv, dt, ld, _ = _stored(kind, wl["values"], H)
+    md = H.HEGRID_MODE_TC_SPLIT if mode == "split" else H.HEGRID_MODE_TC
+    plan = _plan(H, wl)
+    try:
+        H.hegrid_plan_set_tuning(plan, md, -4, 16, 0, 1)
+        a, wa = _run(H, plan, dv, dt, C, ld, M, md)
+        H.hegrid_plan_set_tuning(plan, md, -4, 16, 0, 3)
+        b, wb = _run(H, plan, dv, dt, C, ld, M, md)
+    finally:
+        H.hegrid_plan_destroy(plan)
+    assert np.array_equal(a, b, equal_nan=True)
+    assert np.array_equal(wa, wb)
