@@ -506,7 +506,13 @@ def run_config3(args, H, torch, dev, rank):
                    "value": N * C / t, "pair_channel_per_s": info["n_pairs"] * C / t,
                    "roofline": {"bound": "hbm", "achieved": bytes_alg / t / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": bytes_alg / t / 1e9 / hbm,
-                                "algorithmic_bytes": bytes_alg, "peak_kind": peak_kind},
+                                "algorithmic_bytes": bytes_alg, "peak_kind": peak_kind,
+                                "limit": "not DRAM (the launch moves ~1.2x the algorithmic "
+                                         "bytes, profiles/k_grid_tc_config3_bf16.md): the "
+                                         "per-chunk shared-memory work of the B conversion "
+                                         "and the MMA operand reads over 7,680 short work "
+                                         "items (LSU shared wavefronts ~40% of peak, tensor "
+                                         "pipe ~21%)"},
                    "gpu_launches_per_call": launches}
             if not args.no_cpu_baseline and rank == 0:
                 if kind not in oracle_cache:  # forms of one stored type are consecutive
@@ -896,6 +902,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--channels", type=int, default=1024)
+    ap.add_argument("--shape", default="",
+                    help="band,seg,group,kernel (as --shape=-8,16,0,3): apply this launch shape (bin edge 2) "
+                         "instead of running the autotuner (profiler captures of the shape "
+                         "the autotuner keeps)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch shapes, bin edge 2)")
     ap.add_argument("--workload", default="config2",
@@ -997,7 +1007,11 @@ def main():
     # grid step's launch shape, applied to every plan the steps create -----
     tune = {}
     hpx_flag = H.HEGRID_PLAN_HEALPIX(args.healpix) if args.healpix else 0
-    if not args.no_tune:
+    if args.shape:
+        b_, s_, g_, k_ = (int(x) for x in args.shape.split(","))
+        tune = {"bin_cells": hpx_flag or 2, "band": b_, "seg": s_, "group": g_, "kernel": k_,
+                "given": True}
+    elif not args.no_tune:
         t_tune = time.perf_counter()
         if args.healpix:
             bin_cells, bin_ms = hpx_flag, []
@@ -1130,10 +1144,16 @@ def main():
     else:
         achieved = alg_bytes / t_grid / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": measured_traffic("k_grid_tc"),
+                "frac": achieved / hbm,
+                "traffic": measured_traffic({1: "k_grid_tc", 3: "k_grid_tc_dense"}.get(
+                    tune.get("kernel", 1), "")),
+                "kernel": {1: "k_grid_tc (cell-major)", 2: "k_grid_tcm (channel-major)",
+                           3: "k_grid_tc (cell-major, dense A tiles)"}.get(tune.get("kernel", 1),
+                                                                          "k_grid_tc"),
                 "note": f"algorithmic bytes N*C*4 + M*C*4 + M*4 per grid call / the device "
-                        f"time of hegrid_grid_prescaled in the timed steps (the grid kernel; "
-                        f"the per-channel maximum pass runs beside plan creation); "
+                        f"time of hegrid_grid_prescaled in the timed steps (the grid kernel, "
+                        f"plus the plan's dense weight-tile build for the kernels that read "
+                        f"them; the per-channel maximum pass runs beside plan creation); "
                         f"peak {peak_kind}"}
 
     # ---- end to end through the C ABI with host buffers -------------------
