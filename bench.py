@@ -113,11 +113,18 @@ TRAFFIC = {
                   "bytes": 32.899492224e9 + 1.472701696e9,
                   "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench's tuned launch, "
                              "C=1024; mean of 4)"},
+    "k_grid_tc_dense": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
+                                    "paper_2207_04584_gb300/csrc/ptx.cuh",
+                                    "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
+                        "sha256": "200d51fa6c6e2011c7cf17ae4316ce0307b8adfbacc78be5f1d7721a5f50fb63",
+                        "bytes": 38.2067e9 + 1.473e9,
+                        "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench's tuned "
+                                   "launch with dense A tiles, C=1024; mean of 9)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": "00e4237e8ae40b64adf72dc8b7e533bff35beb024114e47bce159560576459ef",
-                   "bytes": 32.590529728e9 + 1.469339008e9,
+                   "sha256": "294ad160ed33f70c52ce8761fe901806cd36fa1cf7072a76a23e73fde85c5bb1",
+                   "bytes": 30.3695e9 + 1.470e9,
                    "capture": "profiles/k_grid_f32_fast_drift_c256.md (the bench's FP32-form "
                               "launch, C=1024; mean of 4)"},
 }
@@ -906,6 +913,9 @@ def main():
                     help="band,seg,group,kernel (as --shape=-8,16,0,3): apply this launch shape (bin edge 2) "
                          "instead of running the autotuner (profiler captures of the shape "
                          "the autotuner keeps)")
+    ap.add_argument("--step-priority", default="normal", choices=["normal", "high"],
+                    help="priority of the step's stream against the side stream of the "
+                         "channel-maximum pass")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch shapes, bin edge 2)")
     ap.add_argument("--workload", default="config2",
@@ -983,7 +993,13 @@ def main():
     vals_d = host_vals.to(dev)
     map_d = torch.empty((M, C), device=dev)
     w_d = torch.empty(M, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    if args.step_priority == "high":
+        # the step's own stream above the side stream of the channel-maximum
+        # pass, so that the plan's kernels are scheduled first
+        stream = torch.cuda.Stream(dev, priority=-1)
+        torch.cuda.set_stream(stream)
+    else:
+        stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
 
     modes = {"tc_split": H.HEGRID_MODE_TC_SPLIT, "tc": H.HEGRID_MODE_TC,
