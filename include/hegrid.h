@@ -216,10 +216,12 @@ hegrid_status hegrid_grid_batched(int n, hegrid_plan *const *plans, const hegrid
  * pipelines) with its work queue uploaded once and its launches captured in a
  * CUDA graph; launch
  * replays the graph on `stream`.  The plans and buffers named in args must
- * outlive the batch.  create waits (on the host) for the plans to be built
- * and sets *out (NULL on error).
+ * outlive the batch.  create waits (on the host) for the plans to be built,
+ * first builds, on `stream`, the dense weight tiles of plans tuned to a kernel
+ * that reads them (hegrid_plan_set_tuning kernel 2 or 3), and sets *out (NULL
+ * on error).
  * Errors: create: INVALID_ARG (out NULL, and as for hegrid_grid_batched),
- * CUDA (capture or instantiation failed); launch: INVALID_ARG (batch NULL),
+ * OOM (the dense tiles), CUDA (capture or instantiation failed); launch: INVALID_ARG (batch NULL),
  * CUDA; destroy: NULL is a no-op, returns OK.
  */
 hegrid_status hegrid_batch_create(hegrid_batch **out, int n, hegrid_plan *const *plans,

@@ -671,8 +671,17 @@ hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const*
     hegrid_status st = hg::check_args(plans ? plans[i] : nullptr, args[i]);
     if (st != HEGRID_OK) return st;
   }
-  // the plans must be complete before their launches are recorded
+  // the plans must be complete before their launches are recorded; plans
+  // tuned to a kernel that reads the dense weight tiles get them now (they
+  // cannot be built inside the capture)
   for (int i = 0; i < n; ++i) HG_CUDA_TRY(cudaEventSynchronize(plans[i]->ready));
+  for (int i = 0; i < n; ++i) {
+    if (args[i].mode == HEGRID_MODE_FP32 || plans[i]->wtiles) continue;
+    if (plans[i]->tune_tc_kernel != 2 && plans[i]->tune_tc_kernel != 3) continue;
+    hegrid_status st = hg::ensure_wtiles(plans[i], (cudaStream_t)stream);
+    if (st != HEGRID_OK) return st;
+    HG_CUDA_TRY(cudaEventSynchronize(plans[i]->ready));
+  }
   cudaStream_t cap;
   HG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   hegrid_batch* b = new hegrid_batch();
@@ -708,7 +717,6 @@ hegrid_status hegrid_batch_create(hegrid_batch** out, int n, hegrid_plan* const*
     }
     return st;
   }
-  (void)stream;
   *out = b;
   return HEGRID_OK;
 }

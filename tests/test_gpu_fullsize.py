@@ -15,7 +15,7 @@ from helpers import map_error
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "tc_split": 5e-5}
+TOL = {"fp32": 1e-5, "tc_split": 5e-5, "tc_split_dense_a": 5e-5, "tc_split_prescaled": 5e-5}
 
 
 @pytest.fixture(scope="module")
@@ -58,8 +58,11 @@ def plan(H, drift):
     H.hegrid_plan_destroy(p)
 
 
-@pytest.mark.parametrize("mode", ["fp32", "tc_split"])
+@pytest.mark.parametrize("mode", ["fp32", "tc_split", "tc_split_dense_a", "tc_split_prescaled"])
 def test_drift_scan_full_size(H, drift, plan, mode):
+    """Both forms; the split form also with dense A tiles (the kernel the
+    benchmark's autotuner keeps) and through the prescaled call the benchmark
+    step makes (channel maxima computed apart)."""
     wl, cells, ref, Wref, P = drift
     g = wl["geom"]
     M = g["nx"] * g["ny"]
@@ -67,10 +70,17 @@ def test_drift_scan_full_size(H, drift, plan, mode):
     assert (N, C) == (1940838, 1024)
     s = torch.cuda.current_stream().cuda_stream
     md = H.HEGRID_MODE_FP32 if mode == "fp32" else H.HEGRID_MODE_TC_SPLIT
+    H.hegrid_plan_set_tuning(plan, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0,
+                             3 if mode in ("tc_split_dense_a", "tc_split_prescaled") else 1)
     v = torch.from_numpy(wl["values"]).cuda()
     out = torch.full((M, C), -7.0, device="cuda")
     wout = torch.full((M,), -7.0, device="cuda")
-    H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, wout, md, s)
+    if mode == "tc_split_prescaled":
+        chmax = torch.empty(C, dtype=torch.int32, device="cuda")
+        H.hegrid_chan_maxima(v, H.HEGRID_F32, N, C, C, chmax, s)
+        H.hegrid_grid_prescaled(plan, v, H.HEGRID_F32, C, C, chmax, out, C, wout, md, s)
+    else:
+        H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, wout, md, s)
     torch.cuda.synchronize()
     H.hegrid_status_poll(plan)
     idx = torch.from_numpy(cells).cuda()

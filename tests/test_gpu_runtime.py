@@ -58,13 +58,20 @@ def _dev_values(wl, dtype_name):
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batched_uneven_fields(H, use_graph):
+@pytest.mark.parametrize("kernels", ["default", "mixed"])
+def test_batched_uneven_fields(H, use_graph, kernels):
+    """A batch of uneven fields against the oracle; "mixed": the fields' plans
+    tuned in turn to the three tensor-core kernels (cell-major, cell-major with
+    dense A tiles, channel-major), so one batch (and one graph) holds all of
+    them and the dense tiles are built before the capture."""
     wls = _fields()
     plans, args, refs, outs = [], [], [], []
     n_f32 = 0
     try:
-        for wl in wls:
+        for i, wl in enumerate(wls):
             plans.append(_plan(H, wl))
+            if kernels == "mixed":
+                H.hegrid_plan_set_tuning(plans[-1], H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, [1, 3, 2][i % 3])
             C = wl["values"].shape[1]
             M = wl["geom"]["nx"] * wl["geom"]["ny"]
             dv, ld, refv = _dev_values(wl, wl["dtype"])
