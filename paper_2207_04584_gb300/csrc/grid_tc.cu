@@ -38,7 +38,9 @@
 //   warp 17     stages the chunk's sample rows (raw, as stored; eight
 //               four-row TMA tensor gathers per sub-chunk) into a ring;
 //   warp 22     stages the chunk's weight entries (bulk copies) into a
-//               3-deep ring of their own;
+//               3-deep ring of their own (with dense A tiles, kD: copies the
+//               chunk's A tiles whole from the plan's dense weight tiles into
+//               the A/B stage instead, and warps 8-15 convert B as well);
 //   warps 0-7   convert a staged chunk into the B tiles (row = channel; 16-byte
 //               pieces of 8 samples; no barrier among them);
 //   warps 8-15  zero the A tiles and store the chunk's weight entries into

@@ -18,9 +18,10 @@
 // the kernel moves 16 KB of sample rows in and out of shared memory, 16 KB of
 // weight tiles in, and the MMAs read 24 KB of them, about 72 KB against the
 // cell-major kernel's ~125 KB per 128 channels (staged rows in and out,
-// converted B tiles, zeroed and scattered A tiles, entries, operand reads).  Precision, segments, the per-channel
-// scale and W are those of the cell-major kernel (grid_tc.cu): hi*hi + hi*lo
-// (+ lo*hi for 4-byte values) in the split form, hi*hi in the single form.
+// converted B tiles, zeroed and scattered A tiles, entries, operand reads).
+// Precision, segments, the per-channel scale and W are those of the
+// cell-major kernel (grid_tc.cu): hi*hi + hi*lo (+ lo*hi for 4-byte values)
+// in the split form, hi*hi in the single form.
 //
 // Warp roles (one CTA per SM, persistent over work items):
 //   warps 0-7    value warps: warp w serves TMEM lane quarter w & 3 (its
@@ -55,12 +56,11 @@ constexpr int kCK = 32;              // candidates per sub-chunk
 // Rings: the value operands in TMEM and the weight tiles in shared memory
 // are held in two round slots of kRound stages each (kAStg = kBStg = 2 kRound):
 // the MMA warp issues a round's MMAs behind one fence and releases the
-// round's stages with one tcgen05.commit (a commit costs the issuing thread
-// ~300 cycles before its next tcgen05 instruction, measured with clock
-// stamps, so the kernel commits once per round, not once per stage).  A
-// round never spans two accumulation segments; a short round leaves its
-// slot's remaining stages unused.  The sample rows (kRStg stages) are
-// released as soon as the value warps have read them.
+// round's stages with one tcgen05.commit.  A round never spans two
+// accumulation segments; a short round at a segment's end leaves its slot's
+// remaining stages unused (their barriers still complete one phase per
+// round).  The sample rows (kRStg stages) are released as soon as the value
+// warps have read them.
 constexpr int kRound = 4;  // sub-chunks per MMA issue round
 constexpr int kAStg = 2 * kRound;
 constexpr int kBStg = 2 * kRound;
