@@ -116,7 +116,7 @@ TRAFFIC = {
     "k_grid_tc_dense": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                                     "paper_2207_04584_gb300/csrc/ptx.cuh",
                                     "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                        "sha256": "200d51fa6c6e2011c7cf17ae4316ce0307b8adfbacc78be5f1d7721a5f50fb63",
+                        "sha256": "c124a838df4100a1d1605147cf29c7fe4072490089d0953f124db8b748555830",
                         "bytes": 38.2067e9 + 1.473e9,
                         "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench's tuned "
                                    "launch with dense A tiles, C=1024; mean of 9)"},
