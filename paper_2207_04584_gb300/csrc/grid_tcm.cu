@@ -46,6 +46,7 @@
 
 #include "hegrid_internal.cuh"
 #include "ptx.cuh"
+#include "wtile.cuh"
 
 namespace hg {
 namespace {
@@ -71,8 +72,7 @@ constexpr int kTileW = 9;
 constexpr int kDrainW0 = 10;  // 4 warps
 constexpr int kRowW = 14;
 constexpr int kThreadsCM = 15 * 32;
-constexpr uint32_t kHalfTile = (uint32_t)kCN * 64u;  // one 16-bit half: 128 rows x 64 bytes
-constexpr uint32_t kWTileBytes = 2u * kHalfTile;     // hi + lo
+constexpr uint32_t kHalfTile = kWTileHalfBytes;      // one 16-bit half: 128 rows x 64 bytes
 constexpr uint32_t kDCols = kCN;                     // accumulator columns (one per cell)
 constexpr uint32_t kACol0 = 2u * kDCols;             // value operands after the two regions
 constexpr uint32_t kAStageCols = kCK;                // hi: 16 columns, lo: 16 columns
@@ -587,25 +587,13 @@ __global__ void __launch_bounds__(256) k_build_wtiles(PlanView pv, uint8_t* __re
   const int t = threadIdx.x;
   const int64_t s0 = pv.cand_off[b] / kCK;
   const int n_sub = pv.cand_cnt[b] / kCK;
+  wtile_zero<256>(tile, t);
+  __syncthreads();
   for (int j = part; j < n_sub; j += kBuildSplit) {
     const int64_t s = s0 + j;
-#pragma unroll
-    for (int i = t; i < (int)(kWTileBytes / 16); i += 256)
-      reinterpret_cast<uint4*>(tile)[i] = make_uint4(0u, 0u, 0u, 0u);
+    wtile_scatter<256>(tile, pv.ent_ck, pv.ent_w, pv.sub_off[s], pv.sub_off[s + 1], t);
     __syncthreads();
-    const int64_t e0 = pv.sub_off[s], e1 = pv.sub_off[s + 1];
-    for (int64_t e = e0 + t; e < e1; e += 256) {
-      const uint32_t off = pv.ent_ck[e];
-      const float w = pv.ent_w[e] * kTcWeightScale;
-      const __half hw = __float2half_rn(w);
-      const __half lw = __float2half_rn(w - __half2float(hw));
-      *reinterpret_cast<__half*>(tile + off) = hw;
-      *reinterpret_cast<__half*>(tile + kHalfTile + off) = lw;
-    }
-    __syncthreads();
-    uint4* dst = reinterpret_cast<uint4*>(wt + s * (int64_t)kWTileBytes);
-#pragma unroll
-    for (int i = t; i < (int)(kWTileBytes / 16); i += 256) dst[i] = reinterpret_cast<const uint4*>(tile)[i];
+    wtile_flush<256>(tile, wt + s * (int64_t)kWTileBytes, t);
     __syncthreads();
   }
 }
