@@ -1071,7 +1071,8 @@ def main():
         e0.record(stream)
         if overlap:
             side.wait_event(e0)
-            H.hegrid_chan_maxima(vals_d, H.HEGRID_F32, N, C, C, chmax_d, side.cuda_stream)
+            H.hegrid_chan_maxima(vals_d, H.HEGRID_F32, N, C, C, chmax_d, H.HEGRID_MAXIMA_BESIDE,
+                                 side.cuda_stream)
             es = torch.cuda.Event()
             es.record(side)
         plan = new_plan(lon_d, lat_d, 1)

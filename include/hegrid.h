@@ -158,13 +158,19 @@ hegrid_status hegrid_grid(hegrid_plan *plan, const void *values, hegrid_dtype dt
  *
  * values     device [n_samples x ld_values] of `dtype`, as for hegrid_grid.
  * chmax_out  device uint32 [n_channels], written (caller-owned).
+ * flags      0: the pass takes the whole GPU (every SM's threads; HBM-bound).
+ *            HEGRID_MAXIMA_BESIDE: one 128-thread CTA per SM without shared
+ *            memory, so that kernels on other streams (plan creation) keep
+ *            their SM slots while it runs; alone it takes about three times
+ *            as long.  Other bits: INVALID_ARG.
  *
  * Errors: INVALID_ARG (NULL pointers, n_samples < 1, n_channels < 1, bad
- * ld/alignment/dtype); CUDA (launch failure).
+ * ld/alignment/dtype/flags); CUDA (launch failure).
  */
+#define HEGRID_MAXIMA_BESIDE (1u << 0)
 hegrid_status hegrid_chan_maxima(const void *values, hegrid_dtype dtype, int64_t n_samples,
                                  int64_t n_channels, int64_t ld_values, uint32_t *chmax_out,
-                                 void *stream);
+                                 uint32_t flags, void *stream);
 
 /*
  * hegrid_grid_prescaled -- hegrid_grid with the channel maxima already

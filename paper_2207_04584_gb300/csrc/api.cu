@@ -126,6 +126,7 @@ struct AbsmaxJob {
   int64_t block_base;  // first CTA of this entry
 };
 constexpr int kMaxAbsmaxJobs = kMaxJobs;
+constexpr int kAbsmaxLeanThreads = 128;
 struct AbsmaxTable {
   int32_t n;
   AbsmaxJob job[kMaxAbsmaxJobs];
@@ -202,6 +203,40 @@ __global__ void __launch_bounds__(256) k_chan_absmax(const __grid_constant__ Abs
       const int64_t c = cv * vec + e;
       if (c < J.C && m[e] > 0.0f) atomicMax(J.out + c, __float_as_uint(m[e]));
     }
+  }
+}
+
+// The same maxima from one 128-thread CTA per SM, no shared memory and at
+// most 32 registers a thread: each thread keeps its column group's maxima
+// and adds them with atomicMax, so the pass leaves the SMs' shared memory and
+// nearly all their registers and threads to kernels on other streams.
+__global__ void __launch_bounds__(kAbsmaxLeanThreads, 16)
+    k_chan_absmax_lean(const __grid_constant__ AbsmaxTable tab) {
+  int j = 0;
+  while (j + 1 < tab.n && tab.job[j + 1].block_base <= (int64_t)blockIdx.x) ++j;
+  const AbsmaxJob& J = tab.job[j];
+  const int64_t local = (int64_t)blockIdx.x - J.block_base;
+  const int64_t bx = local / J.gy, by = local - bx * J.gy;
+  const int tid = threadIdx.x;
+  const int cols = J.cols, rpt = kAbsmaxLeanThreads / cols;
+  const int cslot = tid % cols, rl = tid / cols;
+  const int64_t cv = by * cols + cslot;
+  const int64_t r0 = bx * J.rows_per_cta;
+  const int64_t r1 = r0 + J.rows_per_cta < J.N ? r0 + J.rows_per_cta : J.N;
+  const int vec = (J.dtype == HEGRID_F32 || J.dtype == HEGRID_BF16X2) ? 4 : 8;
+  if (rl >= rpt || cv >= J.nvec) return;
+  float m[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) m[e] = 0.0f;
+  switch (J.dtype) {
+    case HEGRID_F32: absmax_rows<HEGRID_F32>(J, cv, r0, r1, rl, rpt, m); break;
+    case HEGRID_BF16X2: absmax_rows<HEGRID_BF16X2>(J, cv, r0, r1, rl, rpt, m); break;
+    case HEGRID_BF16: absmax_rows<HEGRID_BF16>(J, cv, r0, r1, rl, rpt, m); break;
+    default: absmax_rows<HEGRID_F16>(J, cv, r0, r1, rl, rpt, m); break;
+  }
+  for (int e = 0; e < vec; ++e) {
+    const int64_t c = cv * vec + e;
+    if (c < J.C && m[e] > 0.0f) atomicMax(J.out + c, __float_as_uint(m[e]));
   }
 }
 
@@ -479,11 +514,25 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
   return st;
 }
 
-}  // namespace
-
-hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s,
-                                 int ctas_per_sm) {
+// Launches the maximum pass over n requests: the full kernel (256 threads,
+// about ctas_per_sm CTAs per SM) or, lean, one k_chan_absmax_lean CTA per SM.
+// Both kernels prefer the largest shared-memory carveout: an SM changes its
+// L1 / shared-memory split only when it is idle, so a pass resident on every
+// SM under a small carveout would keep kernels of other streams that need
+// shared memory (plan creation's sort and pair kernels) off the GPU until it
+// ends.
+hegrid_status launch_absmax(int n, const AbsmaxRequest* req, cudaStream_t s, int ctas_per_sm,
+                            bool lean) {
   if (n <= 0) return HEGRID_OK;
+  static std::once_flag carve;
+  std::call_once(carve, [] {
+    cudaFuncSetAttribute(k_chan_absmax, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_chan_absmax_lean, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+  });
+  const int threads = lean ? kAbsmaxLeanThreads : 256;
+  if (lean) ctas_per_sm = 1;
   int dev = 0, n_sm = 0;
   HG_CUDA_TRY(cudaGetDevice(&dev));
   HG_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -505,8 +554,8 @@ hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s
       J.ld = r.ld;
       J.dtype = r.dtype;
       J.nvec = (int32_t)nvec;
-      J.cols = (int32_t)std::min<int64_t>(nvec, 256);
-      const int rpt = 256 / J.cols;
+      J.cols = (int32_t)std::min<int64_t>(nvec, threads);
+      const int rpt = threads / J.cols;
       J.gy = (int32_t)((nvec + J.cols - 1) / J.cols);
       // about ctas_per_sm CTAs per SM over all channel groups, each thread >= 32 rows
       int64_t gx = std::max<int64_t>(1, (ctas_per_sm * (int64_t)n_sm + J.gy - 1) / J.gy);
@@ -516,11 +565,21 @@ hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s
       blocks += gx * J.gy;
     }
     HG_ARG_CHECK(blocks < ((int64_t)1 << 31), "too many channel-maximum blocks");
-    k_chan_absmax<<<(unsigned)blocks, 256, 0, s>>>(tab);
+    if (lean)
+      k_chan_absmax_lean<<<(unsigned)blocks, kAbsmaxLeanThreads, 0, s>>>(tab);
+    else
+      k_chan_absmax<<<(unsigned)blocks, 256, 0, s>>>(tab);
     count_launch();
     HG_CUDA_TRY(launch_status());
   }
   return HEGRID_OK;
+}
+
+}  // namespace
+
+hegrid_status launch_chan_absmax(int n, const AbsmaxRequest* req, cudaStream_t s,
+                                 int ctas_per_sm) {
+  return launch_absmax(n, req, s, ctas_per_sm, false);
 }
 
 }  // namespace hg
@@ -551,9 +610,10 @@ hegrid_status hegrid_grid(hegrid_plan* plan, const void* values, hegrid_dtype dt
 
 hegrid_status hegrid_chan_maxima(const void* values, hegrid_dtype dtype, int64_t n_samples,
                                  int64_t n_channels, int64_t ld_values, uint32_t* chmax_out,
-                                 void* stream) {
+                                 uint32_t flags, void* stream) {
   hg::set_error("");
   HG_ARG_CHECK(values != nullptr && chmax_out != nullptr, "values or chmax_out is NULL");
+  HG_ARG_CHECK((flags & ~HEGRID_MAXIMA_BESIDE) == 0, "unknown hegrid_chan_maxima flag bits");
   HG_ARG_CHECK(n_samples >= 1, "n_samples must be >= 1");
   HG_ARG_CHECK(n_channels >= 1, "n_channels must be >= 1");
   const int eb = hg::elem_bytes((int)dtype);
@@ -570,7 +630,7 @@ hegrid_status hegrid_chan_maxima(const void* values, hegrid_dtype dtype, int64_t
   r.C = n_channels;
   r.ld = ld_values;
   r.out = chmax_out;
-  return hg::launch_chan_absmax(1, &r, s);
+  return hg::launch_absmax(1, &r, s, 8, (flags & HEGRID_MAXIMA_BESIDE) != 0);
 }
 
 hegrid_status hegrid_grid_prescaled(hegrid_plan* plan, const void* values, hegrid_dtype dtype,

@@ -32,6 +32,7 @@ def HEGRID_PLAN_BIN_CELLS(b):
 
 
 HEGRID_PLAN_SFL = 1 << 13  # plan_create flag: Sanson-Flamsteed map geometry
+HEGRID_MAXIMA_BESIDE = 1 << 0  # hegrid_chan_maxima flag: one lean CTA per SM
 
 
 def HEGRID_PLAN_HEALPIX(k):
@@ -101,7 +102,7 @@ def lib():
                                      ctypes.POINTER(hegrid_kernel), u32, P]
     L.hegrid_grid.argtypes = [P, P, c_int, i64, i64, P, i64, P, u32, P]
     L.hegrid_grid_masked.argtypes = [P, P, c_int, i64, i64, P, i64, P, u32, P]
-    L.hegrid_chan_maxima.argtypes = [P, c_int, i64, i64, i64, P, P]
+    L.hegrid_chan_maxima.argtypes = [P, c_int, i64, i64, i64, P, u32, P]
     L.hegrid_grid_prescaled.argtypes = [P, P, c_int, i64, i64, P, P, i64, P, u32, P]
     L.hegrid_plan_destroy.argtypes = [P]
     L.hegrid_grid_batched.argtypes = [c_int, PP, ctypes.POINTER(hegrid_grid_args), P]
@@ -179,11 +180,12 @@ def hegrid_grid(plan, values, dtype, n_channels, ld_values, map_out, ld_map, wei
                                     int(mode), _ptr(stream)), "hegrid_grid")
 
 
-def hegrid_chan_maxima(values, dtype, n_samples, n_channels, ld_values, chmax_out, stream=None):
+def hegrid_chan_maxima(values, dtype, n_samples, n_channels, ld_values, chmax_out, flags=0,
+                       stream=None):
     """Per-channel largest |v| (FP32 bits) into chmax_out (device uint32 [C])."""
     return _check(lib().hegrid_chan_maxima(_ptr(values), int(dtype), int(n_samples),
                                            int(n_channels), int(ld_values), _ptr(chmax_out),
-                                           _ptr(stream)), "hegrid_chan_maxima")
+                                           int(flags), _ptr(stream)), "hegrid_chan_maxima")
 
 
 def hegrid_grid_prescaled(plan, values, dtype, n_channels, ld_values, chmax, map_out, ld_map,

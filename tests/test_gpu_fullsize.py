@@ -77,7 +77,7 @@ def test_drift_scan_full_size(H, drift, plan, mode):
     wout = torch.full((M,), -7.0, device="cuda")
     if mode == "tc_split_prescaled":
         chmax = torch.empty(C, dtype=torch.int32, device="cuda")
-        H.hegrid_chan_maxima(v, H.HEGRID_F32, N, C, C, chmax, s)
+        H.hegrid_chan_maxima(v, H.HEGRID_F32, N, C, C, chmax, H.HEGRID_MAXIMA_BESIDE, s)
         H.hegrid_grid_prescaled(plan, v, H.HEGRID_F32, C, C, chmax, out, C, wout, md, s)
     else:
         H.hegrid_grid(plan, v, H.HEGRID_F32, C, C, out, C, wout, md, s)

@@ -201,9 +201,11 @@ def test_stream_unaligned_rows(H, dtype, cc, n_chunks):
 
 @pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("kind", ["f32", "bf16", "f16"])
-def test_grid_prescaled_overlapped_with_plan(H, kernel, kind):
+@pytest.mark.parametrize("beside", [False, True])
+def test_grid_prescaled_overlapped_with_plan(H, kernel, kind, beside):
     """The channel maxima computed on a second stream while the plan is built
-    (hegrid_chan_maxima), then hegrid_grid_prescaled: the maxima are each
+    (hegrid_chan_maxima, the full pass or the one-CTA-per-SM pass of
+    HEGRID_MAXIMA_BESIDE), then hegrid_grid_prescaled: the maxima are each
     channel's largest |v| bit for bit, and the map and weight map equal
     hegrid_grid's element for element, for both tensor-core kernels."""
     wl = W.config1(n=15000, C=300, nx=70, ny=50)
@@ -223,7 +225,8 @@ def test_grid_prescaled_overlapped_with_plan(H, kernel, kind):
     ready = torch.cuda.Event()
     ready.record(main)
     side.wait_event(ready)
-    H.hegrid_chan_maxima(v, dt[1], v.shape[0], C, ld, chmax, side.cuda_stream)
+    H.hegrid_chan_maxima(v, dt[1], v.shape[0], C, ld, chmax,
+                         H.HEGRID_MAXIMA_BESIDE if beside else 0, side.cuda_stream)
     done = torch.cuda.Event()
     done.record(side)
     plan = H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),

@@ -45,6 +45,18 @@ def test_bad_plan_flags_rejected_before_cuda(H, flags):
     assert st == H.HEGRID_ERR_INVALID_ARG and out.value is None
 
 
+def test_chan_maxima_flags_checked_before_cuda(H):
+    lib = H.lib()
+    dummy = ctypes.c_void_p(256)
+    assert H.HEGRID_MAXIMA_BESIDE == 1
+    txt = open(os.path.join(ROOT, "include", "hegrid.h")).read()
+    assert "#define HEGRID_MAXIMA_BESIDE (1u << 0)" in txt
+    for flags in (2, 1 << 31):
+        st = lib.hegrid_chan_maxima(dummy, H.HEGRID_F32, 1, 4, 4, dummy, flags, None)
+        assert st == H.HEGRID_ERR_INVALID_ARG
+        assert "flag" in H.hegrid_last_error()
+
+
 def test_masked_and_stream_argument_checks(H):
     lib = H.lib()
     assert lib.hegrid_grid_masked(None, None, 0, 1, 1, None, 1, None, 0, None) == \
