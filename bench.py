@@ -913,6 +913,9 @@ def main():
                     help="band,seg,group,kernel (as --shape=-8,16,0,3): apply this launch shape (bin edge 2) "
                          "instead of running the autotuner (profiler captures of the shape "
                          "the autotuner keeps)")
+    ap.add_argument("--plan-tiles", default="on", choices=["on", "off"],
+                    help="with a tuned kernel that reads dense weight tiles: have plan creation "
+                         "write them (on) or the first grid call build them (off)")
     ap.add_argument("--step-priority", default="normal", choices=["normal", "high"],
                     help="priority of the step's stream against the side stream of the "
                          "channel-maximum pass")
@@ -1047,6 +1050,13 @@ def main():
                                      for q in rep["points"]],
                 "seconds": round(time.perf_counter() - t_tune, 2)}
     flags = tune.get("bin_cells", hpx_flag)
+    # Kernels 2 and 3 read dense weight tiles: plan creation writes them
+    # (HEGRID_PLAN_DENSE_TILES) unless --plan-tiles off, when the first grid
+    # call builds them.
+    if tune.get("kernel", 0) in (2, 3):
+        tune["plan_tiles"] = args.plan_tiles == "on"
+        if tune["plan_tiles"]:
+            flags |= H.HEGRID_PLAN_DENSE_TILES
 
     def new_plan(lon, lat, on_device):
         p = H.hegrid_plan_create(N, lon, lat, on_device, g, wl["fwhm_deg"], 3.0, flags, sh)
@@ -1168,9 +1178,13 @@ def main():
                            3: "k_grid_tc (cell-major, dense A tiles)"}.get(tune.get("kernel", 1),
                                                                           "k_grid_tc"),
                 "note": f"algorithmic bytes N*C*4 + M*C*4 + M*4 per grid call / the device "
-                        f"time of hegrid_grid_prescaled in the timed steps (the grid kernel, "
-                        f"plus the plan's dense weight-tile build for the kernels that read "
-                        f"them; the per-channel maximum pass runs beside plan creation); "
+                        f"time of hegrid_grid_prescaled in the timed steps ("
+                        + ("the grid kernel alone: plan creation wrote the dense weight tiles"
+                           if tune.get("plan_tiles") else
+                           "the grid kernel, plus the dense weight-tile build for the kernels "
+                           "that read them" if tune.get("kernel", 1) in (2, 3) else
+                           "the grid kernel alone")
+                        + f"; the per-channel maximum pass runs beside plan creation); "
                         f"peak {peak_kind}"}
 
     # ---- end to end through the C ABI with host buffers -------------------

@@ -88,6 +88,16 @@ typedef struct {
  * length along the parallel and cells are equal in area.  Map bins only (not
  * with HEGRID_PLAN_HEALPIX). */
 #define HEGRID_PLAN_SFL (1u << 13)
+/* Bit 14: plan creation also writes the plan's dense weight tiles (16 KB per
+ * 32-candidate sub-chunk: the FP16 high and low halves of the weights x 2^15,
+ * 128 cells x 32 candidates), which tensor-core kernels 2 and 3 of
+ * hegrid_plan_set_tuning read; without it those kernels build the tiles on
+ * their first call.  Plan creation then runs its pair kernel in two halves on
+ * two streams (the second created and released by the call) and builds each
+ * half's tiles after its pairs, so that the memory-bound build overlaps the
+ * other half's pair kernel.  The tiles are the same bytes either way; they
+ * take 16 KB per 32 candidate slots (counted in hegrid_plan_info's bytes). */
+#define HEGRID_PLAN_DENSE_TILES (1u << 14)
 
 /*
  * hegrid_plan_create -- bin the samples and build the shared weights.
@@ -98,8 +108,8 @@ typedef struct {
  *                  coords_on_device == 0, device memory otherwise.  Not kept.
  * geom, kern       map geometry and kernel (host structs, copied).
  * flags            HEGRID_PLAN_BIN_CELLS(b) or HEGRID_PLAN_HEALPIX(k), optionally
- *                  | HEGRID_PLAN_SFL (not with HEALPix), or 0; other bits,
- *                  k > 13, or HEALPix with SFL: INVALID_ARG.
+ *                  | HEGRID_PLAN_SFL (not with HEALPix) | HEGRID_PLAN_DENSE_TILES,
+ *                  or 0; other bits, k > 13, or HEALPix with SFL: INVALID_ARG.
  * stream           stream for every launch; the call synchronises it once to
  *                  learn the sizes of the pair ranges it reserves (upper
  *                  bounds from the binned samples); the rest is asynchronous.
@@ -451,7 +461,8 @@ const char *hegrid_last_error(void);
  *
  * lon_deg, lat_deg  device FP64 [n_samples] (caller-owned).
  * geom, kern, flags as for hegrid_plan_create, plain-grid map bins only:
- * HEGRID_PLAN_HEALPIX and HEGRID_PLAN_SFL are INVALID_ARG here.
+ * HEGRID_PLAN_HEALPIX, HEGRID_PLAN_SFL and HEGRID_PLAN_DENSE_TILES are
+ * INVALID_ARG here.
  * perm_out          device int32 [n_samples].
  * bin_off_out       device int32 [bin_off_capacity], capacity >= n_bins + 1.
  * n_bins_out        host; set to the number of bins even when the capacity is

@@ -580,9 +580,10 @@ __global__ void __launch_bounds__(kThreadsCM, 1) k_grid_tcm(const __grid_constan
 // CTA per (block, quarter of its sub-chunks); the tile is assembled in shared
 // memory and written out with coalesced 16-byte stores.
 constexpr int kBuildSplit = 4;
-__global__ void __launch_bounds__(256) k_build_wtiles(PlanView pv, uint8_t* __restrict__ wt) {
+__global__ void __launch_bounds__(256) k_build_wtiles(PlanView pv, uint8_t* __restrict__ wt,
+                                                      int64_t blk0) {
   __shared__ __align__(16) uint8_t tile[kWTileBytes];
-  const int64_t b = blockIdx.x / kBuildSplit;
+  const int64_t b = blk0 + blockIdx.x / kBuildSplit;
   const int part = (int)(blockIdx.x % kBuildSplit);
   const int t = threadIdx.x;
   const int64_t s0 = pv.cand_off[b] / kCK;
@@ -604,9 +605,11 @@ int tcm_channel_tile() { return kCM; }
 int tcm_default_seg() { return kDefaultSegCM; }
 int64_t tcm_wtile_bytes(int64_t slots) { return (slots / kCK) * (int64_t)kWTileBytes; }
 
-hegrid_status launch_build_wtiles(const PlanView& pv, uint8_t* wtiles, cudaStream_t s) {
-  if (pv.n_blocks <= 0) return HEGRID_OK;
-  k_build_wtiles<<<(unsigned)(pv.n_blocks * kBuildSplit), 256, 0, s>>>(pv, wtiles);
+hegrid_status launch_build_wtiles(const PlanView& pv, uint8_t* wtiles, cudaStream_t s,
+                                 int64_t blk0, int64_t n_blk) {
+  if (n_blk < 0) n_blk = pv.n_blocks - blk0;
+  if (n_blk <= 0) return HEGRID_OK;
+  k_build_wtiles<<<(unsigned)(n_blk * kBuildSplit), 256, 0, s>>>(pv, wtiles, blk0);
   count_launch();
   HG_CUDA_TRY(launch_status());
   return HEGRID_OK;

@@ -231,7 +231,8 @@ int tc_default_group();
 // build, and the grid launch (every job's plan must have its tiles).
 int tcm_channel_tile();
 int64_t tcm_wtile_bytes(int64_t slots);
-hegrid_status launch_build_wtiles(const PlanView& pv, uint8_t* wtiles, cudaStream_t s);
+hegrid_status launch_build_wtiles(const PlanView& pv, uint8_t* wtiles, cudaStream_t s,
+                                 int64_t blk0 = 0, int64_t n_blk = -1);
 hegrid_status launch_grid_tcm(const JobTable& jt, cudaStream_t s);
 
 }  // namespace hg

@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(kChunk)
                   int32_t* __restrict__ cand_cnt, int32_t* __restrict__ cand_idx,
                   int64_t* __restrict__ sub_off, uint16_t* __restrict__ ent_ck,
                   float* __restrict__ ent_w, float* __restrict__ wsum,
-                  unsigned long long* __restrict__ totals) {
+                  unsigned long long* __restrict__ totals, int32_t blk0) {
   constexpr int kQ = kChunk / 32;
   // staged candidates' block-local coordinates as float-float (x, y, z, -)
   __shared__ float4 s_eh[kChunk];
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kChunk)
   __shared__ double s_b0[3];                 // unit vector of the block centre
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int b = blockIdx.x;
+  const int b = blk0 + (int)blockIdx.x;  // a launch covers blocks blk0 ..
   const int bbx = b % pp.nbx_b, bby = b / pp.nbx_b;
   const int cell = thread_cell(t);
   const int ix = bbx * HG_BX + (cell % HG_BX), iy = bby * HG_BY + (cell / HG_BX);
@@ -1270,7 +1270,8 @@ int64_t hpx_layout(const hegrid_map_geom& g, double R_deg, double R_rad, int32_t
 }
 
 hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
-                         int coords_on_device, cudaStream_t st, int hpx_log2, bool sfl) {
+                         int coords_on_device, cudaStream_t st, int hpx_log2, bool sfl,
+                         bool dense_tiles) {
   const int32_t N = (int32_t)p->N;
   const hegrid_map_geom& g = p->geom;
   Scratch sc(st);
@@ -1651,16 +1652,64 @@ hegrid_status plan_build(hegrid_plan* p, const double* lon, const double* lat,
   HG_CUDA_TRY(cudaMemsetAsync(p->err_word, 0, 4 * sizeof(int32_t), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->totals, 0, 2 * sizeof(unsigned long long), st));
   HG_CUDA_TRY(cudaMemsetAsync(p->wsum, 0, sizeof(float) * kWsumVariants * p->M, st));
-  if (hpx)
-    k_block_pairs<true><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-        pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
-        p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
-  else
-    k_block_pairs<false><<<(unsigned)p->n_blocks, kChunk, 0, st>>>(
-        pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
-        p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals);
-  count_launch();
-  HG_CUDA_TRY(launch_status());
+  auto pairs = [&](int32_t blk0, int32_t nb, cudaStream_t s) -> hegrid_status {
+    if (nb <= 0) return HEGRID_OK;
+    if (hpx)
+      k_block_pairs<true><<<(unsigned)nb, kChunk, 0, s>>>(
+          pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
+          p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals, blk0);
+    else
+      k_block_pairs<false><<<(unsigned)nb, kChunk, 0, s>>>(
+          pp, wa, p->bin_off, p->perm, sx, sy, sz, p->cand_off, p->blk_pair_off, p->cand_cnt,
+          p->cand_idx, p->sub_off, p->ent_ck, p->ent_w, p->wsum, p->totals, blk0);
+    count_launch();
+    HG_CUDA_TRY(launch_status());
+    return HEGRID_OK;
+  };
+  const int32_t nblk = (int32_t)p->n_blocks;
+  if (!dense_tiles) {
+    hegrid_status e = pairs(0, nblk, st);
+    if (e != HEGRID_OK) return e;
+  } else {
+    // The dense weight tiles (HEGRID_PLAN_DENSE_TILES): the blocks in two
+    // halves, each half's pair kernel and then its tile build on a stream of
+    // its own.  The halves' pair kernels share the GPU, the first finishes
+    // first, and its (memory-bound) tile build runs in the second's last wave.
+    HG_CUDA_TRY(dmalloc(&p->wtiles, tcm_wtile_bytes(p->slots), &bytes, st));
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    auto release = [&]() {
+      if (fork) cudaEventDestroy(fork);
+      if (join) cudaEventDestroy(join);
+      if (s2) cudaStreamDestroy(s2);  // its resources go once its work is done
+    };
+    cudaError_t ce = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventRecord(fork, st);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s2, fork, 0);
+    if (ce != cudaSuccess) {
+      release();
+      set_error(std::string("plan_create: ") + cudaGetErrorString(ce));
+      return HEGRID_ERR_CUDA;
+    }
+    const int32_t half = (nblk + 1) / 2;
+    const PlanView v = p->view();
+    hegrid_status e = pairs(0, half, st);
+    if (e == HEGRID_OK) e = pairs(half, nblk - half, s2);
+    if (e == HEGRID_OK) e = launch_build_wtiles(v, p->wtiles, st, 0, half);
+    if (e == HEGRID_OK) e = launch_build_wtiles(v, p->wtiles, s2, half, nblk - half);
+    // st waits for s2's work even after a failed launch, so that the caller's
+    // synchronisation of st covers every kernel this call issued
+    ce = cudaEventRecord(join, s2);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, join, 0);
+    if (ce != cudaSuccess && e == HEGRID_OK) {
+      set_error(std::string("plan_create: ") + cudaGetErrorString(ce));
+      e = HEGRID_ERR_CUDA;
+    }
+    release();
+    if (e != HEGRID_OK) return e;
+  }
   p->P = -1;  // exact totals: read on first use (plan_totals)
   HG_CUDA_TRY(cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming));
   HG_CUDA_TRY(cudaEventRecord(p->ready, st));
@@ -1714,7 +1763,8 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
   uint32_t bc = flags & 0xffu;
   const int hpx_log2 = (int)((flags >> 8) & 0x1fu);
   const bool sfl = (flags & HEGRID_PLAN_SFL) != 0;
-  HG_ARG_CHECK((flags >> 14) == 0, "unknown plan_create flag bits");
+  const bool dense_tiles = (flags & HEGRID_PLAN_DENSE_TILES) != 0;
+  HG_ARG_CHECK((flags >> 15) == 0, "unknown plan_create flag bits");
   HG_ARG_CHECK(hpx_log2 <= 13, "HEALPix nside above 2^13");
   HG_ARG_CHECK(!(sfl && hpx_log2 > 0), "HEALPix binning works on the plain grid only");
   hegrid_plan* p = new hegrid_plan();
@@ -1735,7 +1785,8 @@ hegrid_status hegrid_plan_create(hegrid_plan** out, int64_t n_samples, const dou
     return HEGRID_ERR_UNSUPPORTED;
   }
   hegrid_status s =
-      hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream, hpx_log2, sfl);
+      hg::plan_build(p, lon_deg, lat_deg, coords_on_device, (cudaStream_t)stream, hpx_log2, sfl,
+                     dense_tiles);
   if (s != HEGRID_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     hg::free_plan_arrays(p, (cudaStream_t)stream);

@@ -32,6 +32,7 @@ def HEGRID_PLAN_BIN_CELLS(b):
 
 
 HEGRID_PLAN_SFL = 1 << 13  # plan_create flag: Sanson-Flamsteed map geometry
+HEGRID_PLAN_DENSE_TILES = 1 << 14  # plan_create flag: write the dense weight tiles
 HEGRID_MAXIMA_BESIDE = 1 << 0  # hegrid_chan_maxima flag: one lean CTA per SM
 
 

@@ -130,7 +130,7 @@ def test_hpx_flag_checks(H):
     with pytest.raises(H.HegridError):
         _plan(H, wl, H.HEGRID_PLAN_HEALPIX(14))  # nside above 2^13
     with pytest.raises(H.HegridError):
-        _plan(H, wl, 1 << 14)  # an unknown flag bit
+        _plan(H, wl, 1 << 15)  # an unknown flag bit
     lon = torch.from_numpy(np.ascontiguousarray(wl["lon"])).cuda()
     lat = torch.from_numpy(np.ascontiguousarray(wl["lat"])).cuda()
     perm = torch.empty(100, dtype=torch.int32, device="cuda")

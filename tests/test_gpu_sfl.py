@@ -97,4 +97,4 @@ def test_sfl_flag_checks(H):
         H.hegrid_plan_create(len(lon), lon, lat, 0, geom, fwhm, 3.0,
                              H.HEGRID_PLAN_SFL | H.HEGRID_PLAN_HEALPIX(12), s)
     with pytest.raises(H.HegridError):
-        H.hegrid_plan_create(len(lon), lon, lat, 0, geom, fwhm, 3.0, 1 << 14, s)
+        H.hegrid_plan_create(len(lon), lon, lat, 0, geom, fwhm, 3.0, 1 << 15, s)

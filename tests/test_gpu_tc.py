@@ -31,12 +31,13 @@ def H():
     return hegrid
 
 
-def _plan(H, wl, kernel=0):
+def _plan(H, wl, kernel=0, flags=0):
     """A plan whose tensor-core calls run `kernel` (0: default, 1: cell-major,
-    2: channel-major)."""
+    2: channel-major, 3: cell-major with dense A tiles)."""
     p = H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
                              np.ascontiguousarray(wl["lat"]), 0, wl["geom"], wl["fwhm_deg"],
-                             wl.get("support", 3.0), 0, torch.cuda.current_stream().cuda_stream)
+                             wl.get("support", 3.0), flags,
+                             torch.cuda.current_stream().cuda_stream)
     if kernel:
         H.hegrid_plan_set_tuning(p, H.HEGRID_MODE_TC_SPLIT, 0, 0, 0, kernel)
     return p
@@ -398,17 +399,20 @@ def test_channel_major_equals_cell_major(H, C, kind, mode):
 @pytest.mark.parametrize("C", [40, 100, 300])
 @pytest.mark.parametrize("kind", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("mode", ["split", "single"])
-def test_dense_a_tiles_equal_built_a_tiles(H, C, kind, mode):
+@pytest.mark.parametrize("tiles", ["first call", "plan flag"])
+def test_dense_a_tiles_equal_built_a_tiles(H, C, kind, mode, tiles):
     """The cell-major kernel with its A tiles copied from the plan's dense
     weight tiles (kernel 3) multiplies exactly the A tiles its A builders would
     assemble from the entries (kernel 1), at every channel-tile width (64 with
-    two sub-chunks per chunk, 128, 256): maps and weight maps equal bit for bit."""
+    two sub-chunks per chunk, 128, 256), whether the tiles were built by the
+    first call that needs them or by plan creation (HEGRID_PLAN_DENSE_TILES):
+    maps and weight maps equal bit for bit."""
     wl = _case(131 + C, n=9000, nx=56, ny=32, C=C)
     g = wl["geom"]
     M = g["nx"] * g["ny"]
     dv, dt, ld, _ = _stored(kind, wl["values"], H)
     md = H.HEGRID_MODE_TC_SPLIT if mode == "split" else H.HEGRID_MODE_TC
-    plan = _plan(H, wl)
+    plan = _plan(H, wl, flags=H.HEGRID_PLAN_DENSE_TILES if tiles == "plan flag" else 0)
     try:
         H.hegrid_plan_set_tuning(plan, md, -4, 16, 0, 1)
         a, wa = _run(H, plan, dv, dt, C, ld, M, md)
@@ -418,3 +422,61 @@ def test_dense_a_tiles_equal_built_a_tiles(H, C, kind, mode):
         H.hegrid_plan_destroy(plan)
     assert np.array_equal(a, b, equal_nan=True)
     assert np.array_equal(wa, wb)
+
+
+@pytest.mark.parametrize("binning", ["map bins", "healpix", "sfl"])
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_plan_written_tiles_equal_first_call_tiles(H, binning, kernel):
+    """Dense weight tiles written by plan creation (HEGRID_PLAN_DENSE_TILES:
+    the pair kernel in two halves on two streams, each half's tiles built after
+    it) give the same maps, bit for bit, as the tiles the first grid call
+    builds, under each binning and for both kernels that read them; the flag
+    adds the tiles' bytes to the plan's device memory."""
+    wl = _case(171, n=9000, nx=56, ny=32, C=148)
+    g = wl["geom"]
+    M = g["nx"] * g["ny"]
+    base = {"map bins": 0, "healpix": H.HEGRID_PLAN_HEALPIX(12), "sfl": H.HEGRID_PLAN_SFL}[binning]
+    vd = torch.from_numpy(wl["values"]).cuda()
+    res = []
+    for flags in (base, base | H.HEGRID_PLAN_DENSE_TILES):
+        plan = _plan(H, wl, kernel, flags)
+        try:
+            info = H.hegrid_plan_info(plan)
+            res.append(_run(H, plan, vd, H.HEGRID_F32, 148, 148, M, H.HEGRID_MODE_TC_SPLIT)
+                       + (info,))
+            assert H.hegrid_status_poll(plan) == H.HEGRID_OK
+        finally:
+            H.hegrid_plan_destroy(plan)
+    (a, wa, ia), (b, wb, ib) = res
+    assert np.array_equal(a, b, equal_nan=True)
+    assert np.array_equal(wa, wb)
+    assert ib["bytes"] > ia["bytes"]
+    og = dict(g, proj="sfl") if binning == "sfl" else g
+    ref, Wref = oracle.Index(wl["lon"], wl["lat"], og, wl["fwhm_deg"]).grid(wl["values"])
+    err, _, _ = map_error(b, ref, Wref)
+    assert err <= TOL_SPLIT, err
+
+
+def test_plan_tiles_split_launch_matches_single_launch_plan(H):
+    """With HEGRID_PLAN_DENSE_TILES the pair kernel runs as two launches (the
+    block halves, on two streams): the exported plan (CSR, weights, W) equals
+    the plan of one launch bit for bit, on an odd block count."""
+    wl = _case(181, n=7000, nx=72, ny=40, C=4)  # 5 x 5 blocks of 16 x 8 cells
+    out = []
+    for flags in (0, H.HEGRID_PLAN_DENSE_TILES):
+        plan = _plan(H, wl, 0, flags)
+        try:
+            info = H.hegrid_plan_info(plan)
+            N = len(wl["lon"])
+            M = wl["geom"]["nx"] * wl["geom"]["ny"]
+            nb_off = np.zeros(M + 1, np.int64)
+            nb_idx = np.zeros(info["n_pairs"], np.int32)
+            nb_w = np.zeros(info["n_pairs"], np.float32)
+            wgt = np.zeros(M, np.float32)
+            H.hegrid_plan_export(plan, None, None, nb_off, nb_idx, nb_w, wgt)
+            out.append((info["n_blocks"], nb_off, nb_idx, nb_w, wgt))
+        finally:
+            H.hegrid_plan_destroy(plan)
+    assert out[0][0] == 25 and out[1][0] == 25
+    for x, y in zip(out[0][1:], out[1][1:]):
+        assert np.array_equal(x, y)

@@ -26,13 +26,15 @@ def H():
 def test_flag_encodings_match_header(H):
     txt = open(os.path.join(ROOT, "include", "hegrid.h")).read()
     assert "#define HEGRID_PLAN_SFL (1u << 13)" in txt
+    assert "#define HEGRID_PLAN_DENSE_TILES (1u << 14)" in txt
+    assert H.HEGRID_PLAN_DENSE_TILES == 1 << 14
     assert re.search(r"#define HEGRID_PLAN_HEALPIX\(k\) \(\(\(uint32_t\)\(k\) & 0x1fu\) << 8\)", txt)
     assert H.HEGRID_PLAN_SFL == 1 << 13
     assert H.HEGRID_PLAN_HEALPIX(12) == 12 << 8 and H.HEGRID_PLAN_HEALPIX(33) == 1 << 8
     assert H.HEGRID_PLAN_BIN_CELLS(3) == 3
 
 
-@pytest.mark.parametrize("flags", [1 << 14, (14 << 8), (1 << 13) | (12 << 8)])
+@pytest.mark.parametrize("flags", [1 << 15, 1 << 31, (14 << 8), (1 << 13) | (12 << 8)])
 def test_bad_plan_flags_rejected_before_cuda(H, flags):
     lib = H.lib()
     out = ctypes.c_void_p()
