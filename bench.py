@@ -116,14 +116,14 @@ TRAFFIC = {
     "k_grid_tc_dense": {"sources": ["paper_2207_04584_gb300/csrc/grid_tc.cu",
                                     "paper_2207_04584_gb300/csrc/ptx.cuh",
                                     "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                        "sha256": "c124a838df4100a1d1605147cf29c7fe4072490089d0953f124db8b748555830",
+                        "sha256": "7a699345de124cb048e4234ceb5094ed1f0841ccd73a9ba59972200f40b8c878",
                         "bytes": 38.2067e9 + 1.473e9,
                         "capture": "profiles/k_grid_tc_fast_drift_c256.md (the bench's tuned "
                                    "launch with dense A tiles, C=1024; mean of 9)"},
     "k_grid_f32": {"sources": ["paper_2207_04584_gb300/csrc/grid_f32.cu",
                                "paper_2207_04584_gb300/csrc/ptx.cuh",
                                "paper_2207_04584_gb300/csrc/hegrid_internal.cuh"],
-                   "sha256": "294ad160ed33f70c52ce8761fe901806cd36fa1cf7072a76a23e73fde85c5bb1",
+                   "sha256": "51985c6f0c8a21fafd8c1b2f45a66b77df626f7deee350802c86d269a179f04f",
                    "bytes": 30.3695e9 + 1.470e9,
                    "capture": "profiles/k_grid_f32_fast_drift_c256.md (the bench's FP32-form "
                               "launch, C=1024; mean of 4)"},

@@ -47,10 +47,10 @@ def _wl():
     return W.config1(n=6000, C=16, nx=48, ny=40)
 
 
-def _plan(H, wl):
+def _plan(H, wl, flags=0):
     return H.hegrid_plan_create(len(wl["lon"]), np.ascontiguousarray(wl["lon"]),
                                 np.ascontiguousarray(wl["lat"]), 0, wl["geom"], wl["fwhm_deg"],
-                                3.0, 0, torch.cuda.current_stream().cuda_stream)
+                                3.0, flags, torch.cuda.current_stream().cuda_stream)
 
 
 def _used(H):
@@ -91,14 +91,19 @@ def test_wait_timeout_sets_status_and_context_survives(H, fault):
     assert err <= 5e-5, err
 
 
-def test_alloc_faults_in_plan_create_leak_nothing(H, fault):
+@pytest.mark.parametrize("tiles", [False, True])
+def test_alloc_faults_in_plan_create_leak_nothing(H, fault, tiles):
+    """Every alloc of plan creation made to fail in turn (with the plan's
+    dense weight tiles: the second stream's pair kernel and tile builds too)
+    returns the error and leaves the pool as it was."""
     wl = _wl()
+    flags = H.HEGRID_PLAN_DENSE_TILES if tiles else 0
     base = _used(H)
     failed = 0
     for k in range(1, 64):
         fault(f"alloc:{k}")
         try:
-            plan = _plan(H, wl)
+            plan = _plan(H, wl, flags)
         except H.HegridError as e:
             assert e.status == H.HEGRID_ERR_OOM, (k, e.status)
             assert _used(H) == base, k
@@ -113,14 +118,19 @@ def test_alloc_faults_in_plan_create_leak_nothing(H, fault):
     assert failed >= 5  # every allocation of plan creation was made to fail once
 
 
-def test_launch_faults_in_plan_create_leak_nothing(H, fault):
+@pytest.mark.parametrize("tiles", [False, True])
+def test_launch_faults_in_plan_create_leak_nothing(H, fault, tiles):
+    """Every launch of plan creation made to fail in turn (with the plan's
+    dense weight tiles: the second stream's pair kernel and tile builds too)
+    returns the error and leaves the pool as it was."""
     wl = _wl()
+    flags = H.HEGRID_PLAN_DENSE_TILES if tiles else 0
     base = _used(H)
     failed = 0
     for k in range(1, 96):
         fault(f"launch:{k}")
         try:
-            plan = _plan(H, wl)
+            plan = _plan(H, wl, flags)
         except H.HegridError as e:
             assert e.status == H.HEGRID_ERR_CUDA, (k, e.status)
             assert _used(H) == base, k
