@@ -255,3 +255,46 @@ def test_grid_prescaled_overlapped_with_plan(H, kernel, kind, beside):
     assert torch.equal(chmax.cpu(), ref.cpu().view(torch.int32))
     assert torch.equal(torch.nan_to_num(a, nan=-1.0), torch.nan_to_num(b, nan=-1.0))
     assert torch.equal(wa, wb)
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16", "f16", "bf16x2"])
+@pytest.mark.parametrize("C", [1, 7, 300, 1030])
+def test_chan_maxima_beside_equals_full(H, kind, C):
+    """The one-CTA-per-SM maximum pass (HEGRID_MAXIMA_BESIDE) returns the
+    full pass's maxima bit for bit, for every stored type and channel counts
+    from one to more than one CTA's columns, over enough rows that several
+    CTAs share each column group; for the plain types they are the largest
+    |v| of each channel."""
+    rng = np.random.default_rng(7 + C)
+    n = 70001
+    vt = torch.from_numpy((rng.standard_normal((n, C)) *
+                           10.0 ** rng.integers(-6, 5, C)).astype(np.float32))
+    if kind == "bf16x2":
+        hi = vt.to(torch.bfloat16)
+        lo = (vt - hi.float()).to(torch.bfloat16)
+        packed = torch.stack([hi, lo], dim=-1).contiguous().view(torch.int32).view(n, C)
+        ld = (C + 3) // 4 * 4
+        v = torch.zeros((n, ld), dtype=torch.int32)
+        v[:, :C] = packed
+        dt, ref = H.HEGRID_BF16X2, None
+    else:
+        tdt, dt, mult = {"f32": (torch.float32, H.HEGRID_F32, 4),
+                         "bf16": (torch.bfloat16, H.HEGRID_BF16, 8),
+                         "f16": (torch.float16, H.HEGRID_F16, 8)}[kind]
+        ld = (C + mult - 1) // mult * mult
+        v = torch.zeros((n, ld), dtype=tdt)
+        v[:, :C] = vt.to(tdt)
+        ref = v[:, :C].float().abs().amax(dim=0).view(torch.int32)
+    v = v.cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    full = torch.full((C,), -1, dtype=torch.int32, device="cuda")
+    lean = torch.full((C,), -1, dtype=torch.int32, device="cuda")
+    H.hegrid_chan_maxima(v, dt, n, C, ld, full, 0, s)
+    H.hegrid_chan_maxima(v, dt, n, C, ld, lean, H.HEGRID_MAXIMA_BESIDE, s)
+    torch.cuda.synchronize()
+    assert torch.equal(full.cpu(), lean.cpu())
+    if ref is not None:
+        assert torch.equal(full.cpu(), ref)
+    with pytest.raises(H.HegridError) as e:
+        H.hegrid_chan_maxima(v, dt, n, C, ld, full, 2, s)
+    assert e.value.status == H.HEGRID_ERR_INVALID_ARG
