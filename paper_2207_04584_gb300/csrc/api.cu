@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -524,17 +525,18 @@ hegrid_status grid_many(int n, hegrid_plan* const* plans, const hegrid_grid_args
 hegrid_status launch_absmax(int n, const AbsmaxRequest* req, cudaStream_t s, int ctas_per_sm,
                             bool lean) {
   if (n <= 0) return HEGRID_OK;
-  static std::once_flag carve;
-  std::call_once(carve, [] {
-    cudaFuncSetAttribute(k_chan_absmax, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(k_chan_absmax_lean, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
-  });
-  const int threads = lean ? kAbsmaxLeanThreads : 256;
-  if (lean) ctas_per_sm = 1;
   int dev = 0, n_sm = 0;
   HG_CUDA_TRY(cudaGetDevice(&dev));
+  static std::atomic<bool> carved[64];  // per device: the attribute is the current device's
+  if (dev >= 0 && dev < 64 && !carved[dev].exchange(true)) {
+    HG_CUDA_TRY(cudaFuncSetAttribute(k_chan_absmax, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+    HG_CUDA_TRY(cudaFuncSetAttribute(k_chan_absmax_lean,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+  }
+  const int threads = lean ? kAbsmaxLeanThreads : 256;
+  if (lean) ctas_per_sm = 1;
   HG_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   for (int base = 0; base < n; base += kMaxAbsmaxJobs) {
     AbsmaxTable tab;
